@@ -1,0 +1,146 @@
+/*
+ * ins.h -- C ABI of libins, the B300 (sm_103a) explicit Runge-Kutta step of the
+ * staggered-grid (MAC) finite-volume incompressible Navier-Stokes solver of
+ * arXiv 2604.18536 ("A differentiable software suite for accelerated
+ * simulation of turbulent flows").
+ *
+ * Problem (paper Sec. 2.3 and 2.6.1):  du/dt = F(u) - G p,  D u = 0,
+ * with L p = D F(u), L = D G, and F(u) = C(u) + nu * diffusion(u) + f.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Cells i in [0, nx), j in [0, ny), k in [0, nz) (nz = 1 in 2-D). Every scalar
+ *   field is one contiguous array of nx*ny*nz values, x fastest:
+ *   index = (k*ny + j)*nx + i. No ghost cells are stored.
+ * - A velocity field is dim such arrays back to back (u^x, u^y[, u^z]).
+ *   u^a[i,j,k] lives on the face to the right of cell (i,j,k) in direction a
+ *   (Sec. 3.1 convention); p lives at cell centres.
+ * - A wall-normal direction (only y may be a wall, x and z then periodic)
+ *   stores u^y on the faces above cells 0..ny-1; the last one is the top wall
+ *   and holds 0. The bottom wall face is not stored.
+ * - Field values are float (INS_F32) or double (INS_F64), as chosen when the
+ *   grid was created. Every field pointer is a DEVICE pointer, 16-byte aligned,
+ *   owned by the caller. The library never allocates or frees caller buffers.
+ * - Calls that launch kernels enqueue them on the grid's stream and return
+ *   without synchronising, unless stated otherwise. All argument checks happen
+ *   before any launch; on an error nothing is enqueued.
+ * - No C++ exception crosses this boundary. Errors return a status code and a
+ *   message readable with ins_last_error() (per calling thread).
+ */
+#ifndef INS_H
+#define INS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    INS_OK = 0,
+    INS_ERR_ARG = 1,          /* null pointer, bad size, misaligned pointer, bad enum  */
+    INS_ERR_UNSUPPORTED = 2,  /* valid request this library does not implement        */
+    INS_ERR_OOM = 3,          /* device workspace allocation failed                    */
+    INS_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed           */
+    INS_ERR_NONFINITE = 5,    /* a NaN/Inf was detected in a result                    */
+    INS_ERR_TIMEOUT = 6       /* reserved: no call in this library waits on the device */
+} ins_status;
+
+typedef enum { INS_PERIODIC = 0, INS_WALL = 1 } ins_bc;
+typedef enum { INS_F32 = 0, INS_F64 = 1 } ins_dtype;
+
+/* Grid description (Sec. 2.1, 2.4, 2.5).
+ * dim            2 or 3.
+ * n[a]           cells per direction (n[2] ignored in 2-D). Periodic directions
+ *                need n[a] = 2^p 3^q 5^r 7^s and n[a] <= 2048 (the FFT radices and
+ *                shared-memory line tiles); a wall direction needs n[a] <= 4096.
+ * bc[a]          INS_PERIODIC or INS_WALL. Supported: all periodic, or y = WALL
+ *                with x (and z) periodic. Other combinations: INS_ERR_UNSUPPORTED.
+ * face_coords[a] HOST pointer to n[a]+1 increasing face coordinates, copied at
+ *                creation. Periodic directions must be uniformly spaced (the
+ *                Poisson solver is spectral there); a wall direction may be
+ *                stretched (e.g. the tanh grid of Sec. 2.5).
+ * dtype          storage and arithmetic type of the fields.
+ * nu             kinematic viscosity (> 0 not required; >= 0).
+ * force[a]       constant body force f^a (App. A momentum equation). */
+typedef struct {
+    int dim;
+    int n[3];
+    int bc[3];
+    const double* face_coords[3];
+    int dtype;
+    double nu;
+    double force[3];
+} ins_grid_desc;
+
+typedef struct ins_grid ins_grid;
+
+/* Message of the last failed call on this thread ("" if none). Never NULL. */
+const char* ins_last_error(void);
+
+/* Library version string. */
+const char* ins_version(void);
+
+/* Create a grid: validates *desc, copies the geometry to the device, builds the
+ * FFT twiddle tables, the spectral inverse-Laplacian table (periodic) or the
+ * Thomas factors (wall direction), and allocates the workspace (about 11 scalar
+ * fields of the grid dtype). stream is a cudaStream_t (NULL = legacy default
+ * stream) on which every later call enqueues its work; the current CUDA device
+ * must be the one the fields live on. This call synchronises the device. */
+ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** out);
+
+/* Free the workspace and the handle (synchronises the grid's stream). NULL is a no-op. */
+ins_status ins_grid_destroy(ins_grid* g);
+
+/* Change the stream later calls enqueue on. */
+ins_status ins_set_stream(ins_grid* g, void* stream);
+
+/* Bytes of device workspace the grid holds. */
+ins_status ins_workspace_bytes(const ins_grid* g, size_t* bytes);
+
+/* Right-hand side of the semi-discrete system (Sec. 2.3, momentum equation):
+ * dudt = F(u) - G p with L p = D F(u) (Sec. 2.6.1). u, dudt: dim fields; p:
+ * one field or NULL. Wall faces of dudt are 0. */
+ins_status ins_rhs(ins_grid* g, const void* u, void* dudt, void* p);
+
+/* Divergence-free projection (Sec. 2.6.1): u_out = u_in - G p with
+ * L p = D u_in. u_out may equal u_in. p may be NULL. */
+ins_status ins_project(ins_grid* g, const void* u_in, void* u_out, void* p);
+
+/* Divergence (App. B divergence kernel): phi = D u. */
+ins_status ins_divergence(ins_grid* g, const void* u, void* phi);
+
+/* One classic RK4 step with a projection at every stage (Sec. 2.6.2):
+ * k_s = F(u_s) - G p_s, u_s = u_0 + dt a_{s,s-1} k_{s-1},
+ * u_{n+1} = u_0 + dt (k_1/6 + k_2/3 + k_3/3 + k_4/6).
+ * u           in/out, dim fields (the step is done in place).
+ * dt_dev      DEVICE pointer to one double holding dt, read by the kernels
+ *             (no host synchronisation); NULL: dt_host is used.
+ * next_dt_dev DEVICE pointer or NULL. If given, receives the CFL time step of
+ *             u_{n+1} (see ins_cfl_dt) with factor cfl. It may equal dt_dev
+ *             (adaptive stepping entirely on the device).
+ * A non-finite value in u_{n+1} sets the grid's error flag (ins_check_finite). */
+ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host,
+                    double* next_dt_dev, double cfl);
+
+/* Adaptive time step (Sec. 2.6.2, convective and diffusive limits):
+ * dt = cfl * min(1 / max_{a,I} |u^a_I| / h_a[i], min_{a,i} d_a[i]^2 / nu)
+ * where d are cell widths and h centre-to-centre distances, every operation
+ * an IEEE FP64 operation (bit-reproducible). Writes one double to dt_dev. */
+ins_status ins_cfl_dt(ins_grid* g, const void* u, double cfl, double* dt_dev);
+
+/* Diagnostics of a velocity field, synchronous. out[0] = kinetic energy
+ * (1/|Omega|) 1/2 sum_a sum_I |Omega^a_I| (u^a_I)^2 (FP64 sums); out[1] =
+ * max |D u|; out[2] = max |u^a|/h_a; out[3] = number of non-finite values.
+ * Returns INS_ERR_NONFINITE (after filling out) if out[3] > 0. */
+ins_status ins_diag(ins_grid* g, const void* u, double out[4]);
+
+/* Reads and clears the grid's device error flag (synchronous).
+ * INS_ERR_NONFINITE if a step produced a NaN/Inf since the last check. */
+ins_status ins_check_finite(ins_grid* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INS_H */

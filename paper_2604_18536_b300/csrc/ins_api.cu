@@ -1,0 +1,797 @@
+// libins: C ABI over the B300 kernels (declarations and contracts in include/ins.h).
+//
+// The grid handle owns: per-direction stencil coefficients (field dtype), FP64
+// geometry for the exact CFL rule and diagnostics, FFT twiddle tables, the
+// spectral inverse-Laplacian table (all-periodic grids) or the FP64 Thomas
+// factors (wall-normal y), and the step workspace (F, RK accumulator, stage
+// state, r/p and the half spectrum). Nothing is allocated after creation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ins.h"
+#include "common.cuh"
+#include "fft.cuh"
+#include "stencil.cuh"
+
+using namespace ins;
+
+namespace {
+
+thread_local std::string g_err;
+
+ins_status fail(ins_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+ins_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(INS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define INS_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+#define INS_LAUNCHED(where)                                \
+    do {                                                   \
+        cudaError_t e_ = cudaGetLastError();               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+bool factor_radices(int L, std::vector<int>& out) {
+    out.clear();
+    int e2 = 0;
+    while (L % 2 == 0) {
+        L /= 2;
+        ++e2;
+    }
+    while (e2 >= 3) {
+        out.push_back(8);
+        e2 -= 3;
+    }
+    if (e2 == 2) out.push_back(4);
+    if (e2 == 1) out.push_back(2);
+    for (int p : {3, 5, 7}) {
+        while (L % p == 0) {
+            out.push_back(p);
+            L /= p;
+        }
+    }
+    return L == 1 && (int)out.size() <= FFT_MAX_STAGES;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct ins_grid {
+    int dim = 0, nx = 1, ny = 1, nz = 1, wall_y = 0, dtype = 0;
+    double nu = 0.0, force[3] = {0, 0, 0};
+    cudaStream_t stream = nullptr;
+    long N = 0;             // cells
+    int nxh = 0;            // nx/2 + 1
+    std::vector<double> d[3], h[3], hlo;  // host geometry
+    double dmin2_nu = INFINITY;
+
+    // one device allocation, carved into pieces
+    void* base = nullptr;
+    size_t bytes = 0;
+    void* coef = nullptr;          // T[3][C_COUNT][n_a] (per direction contiguous)
+    double* geo64 = nullptr;       // h_x h_y h_z | d_x d_y d_z  (nx+ny+nz each)
+    double* one = nullptr;         // a device 1.0 (divisor of an already divided maximum)
+    void* tw[3] = {nullptr, nullptr, nullptr};
+    int radix[3][FFT_MAX_STAGES];
+    int nst[3] = {0, 0, 0};
+    void* scale = nullptr;         // T, [nz][ny][nxh] (periodic)
+    double* lam = nullptr;         // FP64 eigenvalues: x (nxh) | y (ny) | z (nz)
+    double* th_lo = nullptr;       // Thomas: lo[ny]
+    double* th_invm = nullptr;     // [ny][ncol]
+    double* th_cp = nullptr;       // [ny][ncol]
+    void* th_d = nullptr;          // cplx<double> [ny][ncol]
+    void* F = nullptr;
+    void* acc = nullptr;
+    void* us = nullptr;
+    void* rp = nullptr;
+    void* S = nullptr;
+    unsigned long long* cfl_max = nullptr;  // [nx + ny + nz] per-index maxima of |u^a|
+    unsigned int* err_flag = nullptr;       // [1]
+    double* diag = nullptr;                 // [4]
+    unsigned long long* diag_max = nullptr; // [2]
+    int lg_tw_x = 0, lg_tw_y = 0, lg_tw_z = 0;
+    int kchunk = 32;
+};
+
+namespace {
+
+template <typename T>
+Geo<T> make_geo(const ins_grid* g) {
+    Geo<T> G;
+    G.nx = g->nx;
+    G.ny = g->ny;
+    G.nz = g->nz;
+    G.wall_y = g->wall_y;
+    const T* c = reinterpret_cast<const T*>(g->coef);
+    G.c[0] = c;
+    G.c[1] = c + (size_t)C_COUNT * g->nx;
+    G.c[2] = c + (size_t)C_COUNT * (g->nx + g->ny);
+    G.fx = (T)g->force[0];
+    G.fy = (T)g->force[1];
+    G.fz = (T)g->force[2];
+    return G;
+}
+
+template <typename T>
+FftLine<T> make_line(const ins_grid* g, int a) {
+    FftLine<T> pl;
+    pl.L = a == 0 ? g->nx : (a == 1 ? g->ny : g->nz);
+    pl.nst = g->nst[a];
+    for (int s = 0; s < FFT_MAX_STAGES; ++s) pl.radix[s] = s < pl.nst ? g->radix[a][s] : 1;
+    pl.tw = reinterpret_cast<const cplx<T>*>(g->tw[a]);
+    return pl;
+}
+
+template <typename T>
+size_t fft_smem(int L, int lgtw) {
+    return 2ull * L * ((1 << lgtw) + 1) * sizeof(cplx<T>);
+}
+
+template <typename T>
+int choose_lgtw(int L) {
+    int lg = sizeof(T) == 8 ? 3 : 4;   // 128-byte rows of complex values
+    while (lg > 0 && fft_smem<T>(L, lg) > 100 * 1024) --lg;
+    return lg;
+}
+
+// ------------------------------------------------------------ Poisson solve
+template <typename T>
+ins_status poisson(ins_grid* g, const T* r, T* p) {
+    cudaStream_t st = g->stream;
+    const int nx = g->nx, ny = g->ny, nz = g->nz, nxh = g->nxh;
+    const long lines = (long)ny * nz;
+    cplx<T>* S = reinterpret_cast<cplx<T>*>(g->S);
+    FftLine<T> lx = make_line<T>(g, 0);
+    {
+        const int lg = g->lg_tw_x;
+        const long pairs = (lines + 1) / 2;
+        const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);
+        k_fft_x_r2c<T><<<blocks, FFT_THREADS, fft_smem<T>(nx, lg), st>>>(lx, r, S, (int)lines, nxh, lg);
+        INS_LAUNCHED("fft x r2c");
+    }
+    auto strided = [&](int a, int mode) -> ins_status {
+        FftLine<T> pl = make_line<T>(g, a);
+        const int lg = a == 1 ? g->lg_tw_y : g->lg_tw_z;
+        long ncol, cdiv, outer, lstride;
+        if (a == 1) {
+            ncol = (long)nz * nxh;
+            cdiv = nxh;
+            outer = (long)ny * nxh;
+            lstride = nxh;
+        } else {
+            ncol = (long)ny * nxh;
+            cdiv = ncol;
+            outer = 0;
+            lstride = (long)ny * nxh;
+        }
+        const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
+        k_fft_strided<T><<<blocks, FFT_THREADS, fft_smem<T>(pl.L, lg), st>>>(
+            pl, S, ncol, cdiv, outer, lstride, mode, reinterpret_cast<const T*>(g->scale), lg);
+        INS_LAUNCHED("fft strided");
+        return INS_OK;
+    };
+    ins_status s;
+    if (!g->wall_y) {
+        if (g->dim == 2) {
+            if ((s = strided(1, 2)) != INS_OK) return s;
+        } else {
+            if ((s = strided(1, 0)) != INS_OK) return s;
+            if ((s = strided(2, 2)) != INS_OK) return s;
+            if ((s = strided(1, 1)) != INS_OK) return s;
+        }
+    } else {
+        if (g->dim == 3 && (s = strided(2, 0)) != INS_OK) return s;
+        const long ncol = (long)nz * nxh;
+        const double norm = 1.0 / ((double)nx * (g->dim == 3 ? nz : 1));
+        k_thomas<T><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(
+            S, g->th_lo, g->th_invm, g->th_cp, reinterpret_cast<cplx<double>*>(g->th_d), nxh, ny, ncol, norm);
+        INS_LAUNCHED("thomas");
+        if (g->dim == 3 && (s = strided(2, 1)) != INS_OK) return s;
+    }
+    {
+        const int lg = g->lg_tw_x;
+        const long pairs = (lines + 1) / 2;
+        const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);
+        k_fft_x_c2r<T><<<blocks, FFT_THREADS, fft_smem<T>(nx, lg), st>>>(lx, S, p, (int)lines, nxh, lg);
+        INS_LAUNCHED("fft x c2r");
+    }
+    return INS_OK;
+}
+
+// ------------------------------------------------------------ kernels by config
+template <typename T, int DIM, bool WALL>
+ins_status launch_rhs_div(ins_grid* g, const T* u, T* F, T* r) {
+    dim3 blk(BX, BY, 1);
+    dim3 grd((g->nx + BX - 1) / BX, (g->ny + BY - 1) / BY, DIM == 3 ? (g->nz + g->kchunk - 1) / g->kchunk : 1);
+    k_rhs_div<T, DIM, WALL><<<grd, blk, 0, g->stream>>>(make_geo<T>(g), u, F, r, g->kchunk);
+    INS_LAUNCHED("rhs_div");
+    return INS_OK;
+}
+
+dim3 cell_grid(const ins_grid* g) { return dim3((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz); }
+
+template <typename T, int DIM, bool WALL>
+struct Impl {
+    static ins_status rhs(ins_grid* g, const T* u, T* dudt, T* p) {
+        T* F = reinterpret_cast<T*>(g->F);
+        T* rp = reinterpret_cast<T*>(g->rp);
+        ins_status s;
+        if ((s = launch_rhs_div<T, DIM, WALL>(g, u, F, rp)) != INS_OK) return s;
+        T* pp = p ? p : rp;
+        if ((s = poisson<T>(g, rp, pp)) != INS_OK) return s;
+        k_sub_grad<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, pp, dudt);
+        INS_LAUNCHED("sub_grad");
+        return INS_OK;
+    }
+    static ins_status project(ins_grid* g, const T* uin, T* uout, T* p) {
+        T* rp = reinterpret_cast<T*>(g->rp);
+        k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), uin, rp);
+        INS_LAUNCHED("divergence");
+        T* pp = p ? p : rp;
+        ins_status s;
+        if ((s = poisson<T>(g, rp, pp)) != INS_OK) return s;
+        k_sub_grad<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), uin, pp, uout);
+        INS_LAUNCHED("sub_grad");
+        return INS_OK;
+    }
+    static ins_status divergence(ins_grid* g, const T* u, T* phi) {
+        k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi);
+        INS_LAUNCHED("divergence");
+        return INS_OK;
+    }
+    static ins_status step(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
+        static const double A[4] = {0.5, 0.5, 1.0, 0.0};
+        static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+        T* F = reinterpret_cast<T*>(g->F);
+        T* rp = reinterpret_cast<T*>(g->rp);
+        T* acc = reinterpret_cast<T*>(g->acc);
+        T* us = reinterpret_cast<T*>(g->us);
+        ins_status s;
+        for (int st = 0; st < 4; ++st) {
+            const T* src = st == 0 ? u : us;
+            if ((s = launch_rhs_div<T, DIM, WALL>(g, src, F, rp)) != INS_OK) return s;
+            if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+            RkArgs ra;
+            ra.dt_dev = dt_dev;
+            ra.dt_host = dt_host;
+            ra.a_next = A[st];
+            ra.b = B[st];
+            ra.stage = st;
+            ra.mx = (st == 3 && next_dt) ? g->cfl_max : nullptr;
+            ra.err_flag = g->err_flag;
+            k_rk_update<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, u, acc,
+                                                                                   us, ra);
+            INS_LAUNCHED("rk_update");
+        }
+        if (next_dt) {
+            k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz, g->dmin2_nu, cfl,
+                                                    next_dt);
+            INS_LAUNCHED("cfl_finalize");
+        }
+        return INS_OK;
+    }
+    static ins_status cfl(ins_grid* g, const T* u, double cfl, double* dt_dev) {
+        // reuse the stage-4 path's reduction: a read-only pass
+        INS_CUDA(cudaMemsetAsync(g->diag, 0, 4 * sizeof(double), g->stream));
+        INS_CUDA(cudaMemsetAsync(g->diag_max, 0, 2 * sizeof(unsigned long long), g->stream));
+        k_diag<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, g->geo64, g->diag,
+                                                                          g->diag_max);
+        INS_LAUNCHED("diag");
+        // max |u^a|/h_a was reduced into diag_max[1]; finish on the device
+        k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->diag_max + 1, g->one, 1, g->dmin2_nu, cfl, dt_dev);
+        INS_LAUNCHED("cfl_finalize");
+        return INS_OK;
+    }
+    static ins_status diag(ins_grid* g, const T* u, double out[4]) {
+        INS_CUDA(cudaMemsetAsync(g->diag, 0, 4 * sizeof(double), g->stream));
+        INS_CUDA(cudaMemsetAsync(g->diag_max, 0, 2 * sizeof(unsigned long long), g->stream));
+        k_diag<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, g->geo64, g->diag,
+                                                                          g->diag_max);
+        INS_LAUNCHED("diag");
+        double h[4];
+        unsigned long long mx[2];
+        INS_CUDA(cudaMemcpyAsync(h, g->diag, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        INS_CUDA(cudaMemcpyAsync(mx, g->diag_max, sizeof(mx), cudaMemcpyDeviceToHost, g->stream));
+        INS_CUDA(cudaStreamSynchronize(g->stream));
+        double vol = 1.0;
+        for (int a = 0; a < g->dim; ++a) {
+            double L = 0.0;
+            for (double x : g->d[a]) L += x;
+            vol *= L;
+        }
+        double dv, cf;
+        std::memcpy(&dv, &mx[0], 8);
+        std::memcpy(&cf, &mx[1], 8);
+        out[0] = h[0] / vol;
+        out[1] = dv;
+        out[2] = cf;
+        out[3] = h[3];
+        if (h[3] > 0.0 || !std::isfinite(h[0])) return fail(INS_ERR_NONFINITE, "non-finite values in the field");
+        return INS_OK;
+    }
+};
+
+template <typename T, typename Fn>
+ins_status dispatch(ins_grid* g, Fn fn) {
+    if (g->dim == 2) {
+        if (g->wall_y) return fn(Impl<T, 2, true>());
+        return fn(Impl<T, 2, false>());
+    }
+    if (g->wall_y) return fn(Impl<T, 3, true>());
+    return fn(Impl<T, 3, false>());
+}
+
+template <typename Fn>
+ins_status dispatch_dtype(ins_grid* g, Fn fn) {
+    if (g->dtype == INS_F64) return fn((double)0);
+    return fn((float)0);
+}
+
+// ------------------------------------------------------------ creation helpers
+template <typename T>
+ins_status set_smem_attrs() {
+    const int mx = 200 * 1024;   // covers 2 * 2048 * 2 * 16 B (FP64, one line per tile)
+    INS_CUDA(cudaFuncSetAttribute(k_fft_x_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    INS_CUDA(cudaFuncSetAttribute(k_fft_x_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    INS_CUDA(cudaFuncSetAttribute(k_fft_strided<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    return INS_OK;
+}
+
+template <typename T>
+void fill_coefs(const ins_grid* g, std::vector<T>& out) {
+    const int n3[3] = {g->nx, g->ny, g->nz};
+    out.clear();
+    for (int a = 0; a < 3; ++a) {
+        const int n = n3[a];
+        std::vector<double> c((size_t)C_COUNT * n, 0.0);
+        if (a < g->dim) {
+            const auto& d = g->d[a];
+            const auto& h = g->h[a];
+            const bool wall = (a == 1 && g->wall_y);
+            for (int i = 0; i < n; ++i) {
+                const double dn = (i + 1 < n) ? d[i + 1] : (wall ? d[n - 1] : d[0]);
+                const double hp = (i > 0) ? h[i - 1] : g->hlo[a];
+                c[C_INV_H * n + i] = 1.0 / h[i];
+                c[C_INV_D * n + i] = 1.0 / d[i];
+                c[C_CONV_AA * n + i] = 0.25 / h[i];
+                c[C_CONV_AB * n + i] = 0.5 / d[i];
+                c[C_WL * n + i] = d[i] / (d[i] + dn);
+                c[C_WR * n + i] = dn / (d[i] + dn);
+                c[C_DIFF_AP * n + i] = g->nu / (dn * h[i]);
+                c[C_DIFF_AM * n + i] = g->nu / (d[i] * h[i]);
+                c[C_DIFF_BP * n + i] = g->nu / (h[i] * d[i]);
+                c[C_DIFF_BM * n + i] = g->nu / (hp * d[i]);
+            }
+        }
+        for (double v : c) out.push_back((T)v);
+    }
+}
+
+template <typename T>
+ins_status upload_twiddles(ins_grid* g, int a, void* dst, int L) {
+    std::vector<T> tw(2 * (size_t)L);
+    for (int m = 0; m < L; ++m) {
+        const double ang = 2.0 * M_PI * (double)m / (double)L;
+        tw[2 * m] = (T)std::cos(ang);
+        tw[2 * m + 1] = (T)(-std::sin(ang));
+    }
+    INS_CUDA(cudaMemcpy(dst, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return INS_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* ins_last_error(void) { return g_err.c_str(); }
+
+const char* ins_version(void) { return "libins 0.1 (sm_103a)"; }
+
+ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** out) {
+    g_err.clear();
+    if (!desc || !out) return fail(INS_ERR_ARG, "ins_grid_create: null desc or out");
+    *out = nullptr;
+    const ins_grid_desc& D = *desc;
+    if (D.dim != 2 && D.dim != 3) return fail(INS_ERR_ARG, "dim must be 2 or 3");
+    if (D.dtype != INS_F32 && D.dtype != INS_F64) return fail(INS_ERR_ARG, "dtype must be INS_F32 or INS_F64");
+    if (!(D.nu >= 0.0) || !std::isfinite(D.nu)) return fail(INS_ERR_ARG, "nu must be finite and >= 0");
+    for (int a = 0; a < D.dim; ++a) {
+        if (D.n[a] < 2 || D.n[a] > 4096) return fail(INS_ERR_ARG, "n[a] must be in [2, 4096]");
+        if (D.bc[a] != INS_PERIODIC && D.bc[a] != INS_WALL) return fail(INS_ERR_ARG, "bc must be PERIODIC or WALL");
+        if (!D.face_coords[a]) return fail(INS_ERR_ARG, "face_coords[a] is null");
+        if (!std::isfinite(D.force[a])) return fail(INS_ERR_ARG, "force must be finite");
+    }
+    for (int a = 0; a < D.dim; ++a) {
+        const bool wall = D.bc[a] == INS_WALL;
+        if (wall && a != 1) return fail(INS_ERR_UNSUPPORTED, "only y may be a wall direction");
+    }
+    const bool wall_y = D.bc[1] == INS_WALL;
+    const long N = (long)D.n[0] * D.n[1] * (D.dim == 3 ? D.n[2] : 1);
+    if (N > (1L << 31) - 1) return fail(INS_ERR_UNSUPPORTED, "more than 2^31 - 1 cells");
+
+    ins_grid* g = new ins_grid();
+    g->dim = D.dim;
+    g->nx = D.n[0];
+    g->ny = D.n[1];
+    g->nz = D.dim == 3 ? D.n[2] : 1;
+    g->wall_y = wall_y ? 1 : 0;
+    g->dtype = D.dtype;
+    g->nu = D.nu;
+    for (int a = 0; a < 3; ++a) g->force[a] = a < D.dim ? D.force[a] : 0.0;
+    g->stream = reinterpret_cast<cudaStream_t>(stream);
+    g->N = N;
+    g->nxh = g->nx / 2 + 1;
+    g->hlo.assign(3, 1.0);
+    const int n3[3] = {g->nx, g->ny, g->nz};
+    auto bail = [&](ins_status s, const std::string& m) {
+        if (g->base) cudaFree(g->base);
+        delete g;
+        return fail(s, m);
+    };
+    // geometry (host, FP64)
+    double dmin = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        const int n = n3[a];
+        if (a >= D.dim) {
+            g->d[a].assign(n, 1.0);
+            g->h[a].assign(n, 1.0);
+            continue;
+        }
+        const double* f = D.face_coords[a];
+        g->d[a].resize(n);
+        for (int i = 0; i < n; ++i) {
+            const double w = f[i + 1] - f[i];
+            if (!(w > 0.0) || !std::isfinite(w)) return bail(INS_ERR_ARG, "face coordinates must increase strictly");
+            g->d[a][i] = w;
+            dmin = std::fmin(dmin, w);
+        }
+        const bool wall = D.bc[a] == INS_WALL;
+        g->h[a].resize(n);
+        for (int i = 0; i < n; ++i) {
+            const double dn = (i + 1 < n) ? g->d[a][i + 1] : (wall ? g->d[a][n - 1] : g->d[a][0]);
+            g->h[a][i] = 0.5 * (g->d[a][i] + dn);
+        }
+        g->hlo[a] = wall ? g->d[a][0] : 0.5 * (g->d[a][n - 1] + g->d[a][0]);
+        if (!wall) {
+            double mean = 0.0;
+            for (double w : g->d[a]) mean += w;
+            mean /= n;
+            for (double w : g->d[a])
+                if (std::fabs(w - mean) > 1e-10 * mean)
+                    return bail(INS_ERR_UNSUPPORTED, "periodic directions must be uniformly spaced");
+            std::vector<int> rad;
+            if (n > 2048) return bail(INS_ERR_UNSUPPORTED, "periodic n must be <= 2048");
+            if (!factor_radices(n, rad)) return bail(INS_ERR_UNSUPPORTED, "periodic n must be 2^p 3^q 5^r 7^s");
+            g->nst[a] = (int)rad.size();
+            for (size_t s = 0; s < rad.size(); ++s) g->radix[a][s] = rad[s];
+        }
+    }
+    g->dmin2_nu = g->nu > 0.0 ? dmin * dmin / g->nu : INFINITY;
+
+    const size_t ts = D.dtype == INS_F64 ? 8 : 4;
+    const int dim = g->dim;
+    const long nxh = g->nxh;
+    const long spec = nxh * g->ny * g->nz;
+    const long ncol = (long)g->nz * nxh;
+    // layout of the single allocation
+    std::vector<size_t> sizes;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t off = 0;
+    size_t o_coef, o_geo, o_one, o_tw[3], o_scale = 0, o_lam, o_thlo = 0, o_thinv = 0, o_thcp = 0, o_thd = 0, o_F, o_acc,
+                                             o_us, o_rp, o_S, o_cfl, o_err, o_diag, o_dmax;
+    const size_t nsum = (size_t)g->nx + g->ny + g->nz;
+    o_coef = off; off += al((size_t)C_COUNT * nsum * ts);
+    o_geo = off; off += al(2 * nsum * 8);
+    o_one = off; off += al(8);
+    for (int a = 0; a < 3; ++a) {
+        o_tw[a] = off;
+        off += al((size_t)n3[a] * 2 * ts);
+    }
+    o_lam = off; off += al(nsum * 8);
+    if (!wall_y) {
+        o_scale = off; off += al((size_t)spec * ts);
+    } else {
+        o_thlo = off; off += al((size_t)g->ny * 8);
+        o_thinv = off; off += al((size_t)g->ny * ncol * 8);
+        o_thcp = off; off += al((size_t)g->ny * ncol * 8);
+        o_thd = off; off += al((size_t)g->ny * ncol * 16);
+    }
+    o_F = off; off += al((size_t)dim * N * ts);
+    o_acc = off; off += al((size_t)dim * N * ts);
+    o_us = off; off += al((size_t)dim * N * ts);
+    o_rp = off; off += al((size_t)N * ts);
+    o_S = off; off += al((size_t)spec * 2 * ts);
+    o_cfl = off; off += al(nsum * 8);
+    o_err = off; off += al(4);
+    o_diag = off; off += al(4 * 8);
+    o_dmax = off; off += al(2 * 8);
+    g->bytes = off;
+    cudaError_t e = cudaMalloc(&g->base, off);
+    if (e != cudaSuccess) {
+        g->base = nullptr;
+        cudaGetLastError();
+        return bail(INS_ERR_OOM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+    }
+    char* b = reinterpret_cast<char*>(g->base);
+    g->coef = b + o_coef;
+    g->geo64 = reinterpret_cast<double*>(b + o_geo);
+    g->one = reinterpret_cast<double*>(b + o_one);
+    for (int a = 0; a < 3; ++a) g->tw[a] = b + o_tw[a];
+    g->lam = reinterpret_cast<double*>(b + o_lam);
+    if (!wall_y) {
+        g->scale = b + o_scale;
+    } else {
+        g->th_lo = reinterpret_cast<double*>(b + o_thlo);
+        g->th_invm = reinterpret_cast<double*>(b + o_thinv);
+        g->th_cp = reinterpret_cast<double*>(b + o_thcp);
+        g->th_d = b + o_thd;
+    }
+    g->F = b + o_F;
+    g->acc = b + o_acc;
+    g->us = b + o_us;
+    g->rp = b + o_rp;
+    g->S = b + o_S;
+    g->cfl_max = reinterpret_cast<unsigned long long*>(b + o_cfl);
+    g->err_flag = reinterpret_cast<unsigned int*>(b + o_err);
+    g->diag = reinterpret_cast<double*>(b + o_diag);
+    g->diag_max = reinterpret_cast<unsigned long long*>(b + o_dmax);
+
+    auto up = [&](void* dst, const void* src, size_t n) -> bool {
+        return cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    // coefficients
+    bool ok = true;
+    if (D.dtype == INS_F64) {
+        std::vector<double> c;
+        fill_coefs<double>(g, c);
+        ok &= up(g->coef, c.data(), c.size() * 8);
+    } else {
+        std::vector<float> c;
+        fill_coefs<float>(g, c);
+        ok &= up(g->coef, c.data(), c.size() * 4);
+    }
+    {
+        std::vector<double> geo(2 * nsum);
+        size_t o = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < n3[a]; ++i) geo[o++] = g->h[a][i];
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < n3[a]; ++i) geo[o++] = g->d[a][i];
+        ok &= up(g->geo64, geo.data(), geo.size() * 8);
+        const double one = 1.0;
+        ok &= up(g->one, &one, 8);
+    }
+    if (!ok) return bail(INS_ERR_CUDA, "geometry upload failed");
+    for (int a = 0; a < dim; ++a) {
+        if (a == 1 && wall_y) continue;
+        ins_status s = D.dtype == INS_F64 ? upload_twiddles<double>(g, a, g->tw[a], n3[a])
+                                          : upload_twiddles<float>(g, a, g->tw[a], n3[a]);
+        if (s != INS_OK) {
+            std::string m = g_err;
+            return bail(s, m);
+        }
+    }
+    // eigenvalues of D G along periodic directions: -4 sin^2(pi k/n) / (d h)
+    {
+        std::vector<double> lam(nsum, 0.0);
+        size_t o = 0;
+        for (int a = 0; a < 3; ++a) {
+            const int n = n3[a];
+            const bool per = a < dim && !(a == 1 && wall_y);
+            for (int k = 0; k < n; ++k) {
+                double v = 0.0;
+                if (per) {
+                    const double s = std::sin(M_PI * (double)k / (double)n);
+                    v = -4.0 * s * s / (g->d[a][0] * g->h[a][0]);
+                }
+                lam[o++] = v;
+            }
+        }
+        ok &= up(g->lam, lam.data(), lam.size() * 8);
+        if (!wall_y) {
+            const double ntot = (double)N;
+            if (D.dtype == INS_F64)
+                k_make_scale<double><<<1024, 256>>>(reinterpret_cast<double*>(g->scale), g->lam, g->lam + g->nx,
+                                                    g->lam + g->nx + g->ny, (int)nxh, g->ny, g->nz, ntot);
+            else
+                k_make_scale<float><<<1024, 256>>>(reinterpret_cast<float*>(g->scale), g->lam, g->lam + g->nx,
+                                                   g->lam + g->nx + g->ny, (int)nxh, g->ny, g->nz, ntot);
+            if (cudaGetLastError() != cudaSuccess) return bail(INS_ERR_CUDA, "scale table kernel failed");
+        } else {
+            // Thomas factors per (kx, kz) mode, FP64, constant in time
+            const int ny = g->ny;
+            const auto& d = g->d[1];
+            const auto& h = g->h[1];
+            std::vector<double> lo(ny, 0.0), upc(ny, 0.0);
+            for (int j = 1; j < ny; ++j) lo[j] = 1.0 / (d[j] * h[j - 1]);
+            for (int j = 0; j + 1 < ny; ++j) upc[j] = 1.0 / (d[j] * h[j]);
+            std::vector<double> invm((size_t)ny * ncol), cp((size_t)ny * ncol);
+            for (long col = 0; col < ncol; ++col) {
+                const int kx = (int)(col % nxh), kz = (int)(col / nxh);
+                const double lamxz = lam[kx] + (dim == 3 ? lam[g->nx + g->ny + kz] : 0.0);
+                double cprev = 0.0;
+                for (int j = 0; j < ny; ++j) {
+                    double diag = -lo[j] - upc[j] + lamxz;
+                    double upj = upc[j];
+                    if (col == 0 && j == 0) {
+                        diag = 1.0;
+                        upj = 0.0;
+                    }
+                    const double m = diag - lo[j] * cprev;
+                    const double c = upj / m;
+                    invm[(size_t)j * ncol + col] = 1.0 / m;
+                    cp[(size_t)j * ncol + col] = c;
+                    cprev = c;
+                }
+            }
+            ok &= up(g->th_lo, lo.data(), (size_t)ny * 8);
+            ok &= up(g->th_invm, invm.data(), invm.size() * 8);
+            ok &= up(g->th_cp, cp.data(), cp.size() * 8);
+        }
+    }
+    if (!ok) return bail(INS_ERR_CUDA, "table upload failed");
+    if (cudaMemset(g->cfl_max, 0, nsum * 8) != cudaSuccess || cudaMemset(g->err_flag, 0, 4) != cudaSuccess)
+        return bail(INS_ERR_CUDA, "memset failed");
+    ins_status s = D.dtype == INS_F64 ? set_smem_attrs<double>() : set_smem_attrs<float>();
+    if (s != INS_OK) {
+        std::string m = g_err;
+        return bail(s, m);
+    }
+    if (D.dtype == INS_F64) {
+        g->lg_tw_x = choose_lgtw<double>(g->nx);
+        g->lg_tw_y = choose_lgtw<double>(g->ny);
+        g->lg_tw_z = choose_lgtw<double>(g->nz);
+    } else {
+        g->lg_tw_x = choose_lgtw<float>(g->nx);
+        g->lg_tw_y = choose_lgtw<float>(g->ny);
+        g->lg_tw_z = choose_lgtw<float>(g->nz);
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return bail(INS_ERR_CUDA, std::string("grid setup failed: ") + cudaGetErrorString(e));
+    *out = g;
+    return INS_OK;
+}
+
+ins_status ins_grid_destroy(ins_grid* g) {
+    if (!g) return INS_OK;
+    cudaStreamSynchronize(g->stream);
+    cudaError_t e = cudaFree(g->base);
+    delete g;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
+    return INS_OK;
+}
+
+ins_status ins_set_stream(ins_grid* g, void* stream) {
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    g->stream = reinterpret_cast<cudaStream_t>(stream);
+    return INS_OK;
+}
+
+ins_status ins_workspace_bytes(const ins_grid* g, size_t* bytes) {
+    if (!g || !bytes) return fail(INS_ERR_ARG, "null argument");
+    *bytes = g->bytes;
+    return INS_OK;
+}
+
+static ins_status check_ptr(const ins_grid* g, const void* p, const char* name) {
+    if (!p) return fail(INS_ERR_ARG, std::string(name) + " is null");
+    const size_t al = g->dtype == INS_F64 ? 8 : 4;
+    if (reinterpret_cast<uintptr_t>(p) % al) return fail(INS_ERR_ARG, std::string(name) + " is misaligned");
+    return INS_OK;
+}
+
+#define CHECK(x)                        \
+    do {                                \
+        ins_status s_ = (x);            \
+        if (s_ != INS_OK) return s_;    \
+    } while (0)
+
+ins_status ins_rhs(ins_grid* g, const void* u, void* dudt, void* p) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u, "u"));
+    CHECK(check_ptr(g, dudt, "dudt"));
+    if (p) CHECK(check_ptr(g, p, "p"));
+    return dispatch_dtype(g, [&](auto z) {
+        using T = decltype(z);
+        return dispatch<T>(g, [&](auto impl) {
+            return decltype(impl)::rhs(g, (const T*)u, (T*)dudt, (T*)p);
+        });
+    });
+}
+
+ins_status ins_project(ins_grid* g, const void* u_in, void* u_out, void* p) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u_in, "u_in"));
+    CHECK(check_ptr(g, u_out, "u_out"));
+    if (p) CHECK(check_ptr(g, p, "p"));
+    return dispatch_dtype(g, [&](auto z) {
+        using T = decltype(z);
+        return dispatch<T>(g, [&](auto impl) {
+            return decltype(impl)::project(g, (const T*)u_in, (T*)u_out, (T*)p);
+        });
+    });
+}
+
+ins_status ins_divergence(ins_grid* g, const void* u, void* phi) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u, "u"));
+    CHECK(check_ptr(g, phi, "phi"));
+    return dispatch_dtype(g, [&](auto z) {
+        using T = decltype(z);
+        return dispatch<T>(g, [&](auto impl) { return decltype(impl)::divergence(g, (const T*)u, (T*)phi); });
+    });
+}
+
+ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host, double* next_dt_dev, double cfl) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u, "u"));
+    if (!dt_dev && !(std::isfinite(dt_host) && dt_host >= 0.0)) return fail(INS_ERR_ARG, "dt_host must be finite, >= 0");
+    if (next_dt_dev && !(std::isfinite(cfl) && cfl > 0.0)) return fail(INS_ERR_ARG, "cfl must be finite and > 0");
+    return dispatch_dtype(g, [&](auto z) {
+        using T = decltype(z);
+        return dispatch<T>(g, [&](auto impl) {
+            return decltype(impl)::step(g, (T*)u, dt_dev, dt_host, next_dt_dev, cfl);
+        });
+    });
+}
+
+ins_status ins_cfl_dt(ins_grid* g, const void* u, double cfl, double* dt_dev) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u, "u"));
+    if (!dt_dev) return fail(INS_ERR_ARG, "dt_dev is null");
+    if (!(std::isfinite(cfl) && cfl > 0.0)) return fail(INS_ERR_ARG, "cfl must be finite and > 0");
+    return dispatch_dtype(g, [&](auto z) {
+        using T = decltype(z);
+        return dispatch<T>(g, [&](auto impl) { return decltype(impl)::cfl(g, (const T*)u, cfl, dt_dev); });
+    });
+}
+
+ins_status ins_diag(ins_grid* g, const void* u, double out[4]) {
+    g_err.clear();
+    if (!g || !out) return fail(INS_ERR_ARG, "null argument");
+    CHECK(check_ptr(g, u, "u"));
+    return dispatch_dtype(g, [&](auto z) {
+        using T = decltype(z);
+        return dispatch<T>(g, [&](auto impl) { return decltype(impl)::diag(g, (const T*)u, out); });
+    });
+}
+
+ins_status ins_check_finite(ins_grid* g) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    unsigned int f = 0;
+    INS_CUDA(cudaMemcpyAsync(&f, g->err_flag, 4, cudaMemcpyDeviceToHost, g->stream));
+    INS_CUDA(cudaStreamSynchronize(g->stream));
+    if (f) {
+        INS_CUDA(cudaMemsetAsync(g->err_flag, 0, 4, g->stream));
+        INS_CUDA(cudaStreamSynchronize(g->stream));
+        return fail(INS_ERR_NONFINITE, "a step produced a non-finite value");
+    }
+    return INS_OK;
+}
+
+}  // extern "C"

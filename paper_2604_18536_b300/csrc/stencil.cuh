@@ -1,0 +1,458 @@
+// Stencil kernels of the staggered finite-volume scheme (paper App. A momentum
+// equation, App. B kernels) and the fused projection + RK update.
+//
+// k_rhs_div: F(u) = C(u) + nu diffusion(u) + f on every velocity face and
+// r = D F(u) in every cell, one pass over u. A CTA owns a BX x BY column of
+// cells and marches up z through a chunk of planes. Three planes (k-1, k, k+1)
+// of all velocity components, with a halo of 2 cells below and 1 above in x
+// and y, sit in shared memory as a ring. Each thread computes F at its own
+// three faces; the faces just below the tile in x and y (needed by the
+// divergence) are computed by extra threads, and F^z at k-1 is carried in a
+// register from the previous plane. Boundary rules are applied while loading
+// the planes: periodic wrap, or at a no-slip wall in y the odd ghost for the
+// tangential components and 0 for the wall-normal one (Sec. 2.4).
+//
+// Convection (energy-conserving form of App. A): for u^a and flux direction b
+//  b == a: -((u_{i} + u_{i+1})^2 - (u_{i-1} + u_i)^2) * 0.25 / h_a[i]
+//  b != a: -(V+ (u + u_{+b}) - V- (u_{-b} + u)) * 0.5 / d_b[j]
+//          V+ = wl_a[i] u^b + wr_a[i] u^b_{+a} (volume weights along a), V- the same one b-cell lower.
+#pragma once
+
+#include "common.cuh"
+
+namespace ins {
+
+constexpr int BX = 32;
+constexpr int BY = 8;
+constexpr int SX = BX + 3;   // smem plane covers i0-2 .. i0+BX
+constexpr int SY = BY + 3;   //                   j0-2 .. j0+BY
+constexpr int SPL = SX * SY;
+
+__device__ __forceinline__ int pmod(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// Load plane gk (already wrapped) of the DIM velocity components into s[comp][...].
+template <typename T, int DIM, bool WALL>
+__device__ __forceinline__ void load_plane(const Geo<T>& g, const T* __restrict__ u, long N, int gk, int i0, int j0,
+                                           T (*s)[SPL]) {
+    const int nx = g.nx, ny = g.ny;
+    for (int idx = threadIdx.x + threadIdx.y * BX; idx < SPL; idx += BX * BY) {
+        const int li = idx % SX, lj = idx / SX;
+        const int gi = pmod(i0 - 2 + li, nx);
+        int gj = j0 - 2 + lj;
+        const long plane = (long)gk * nx * ny;
+        if (!WALL) {
+            gj = pmod(gj, ny);
+            const long a = plane + (long)gj * nx + gi;
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) s[c][idx] = u[c * N + a];
+        } else {
+            if (gj >= 0 && gj < ny) {
+                const long a = plane + (long)gj * nx + gi;
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) s[c][idx] = u[c * N + a];
+            } else {
+                // mirrored ghost cell: tangential components odd, wall-normal one 0
+                int m = gj < 0 ? -gj - 1 : 2 * ny - 1 - gj;
+                m = m < 0 ? 0 : (m >= ny ? ny - 1 : m);
+                const long a = plane + (long)m * nx + gi;
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) s[c][idx] = (c == 1) ? (T)0 : -u[c * N + a];
+            }
+        }
+    }
+}
+
+// F^x at local (li, lj) = global (i, j, k); planes m (k-1), o (k), p (k+1).
+template <typename T, int DIM>
+__device__ __forceinline__ T Fx_at(const Geo<T>& g, const T (*m)[SPL], const T (*o)[SPL], const T (*p)[SPL], int li,
+                                   int lj, int i, int j, int k) {
+    const int c0 = lj * SX + li;
+    const T uc = o[0][c0], ue = o[0][c0 + 1], uw = o[0][c0 - 1], un = o[0][c0 + SX], us = o[0][c0 - SX];
+    const T wl = g.coef(0, C_WL, i), wr = g.coef(0, C_WR, i);
+    T s1 = uc + ue, s2 = uw + uc;
+    T conv = -(s1 * s1 - s2 * s2) * g.coef(0, C_CONV_AA, i);
+    {
+        const T vp = wl * o[1][c0] + wr * o[1][c0 + 1];
+        const T vm = wl * o[1][c0 - SX] + wr * o[1][c0 + 1 - SX];
+        conv -= (vp * (uc + un) - vm * (us + uc)) * g.coef(1, C_CONV_AB, j);
+    }
+    T dif = g.coef(0, C_DIFF_AP, i) * (ue - uc) - g.coef(0, C_DIFF_AM, i) * (uc - uw) +
+            g.coef(1, C_DIFF_BP, j) * (un - uc) - g.coef(1, C_DIFF_BM, j) * (uc - us);
+    if (DIM == 3) {
+        const T ut = p[0][c0], ub = m[0][c0];
+        const T vp = wl * o[2][c0] + wr * o[2][c0 + 1];
+        const T vm = wl * m[2][c0] + wr * m[2][c0 + 1];
+        conv -= (vp * (uc + ut) - vm * (ub + uc)) * g.coef(2, C_CONV_AB, k);
+        dif += g.coef(2, C_DIFF_BP, k) * (ut - uc) - g.coef(2, C_DIFF_BM, k) * (uc - ub);
+    }
+    return conv + dif + g.fx;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ T Fy_at(const Geo<T>& g, const T (*m)[SPL], const T (*o)[SPL], const T (*p)[SPL], int li,
+                                   int lj, int i, int j, int k) {
+    const int c0 = lj * SX + li;
+    const T uc = o[1][c0], un = o[1][c0 + SX], us = o[1][c0 - SX], ue = o[1][c0 + 1], uw = o[1][c0 - 1];
+    const T wl = g.coef(1, C_WL, j), wr = g.coef(1, C_WR, j);
+    T s1 = uc + un, s2 = us + uc;
+    T conv = -(s1 * s1 - s2 * s2) * g.coef(1, C_CONV_AA, j);
+    {
+        const T vp = wl * o[0][c0] + wr * o[0][c0 + SX];
+        const T vm = wl * o[0][c0 - 1] + wr * o[0][c0 - 1 + SX];
+        conv -= (vp * (uc + ue) - vm * (uw + uc)) * g.coef(0, C_CONV_AB, i);
+    }
+    T dif = g.coef(1, C_DIFF_AP, j) * (un - uc) - g.coef(1, C_DIFF_AM, j) * (uc - us) +
+            g.coef(0, C_DIFF_BP, i) * (ue - uc) - g.coef(0, C_DIFF_BM, i) * (uc - uw);
+    if (DIM == 3) {
+        const T ut = p[1][c0], ub = m[1][c0];
+        const T vp = wl * o[2][c0] + wr * o[2][c0 + SX];
+        const T vm = wl * m[2][c0] + wr * m[2][c0 + SX];
+        conv -= (vp * (uc + ut) - vm * (ub + uc)) * g.coef(2, C_CONV_AB, k);
+        dif += g.coef(2, C_DIFF_BP, k) * (ut - uc) - g.coef(2, C_DIFF_BM, k) * (uc - ub);
+    }
+    return conv + dif + g.fy;
+}
+
+template <typename T>
+__device__ __forceinline__ T Fz_at(const Geo<T>& g, const T (*m)[SPL], const T (*o)[SPL], const T (*p)[SPL], int li,
+                                   int lj, int i, int j, int k) {
+    const int c0 = lj * SX + li;
+    const T uc = o[2][c0], ut = p[2][c0], ub = m[2][c0], ue = o[2][c0 + 1], uw = o[2][c0 - 1], un = o[2][c0 + SX],
+            us = o[2][c0 - SX];
+    const T wl = g.coef(2, C_WL, k), wr = g.coef(2, C_WR, k);
+    T s1 = uc + ut, s2 = ub + uc;
+    T conv = -(s1 * s1 - s2 * s2) * g.coef(2, C_CONV_AA, k);
+    {
+        const T vp = wl * o[0][c0] + wr * p[0][c0];
+        const T vm = wl * o[0][c0 - 1] + wr * p[0][c0 - 1];
+        conv -= (vp * (uc + ue) - vm * (uw + uc)) * g.coef(0, C_CONV_AB, i);
+    }
+    {
+        const T vp = wl * o[1][c0] + wr * p[1][c0];
+        const T vm = wl * o[1][c0 - SX] + wr * p[1][c0 - SX];
+        conv -= (vp * (uc + un) - vm * (us + uc)) * g.coef(1, C_CONV_AB, j);
+    }
+    const T dif = g.coef(2, C_DIFF_AP, k) * (ut - uc) - g.coef(2, C_DIFF_AM, k) * (uc - ub) +
+                  g.coef(0, C_DIFF_BP, i) * (ue - uc) - g.coef(0, C_DIFF_BM, i) * (uc - uw) +
+                  g.coef(1, C_DIFF_BP, j) * (un - uc) - g.coef(1, C_DIFF_BM, j) * (uc - us);
+    return conv + dif + g.fz;
+}
+
+// F (dim fields, may be null) and r = D F. Grid: (ceil(nx/BX), ceil(ny/BY), ceil(nz/kchunk)).
+template <typename T, int DIM, bool WALL>
+__global__ void __launch_bounds__(BX* BY) k_rhs_div(Geo<T> g, const T* __restrict__ u, T* __restrict__ F,
+                                                    T* __restrict__ r, int kchunk) {
+    __shared__ T su[3][DIM][SPL];
+    __shared__ T sFx[BY][BX + 1];
+    __shared__ T sFy[BY + 1][BX];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long N = (long)nx * ny * nz;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool inside = i < nx && j < ny;
+    const int li = tx + 2, lj = ty + 2;
+    const int ih = pmod(i0 - 1, nx);                 // the halo column, global index
+    const int jh = pmod(j0 - 1, ny);                 // the halo row, global index
+    const bool bottom_wall_halo = WALL && j0 == 0;   // F^y below row 0 is the wall: 0
+    const int ic = i < nx ? i : nx - 1, jc = j < ny ? j : ny - 1;
+    const T iDx = g.coef(0, C_INV_D, ic), iDy = g.coef(1, C_INV_D, jc);
+
+    if (DIM == 2) {
+        load_plane<T, DIM, WALL>(g, u, N, 0, i0, j0, su[0]);
+        __syncthreads();
+        const T(*o)[SPL] = su[0];
+        T fx = Fx_at<T, 2>(g, o, o, o, li, lj, ic, jc, 0);
+        T fy = Fy_at<T, 2>(g, o, o, o, li, lj, ic, jc, 0);
+        if (WALL && j == ny - 1) fy = (T)0;
+        sFx[ty][tx + 1] = fx;
+        sFy[ty + 1][tx] = fy;
+        if (tx == 0) sFx[ty][0] = Fx_at<T, 2>(g, o, o, o, 1, lj, ih, jc, 0);
+        if (ty == 0) sFy[0][tx] = bottom_wall_halo ? (T)0 : Fy_at<T, 2>(g, o, o, o, li, 1, ic, jh, 0);
+        __syncthreads();
+        if (inside) {
+            const long a = (long)j * nx + i;
+            if (F) {
+                F[a] = fx;
+                F[N + a] = fy;
+            }
+            r[a] = (fx - sFx[ty][tx]) * iDx + (fy - sFy[ty][tx]) * iDy;
+        }
+        return;
+    }
+
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(kb + kchunk, nz);
+    // ring of plane slots: sm = k-1, so = k, sp = k+1
+    int sm = 0, so = 1, sp = 2;
+    load_plane<T, DIM, WALL>(g, u, N, pmod(kb - 2, nz), i0, j0, su[sm]);
+    load_plane<T, DIM, WALL>(g, u, N, pmod(kb - 1, nz), i0, j0, su[so]);
+    load_plane<T, DIM, WALL>(g, u, N, pmod(kb, nz), i0, j0, su[sp]);
+    __syncthreads();
+    T fz_prev = Fz_at<T>(g, su[sm], su[so], su[sp], li, lj, ic, jc, pmod(kb - 1, nz));
+    __syncthreads();
+    load_plane<T, DIM, WALL>(g, u, N, pmod(kb + 1, nz), i0, j0, su[sm]);
+    { int t = sm; sm = so; so = sp; sp = t; }
+    __syncthreads();
+    for (int k = kb; k < ke; ++k) {
+        const T(*m)[SPL] = su[sm];
+        const T(*o)[SPL] = su[so];
+        const T(*p)[SPL] = su[sp];
+        const T fx = Fx_at<T, 3>(g, m, o, p, li, lj, ic, jc, k);
+        T fy = Fy_at<T, 3>(g, m, o, p, li, lj, ic, jc, k);
+        if (WALL && j == ny - 1) fy = (T)0;
+        const T fz = Fz_at<T>(g, m, o, p, li, lj, ic, jc, k);
+        sFx[ty][tx + 1] = fx;
+        sFy[ty + 1][tx] = fy;
+        if (tx == 0) sFx[ty][0] = Fx_at<T, 3>(g, m, o, p, 1, lj, ih, jc, k);
+        if (ty == 0) sFy[0][tx] = bottom_wall_halo ? (T)0 : Fy_at<T, 3>(g, m, o, p, li, 1, ic, jh, k);
+        __syncthreads();
+        if (inside) {
+            const long a = ((long)k * ny + j) * nx + i;
+            if (F) {
+                F[a] = fx;
+                F[N + a] = fy;
+                F[2 * N + a] = fz;
+            }
+            r[a] = (fx - sFx[ty][tx]) * iDx + (fy - sFy[ty][tx]) * iDy + (fz - fz_prev) * g.coef(2, C_INV_D, k);
+        }
+        fz_prev = fz;
+        if (k + 1 < ke) load_plane<T, DIM, WALL>(g, u, N, pmod(k + 2, nz), i0, j0, su[sm]);
+        { int t = sm; sm = so; so = sp; sp = t; }
+        __syncthreads();
+    }
+}
+
+// phi = D u (used by the projection).
+template <typename T, int DIM, bool WALL>
+__global__ void k_divergence(Geo<T> g, const T* __restrict__ u, T* __restrict__ phi) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long N = (long)nx * ny * nz;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long a = ((long)k * ny + j) * nx + i;
+    const int im = i == 0 ? nx - 1 : i - 1;
+    T d = (u[a] - u[a - i + im]) * g.coef(0, C_INV_D, i);
+    T uym;
+    if (j == 0) uym = WALL ? (T)0 : u[N + a + (long)(ny - 1) * nx];
+    else uym = u[N + a - nx];
+    d += (u[N + a] - uym) * g.coef(1, C_INV_D, j);
+    if (DIM == 3) {
+        const long az = k == 0 ? a + (long)(nz - 1) * nx * ny : a - (long)nx * ny;
+        d += (u[2 * N + a] - u[2 * N + az]) * g.coef(2, C_INV_D, k);
+    }
+    phi[a] = d;
+}
+
+// out = src - G p (projection of u, or the projected right-hand side of F).
+template <typename T, int DIM, bool WALL>
+__global__ void k_sub_grad(Geo<T> g, const T* __restrict__ src, const T* __restrict__ p, T* __restrict__ out) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long N = (long)nx * ny * nz;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long a = ((long)k * ny + j) * nx + i;
+    const T p0 = p[a];
+    const T pe = p[a - i + (i + 1 == nx ? 0 : i + 1)];
+    out[a] = src[a] - (pe - p0) * g.coef(0, C_INV_H, i);
+    if (WALL && j == ny - 1) {
+        out[N + a] = (T)0;
+    } else {
+        const T pn = p[j + 1 == ny ? a - (long)(ny - 1) * nx : a + nx];
+        out[N + a] = src[N + a] - (pn - p0) * g.coef(1, C_INV_H, j);
+    }
+    if (DIM == 3) {
+        const long plane = (long)nx * ny;
+        const T pt = p[k + 1 == nz ? a - (long)(nz - 1) * plane : a + plane];
+        out[2 * N + a] = src[2 * N + a] - (pt - p0) * g.coef(2, C_INV_H, k);
+    }
+}
+
+// Stage update of classic RK4 (Sec. 2.6.2), k = F - G p:
+//  stage 0: acc = b0 k;          us = u0 + dt a1 k
+//  stage 1,2: acc += b k;        us = u0 + dt a k
+//  stage 3: u0 = u0 + dt (acc + b3 k) (in place), plus the CFL maxima and the finite check.
+// CFL maxima: max_I |u^a_I| / h_a[i_a] = max_i (max over the other indices of |u^a|) / h_a[i]
+// because a correctly rounded division by a fixed positive h is monotone. The stage-3
+// update therefore only reduces max |u^a| per index of direction a (bit patterns of
+// non-negative doubles order like the doubles) into mx[off_a + i]; the divisions happen
+// once per index in k_cfl_finalize, giving the same bits as dividing every element.
+struct RkArgs {
+    const double* dt_dev;
+    double dt_host;
+    double a_next;   // a_{s+1,s}
+    double b;        // b_s
+    int stage;
+    unsigned long long* mx;   // [nx + ny + nz] per-index maxima of |u^a|; null: skip
+    unsigned int* err_flag;   // bit 0: non-finite value seen
+};
+
+// Block shape must be (32, 8): x rows of one warp each.
+template <typename T, int DIM, bool WALL>
+__global__ void __launch_bounds__(256) k_rk_update(Geo<T> g, const T* __restrict__ F, const T* __restrict__ p,
+                                                   T* __restrict__ u0, T* __restrict__ acc, T* __restrict__ us,
+                                                   RkArgs ra) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long N = (long)nx * ny * nz;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    const bool in = i < nx && j < ny;
+    const double dt = ra.dt_dev ? *ra.dt_dev : ra.dt_host;
+    const T dta = (T)(dt * ra.a_next), bb = (T)ra.b, dtt = (T)dt;
+    double q[3] = {0.0, 0.0, 0.0};
+    bool bad = false;
+    if (in) {
+        const long a = ((long)k * ny + j) * nx + i;
+        const T p0 = p[a];
+        T kk[3];
+        kk[0] = F[a] - (p[a - i + (i + 1 == nx ? 0 : i + 1)] - p0) * g.coef(0, C_INV_H, i);
+        if (WALL && j == ny - 1) kk[1] = (T)0;
+        else kk[1] = F[N + a] - (p[j + 1 == ny ? a - (long)(ny - 1) * nx : a + nx] - p0) * g.coef(1, C_INV_H, j);
+        if (DIM == 3) {
+            const long plane = (long)nx * ny;
+            kk[2] = F[2 * N + a] - (p[k + 1 == nz ? a - (long)(nz - 1) * plane : a + plane] - p0) *
+                                       g.coef(2, C_INV_H, k);
+        }
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            const long e = c * N + a;
+            const T u0v = u0[e];
+            if (ra.stage == 0) {
+                acc[e] = bb * kk[c];
+                us[e] = u0v + dta * kk[c];
+            } else if (ra.stage < 3) {
+                acc[e] = acc[e] + bb * kk[c];
+                us[e] = u0v + dta * kk[c];
+            } else {
+                const T un = u0v + dtt * (acc[e] + bb * kk[c]);
+                u0[e] = un;
+                q[c] = fabs((double)un);
+                bad |= !isfinite(un);
+            }
+        }
+    }
+    if (ra.stage == 3) {
+        if (ra.mx) {
+            __shared__ double sx[8][33];
+            const int lane = threadIdx.x, row = threadIdx.y;
+            // x: max over the 8 rows of the block, per column i
+            sx[row][lane] = q[0];
+            // y: max over the warp (one row j)
+            double qy = q[1];
+            for (int o = 16; o > 0; o >>= 1) qy = fmax(qy, __shfl_xor_sync(0xffffffffu, qy, o));
+            if (lane == 0 && j < ny && qy > 0.0)
+                atomicMax(&ra.mx[nx + j], (unsigned long long)__double_as_longlong(qy));
+            double qz = q[2];
+            if (DIM == 3) {
+                for (int o = 16; o > 0; o >>= 1) qz = fmax(qz, __shfl_xor_sync(0xffffffffu, qz, o));
+            }
+            __syncthreads();
+            if (row == 0) {
+                double m = sx[0][lane];
+#pragma unroll
+                for (int r = 1; r < 8; ++r) m = fmax(m, sx[r][lane]);
+                if (i < nx && m > 0.0) atomicMax(&ra.mx[i], (unsigned long long)__double_as_longlong(m));
+            }
+            if (DIM == 3) {
+                __syncthreads();
+                if (lane == 0) sx[row][32] = qz;
+                __syncthreads();
+                if (row == 0 && lane == 0) {
+                    double m = sx[0][32];
+                    for (int r = 1; r < 8; ++r) m = fmax(m, sx[r][32]);
+                    if (m > 0.0) atomicMax(&ra.mx[nx + ny + k], (unsigned long long)__double_as_longlong(m));
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(ra.err_flag, 1u);
+    }
+}
+
+// dt = cfl * min(1 / max_{a,i} mx[off_a + i] / h_a[i], dmin^2 / nu); resets mx to 0.
+// h64 holds h_x, h_y, h_z back to back (the same layout as mx). One block of 256 threads.
+__global__ void k_cfl_finalize(unsigned long long* mx, const double* __restrict__ h64, int ntot, double dmin2_nu,
+                               double cfl, double* dt_out) {
+    __shared__ double red[256];
+    double m = 0.0;
+    for (int t = threadIdx.x; t < ntot; t += blockDim.x) {
+        const double v = __longlong_as_double((long long)mx[t]);
+        m = fmax(m, v / h64[t]);
+        mx[t] = 0ull;
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mm = red[0];
+        const double conv = mm == 0.0 ? INFINITY : 1.0 / mm;
+        *dt_out = cfl * fmin(conv, dmin2_nu);
+    }
+}
+
+// Per-block partial sums/maxima for ins_diag: ke (weighted), max |div|, max |u|/h, nonfinite count.
+template <typename T, int DIM, bool WALL>
+__global__ void k_diag(Geo<T> g, const T* __restrict__ u, const double* __restrict__ vol_face, double* __restrict__ out,
+                       unsigned long long* __restrict__ maxes) {
+    // vol_face: per-direction face-volume factors, [a][n_a] products handled on the fly:
+    // |Omega^a_I| = h_a[i_a] * prod_{b != a} d_b[i_b], given as three per-direction arrays
+    // w_h[a] at vol_face + a*(nx+ny+nz) (h_a) and w_d at vol_face + 3*(nx+ny+nz) (d).
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long N = (long)nx * ny * nz;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    const int off[3] = {0, nx, nx + ny};
+    const int S = nx + ny + nz;
+    const double* hh = vol_face;            // h_a at hh[off[a] + idx]
+    const double* dd = vol_face + S;        // d_a at dd[off[a] + idx]
+    double ke = 0.0, dv = 0.0, cf = 0.0, nf = 0.0;
+    if (i < nx && j < ny) {
+        const long a = ((long)k * ny + j) * nx + i;
+        const int id[3] = {i, j, k};
+        for (int c = 0; c < DIM; ++c) {
+            const double v = (double)u[c * N + a];
+            double w = hh[off[c] + id[c]];
+            for (int b = 0; b < DIM; ++b)
+                if (b != c) w *= dd[off[b] + id[b]];
+            if (WALL && c == 1 && j == ny - 1) w = 0.0;
+            ke += 0.5 * w * v * v;
+            cf = fmax(cf, fabs(v) / hh[off[c] + id[c]]);
+            if (!isfinite(v)) nf += 1.0;
+        }
+        // divergence
+        const int im = i == 0 ? nx - 1 : i - 1;
+        double d = ((double)u[a] - (double)u[a - i + im]) / dd[off[0] + i];
+        double uym = (j == 0) ? (WALL ? 0.0 : (double)u[N + a + (long)(ny - 1) * nx]) : (double)u[N + a - nx];
+        d += ((double)u[N + a] - uym) / dd[off[1] + j];
+        if (DIM == 3) {
+            const long az = k == 0 ? a + (long)(nz - 1) * nx * ny : a - (long)nx * ny;
+            d += ((double)u[2 * N + a] - (double)u[2 * N + az]) / dd[off[2] + k];
+        }
+        dv = fabs(d);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ke += __shfl_xor_sync(0xffffffffu, ke, o);
+        nf += __shfl_xor_sync(0xffffffffu, nf, o);
+        dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+        cf = fmax(cf, __shfl_xor_sync(0xffffffffu, cf, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], ke);
+        atomicAdd(&out[3], nf);
+        if (dv > 0.0 || dv != dv) atomicMax(&maxes[0], (unsigned long long)__double_as_longlong(dv));
+        if (cf > 0.0 || cf != cf) atomicMax(&maxes[1], (unsigned long long)__double_as_longlong(cf));
+    }
+}
+
+}  // namespace ins

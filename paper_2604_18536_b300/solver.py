@@ -1,0 +1,161 @@
+"""Python face of libins: torch tensors in, pointers out. Argument marshalling only.
+
+Every computation runs in the CUDA kernels of libins; PyTorch only owns the
+device memory and the stream. A velocity field is a tensor of shape
+(dim, nz, ny, nx) in 3-D or (dim, ny, nx) in 2-D (x fastest), contiguous, on
+the grid's device and in the grid's dtype; a scalar field drops the first axis.
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import GridDesc, check, lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Grid:
+    """A staggered grid and its device workspace (``ins_grid_create``).
+
+    faces: list of dim 1-D arrays of face coordinates (n_a + 1 each, host FP64)
+    bc:    list of "periodic" | "wall" (only y may be a wall)
+    nu, force: viscosity and constant body force
+    dtype: torch.float32 or torch.float64
+    """
+
+    def __init__(self, faces, bc, nu, force=None, dtype=torch.float64, device=None):
+        self.dim = len(faces)
+        self.faces = [np.ascontiguousarray(f, dtype=np.float64) for f in faces]
+        self.n = tuple(len(f) - 1 for f in self.faces)
+        self.shape = tuple(reversed(self.n))
+        self.bc = list(bc)
+        self.nu = float(nu)
+        self.force = [0.0] * self.dim if force is None else [float(x) for x in force]
+        if dtype not in (torch.float32, torch.float64):
+            raise ValueError("dtype must be torch.float32 or torch.float64")
+        self.dtype = dtype
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        d = GridDesc()
+        d.dim = self.dim
+        for a in range(3):
+            d.n[a] = self.n[a] if a < self.dim else 1
+            d.bc[a] = (_lib.INS_WALL if self.bc[a] == "wall" else _lib.INS_PERIODIC) if a < self.dim else 0
+            d.face_coords[a] = (self.faces[a].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                                if a < self.dim else None)
+            d.force[a] = self.force[a] if a < self.dim else 0.0
+        d.dtype = _lib.INS_F64 if dtype == torch.float64 else _lib.INS_F32
+        d.nu = self.nu
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().ins_grid_create(ctypes.byref(d), ctypes.c_void_p(self._stream()), ctypes.byref(h)),
+                  "ins_grid_create")
+        self._h = h
+
+    # ------------------------------------------------------------ plumbing
+    def _stream(self):
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _sync_stream(self):
+        check(lib().ins_set_stream(self._h, ctypes.c_void_p(self._stream())), "ins_set_stream")
+
+    def _check_u(self, u, name="u"):
+        want = (self.dim,) + self.shape
+        if tuple(u.shape) != want or u.dtype != self.dtype or not u.is_cuda or not u.is_contiguous():
+            raise ValueError(f"{name}: expected contiguous {self.dtype} CUDA tensor of shape {want}, got "
+                             f"{tuple(u.shape)} {u.dtype} {u.device}")
+
+    def _check_p(self, p, name="p"):
+        if tuple(p.shape) != self.shape or p.dtype != self.dtype or not p.is_cuda or not p.is_contiguous():
+            raise ValueError(f"{name}: expected contiguous {self.dtype} CUDA tensor of shape {self.shape}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ins_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_velocity(self):
+        return torch.zeros((self.dim,) + self.shape, dtype=self.dtype, device=self.device)
+
+    def new_scalar(self):
+        return torch.zeros(self.shape, dtype=self.dtype, device=self.device)
+
+    def workspace_bytes(self):
+        b = ctypes.c_size_t()
+        check(lib().ins_workspace_bytes(self._h, ctypes.byref(b)), "ins_workspace_bytes")
+        return b.value
+
+    # ------------------------------------------------------------ operators
+    def rhs(self, u, out=None, p=None):
+        """dudt = F(u) - G p with L p = D F(u)   (ins_rhs)."""
+        self._check_u(u)
+        out = self.new_velocity() if out is None else out
+        self._check_u(out, "out")
+        if p is not None:
+            self._check_p(p)
+        self._sync_stream()
+        check(lib().ins_rhs(self._h, _ptr(u), _ptr(out), _ptr(p)), "ins_rhs")
+        return out
+
+    def project(self, u, out=None, p=None):
+        """u - G p with L p = D u   (ins_project). out may be u itself."""
+        self._check_u(u)
+        out = self.new_velocity() if out is None else out
+        self._check_u(out, "out")
+        if p is not None:
+            self._check_p(p)
+        self._sync_stream()
+        check(lib().ins_project(self._h, _ptr(u), _ptr(out), _ptr(p)), "ins_project")
+        return out
+
+    def divergence(self, u, out=None):
+        self._check_u(u)
+        out = self.new_scalar() if out is None else out
+        self._check_p(out, "out")
+        self._sync_stream()
+        check(lib().ins_divergence(self._h, _ptr(u), _ptr(out)), "ins_divergence")
+        return out
+
+    def step(self, u, dt=None, dt_dev=None, next_dt_dev=None, cfl=0.3):
+        """One RK4 step in place (ins_step). dt: host float, or dt_dev: a CUDA float64 tensor of one element."""
+        self._check_u(u)
+        if dt_dev is None and dt is None:
+            raise ValueError("give dt or dt_dev")
+        for t in (dt_dev, next_dt_dev):
+            if t is not None and (t.dtype != torch.float64 or not t.is_cuda or t.numel() < 1):
+                raise ValueError("dt tensors must be CUDA float64")
+        self._sync_stream()
+        check(lib().ins_step(self._h, _ptr(u), _ptr(dt_dev), float(dt if dt is not None else 0.0),
+                             _ptr(next_dt_dev), float(cfl)), "ins_step")
+        return u
+
+    def cfl_dt(self, u, cfl, out=None):
+        self._check_u(u)
+        out = torch.zeros(1, dtype=torch.float64, device=self.device) if out is None else out
+        self._sync_stream()
+        check(lib().ins_cfl_dt(self._h, _ptr(u), float(cfl), _ptr(out)), "ins_cfl_dt")
+        return out
+
+    def diag(self, u, raise_nonfinite=True):
+        """{'ke', 'max_div', 'max_u_over_h', 'nonfinite'} (synchronous)."""
+        self._check_u(u)
+        out = (ctypes.c_double * 4)()
+        self._sync_stream()
+        st = lib().ins_diag(self._h, _ptr(u), out)
+        if st != _lib.INS_ERR_NONFINITE or raise_nonfinite:
+            check(st, "ins_diag")
+        return {"ke": out[0], "max_div": out[1], "max_u_over_h": out[2], "nonfinite": int(out[3])}
+
+    def check_finite(self):
+        self._sync_stream()
+        check(lib().ins_check_finite(self._h), "ins_check_finite")

@@ -1,0 +1,226 @@
+"""GPU (libins, sm_103a) versus the FP64 oracle, element by element on seeded inputs.
+
+Tolerances (relative L2 field error): FP64 <= 1e-12 per call/step and <= 1e-10 after
+100 steps; FP32 <= 2e-5 per call/step (the FP32 path is compared with the FP64 oracle
+run on the same FP32-rounded input). The CFL time step is compared bit for bit.
+Sizes span several 32 x 8 stencil tiles and z chunks with ragged tails, and FFT
+lengths with every radix (2, 3, 4, 5, 7, 8).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import operators as op, poisson, timestep, diagnostics
+from oracle.grid import Grid as OGrid
+from paper_2604_18536_b300 import inputs
+from paper_2604_18536_b300.solver import Grid
+from paper_2604_18536_b300._lib import InsError, INS_ERR_NONFINITE
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
+PI = np.pi
+
+
+def case(name):
+    U = inputs.uniform_faces
+    if name == "p2":
+        return dict(faces=[U(72, 0, 2 * PI), U(40, 0, 1.5 * PI)], bc=["periodic"] * 2, nu=0.05, force=None)
+    if name == "p3":
+        return dict(faces=[U(40, 0, 2 * PI), U(24, 0, 1.5 * PI), U(36, 0, 3.0)], bc=["periodic"] * 3, nu=0.02,
+                    force=None)
+    if name == "p3tiny":
+        return dict(faces=[U(6, 0, 1.0), U(10, 0, 2.0), U(14, 0, 1.5)], bc=["periodic"] * 3, nu=0.01, force=None)
+    if name == "c3":
+        return dict(faces=inputs.channel_faces(36, 20, 28), bc=["periodic", "wall", "periodic"], nu=1 / 180,
+                    force=[1.0, 0.0, 0.0])
+    if name == "c2":
+        return dict(faces=[U(30, 0, 4 * PI), inputs.tanh_faces(18, 0, 2, 1.5)], bc=["periodic", "wall"], nu=0.05,
+                    force=[1.0, 0.0])
+    raise KeyError(name)
+
+
+CASES = ["p2", "p3", "p3tiny", "c3", "c2"]
+DTYPES = [torch.float64, torch.float32]
+
+
+def grids(name, dtype):
+    c = case(name)
+    og = OGrid(c["faces"], c["bc"], c["nu"], c["force"])
+    gg = Grid(c["faces"], c["bc"], c["nu"], c["force"], dtype=dtype)
+    return og, gg
+
+
+def rand_u(og, seed, project=False, scale=1.0):
+    u = inputs.random_field((og.dim,) + og.shape, seed, scale)
+    for a in range(og.dim):
+        u[a] *= og.face_mask(a)
+    if project:
+        u, _ = poisson.project(og, u)
+    return u
+
+
+def dev(x, dtype):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def rounded(x, dtype):
+    """The input as the GPU sees it (FP32 rounding), in FP64 for the oracle."""
+    return x.astype(np.float32).astype(np.float64) if dtype == torch.float32 else x
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def demean(og, p):
+    v = og.cell_volume()
+    return p - np.sum(v * p) / np.sum(v)
+
+
+# ------------------------------------------------------------------ operators
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", CASES)
+def test_rhs_parity(name, dtype):
+    og, gg = grids(name, dtype)
+    u = rounded(rand_u(og, 1), dtype)
+    p = gg.new_scalar()
+    du = host(gg.rhs(dev(u, dtype), p=p))
+    du_o, p_o = poisson.rhs(og, u)
+    assert rel(du, du_o) <= TOL[dtype], rel(du, du_o)
+    pd = demean(og, host(p))
+    po = demean(og, p_o)
+    assert rel(pd, po) <= 5 * TOL[dtype], rel(pd, po)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", CASES)
+def test_project_parity(name, dtype):
+    og, gg = grids(name, dtype)
+    u = rounded(rand_u(og, 2), dtype)
+    ut = dev(u, dtype)
+    out = host(gg.project(ut))
+    ref, _ = poisson.project(og, u)
+    assert rel(out, ref) <= TOL[dtype], rel(out, ref)
+    # divergence of the projected field at round-off: relative to the input divergence,
+    # with room for the conditioning of L (the oracle's own projection reaches ~30 eps)
+    eps = np.finfo(np.float64 if dtype == torch.float64 else np.float32).eps
+    assert np.max(np.abs(op.divergence(og, out))) < 1000 * eps * np.max(np.abs(op.divergence(og, u)))
+    # in place
+    gg.project(ut, out=ut)
+    assert rel(host(ut), ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", CASES)
+def test_divergence_parity(name, dtype):
+    og, gg = grids(name, dtype)
+    u = rounded(rand_u(og, 3), dtype)
+    d = host(gg.divergence(dev(u, dtype)))
+    assert rel(d, op.divergence(og, u)) <= TOL[dtype]
+
+
+# ------------------------------------------------------------------ RK4 step
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", CASES)
+def test_step_parity(name, dtype):
+    og, gg = grids(name, dtype)
+    u0 = rand_u(og, 4, project=True)
+    u0 = rounded(u0, dtype)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    ut = dev(u0, dtype)
+    gg.step(ut, dt=dt)
+    ref = timestep.rk4_step(og, u0, dt)
+    assert rel(host(ut), ref) <= TOL[dtype], rel(host(ut), ref)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", ["p3", "c3"])
+def test_step_device_dt_and_cfl_bitexact(name, dtype):
+    og, gg = grids(name, dtype)
+    u0 = rounded(rand_u(og, 5, project=True), dtype)
+    ut = dev(u0, dtype)
+    dt_dev = gg.cfl_dt(ut, 0.3)
+    assert dt_dev.item() == timestep.cfl_dt(og, u0, 0.3)          # bit for bit
+    dt0 = dt_dev.item()
+    gg.step(ut, dt_dev=dt_dev, next_dt_dev=dt_dev, cfl=0.3)     # adaptive, all on the device
+    u1 = host(ut)
+    assert rel(u1, timestep.rk4_step(og, u0, dt0)) <= TOL[dtype]
+    assert dt_dev.item() == timestep.cfl_dt(og, u1, 0.3)          # next dt from u_{n+1}, bit for bit
+
+
+def test_taylor_green_100_steps_fp64():
+    """Config: 2-D TGV 64^2 FP64, dt = 0.01, 100 steps: <= 1e-10 against the oracle."""
+    n, nu, dt = 64, 0.01, 0.01
+    faces = inputs.periodic_box(n, 2)
+    og = OGrid(faces, ["periodic"] * 2, nu)
+    gg = Grid(faces, ["periodic"] * 2, nu, dtype=torch.float64)
+    u0 = inputs.taylor_green_2d(faces)
+    ut = dev(u0, torch.float64)
+    for _ in range(100):
+        gg.step(ut, dt=dt)
+    ref = timestep.integrate(og, u0, dt, 100)
+    assert rel(host(ut), ref) <= 1e-10
+    exact = inputs.taylor_green_2d(faces, t=1.0, nu=nu)
+    assert rel(host(ut), exact) < 2e-3       # O(D^2) spatial error
+
+
+def test_random_3d_100_steps_fp64():
+    og, gg = grids("p3tiny", torch.float64)
+    u0 = rand_u(og, 6, project=True)
+    dt = 0.3 * timestep.cfl_dt(og, u0, 0.3)
+    ut = dev(u0, torch.float64)
+    for _ in range(100):
+        gg.step(ut, dt=dt)
+    ref = timestep.integrate(og, u0, dt, 100)
+    assert rel(host(ut), ref) <= 1e-10
+
+
+# ------------------------------------------------------------------ diagnostics, failure paths
+@pytest.mark.parametrize("name", ["p3", "c3"])
+def test_diag(name):
+    og, gg = grids(name, torch.float64)
+    u = rand_u(og, 7)
+    d = gg.diag(dev(u, torch.float64))
+    assert abs(d["ke"] - diagnostics.kinetic_energy(og, u)) <= 1e-12 * diagnostics.kinetic_energy(og, u)
+    assert abs(d["max_div"] - np.max(np.abs(op.divergence(og, u)))) <= 1e-12 * d["max_div"]
+    assert d["max_u_over_h"] == timestep.max_u_over_h(og, u)
+    assert d["nonfinite"] == 0
+
+
+def test_nonfinite_input_is_reported():
+    """Host-side fault injection: a NaN in the input sets the device error flag."""
+    og, gg = grids("p3tiny", torch.float64)
+    u = rand_u(og, 8, project=True)
+    u[0, 1, 2, 3] = np.nan
+    ut = dev(u, torch.float64)
+    gg.step(ut, dt=1e-3)
+    with pytest.raises(InsError) as e:
+        gg.check_finite()
+    assert e.value.status == INS_ERR_NONFINITE
+    gg.check_finite()          # the flag was cleared
+    with pytest.raises(InsError):
+        gg.diag(ut)
+
+
+def test_step_is_deterministic():
+    og, gg = grids("p3", torch.float64)
+    u0 = rand_u(og, 10, project=True)
+    a = dev(u0, torch.float64)
+    b = dev(u0, torch.float64)
+    for t in (a, b):
+        gg.step(t, dt=1e-2)
+    assert torch.equal(a, b)
+
+
+def test_bad_tensor_arguments():
+    og, gg = grids("p3tiny", torch.float64)
+    with pytest.raises(ValueError):
+        gg.rhs(torch.zeros((3, 4, 4, 4), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        gg.rhs(gg.new_velocity().float())
