@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""RK4-step throughput of the staggered-grid Navier-Stokes solver on one B300 per rank.
+
+Workload: 3-D decaying isotropic turbulence on a 256^3 periodic MAC grid on
+[0, 2 pi]^3, nu = 1/1600, seeded random Fourier velocity with
+E(k) ~ k^4 exp(-2 (k/4)^2), projected divergence free and scaled to unit
+kinetic energy; classic RK4 with a projection every stage and an adaptive
+CFL 0.3 time step computed on the device. FP64 and FP32 run side by side;
+the headline value is the FP64 one, the FP32 run is reported under "fp32".
+
+A step = one full RK4 step (4 x [F + divergence, FFT Poisson solve,
+projection + RK update]) plus the CFL reduction for the next step.
+Metric: cell-updates/s = cells * steps / seconds (whole job over all ranks).
+
+Timing: W untimed warm-up steps, then K steps between CUDA events on the
+solver's stream, bracketed by a barrier and a device synchronize; the field
+(402 MB FP64, 201 MB FP32) is larger than the 126 MB L2, so no L2 flush is
+added. Multi-GPU: independent replicas (one trajectory per rank, seed = rank),
+no data-path collective; the max time over ranks is used.
+
+--impl reference times the FP64 CPU oracle on this host instead (a bounded
+sample: one RK4 step per timed step at 128^3 of the same workload).
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RK-step cell-updates/s FP64 and FP32 at 256^3 (% of HBM peak); adjoint/forward ratio"
+UNIT = "cell-updates/s"
+NU = 1.0 / 1600.0
+CFL = 0.3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtypes", default="f64,f32")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ byte/op model
+def kernel_model(name, n, s, launches_by_stage=None):
+    """Algorithmic bytes and FP64-pipe operations per launch of each kernel family.
+
+    N cells, spec = (n/2+1) n^2 complex values of 2 s bytes; s = value size.
+    rhs_div: reads u (3N), writes F (3N) and r (N); 111 ops/cell for F + 6 for D F.
+    fft_*:   each pass reads and writes its data once.
+    rk_update: 13 / 16 / 16 / 13 values per cell for stages 1-4 (mean 14.5).
+    """
+    N = n ** 3
+    spec = (n // 2 + 1) * n * n
+    if name == "rhs_div":
+        return 7 * N * s, 117 * N
+    if name == "fft_x_r2c" or name == "fft_x_c2r":
+        return N * s + spec * 2 * s, None
+    if name == "fft_strided":
+        return 2 * spec * 2 * s, None
+    if name == "rk_update":
+        return 14.5 * N * s, None
+    return None, None
+
+
+def step_model_bytes(n, s):
+    """Model bytes of one RK4 step with F stored: 126 values per cell."""
+    return 126 * n ** 3 * s
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2604_18536_b300 import inputs
+    from paper_2604_18536_b300.solver import Grid, measure_fma_rate
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    n = args.n
+    N = n ** 3
+    faces = inputs.periodic_box(n, 3)
+    raw = inputs.spectrum_velocity_raw(n, 3, seed=args.seed + rank, k0=4.0)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    fp64_flops = measure_fma_rate(torch.float64)
+    fp64_ops_peak = fp64_flops / 2.0          # one FP64 add/mul/fma per pipe slot
+    results = {}
+    for tag in args.dtypes.split(","):
+        dtype = torch.float64 if tag == "f64" else torch.float32
+        s = 8 if tag == "f64" else 4
+        g = Grid(faces, ["periodic"] * 3, NU, dtype=dtype)
+        stream = torch.cuda.current_stream()
+        u = torch.tensor(raw, dtype=dtype, device="cuda")
+        g.project(u, out=u)
+        ke = g.diag(u)["ke"]
+        u.mul_(1.0 / math.sqrt(ke))      # unit kinetic energy (initial-condition setup, untimed)
+        dt = g.cfl_dt(u, CFL)
+        for _ in range(args.warmup):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        time.sleep(0.3)
+        g.profile(True)
+        l0 = g.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = g.launch_count() - l0
+        prof = g.profile_read()
+        g.profile(False)
+        clocks = clk.stop()
+        barrier()
+        ms_max = max_over_ranks(ms)
+        diag = g.diag(u)
+        # roofline of the dominant kernel (largest share of event-timed time)
+        tot = sum(v[1] for v in prof.values())
+        dom = max(prof.items(), key=lambda kv: kv[1][1])
+        dname, (dl, dms) = dom
+        b, ops = kernel_model(dname, n, s)
+        avg_s = dms / dl / 1e3
+        if tag == "f64" and ops is not None:
+            roof = {"bound": "alu", "kernel": dname, "achieved": ops / avg_s / 1e9, "peak": fp64_ops_peak / 1e9,
+                    "unit": "Gop/s (FP64 pipe ops)", "frac": ops / avg_s / fp64_ops_peak, "traffic": None,
+                    "peak_source": "measured live: dependent-FMA kernel, %.3f TFLOP/s / 2" % (fp64_flops / 1e12),
+                    "hbm_frac_of_kernel": (b / avg_s / 1e9) / hbm_peak}
+        else:
+            roof = {"bound": "hbm", "kernel": dname, "achieved": b / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": (b / avg_s / 1e9) / hbm_peak, "traffic": None,
+                    "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % hbm_src}
+        kernels = {k: {"launches": v[0], "total_ms": round(v[1], 4), "share": round(v[1] / tot, 4),
+                       "avg_us": round(v[1] / v[0] * 1e3, 2)} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+        step_s = ms_max / args.steps / 1e3
+        value = N * world / step_s
+        res = {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roof, "kernels": kernels,
+               "gpu_launches": launches, "clocks": clocks,
+               "step_hbm_frac": step_model_bytes(n, s) / step_s / 1e9 / hbm_peak,
+               "final_ke": diag["ke"], "final_max_div": diag["max_div"], "workspace_bytes": g.workspace_bytes()}
+        # end to end through the public API with host buffers (pinned), copies inside the timed region
+        if not args.no_e2e:
+            uh = u.detach().cpu().pin_memory()
+            ksteps = max(1, min(args.steps, 5))
+            barrier()
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(ksteps):
+                u.copy_(uh, non_blocking=True)
+                g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+                uh.copy_(u, non_blocking=True)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            ems = max_over_ranks(f0.elapsed_time(f1))
+            res["e2e"] = {"value": N * world / (ems / ksteps / 1e3), "unit": UNIT,
+                          "h2d_bytes_per_step": 3 * N * s, "d2h_bytes_per_step": 3 * N * s, "steps": ksteps}
+        results[tag] = res
+        g.close()
+        del u
+        torch.cuda.empty_cache()
+
+    if rank == 0:
+        prim = results.get("f64") or next(iter(results.values()))
+        line = {
+            "metric": METRIC, "value": prim["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": prim["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if "f64" in results else "f32",
+            "data": "synthetic (seeded random Fourier velocity, E(k)~k^4 exp(-2(k/4)^2), projected, unit KE)",
+            "config": {"workload": "3-D decaying isotropic turbulence, 256^3 periodic MAC grid, nu=1/1600, "
+                                   "RK4 + per-stage projection, CFL 0.3 (device-side adaptive dt)",
+                       "n": n, "cells": N, "global_batch": world, "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": prim["roofline"], "e2e": prim.get("e2e"), "gpu_launches": prim["gpu_launches"],
+            "clocks": prim["clocks"], "step_hbm_frac": prim["step_hbm_frac"], "kernels": prim["kernels"],
+            "adjoint_forward_ratio": None,
+        }
+        if "f32" in results and "f64" in results:
+            f = results["f32"]
+            line["fp32"] = {k: f[k] for k in ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
+                                               "step_hbm_frac", "kernels", "clocks") if k in f}
+            line["fp32"]["speedup_vs_fp64"] = f["value"] / prim["value"]
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(steps=1)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ oracle on the host
+def cpu_baseline(steps=1, n=128, seed=0):
+    """FP64 numpy oracle, as it stands, on a bounded sample: RK4 steps of the same workload at 128^3."""
+    from oracle.grid import Grid as OGrid
+    from oracle import poisson, timestep, diagnostics
+    from paper_2604_18536_b300 import inputs
+    faces = inputs.periodic_box(n, 3)
+    og = OGrid(faces, ["periodic"] * 3, NU)
+    u, _ = poisson.project(og, inputs.spectrum_velocity_raw(n, 3, seed=seed, k0=4.0))
+    u = u / math.sqrt(diagnostics.kinetic_energy(og, u))
+    dt = timestep.cfl_dt(og, u, CFL)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = timestep.rk4_step(og, u, dt)
+        dt = timestep.cfl_dt(og, u, CFL)
+    sec = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d RK4 step(s) + CFL of the same workload at %d^3, FP64 numpy (single-threaded), %.1f s"
+                      % (steps, n, sec)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = 128
+    from oracle.grid import Grid as OGrid
+    from oracle import poisson, timestep, diagnostics
+    from paper_2604_18536_b300 import inputs
+    faces = inputs.periodic_box(n, 3)
+    og = OGrid(faces, ["periodic"] * 3, NU)
+    u, _ = poisson.project(og, inputs.spectrum_velocity_raw(n, 3, seed=args.seed, k0=4.0))
+    u = u / math.sqrt(diagnostics.kinetic_energy(og, u))
+    dt = timestep.cfl_dt(og, u, CFL)
+    for _ in range(args.warmup):
+        u = timestep.rk4_step(og, u, dt)
+        dt = timestep.cfl_dt(og, u, CFL)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = timestep.rk4_step(og, u, dt)
+        dt = timestep.cfl_dt(og, u, CFL)
+    sec = time.perf_counter() - t0
+    value = n ** 3 * args.steps / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random Fourier velocity)",
+            "config": {"workload": "3-D decaying isotropic turbulence, nu=1/1600, RK4 + per-stage projection, "
+                                   "CFL 0.3; bounded CPU sample at 128^3 of the 256^3 workload", "n": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d RK4 steps at 128^3, FP64 numpy oracle" % args.steps},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -139,6 +139,33 @@ ins_status ins_diag(ins_grid* g, const void* u, double out[4]);
  * INS_ERR_NONFINITE if a step produced a NaN/Inf since the last check. */
 ins_status ins_check_finite(ins_grid* g);
 
+/* ---------------------------------------------------------------- measurement
+ * Tracing support (the paper describes none; these calls serve benchmarking). */
+
+/* Number of kernels this grid has launched since creation (every call above
+ * that launches work counts each kernel once). */
+ins_status ins_launch_count(const ins_grid* g, unsigned long long* n);
+
+/* Per-kernel timing with CUDA events recorded on the grid's stream around every
+ * launch (off by default). Enabling creates an event pool of 8192 launches;
+ * read the profile before it fills. Enabling again clears pending records. */
+ins_status ins_profile_enable(ins_grid* g, int on);
+
+typedef struct {
+    char name[32];        /* kernel family, e.g. "rhs_div", "fft_strided"     */
+    long long launches;   /* launches recorded since the last read              */
+    double total_ms;      /* sum of their event-measured durations             */
+} ins_kernel_stat;
+
+/* Synchronises the stream, fills up to cap entries, sets *n_out, and clears the
+ * records. INS_ERR_ARG if launches were dropped because the pool was full. */
+ins_status ins_profile_read(ins_grid* g, ins_kernel_stat* out, int cap, int* n_out);
+
+/* Measures the device's dependent-FMA throughput for dtype (INS_F32/INS_F64)
+ * with a ~0.1 s kernel on stream, in FLOP/s (one FMA = 2 FLOP). Allocates and
+ * frees a small scratch buffer; synchronous. */
+ins_status ins_measure_fma_rate(int dtype, void* stream, double* flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,10 @@ class GridDesc(_c.Structure):
     ]
 
 
+class KernelStat(_c.Structure):
+    _fields_ = [("name", _c.c_char * 32), ("launches", _c.c_longlong), ("total_ms", _c.c_double)]
+
+
 SIGNATURES = {
     "ins_last_error": (_c.c_char_p, []),
     "ins_version": (_c.c_char_p, []),
@@ -57,6 +61,10 @@ SIGNATURES = {
     "ins_cfl_dt": (_c.c_int, [_vp, _vp, _c.c_double, _vp]),
     "ins_diag": (_c.c_int, [_vp, _vp, _dp]),
     "ins_check_finite": (_c.c_int, [_vp]),
+    "ins_launch_count": (_c.c_int, [_vp, _c.POINTER(_c.c_ulonglong)]),
+    "ins_profile_enable": (_c.c_int, [_vp, _c.c_int]),
+    "ins_profile_read": (_c.c_int, [_vp, _c.POINTER(KernelStat), _c.c_int, _c.POINTER(_c.c_int)]),
+    "ins_measure_fma_rate": (_c.c_int, [_c.c_int, _vp, _dp]),
 }
 
 _LIB = None

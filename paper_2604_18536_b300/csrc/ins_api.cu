@@ -109,6 +109,14 @@ struct ins_grid {
     unsigned long long* diag_max = nullptr; // [2]
     int lg_tw_x = 0, lg_tw_y = 0, lg_tw_z = 0;
     int kchunk = 32;
+    // launch accounting and opt-in per-kernel CUDA-event timing
+    unsigned long long launches = 0;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    long long prof_dropped = 0;
+    std::vector<std::string> names;
+    std::vector<int> rec_name;   // per recorded launch: name id (events 2r, 2r+1)
 };
 
 namespace {
@@ -140,6 +148,38 @@ FftLine<T> make_line(const ins_grid* g, int a) {
     return pl;
 }
 
+int prof_begin(ins_grid* g, const char* name) {
+    ++g->launches;
+    if (!g->prof) return -1;
+    if (g->ev_used + 2 > g->ev.size()) {
+        ++g->prof_dropped;
+        return -1;
+    }
+    int id = -1;
+    for (size_t i = 0; i < g->names.size(); ++i)
+        if (g->names[i] == name) id = (int)i;
+    if (id < 0) {
+        g->names.push_back(name);
+        id = (int)g->names.size() - 1;
+    }
+    const int r = (int)g->rec_name.size();
+    g->rec_name.push_back(id);
+    cudaEventRecord(g->ev[g->ev_used], g->stream);
+    g->ev_used += 2;
+    return r;
+}
+
+void prof_end(ins_grid* g, int r) { cudaEventRecord(g->ev[2 * (size_t)r + 1], g->stream); }
+
+// Launch a kernel with launch accounting, optional event timing and an error check.
+#define KLAUNCH(g, name, ...)                    \
+    do {                                         \
+        const int pr_ = prof_begin((g), (name)); \
+        __VA_ARGS__;                             \
+        if (pr_ >= 0) prof_end((g), pr_);        \
+        INS_LAUNCHED(name);                      \
+    } while (0)
+
 template <typename T>
 size_t fft_smem(int L, int lgtw) {
     return 2ull * L * ((1 << lgtw) + 1) * sizeof(cplx<T>);
@@ -164,8 +204,7 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
         const int lg = g->lg_tw_x;
         const long pairs = (lines + 1) / 2;
         const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);
-        k_fft_x_r2c<T><<<blocks, FFT_THREADS, fft_smem<T>(nx, lg), st>>>(lx, r, S, (int)lines, nxh, lg);
-        INS_LAUNCHED("fft x r2c");
+        KLAUNCH(g, "fft_x_r2c", k_fft_x_r2c<T><<<blocks, FFT_THREADS, fft_smem<T>(nx, lg), st>>>(lx, r, S, (int)lines, nxh, lg));
     }
     auto strided = [&](int a, int mode) -> ins_status {
         FftLine<T> pl = make_line<T>(g, a);
@@ -183,9 +222,8 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
             lstride = (long)ny * nxh;
         }
         const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
-        k_fft_strided<T><<<blocks, FFT_THREADS, fft_smem<T>(pl.L, lg), st>>>(
-            pl, S, ncol, cdiv, outer, lstride, mode, reinterpret_cast<const T*>(g->scale), lg);
-        INS_LAUNCHED("fft strided");
+        KLAUNCH(g, "fft_strided", k_fft_strided<T><<<blocks, FFT_THREADS, fft_smem<T>(pl.L, lg), st>>>(
+            pl, S, ncol, cdiv, outer, lstride, mode, reinterpret_cast<const T*>(g->scale), lg));
         return INS_OK;
     };
     ins_status s;
@@ -201,17 +239,15 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
         if (g->dim == 3 && (s = strided(2, 0)) != INS_OK) return s;
         const long ncol = (long)nz * nxh;
         const double norm = 1.0 / ((double)nx * (g->dim == 3 ? nz : 1));
-        k_thomas<T><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(
-            S, g->th_lo, g->th_invm, g->th_cp, reinterpret_cast<cplx<double>*>(g->th_d), nxh, ny, ncol, norm);
-        INS_LAUNCHED("thomas");
+        KLAUNCH(g, "thomas", k_thomas<T><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(
+            S, g->th_lo, g->th_invm, g->th_cp, reinterpret_cast<cplx<double>*>(g->th_d), nxh, ny, ncol, norm));
         if (g->dim == 3 && (s = strided(2, 1)) != INS_OK) return s;
     }
     {
         const int lg = g->lg_tw_x;
         const long pairs = (lines + 1) / 2;
         const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);
-        k_fft_x_c2r<T><<<blocks, FFT_THREADS, fft_smem<T>(nx, lg), st>>>(lx, S, p, (int)lines, nxh, lg);
-        INS_LAUNCHED("fft x c2r");
+        KLAUNCH(g, "fft_x_c2r", k_fft_x_c2r<T><<<blocks, FFT_THREADS, fft_smem<T>(nx, lg), st>>>(lx, S, p, (int)lines, nxh, lg));
     }
     return INS_OK;
 }
@@ -221,8 +257,7 @@ template <typename T, int DIM, bool WALL>
 ins_status launch_rhs_div(ins_grid* g, const T* u, T* F, T* r) {
     dim3 blk(BX, BY, 1);
     dim3 grd((g->nx + BX - 1) / BX, (g->ny + BY - 1) / BY, DIM == 3 ? (g->nz + g->kchunk - 1) / g->kchunk : 1);
-    k_rhs_div<T, DIM, WALL><<<grd, blk, 0, g->stream>>>(make_geo<T>(g), u, F, r, g->kchunk);
-    INS_LAUNCHED("rhs_div");
+    KLAUNCH(g, "rhs_div", k_rhs_div<T, DIM, WALL><<<grd, blk, 0, g->stream>>>(make_geo<T>(g), u, F, r, g->kchunk));
     return INS_OK;
 }
 
@@ -237,24 +272,20 @@ struct Impl {
         if ((s = launch_rhs_div<T, DIM, WALL>(g, u, F, rp)) != INS_OK) return s;
         T* pp = p ? p : rp;
         if ((s = poisson<T>(g, rp, pp)) != INS_OK) return s;
-        k_sub_grad<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, pp, dudt);
-        INS_LAUNCHED("sub_grad");
+        KLAUNCH(g, "sub_grad", k_sub_grad<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, pp, dudt));
         return INS_OK;
     }
     static ins_status project(ins_grid* g, const T* uin, T* uout, T* p) {
         T* rp = reinterpret_cast<T*>(g->rp);
-        k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), uin, rp);
-        INS_LAUNCHED("divergence");
+        KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), uin, rp));
         T* pp = p ? p : rp;
         ins_status s;
         if ((s = poisson<T>(g, rp, pp)) != INS_OK) return s;
-        k_sub_grad<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), uin, pp, uout);
-        INS_LAUNCHED("sub_grad");
+        KLAUNCH(g, "sub_grad", k_sub_grad<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), uin, pp, uout));
         return INS_OK;
     }
     static ins_status divergence(ins_grid* g, const T* u, T* phi) {
-        k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi);
-        INS_LAUNCHED("divergence");
+        KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi));
         return INS_OK;
     }
     static ins_status step(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
@@ -277,14 +308,12 @@ struct Impl {
             ra.stage = st;
             ra.mx = (st == 3 && next_dt) ? g->cfl_max : nullptr;
             ra.err_flag = g->err_flag;
-            k_rk_update<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, u, acc,
-                                                                                   us, ra);
-            INS_LAUNCHED("rk_update");
+            KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, u, acc,
+                                                                                   us, ra));
         }
         if (next_dt) {
-            k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz, g->dmin2_nu, cfl,
-                                                    next_dt);
-            INS_LAUNCHED("cfl_finalize");
+            KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz, g->dmin2_nu, cfl,
+                                                    next_dt));
         }
         return INS_OK;
     }
@@ -292,20 +321,17 @@ struct Impl {
         // reuse the stage-4 path's reduction: a read-only pass
         INS_CUDA(cudaMemsetAsync(g->diag, 0, 4 * sizeof(double), g->stream));
         INS_CUDA(cudaMemsetAsync(g->diag_max, 0, 2 * sizeof(unsigned long long), g->stream));
-        k_diag<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, g->geo64, g->diag,
-                                                                          g->diag_max);
-        INS_LAUNCHED("diag");
+        KLAUNCH(g, "diag", k_diag<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(
+                               make_geo<T>(g), u, g->geo64, g->diag, g->diag_max));
         // max |u^a|/h_a was reduced into diag_max[1]; finish on the device
-        k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->diag_max + 1, g->one, 1, g->dmin2_nu, cfl, dt_dev);
-        INS_LAUNCHED("cfl_finalize");
+        KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->diag_max + 1, g->one, 1, g->dmin2_nu, cfl, dt_dev));
         return INS_OK;
     }
     static ins_status diag(ins_grid* g, const T* u, double out[4]) {
         INS_CUDA(cudaMemsetAsync(g->diag, 0, 4 * sizeof(double), g->stream));
         INS_CUDA(cudaMemsetAsync(g->diag_max, 0, 2 * sizeof(unsigned long long), g->stream));
-        k_diag<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, g->geo64, g->diag,
-                                                                          g->diag_max);
-        INS_LAUNCHED("diag");
+        KLAUNCH(g, "diag", k_diag<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(
+                               make_geo<T>(g), u, g->geo64, g->diag, g->diag_max));
         double h[4];
         unsigned long long mx[2];
         INS_CUDA(cudaMemcpyAsync(h, g->diag, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
@@ -794,4 +820,106 @@ ins_status ins_check_finite(ins_grid* g) {
     return INS_OK;
 }
 
+ins_status ins_launch_count(const ins_grid* g, unsigned long long* n) {
+    if (!g || !n) return fail(INS_ERR_ARG, "null argument");
+    *n = g->launches;
+    return INS_OK;
+}
+
+ins_status ins_profile_enable(ins_grid* g, int on) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    if (on && g->ev.empty()) {
+        g->ev.resize(16384);
+        for (auto& e : g->ev) INS_CUDA(cudaEventCreate(&e));
+    }
+    g->prof = on != 0;
+    g->ev_used = 0;
+    g->rec_name.clear();
+    g->prof_dropped = 0;
+    return INS_OK;
+}
+
+ins_status ins_profile_read(ins_grid* g, ins_kernel_stat* out, int cap, int* n_out) {
+    g_err.clear();
+    if (!g || !n_out || (cap > 0 && !out)) return fail(INS_ERR_ARG, "null argument");
+    INS_CUDA(cudaStreamSynchronize(g->stream));
+    std::vector<double> tot(g->names.size(), 0.0);
+    std::vector<long long> cnt(g->names.size(), 0);
+    for (size_t r = 0; r < g->rec_name.size(); ++r) {
+        float ms = 0.f;
+        INS_CUDA(cudaEventElapsedTime(&ms, g->ev[2 * r], g->ev[2 * r + 1]));
+        tot[g->rec_name[r]] += ms;
+        cnt[g->rec_name[r]] += 1;
+    }
+    int n = 0;
+    for (size_t i = 0; i < g->names.size() && n < cap; ++i) {
+        if (!cnt[i]) continue;
+        std::memset(out[n].name, 0, sizeof(out[n].name));
+        std::strncpy(out[n].name, g->names[i].c_str(), sizeof(out[n].name) - 1);
+        out[n].launches = cnt[i];
+        out[n].total_ms = tot[i];
+        ++n;
+    }
+    *n_out = n;
+    g->ev_used = 0;
+    g->rec_name.clear();
+    if (g->prof_dropped) {
+        g->prof_dropped = 0;
+        return fail(INS_ERR_ARG, "event pool exhausted: read the profile more often");
+    }
+    return INS_OK;
+}
+
 }  // extern "C"
+
+namespace {
+template <typename T, int CH>
+__global__ void k_fma_rate(T* out, int iters, T a, T b) {
+    T acc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = (T)(threadIdx.x + c);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) acc[c] = fma(acc[c], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) s += acc[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+ins_status fma_rate(void* stream, double* flops) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    INS_CUDA(cudaGetDevice(&dev));
+    INS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256;
+    const int iters = sizeof(T) == 8 ? 4000 : 100000;
+    T* out = nullptr;
+    INS_CUDA(cudaMalloc(&out, (size_t)blocks * threads * sizeof(T)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fma_rate<T, 8><<<blocks, threads, 0, st>>>(out, 64, (T)1.0000001, (T)1e-9);
+    cudaEventRecord(e0, st);
+    k_fma_rate<T, 8><<<blocks, threads, 0, st>>>(out, iters, (T)1.0000001, (T)1e-9);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) return cuda_fail(e, "fma rate");
+    *flops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3);
+    return INS_OK;
+}
+}  // namespace
+
+extern "C" ins_status ins_measure_fma_rate(int dtype, void* stream, double* flops_per_s) {
+    g_err.clear();
+    if (!flops_per_s || (dtype != INS_F32 && dtype != INS_F64)) return fail(INS_ERR_ARG, "bad argument");
+    return dtype == INS_F64 ? fma_rate<double>(stream, flops_per_s) : fma_rate<float>(stream, flops_per_s);
+}

@@ -19,6 +19,17 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def measure_fma_rate(dtype=torch.float64, device=None):
+    """Dependent-FMA throughput of the current device in FLOP/s (ins_measure_fma_rate)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    out = ctypes.c_double()
+    with torch.cuda.device(dev):
+        st = torch.cuda.current_stream(dev).cuda_stream
+        check(lib().ins_measure_fma_rate(_lib.INS_F64 if dtype == torch.float64 else _lib.INS_F32,
+                                         ctypes.c_void_p(st), ctypes.byref(out)), "ins_measure_fma_rate")
+    return out.value
+
+
 class Grid:
     """A staggered grid and its device workspace (``ins_grid_create``).
 
@@ -155,6 +166,24 @@ class Grid:
         if st != _lib.INS_ERR_NONFINITE or raise_nonfinite:
             check(st, "ins_diag")
         return {"ke": out[0], "max_div": out[1], "max_u_over_h": out[2], "nonfinite": int(out[3])}
+
+    # ------------------------------------------------------------ measurement
+    def launch_count(self):
+        n = ctypes.c_ulonglong()
+        check(lib().ins_launch_count(self._h, ctypes.byref(n)), "ins_launch_count")
+        return n.value
+
+    def profile(self, on=True):
+        check(lib().ins_profile_enable(self._h, int(bool(on))), "ins_profile_enable")
+
+    def profile_read(self):
+        """{kernel name: (launches, total_ms)} since the last read (synchronous)."""
+        cap = 64
+        arr = (_lib.KernelStat * cap)()
+        n = ctypes.c_int()
+        self._sync_stream()
+        check(lib().ins_profile_read(self._h, arr, cap, ctypes.byref(n)), "ins_profile_read")
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n.value)}
 
     def check_finite(self):
         self._sync_stream()
