@@ -139,6 +139,28 @@ ins_status ins_diag(ins_grid* g, const void* u, double out[4]);
  * INS_ERR_NONFINITE if a step produced a NaN/Inf since the last check. */
 ins_status ins_check_finite(ins_grid* g);
 
+/* CFL time step without a grid handle and without any device allocation.
+ * The paper has no counterpart: this is a library convenience for callers that
+ * cannot call cudaMalloc (for example code under a memory manager that has
+ * reserved nearly all device memory for its own pool, or a plug-in that must
+ * keep the device footprint fixed); ins_grid_create, and so ins_cfl_dt, needs
+ * cudaMalloc. Result: the same double as ins_cfl_dt on a grid built from *desc
+ * (bit for bit). desc: as for ins_grid_create (only dim, n, bc, face_coords,
+ * dtype and nu are read; n[a] <= 4096 per direction, else INS_ERR_ARG with a
+ * message naming the limit). u: DEVICE velocity field; dt_dev: DEVICE double;
+ * stream: cudaStream_t the work is enqueued on.
+ * Scratch: a static device array of 192 KiB inside the library (per-index
+ * maxima and spacings), held by every GPU that loads the library until the
+ * process exits; nothing is allocated or freed by this call. The first call on
+ * each device looks up that array's device address (cudaGetSymbolAddress);
+ * make this first call before any stream capture. Every call shares the array
+ * and clears what must start at zero, so calls whose work overlaps on the GPU
+ * (other streams, other host threads on the same device) race: serialise them.
+ * The spacings are copied from pageable host memory, so the call waits for the
+ * stream's earlier work before returning. */
+ins_status ins_cfl_dt_noalloc(const ins_grid_desc* desc, const void* u, double cfl, double* dt_dev,
+                              void* stream);
+
 /* ---------------------------------------------------------------- measurement
  * Tracing support (the paper describes none; these calls serve benchmarking). */
 

@@ -65,6 +65,7 @@ SIGNATURES = {
     "ins_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "ins_profile_read": (_c.c_int, [_vp, _c.POINTER(KernelStat), _c.c_int, _c.POINTER(_c.c_int)]),
     "ins_measure_fma_rate": (_c.c_int, [_c.c_int, _vp, _dp]),
+    "ins_cfl_dt_noalloc": (_c.c_int, [_c.POINTER(GridDesc), _vp, _c.c_double, _vp, _vp]),
 }
 
 _LIB = None
