@@ -118,14 +118,14 @@ def kernel_model(name, n, s, launches_by_stage=None):
     """Algorithmic bytes and FP64-pipe operations per launch of each kernel family.
 
     N cells, spec = (n/2+1) n^2 complex values of 2 s bytes; s = value size.
-    rhs_div: reads u (3N), writes F (3N) and r (N); 111 ops/cell for F + 6 for D F.
+    rhs_div: reads u (3N), writes F (3N) and r (N); 78 FP64 ops/cell for F (uniform grid, 26 per component) + 6 for D F.
     fft_*:   each pass reads and writes its data once.
     rk_update: 13 / 16 / 16 / 13 values per cell for stages 1-4 (mean 14.5).
     """
     N = n ** 3
     spec = (n // 2 + 1) * n * n
     if name == "rhs_div":
-        return 7 * N * s, 117 * N
+        return 7 * N * s, 84 * N
     if name == "fft_x_r2c" or name == "fft_x_c2r":
         return N * s + spec * 2 * s, None
     if name == "fft_strided":

@@ -17,7 +17,10 @@
 #include "../../include/ins.h"
 #include "common.cuh"
 #include "fft.cuh"
+#include "fft_reg.cuh"
+#include "rhs.cuh"
 #include "stencil.cuh"
+#include "rk.cuh"
 
 using namespace ins;
 
@@ -88,6 +91,7 @@ struct ins_grid {
     void* base = nullptr;
     size_t bytes = 0;
     void* coef = nullptr;          // T[3][C_COUNT][n_a] (per direction contiguous)
+    void* ycoef = nullptr;         // T[CY_COUNT][ny]: per-row coefficients of a stretched wall direction
     double* geo64 = nullptr;       // h_x h_y h_z | d_x d_y d_z  (nx+ny+nz each)
     double* one = nullptr;         // a device 1.0 (divisor of an already divided maximum)
     void* tw[3] = {nullptr, nullptr, nullptr};
@@ -194,6 +198,54 @@ int choose_lgtw(int L) {
 }
 
 // ------------------------------------------------------------ Poisson solve
+// Register-resident FFT passes for L = R1 R2 in {16, 32, 64, 128, 256}; other lengths use the
+// shared-memory Stockham kernels.
+bool reg_fft_len(int L) { return L == 16 || L == 32 || L == 64 || L == 128 || L == 256; }
+
+template <typename T, int R1, int R2>
+void launch_strided_reg(cudaStream_t st, const cplx<T>* tw, cplx<T>* S, long ncol, long cdiv, long outer,
+                        long lstride, int mode, const T* scale) {
+    using Sh = RegShape<T, R1, R2>;
+    const unsigned blocks = (unsigned)((ncol + Sh::TW - 1) / Sh::TW);
+    k_fft_strided_reg<T, R1, R2><<<blocks, Sh::NT, 0, st>>>(tw, S, ncol, cdiv, outer, lstride, mode, scale);
+}
+
+template <typename T>
+void strided_reg(int L, cudaStream_t st, const cplx<T>* tw, cplx<T>* S, long ncol, long cdiv, long outer,
+                 long lstride, int mode, const T* scale) {
+    switch (L) {
+        case 16: launch_strided_reg<T, 4, 4>(st, tw, S, ncol, cdiv, outer, lstride, mode, scale); break;
+        case 32: launch_strided_reg<T, 8, 4>(st, tw, S, ncol, cdiv, outer, lstride, mode, scale); break;
+        case 64: launch_strided_reg<T, 8, 8>(st, tw, S, ncol, cdiv, outer, lstride, mode, scale); break;
+        case 128: launch_strided_reg<T, 16, 8>(st, tw, S, ncol, cdiv, outer, lstride, mode, scale); break;
+        default: launch_strided_reg<T, 16, 16>(st, tw, S, ncol, cdiv, outer, lstride, mode, scale); break;
+    }
+}
+
+template <typename T, int R1, int R2>
+void launch_x_reg(bool forward, cudaStream_t st, const cplx<T>* tw, const T* in, cplx<T>* S, T* out, int lines,
+                  int nxh) {
+    using Sh = RegShape<T, R1, R2>;
+    const long pairs = (lines + 1) / 2;
+    const unsigned blocks = (unsigned)((pairs + Sh::TW - 1) / Sh::TW);
+    if (forward)
+        k_fft_x_r2c_reg<T, R1, R2><<<blocks, Sh::NT, 0, st>>>(tw, in, S, lines, nxh);
+    else
+        k_fft_x_c2r_reg<T, R1, R2><<<blocks, Sh::NT, 0, st>>>(tw, S, out, lines, nxh);
+}
+
+template <typename T>
+void x_reg(int L, bool forward, cudaStream_t st, const cplx<T>* tw, const T* in, cplx<T>* S, T* out, int lines,
+           int nxh) {
+    switch (L) {
+        case 16: launch_x_reg<T, 4, 4>(forward, st, tw, in, S, out, lines, nxh); break;
+        case 32: launch_x_reg<T, 8, 4>(forward, st, tw, in, S, out, lines, nxh); break;
+        case 64: launch_x_reg<T, 8, 8>(forward, st, tw, in, S, out, lines, nxh); break;
+        case 128: launch_x_reg<T, 16, 8>(forward, st, tw, in, S, out, lines, nxh); break;
+        default: launch_x_reg<T, 16, 16>(forward, st, tw, in, S, out, lines, nxh); break;
+    }
+}
+
 template <typename T>
 ins_status poisson(ins_grid* g, const T* r, T* p) {
     cudaStream_t st = g->stream;
@@ -201,7 +253,9 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
     const long lines = (long)ny * nz;
     cplx<T>* S = reinterpret_cast<cplx<T>*>(g->S);
     FftLine<T> lx = make_line<T>(g, 0);
-    {
+    if (reg_fft_len(nx)) {
+        KLAUNCH(g, "fft_x_r2c", x_reg<T>(nx, true, st, lx.tw, r, S, nullptr, (int)lines, nxh));
+    } else {
         const int lg = g->lg_tw_x;
         const long pairs = (lines + 1) / 2;
         const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);
@@ -221,6 +275,11 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
             cdiv = ncol;
             outer = 0;
             lstride = (long)ny * nxh;
+        }
+        if (reg_fft_len(pl.L)) {
+            KLAUNCH(g, "fft_strided", strided_reg<T>(pl.L, st, pl.tw, S, ncol, cdiv, outer, lstride, mode,
+                                                     reinterpret_cast<const T*>(g->scale)));
+            return INS_OK;
         }
         const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
         KLAUNCH(g, "fft_strided", k_fft_strided<T><<<blocks, FFT_THREADS, fft_smem<T>(pl.L, lg), st>>>(
@@ -244,7 +303,9 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
             S, g->th_lo, g->th_invm, g->th_cp, reinterpret_cast<cplx<double>*>(g->th_d), nxh, ny, ncol, norm));
         if (g->dim == 3 && (s = strided(2, 1)) != INS_OK) return s;
     }
-    {
+    if (reg_fft_len(nx)) {
+        KLAUNCH(g, "fft_x_c2r", x_reg<T>(nx, false, st, lx.tw, nullptr, S, p, (int)lines, nxh));
+    } else {
         const int lg = g->lg_tw_x;
         const long pairs = (lines + 1) / 2;
         const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);
@@ -254,15 +315,49 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
 }
 
 // ------------------------------------------------------------ kernels by config
+template <typename T>
+RhsCoef<T> make_rhs_coef(const ins_grid* g) {
+    RhsCoef<T> c;
+    c.nx = g->nx;
+    c.ny = g->ny;
+    c.nz = g->nz;
+    double D[3];
+    for (int a = 0; a < 3; ++a) {
+        double s = 0.0;
+        for (double w : g->d[a]) s += w;
+        D[a] = s / g->d[a].size();
+    }
+    c.cx = (T)(0.25 / D[0]);
+    c.cy = (T)(0.25 / D[1]);
+    c.cz = (T)(0.25 / D[2]);
+    c.dx = (T)(g->nu / (D[0] * D[0]));
+    c.dy = (T)(g->nu / (D[1] * D[1]));
+    c.dz = (T)(g->nu / (D[2] * D[2]));
+    c.ix = (T)(1.0 / D[0]);
+    c.iy = (T)(1.0 / D[1]);
+    c.iz = (T)(1.0 / D[2]);
+    c.fx = (T)g->force[0];
+    c.fy = (T)g->force[1];
+    c.fz = (T)g->force[2];
+    c.yc = reinterpret_cast<const T*>(g->ycoef);
+    return c;
+}
+
 template <typename T, int DIM, bool WALL>
 ins_status launch_rhs_div(ins_grid* g, const T* u, T* F, T* r) {
-    dim3 blk(BX, BY, 1);
-    dim3 grd((g->nx + BX - 1) / BX, (g->ny + BY - 1) / BY, DIM == 3 ? (g->nz + g->kchunk - 1) / g->kchunk : 1);
-    KLAUNCH(g, "rhs_div", k_rhs_div<T, DIM, WALL><<<grd, blk, 0, g->stream>>>(make_geo<T>(g), u, F, r, g->kchunk));
+    dim3 blk(RBX, RBY, 1);
+    dim3 grd((g->nx + RBX - 1) / RBX, (g->ny + RBY - 1) / RBY, DIM == 3 ? (g->nz + g->kchunk - 1) / g->kchunk : 1);
+    KLAUNCH(g, "rhs_div", k_rhs_div<T, DIM, WALL><<<grd, blk, 0, g->stream>>>(make_rhs_coef<T>(g), u, F, r, g->kchunk));
     return INS_OK;
 }
 
 dim3 cell_grid(const ins_grid* g) { return dim3((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz); }
+
+// The vector RK update needs whole 16-byte vectors per row and an aligned caller field.
+template <typename T>
+bool rk_vec_ok(const ins_grid* g, const void* u) {
+    return g->nx % VecT<T>::N == 0 && reinterpret_cast<uintptr_t>(u) % 16 == 0;
+}
 
 template <typename T, int DIM, bool WALL>
 struct Impl {
@@ -309,8 +404,25 @@ struct Impl {
             ra.stage = st;
             ra.mx = (st == 3 && next_dt) ? g->cfl_max : nullptr;
             ra.err_flag = g->err_flag;
-            KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, u, acc,
-                                                                                   us, ra));
+            if (rk_vec_ok<T>(g, u)) {
+                constexpr int VEC = VecT<T>::N;
+                RkCoef<T> rc;
+                rc.nx = g->nx;
+                rc.ny = g->ny;
+                rc.nz = g->nz;
+                rc.ihx = (T)(1.0 / g->h[0][0]);
+                rc.ihz = (T)(1.0 / g->h[2][0]);
+                rc.ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
+                const int bx = (g->nx / VEC + 31) / 32, by = (g->ny + 7) / 8;
+                int kc = (int)(((long)bx * by * g->nz) / 2368);
+                kc = kc < 1 ? 1 : (kc > g->nz ? g->nz : kc);
+                const dim3 grd(bx, by, (g->nz + kc - 1) / kc);
+                KLAUNCH(g, "rk_update", k_rk_update_vec<T, DIM, WALL><<<grd, dim3(32, 8), 0, g->stream>>>(
+                                            rc, F, rp, u, acc, us, ra, kc));
+            } else {
+                KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, u, acc,
+                                                                                       us, ra));
+            }
         }
         if (next_dt) {
             KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz, g->dmin2_nu, cfl,
@@ -527,6 +639,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
                                              o_us, o_rp, o_S, o_cfl, o_err, o_diag, o_dmax;
     const size_t nsum = (size_t)g->nx + g->ny + g->nz;
     o_coef = off; off += al((size_t)C_COUNT * nsum * ts);
+    const size_t o_ycoef = off; off += al((size_t)CY_COUNT * g->ny * ts);
     o_geo = off; off += al(2 * nsum * 8);
     o_one = off; off += al(8);
     for (int a = 0; a < 3; ++a) {
@@ -560,6 +673,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     }
     char* b = reinterpret_cast<char*>(g->base);
     g->coef = b + o_coef;
+    g->ycoef = b + o_ycoef;
     g->geo64 = reinterpret_cast<double*>(b + o_geo);
     g->one = reinterpret_cast<double*>(b + o_one);
     for (int a = 0; a < 3; ++a) g->tw[a] = b + o_tw[a];
@@ -595,6 +709,32 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
         std::vector<float> c;
         fill_coefs<float>(g, c);
         ok &= up(g->coef, c.data(), c.size() * 4);
+    }
+    {
+        // per-row coefficients of y (used by k_rhs_div when y is a wall direction)
+        const int ny = g->ny;
+        const auto& d = g->d[1];
+        const auto& h = g->h[1];
+        std::vector<double> yc((size_t)CY_COUNT * ny);
+        for (int j = 0; j < ny; ++j) {
+            const double dn = (j + 1 < ny) ? d[j + 1] : (wall_y ? d[ny - 1] : d[0]);
+            const double hp = (j > 0) ? h[j - 1] : g->hlo[1];
+            yc[CY_F * ny + j] = 0.25 / d[j];
+            yc[CY_S * ny + j] = 0.25 / h[j];
+            yc[CY_WL * ny + j] = d[j] / (d[j] + dn);
+            yc[CY_WR * ny + j] = dn / (d[j] + dn);
+            yc[CY_AP * ny + j] = g->nu / (dn * h[j]);
+            yc[CY_AM * ny + j] = g->nu / (d[j] * h[j]);
+            yc[CY_BP * ny + j] = g->nu / (h[j] * d[j]);
+            yc[CY_BM * ny + j] = g->nu / (hp * d[j]);
+            yc[CY_I * ny + j] = 1.0 / d[j];
+        }
+        if (D.dtype == INS_F64) {
+            ok &= up(g->ycoef, yc.data(), yc.size() * 8);
+        } else {
+            std::vector<float> yf(yc.begin(), yc.end());
+            ok &= up(g->ycoef, yf.data(), yf.size() * 4);
+        }
     }
     {
         std::vector<double> geo(2 * nsum);

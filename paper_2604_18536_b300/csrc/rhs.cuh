@@ -1,0 +1,356 @@
+// F(u) = C(u) + nu diffusion(u) + f on every velocity face and r = D F(u) in
+// every cell (paper App. A discrete momentum equation, App. B kernels), one
+// pass over u.
+//
+// Layout of the work: a CTA of 32 x 8 threads owns a 32 x 8 column of cells
+// and marches up z through a chunk of planes. Three planes (k-1, k, k+1) of
+// every velocity component, with a halo of 2 cells below and 1 above in x and
+// y, sit in shared memory as a ring; plane k+2 is loaded into registers while
+// plane k is computed and committed to the ring afterwards. Each thread
+// computes F at its own three faces. The divergence also needs F^x one cell to
+// the left of the tile and F^y one row below it: warp 1 (8 lanes) and warp 0
+// compute those, so only two of the eight warps do one extra evaluation, and
+// F^z one plane below is carried in a register from the previous plane.
+//
+// Coefficients: x and z are periodic and uniform, so their coefficients are
+// kernel parameters; y is uniform too unless it is a wall direction, where the
+// per-row coefficients of the stretched grid are read once per thread (they
+// do not change along the z march). With uniform interpolation directions the
+// interpolation weights 1/2 are folded into the coefficients:
+//   self term   b == a: -((u_i + u_{i+1})^2 - (u_{i-1} + u_i)^2) * 0.25/h_a
+//   cross term  b != a: -(V+ T+ - V- T-) * 0.5/d_b with V = w_l u^b + w_r u^b_{+a}
+//               (volume weights along a) and T = sums of the transported u^a;
+//               when a is uniform V+ = u^b + u^b_{+a} and the factor is 0.25/d_b.
+// Boundary rules are applied while loading: periodic wrap, or at a no-slip
+// wall in y the odd ghost for u^x, u^z and 0 for u^y (paper Sec. 2.4).
+#pragma once
+
+#include "common.cuh"
+
+namespace ins {
+
+constexpr int RBX = 32;
+constexpr int RBY = 8;
+constexpr int RSX = RBX + 3;   // plane covers i0-2 .. i0+RBX
+constexpr int RSY = RBY + 3;   //              j0-2 .. j0+RBY
+constexpr int RSPL = RSX * RSY;
+constexpr int RNT = RBX * RBY;
+constexpr int RPF = (RSPL + RNT - 1) / RNT;   // plane elements per thread
+
+// per-row y coefficients of a wall (stretched) direction, arrays over j
+enum YCoef { CY_F = 0, CY_S, CY_WL, CY_WR, CY_AP, CY_AM, CY_BP, CY_BM, CY_I, CY_COUNT };
+//  CY_F  0.25/d_y[j]          cross terms with flux direction y (uniform interpolation direction)
+//  CY_S  0.25/h_y[j]          self term of u^y
+//  CY_WL, CY_WR               volume weights d_j/(d_j+d_{j+1}), d_{j+1}/(d_j+d_{j+1})
+//  CY_AP nu/(d_{j+1} h_j), CY_AM nu/(d_j h_j)        diffusion of u^y along y
+//  CY_BP nu/(h_j d_j),     CY_BM nu/(h_{j-1} d_j)    diffusion of u^x, u^z along y
+//  CY_I  1/d_y[j]                                    divergence
+
+template <typename T>
+struct RhsCoef {
+    int nx, ny, nz;
+    T cx, cy, cz;   // 0.25/D
+    T dx, dy, dz;   // nu/D^2
+    T ix, iy, iz;   // 1/D
+    T fx, fy, fz;   // body force
+    const T* yc;    // wall: CY_COUNT arrays of ny values
+};
+
+template <typename T>
+struct YRow {
+    T f, s, wl, wr, ap, am, bp, bm, i;
+};
+
+template <typename T, bool WALL>
+__device__ __forceinline__ YRow<T> yrow(const RhsCoef<T>& c, int j) {
+    YRow<T> r;
+    if constexpr (WALL) {
+        const T* y = c.yc;
+        const int n = c.ny;
+        r.f = __ldg(y + CY_F * n + j);
+        r.s = __ldg(y + CY_S * n + j);
+        r.wl = __ldg(y + CY_WL * n + j);
+        r.wr = __ldg(y + CY_WR * n + j);
+        r.ap = __ldg(y + CY_AP * n + j);
+        r.am = __ldg(y + CY_AM * n + j);
+        r.bp = __ldg(y + CY_BP * n + j);
+        r.bm = __ldg(y + CY_BM * n + j);
+        r.i = __ldg(y + CY_I * n + j);
+    } else {
+        r.f = c.cy;
+        r.s = c.cy;
+        r.wl = r.wr = (T)0.5;
+        r.ap = r.am = r.bp = r.bm = c.dy;
+        r.i = c.iy;
+    }
+    return r;
+}
+
+// Plane arrays in shared memory: P[comp][lj * RSX + li].
+template <typename T>
+using Plane = T (*)[RSPL];
+template <typename T>
+using CPlane = const T (*)[RSPL];
+
+template <typename T, int DIM, bool WALL>
+__device__ __forceinline__ T eval_Fx(const RhsCoef<T>& c, const YRow<T>& y, CPlane<T> m, CPlane<T> o, CPlane<T> p,
+                                     int c0) {
+    const T uc = o[0][c0], ue = o[0][c0 + 1], uw = o[0][c0 - 1], un = o[0][c0 + RSX], us = o[0][c0 - RSX];
+    const T s1 = uc + ue, s2 = uw + uc;
+    const T X = fma(s1, s1, -s2 * s2);
+    // u^y interpolated along x (uniform): weights folded into y.f
+    const T vp = o[1][c0] + o[1][c0 + 1], vm = o[1][c0 - RSX] + o[1][c0 + 1 - RSX];
+    const T Y = fma(vp, uc + un, -vm * (us + uc));
+    T acc = fma(c.dx, ue + uw, c.fx);
+    acc = fma(y.bp, un, acc);
+    acc = fma(y.bm, us, acc);
+    T dsum = (T)2 * c.dx + y.bp + y.bm;
+    if constexpr (DIM == 3) {
+        const T ut = p[0][c0], ub = m[0][c0];
+        const T wp = o[2][c0] + o[2][c0 + 1], wm = m[2][c0] + m[2][c0 + 1];
+        const T Z = fma(wp, uc + ut, -wm * (ub + uc));
+        acc = fma(c.dz, ut + ub, acc);
+        dsum += (T)2 * c.dz;
+        acc = fma(-c.cz, Z, acc);
+    }
+    acc = fma(-dsum, uc, acc);
+    acc = fma(-c.cx, X, acc);
+    return fma(-y.f, Y, acc);
+}
+
+template <typename T, int DIM, bool WALL>
+__device__ __forceinline__ T eval_Fy(const RhsCoef<T>& c, const YRow<T>& y, CPlane<T> m, CPlane<T> o, CPlane<T> p,
+                                     int c0) {
+    const T uc = o[1][c0], un = o[1][c0 + RSX], us = o[1][c0 - RSX], ue = o[1][c0 + 1], uw = o[1][c0 - 1];
+    const T s1 = uc + un, s2 = us + uc;
+    const T Ys = fma(s1, s1, -s2 * s2);
+    T vp, vm, cxf;
+    if constexpr (WALL) {   // u^x interpolated along the stretched y with volume weights
+        vp = fma(y.wl, o[0][c0], y.wr * o[0][c0 + RSX]);
+        vm = fma(y.wl, o[0][c0 - 1], y.wr * o[0][c0 - 1 + RSX]);
+        cxf = (T)2 * c.cx;
+    } else {
+        vp = o[0][c0] + o[0][c0 + RSX];
+        vm = o[0][c0 - 1] + o[0][c0 - 1 + RSX];
+        cxf = c.cx;
+    }
+    const T X = fma(vp, uc + ue, -vm * (uw + uc));
+    T acc = fma(c.dx, ue + uw, c.fy);
+    acc = fma(y.ap, un, acc);
+    acc = fma(y.am, us, acc);
+    T dsum = (T)2 * c.dx + y.ap + y.am;
+    if constexpr (DIM == 3) {
+        const T ut = p[1][c0], ub = m[1][c0];
+        T wp, wm, czf;
+        if constexpr (WALL) {
+            wp = fma(y.wl, o[2][c0], y.wr * o[2][c0 + RSX]);
+            wm = fma(y.wl, m[2][c0], y.wr * m[2][c0 + RSX]);
+            czf = (T)2 * c.cz;
+        } else {
+            wp = o[2][c0] + o[2][c0 + RSX];
+            wm = m[2][c0] + m[2][c0 + RSX];
+            czf = c.cz;
+        }
+        const T Z = fma(wp, uc + ut, -wm * (ub + uc));
+        acc = fma(c.dz, ut + ub, acc);
+        dsum += (T)2 * c.dz;
+        acc = fma(-czf, Z, acc);
+    }
+    acc = fma(-dsum, uc, acc);
+    acc = fma(-y.s, Ys, acc);
+    return fma(-cxf, X, acc);
+}
+
+template <typename T, bool WALL>
+__device__ __forceinline__ T eval_Fz(const RhsCoef<T>& c, const YRow<T>& y, CPlane<T> m, CPlane<T> o, CPlane<T> p,
+                                     int c0) {
+    const T uc = o[2][c0], ut = p[2][c0], ub = m[2][c0], ue = o[2][c0 + 1], uw = o[2][c0 - 1], un = o[2][c0 + RSX],
+            us = o[2][c0 - RSX];
+    const T s1 = uc + ut, s2 = ub + uc;
+    const T Zs = fma(s1, s1, -s2 * s2);
+    const T vp = o[0][c0] + p[0][c0], vm = o[0][c0 - 1] + p[0][c0 - 1];
+    const T X = fma(vp, uc + ue, -vm * (uw + uc));
+    const T wp = o[1][c0] + p[1][c0], wm = o[1][c0 - RSX] + p[1][c0 - RSX];
+    const T Y = fma(wp, uc + un, -wm * (us + uc));
+    T acc = fma(c.dx, ue + uw, c.fz);
+    acc = fma(c.dz, ut + ub, acc);
+    acc = fma(y.bp, un, acc);
+    acc = fma(y.bm, us, acc);
+    acc = fma(-((T)2 * (c.dx + c.dz) + y.bp + y.bm), uc, acc);
+    acc = fma(-c.cz, Zs, acc);
+    acc = fma(-c.cx, X, acc);
+    return fma(-y.f, Y, acc);
+}
+
+// Where each thread's share of a plane comes from (the same for every plane).
+template <bool WALL>
+struct PlaneMap {
+    int off[RPF];       // in-plane offset (row * nx + column), -1 when the thread has no element
+    bool ghost[RPF];    // wall ghost: negate u^x, u^z; u^y is 0
+};
+
+template <bool WALL>
+__device__ __forceinline__ PlaneMap<WALL> plane_map(int nx, int ny, int i0, int j0) {
+    PlaneMap<WALL> pm;
+    const int tid = threadIdx.x + threadIdx.y * RBX;
+#pragma unroll
+    for (int q = 0; q < RPF; ++q) {
+        const int idx = tid + q * RNT;
+        pm.off[q] = -1;
+        pm.ghost[q] = false;
+        if (idx < RSPL) {
+            const int li = idx % RSX, lj = idx / RSX;
+            int gi = (i0 - 2 + li) % nx;
+            if (gi < 0) gi += nx;
+            int gj = j0 - 2 + lj;
+            if (!WALL) {
+                gj %= ny;
+                if (gj < 0) gj += ny;
+            } else if (gj < 0 || gj >= ny) {
+                int mj = gj < 0 ? -gj - 1 : 2 * ny - 1 - gj;
+                gj = mj < 0 ? 0 : (mj >= ny ? ny - 1 : mj);
+                pm.ghost[q] = true;
+            }
+            pm.off[q] = gj * nx + gi;
+        }
+    }
+    return pm;
+}
+
+template <typename T, int DIM, bool WALL>
+__device__ __forceinline__ void plane_fetch(const PlaneMap<WALL>& pm, const T* __restrict__ u, long N, long base,
+                                            T (&v)[DIM][RPF]) {
+#pragma unroll
+    for (int q = 0; q < RPF; ++q) {
+        if (pm.off[q] >= 0) {
+#pragma unroll
+            for (int cc = 0; cc < DIM; ++cc) {
+                T x = u[cc * N + base + pm.off[q]];
+                if (WALL && pm.ghost[q]) x = (cc == 1) ? (T)0 : -x;
+                v[cc][q] = x;
+            }
+        }
+    }
+}
+
+template <typename T, int DIM, bool WALL>
+__device__ __forceinline__ void plane_commit(const PlaneMap<WALL>& pm, Plane<T> s, const T (&v)[DIM][RPF]) {
+    const int tid = threadIdx.x + threadIdx.y * RBX;
+#pragma unroll
+    for (int q = 0; q < RPF; ++q)
+        if (pm.off[q] >= 0) {
+#pragma unroll
+            for (int cc = 0; cc < DIM; ++cc) s[cc][tid + q * RNT] = v[cc][q];
+        }
+}
+
+// F (dim fields, may be null) and r = D F. Grid: (ceil(nx/32), ceil(ny/8), ceil(nz/kchunk)), block (32, 8).
+template <typename T, int DIM, bool WALL>
+__global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restrict__ u, T* __restrict__ F,
+                                                 T* __restrict__ r, int kchunk) {
+    __shared__ T su[3][DIM][RSPL];
+    __shared__ T sFx[RBY][RBX + 1];
+    __shared__ T sFy[RBY + 1][RBX];
+    const int nx = c.nx, ny = c.ny, nz = c.nz;
+    const long N = (long)nx * ny * nz;
+    const long plane = (long)nx * ny;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * RBX, j0 = blockIdx.y * RBY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool inside = i < nx && j < ny;
+    const int c0 = (ty + 2) * RSX + (tx + 2);
+    const YRow<T> yr = yrow<T, WALL>(c, j < ny ? j : ny - 1);
+    // halo work: warp 0 computes F^y one row below the tile, warp 1 (lanes 0..7) F^x left of it
+    const bool hy = ty == 0;
+    const bool hx = ty == 1 && tx < RBY;
+    const bool hy_wall = WALL && j0 == 0;   // the row below is the bottom wall: F^y = 0
+    const int jhy = j0 - 1 < 0 ? ny - 1 : j0 - 1;
+    const int jhx = j0 + tx < ny ? j0 + tx : ny - 1;
+    const int c0hy = 1 * RSX + (tx + 2);
+    const int c0hx = (tx + 2) * RSX + 1;
+    const PlaneMap<WALL> pm = plane_map<WALL>(nx, ny, i0, j0);
+    T v[DIM][RPF];
+
+    if constexpr (DIM == 2) {
+        plane_fetch<T, DIM, WALL>(pm, u, N, 0, v);
+        plane_commit<T, DIM, WALL>(pm, su[0], v);
+        __syncthreads();
+        CPlane<T> o = su[0];
+        const T fx = eval_Fx<T, 2, WALL>(c, yr, o, o, o, c0);
+        T fy = eval_Fy<T, 2, WALL>(c, yr, o, o, o, c0);
+        if (WALL && j == ny - 1) fy = (T)0;
+        sFx[ty][tx + 1] = fx;
+        sFy[ty + 1][tx] = fy;
+        if (hy) sFy[0][tx] = hy_wall ? (T)0 : eval_Fy<T, 2, WALL>(c, yrow<T, WALL>(c, jhy), o, o, o, c0hy);
+        if (hx) sFx[tx][0] = eval_Fx<T, 2, WALL>(c, yrow<T, WALL>(c, jhx), o, o, o, c0hx);
+        __syncthreads();
+        if (inside) {
+            const long a = (long)j * nx + i;
+            if (F) {
+                F[a] = fx;
+                F[N + a] = fy;
+            }
+            r[a] = (fx - sFx[ty][tx]) * c.ix + (fy - sFy[ty][tx]) * yr.i;
+        }
+        return;
+    } else {
+        const int kb = blockIdx.z * kchunk;
+        const int ke = min(kb + kchunk, nz);
+        auto wrapz = [nz](int k) { return k < 0 ? k + nz : (k >= nz ? k - nz : k); };
+        int sm = 0, so = 1, sp = 2;
+        plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(kb - 2) * plane, v);
+        plane_commit<T, DIM, WALL>(pm, su[sm], v);
+        plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(kb - 1) * plane, v);
+        plane_commit<T, DIM, WALL>(pm, su[so], v);
+        plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(kb) * plane, v);
+        plane_commit<T, DIM, WALL>(pm, su[sp], v);
+        plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(kb + 1) * plane, v);
+        __syncthreads();
+        T fz_prev = eval_Fz<T, WALL>(c, yr, su[sm], su[so], su[sp], c0);
+        __syncthreads();
+        plane_commit<T, DIM, WALL>(pm, su[sm], v);
+        {
+            const int t = sm;
+            sm = so;
+            so = sp;
+            sp = t;
+        }
+        __syncthreads();
+        for (int k = kb; k < ke; ++k) {
+            const bool more = k + 1 < ke;
+            if (more) plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(k + 2) * plane, v);
+            CPlane<T> m = su[sm];
+            CPlane<T> o = su[so];
+            CPlane<T> p = su[sp];
+            const T fx = eval_Fx<T, 3, WALL>(c, yr, m, o, p, c0);
+            T fy = eval_Fy<T, 3, WALL>(c, yr, m, o, p, c0);
+            if (WALL && j == ny - 1) fy = (T)0;
+            const T fz = eval_Fz<T, WALL>(c, yr, m, o, p, c0);
+            sFx[ty][tx + 1] = fx;
+            sFy[ty + 1][tx] = fy;
+            if (hy) sFy[0][tx] = hy_wall ? (T)0 : eval_Fy<T, 3, WALL>(c, yrow<T, WALL>(c, jhy), m, o, p, c0hy);
+            if (hx) sFx[tx][0] = eval_Fx<T, 3, WALL>(c, yrow<T, WALL>(c, jhx), m, o, p, c0hx);
+            __syncthreads();
+            if (inside) {
+                const long a = (long)k * plane + (long)j * nx + i;
+                if (F) {
+                    F[a] = fx;
+                    F[N + a] = fy;
+                    F[2 * N + a] = fz;
+                }
+                r[a] = (fx - sFx[ty][tx]) * c.ix + (fy - sFy[ty][tx]) * yr.i + (fz - fz_prev) * c.iz;
+            }
+            fz_prev = fz;
+            if (more) plane_commit<T, DIM, WALL>(pm, su[sm], v);
+            {
+                const int t = sm;
+                sm = so;
+                so = sp;
+                sp = t;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace ins

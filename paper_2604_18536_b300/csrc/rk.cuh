@@ -1,0 +1,185 @@
+// Projection + classic RK4 stage update with 16-byte vector accesses and a z march
+// (paper Sec. 2.6.2; pressure gradient of App. B).
+//
+// k = F - G p, (G p)^a = (p_{I+e_a} - p_I) / h_a, then
+//   stage 0: acc = b0 k;    us = u0 + dt a1 k
+//   stage 1,2: acc += b k;  us = u0 + dt a k
+//   stage 3: u0 = u0 + dt (acc + b3 k) in place, the CFL per-index maxima of
+//            |u_{n+1}| and the non-finite flag.
+// Each thread owns VEC consecutive cells in x (one float4 / double2) of one row
+// j and marches through a chunk of z planes: the pressure of plane k+1 loaded
+// for G p in z is the centre pressure of the next plane, and the x neighbour of
+// the last cell of a vector comes from the next lane by a warp shuffle.
+// x and z are periodic and uniform (constant 1/h); y may be a stretched wall
+// direction (1/h_y[j] is constant along the march).
+#pragma once
+
+#include "common.cuh"
+#include "stencil.cuh"
+
+namespace ins {
+
+template <typename T>
+struct VecT;
+template <>
+struct VecT<float> {
+    using V = float4;
+    static constexpr int N = 4;
+    static __device__ __forceinline__ void ld(const float* p, float (&x)[4]) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+    static __device__ __forceinline__ void st(float* p, const float (&x)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+};
+template <>
+struct VecT<double> {
+    using V = double2;
+    static constexpr int N = 2;
+    static __device__ __forceinline__ void ld(const double* p, double (&x)[2]) {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        x[0] = v.x; x[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(double* p, const double (&x)[2]) {
+        *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+    }
+};
+
+template <typename T>
+struct RkCoef {
+    int nx, ny, nz;
+    T ihx, ihz;          // 1/h of the uniform x and z directions
+    const T* ihy;        // 1/h_y[j]
+};
+
+// Block (32, 8); grid (ceil(nx/VEC/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx % VEC == 0 and
+// 16-byte aligned field pointers.
+template <typename T, int DIM, bool WALL>
+__global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __restrict__ F, const T* __restrict__ p,
+                                                       T* __restrict__ u0, T* __restrict__ acc, T* __restrict__ us,
+                                                       RkArgs ra, int kchunk) {
+    using VT = VecT<T>;
+    constexpr int VEC = VT::N;
+    const int nx = c.nx, ny = c.ny, nz = c.nz;
+    const long N = (long)nx * ny * nz;
+    const long plane = (long)nx * ny;
+    const int nvx = nx / VEC;
+    const int lane = threadIdx.x, row = threadIdx.y;
+    const int iv = blockIdx.x * 32 + lane;
+    const int i0 = iv * VEC;
+    const int j = blockIdx.y * 8 + row;
+    const bool ok = iv < nvx && j < ny;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(kb + kchunk, nz);
+    const double dt = ra.dt_dev ? *ra.dt_dev : ra.dt_host;
+    const T dta = (T)(dt * ra.a_next), bb = (T)ra.b, dtt = (T)dt;
+    const T ihy = __ldg(&c.ihy[j < ny ? j : ny - 1]);
+    const bool top = WALL && j == ny - 1;
+    const bool last_vec = iv == nvx - 1;
+    const bool need_global_next = last_vec || lane == 31;
+    const long jrow = (long)(j < ny ? j : 0) * nx;
+    const long jnext = (long)(j + 1 < ny ? j + 1 : 0) * nx;   // periodic wrap in y
+    double mxx[VEC], mxy = 0.0;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) mxx[e] = 0.0;
+    bool bad = false;
+    T P0[VEC], Pt[VEC];
+    if (ok) VT::ld(p + (long)kb * plane + jrow + i0, P0);
+    else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) P0[e] = (T)0;
+    }
+    for (int k = kb; k < ke; ++k) {
+        const long base = (long)k * plane;
+        const long a = base + jrow + i0;
+        const long kt = (k + 1 < nz ? (long)(k + 1) : 0) * plane;
+        // x neighbour of the last element: first element of the next vector (next lane or wrap)
+        T pnext = __shfl_down_sync(0xffffffffu, P0[0], 1);
+        T Pn[VEC];
+        double qz = 0.0;
+        if (ok) {
+            if (need_global_next) pnext = p[base + jrow + (last_vec ? 0 : i0 + VEC)];
+            if (DIM == 3) VT::ld(p + kt + jrow + i0, Pt);
+            if (!top) VT::ld(p + base + jnext + i0, Pn);
+            T f[3][VEC], kk[3][VEC];
+            VT::ld(F + a, f[0]);
+            VT::ld(F + N + a, f[1]);
+            if (DIM == 3) VT::ld(F + 2 * N + a, f[2]);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const T pe = e + 1 < VEC ? P0[e + 1] : pnext;
+                kk[0][e] = fma(P0[e] - pe, c.ihx, f[0][e]);
+                kk[1][e] = top ? (T)0 : fma(P0[e] - Pn[e], ihy, f[1][e]);
+                if (DIM == 3) kk[2][e] = fma(P0[e] - Pt[e], c.ihz, f[2][e]);
+            }
+#pragma unroll
+            for (int cc = 0; cc < DIM; ++cc) {
+                const long ea = cc * N + a;
+                T uv[VEC], av[VEC];
+                VT::ld(u0 + ea, uv);
+                if (ra.stage == 0) {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        av[e] = bb * kk[cc][e];
+                        uv[e] = fma(dta, kk[cc][e], uv[e]);
+                    }
+                    VT::st(acc + ea, av);
+                    VT::st(us + ea, uv);
+                } else if (ra.stage < 3) {
+                    VT::ld(acc + ea, av);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        av[e] = fma(bb, kk[cc][e], av[e]);
+                        uv[e] = fma(dta, kk[cc][e], uv[e]);
+                    }
+                    VT::st(acc + ea, av);
+                    VT::st(us + ea, uv);
+                } else {
+                    VT::ld(acc + ea, av);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        uv[e] = fma(dtt, fma(bb, kk[cc][e], av[e]), uv[e]);
+                        bad |= !isfinite(uv[e]);
+                        const double q = fabs((double)uv[e]);
+                        if (cc == 0) mxx[e] = fmax(mxx[e], q);
+                        else if (cc == 1) mxy = fmax(mxy, q);
+                        else qz = fmax(qz, q);
+                    }
+                    VT::st(u0 + ea, uv);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) Pt[e] = (T)0;
+        }
+        if (ra.stage == 3 && ra.mx && DIM == 3) {
+            for (int o = 16; o > 0; o >>= 1) qz = fmax(qz, __shfl_xor_sync(0xffffffffu, qz, o));
+            if (lane == 0 && qz > 0.0) atomicMax(&ra.mx[nx + ny + k], (unsigned long long)__double_as_longlong(qz));
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) P0[e] = Pt[e];
+    }
+    if (ra.stage == 3) {
+        if (ra.mx) {
+            __shared__ double sx[8][32 * VEC + 1];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) sx[row][lane * VEC + e] = mxx[e];
+            for (int o = 16; o > 0; o >>= 1) mxy = fmax(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+            if (lane == 0 && j < ny && mxy > 0.0)
+                atomicMax(&ra.mx[nx + j], (unsigned long long)__double_as_longlong(mxy));
+            __syncthreads();
+            if (row == 0 && iv < nvx) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    double m = sx[0][lane * VEC + e];
+                    for (int r = 1; r < 8; ++r) m = fmax(m, sx[r][lane * VEC + e]);
+                    if (m > 0.0) atomicMax(&ra.mx[i0 + e], (unsigned long long)__double_as_longlong(m));
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(ra.err_flag, 1u);
+    }
+}
+
+}  // namespace ins

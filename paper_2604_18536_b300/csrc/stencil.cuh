@@ -1,230 +1,15 @@
 // Stencil kernels of the staggered finite-volume scheme (paper App. A momentum
 // equation, App. B kernels) and the fused projection + RK update.
 //
-// k_rhs_div: F(u) = C(u) + nu diffusion(u) + f on every velocity face and
-// r = D F(u) in every cell, one pass over u. A CTA owns a BX x BY column of
-// cells and marches up z through a chunk of planes. Three planes (k-1, k, k+1)
-// of all velocity components, with a halo of 2 cells below and 1 above in x
-// and y, sit in shared memory as a ring. Each thread computes F at its own
-// three faces; the faces just below the tile in x and y (needed by the
-// divergence) are computed by extra threads, and F^z at k-1 is carried in a
-// register from the previous plane. Boundary rules are applied while loading
-// the planes: periodic wrap, or at a no-slip wall in y the odd ghost for the
-// tangential components and 0 for the wall-normal one (Sec. 2.4).
-//
-// Convection (energy-conserving form of App. A): for u^a and flux direction b
-//  b == a: -((u_{i} + u_{i+1})^2 - (u_{i-1} + u_i)^2) * 0.25 / h_a[i]
-//  b != a: -(V+ (u + u_{+b}) - V- (u_{-b} + u)) * 0.5 / d_b[j]
-//          V+ = wl_a[i] u^b + wr_a[i] u^b_{+a} (volume weights along a), V- the same one b-cell lower.
+// k_divergence, k_sub_grad: D u and src - G p (projection, right-hand side).
+// k_rk_update: k = F - G p and the classic RK4 stage update; k_cfl_finalize: the
+// CFL time step from per-index maxima; k_diag: energy, divergence, CFL maxima.
+// (F and D F are computed by k_rhs_div in rhs.cuh.)
 #pragma once
 
 #include "common.cuh"
 
 namespace ins {
-
-constexpr int BX = 32;
-constexpr int BY = 8;
-constexpr int SX = BX + 3;   // smem plane covers i0-2 .. i0+BX
-constexpr int SY = BY + 3;   //                   j0-2 .. j0+BY
-constexpr int SPL = SX * SY;
-
-__device__ __forceinline__ int pmod(int i, int n) {
-    int r = i % n;
-    return r < 0 ? r + n : r;
-}
-
-// Load plane gk (already wrapped) of the DIM velocity components into s[comp][...].
-template <typename T, int DIM, bool WALL>
-__device__ __forceinline__ void load_plane(const Geo<T>& g, const T* __restrict__ u, long N, int gk, int i0, int j0,
-                                           T (*s)[SPL]) {
-    const int nx = g.nx, ny = g.ny;
-    for (int idx = threadIdx.x + threadIdx.y * BX; idx < SPL; idx += BX * BY) {
-        const int li = idx % SX, lj = idx / SX;
-        const int gi = pmod(i0 - 2 + li, nx);
-        int gj = j0 - 2 + lj;
-        const long plane = (long)gk * nx * ny;
-        if (!WALL) {
-            gj = pmod(gj, ny);
-            const long a = plane + (long)gj * nx + gi;
-#pragma unroll
-            for (int c = 0; c < DIM; ++c) s[c][idx] = u[c * N + a];
-        } else {
-            if (gj >= 0 && gj < ny) {
-                const long a = plane + (long)gj * nx + gi;
-#pragma unroll
-                for (int c = 0; c < DIM; ++c) s[c][idx] = u[c * N + a];
-            } else {
-                // mirrored ghost cell: tangential components odd, wall-normal one 0
-                int m = gj < 0 ? -gj - 1 : 2 * ny - 1 - gj;
-                m = m < 0 ? 0 : (m >= ny ? ny - 1 : m);
-                const long a = plane + (long)m * nx + gi;
-#pragma unroll
-                for (int c = 0; c < DIM; ++c) s[c][idx] = (c == 1) ? (T)0 : -u[c * N + a];
-            }
-        }
-    }
-}
-
-// F^x at local (li, lj) = global (i, j, k); planes m (k-1), o (k), p (k+1).
-template <typename T, int DIM>
-__device__ __forceinline__ T Fx_at(const Geo<T>& g, const T (*m)[SPL], const T (*o)[SPL], const T (*p)[SPL], int li,
-                                   int lj, int i, int j, int k) {
-    const int c0 = lj * SX + li;
-    const T uc = o[0][c0], ue = o[0][c0 + 1], uw = o[0][c0 - 1], un = o[0][c0 + SX], us = o[0][c0 - SX];
-    const T wl = g.coef(0, C_WL, i), wr = g.coef(0, C_WR, i);
-    T s1 = uc + ue, s2 = uw + uc;
-    T conv = -(s1 * s1 - s2 * s2) * g.coef(0, C_CONV_AA, i);
-    {
-        const T vp = wl * o[1][c0] + wr * o[1][c0 + 1];
-        const T vm = wl * o[1][c0 - SX] + wr * o[1][c0 + 1 - SX];
-        conv -= (vp * (uc + un) - vm * (us + uc)) * g.coef(1, C_CONV_AB, j);
-    }
-    T dif = g.coef(0, C_DIFF_AP, i) * (ue - uc) - g.coef(0, C_DIFF_AM, i) * (uc - uw) +
-            g.coef(1, C_DIFF_BP, j) * (un - uc) - g.coef(1, C_DIFF_BM, j) * (uc - us);
-    if (DIM == 3) {
-        const T ut = p[0][c0], ub = m[0][c0];
-        const T vp = wl * o[2][c0] + wr * o[2][c0 + 1];
-        const T vm = wl * m[2][c0] + wr * m[2][c0 + 1];
-        conv -= (vp * (uc + ut) - vm * (ub + uc)) * g.coef(2, C_CONV_AB, k);
-        dif += g.coef(2, C_DIFF_BP, k) * (ut - uc) - g.coef(2, C_DIFF_BM, k) * (uc - ub);
-    }
-    return conv + dif + g.fx;
-}
-
-template <typename T, int DIM>
-__device__ __forceinline__ T Fy_at(const Geo<T>& g, const T (*m)[SPL], const T (*o)[SPL], const T (*p)[SPL], int li,
-                                   int lj, int i, int j, int k) {
-    const int c0 = lj * SX + li;
-    const T uc = o[1][c0], un = o[1][c0 + SX], us = o[1][c0 - SX], ue = o[1][c0 + 1], uw = o[1][c0 - 1];
-    const T wl = g.coef(1, C_WL, j), wr = g.coef(1, C_WR, j);
-    T s1 = uc + un, s2 = us + uc;
-    T conv = -(s1 * s1 - s2 * s2) * g.coef(1, C_CONV_AA, j);
-    {
-        const T vp = wl * o[0][c0] + wr * o[0][c0 + SX];
-        const T vm = wl * o[0][c0 - 1] + wr * o[0][c0 - 1 + SX];
-        conv -= (vp * (uc + ue) - vm * (uw + uc)) * g.coef(0, C_CONV_AB, i);
-    }
-    T dif = g.coef(1, C_DIFF_AP, j) * (un - uc) - g.coef(1, C_DIFF_AM, j) * (uc - us) +
-            g.coef(0, C_DIFF_BP, i) * (ue - uc) - g.coef(0, C_DIFF_BM, i) * (uc - uw);
-    if (DIM == 3) {
-        const T ut = p[1][c0], ub = m[1][c0];
-        const T vp = wl * o[2][c0] + wr * o[2][c0 + SX];
-        const T vm = wl * m[2][c0] + wr * m[2][c0 + SX];
-        conv -= (vp * (uc + ut) - vm * (ub + uc)) * g.coef(2, C_CONV_AB, k);
-        dif += g.coef(2, C_DIFF_BP, k) * (ut - uc) - g.coef(2, C_DIFF_BM, k) * (uc - ub);
-    }
-    return conv + dif + g.fy;
-}
-
-template <typename T>
-__device__ __forceinline__ T Fz_at(const Geo<T>& g, const T (*m)[SPL], const T (*o)[SPL], const T (*p)[SPL], int li,
-                                   int lj, int i, int j, int k) {
-    const int c0 = lj * SX + li;
-    const T uc = o[2][c0], ut = p[2][c0], ub = m[2][c0], ue = o[2][c0 + 1], uw = o[2][c0 - 1], un = o[2][c0 + SX],
-            us = o[2][c0 - SX];
-    const T wl = g.coef(2, C_WL, k), wr = g.coef(2, C_WR, k);
-    T s1 = uc + ut, s2 = ub + uc;
-    T conv = -(s1 * s1 - s2 * s2) * g.coef(2, C_CONV_AA, k);
-    {
-        const T vp = wl * o[0][c0] + wr * p[0][c0];
-        const T vm = wl * o[0][c0 - 1] + wr * p[0][c0 - 1];
-        conv -= (vp * (uc + ue) - vm * (uw + uc)) * g.coef(0, C_CONV_AB, i);
-    }
-    {
-        const T vp = wl * o[1][c0] + wr * p[1][c0];
-        const T vm = wl * o[1][c0 - SX] + wr * p[1][c0 - SX];
-        conv -= (vp * (uc + un) - vm * (us + uc)) * g.coef(1, C_CONV_AB, j);
-    }
-    const T dif = g.coef(2, C_DIFF_AP, k) * (ut - uc) - g.coef(2, C_DIFF_AM, k) * (uc - ub) +
-                  g.coef(0, C_DIFF_BP, i) * (ue - uc) - g.coef(0, C_DIFF_BM, i) * (uc - uw) +
-                  g.coef(1, C_DIFF_BP, j) * (un - uc) - g.coef(1, C_DIFF_BM, j) * (uc - us);
-    return conv + dif + g.fz;
-}
-
-// F (dim fields, may be null) and r = D F. Grid: (ceil(nx/BX), ceil(ny/BY), ceil(nz/kchunk)).
-template <typename T, int DIM, bool WALL>
-__global__ void __launch_bounds__(BX* BY) k_rhs_div(Geo<T> g, const T* __restrict__ u, T* __restrict__ F,
-                                                    T* __restrict__ r, int kchunk) {
-    __shared__ T su[3][DIM][SPL];
-    __shared__ T sFx[BY][BX + 1];
-    __shared__ T sFy[BY + 1][BX];
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const long N = (long)nx * ny * nz;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
-    const int i = i0 + tx, j = j0 + ty;
-    const bool inside = i < nx && j < ny;
-    const int li = tx + 2, lj = ty + 2;
-    const int ih = pmod(i0 - 1, nx);                 // the halo column, global index
-    const int jh = pmod(j0 - 1, ny);                 // the halo row, global index
-    const bool bottom_wall_halo = WALL && j0 == 0;   // F^y below row 0 is the wall: 0
-    const int ic = i < nx ? i : nx - 1, jc = j < ny ? j : ny - 1;
-    const T iDx = g.coef(0, C_INV_D, ic), iDy = g.coef(1, C_INV_D, jc);
-
-    if (DIM == 2) {
-        load_plane<T, DIM, WALL>(g, u, N, 0, i0, j0, su[0]);
-        __syncthreads();
-        const T(*o)[SPL] = su[0];
-        T fx = Fx_at<T, 2>(g, o, o, o, li, lj, ic, jc, 0);
-        T fy = Fy_at<T, 2>(g, o, o, o, li, lj, ic, jc, 0);
-        if (WALL && j == ny - 1) fy = (T)0;
-        sFx[ty][tx + 1] = fx;
-        sFy[ty + 1][tx] = fy;
-        if (tx == 0) sFx[ty][0] = Fx_at<T, 2>(g, o, o, o, 1, lj, ih, jc, 0);
-        if (ty == 0) sFy[0][tx] = bottom_wall_halo ? (T)0 : Fy_at<T, 2>(g, o, o, o, li, 1, ic, jh, 0);
-        __syncthreads();
-        if (inside) {
-            const long a = (long)j * nx + i;
-            if (F) {
-                F[a] = fx;
-                F[N + a] = fy;
-            }
-            r[a] = (fx - sFx[ty][tx]) * iDx + (fy - sFy[ty][tx]) * iDy;
-        }
-        return;
-    }
-
-    const int kb = blockIdx.z * kchunk;
-    const int ke = min(kb + kchunk, nz);
-    // ring of plane slots: sm = k-1, so = k, sp = k+1
-    int sm = 0, so = 1, sp = 2;
-    load_plane<T, DIM, WALL>(g, u, N, pmod(kb - 2, nz), i0, j0, su[sm]);
-    load_plane<T, DIM, WALL>(g, u, N, pmod(kb - 1, nz), i0, j0, su[so]);
-    load_plane<T, DIM, WALL>(g, u, N, pmod(kb, nz), i0, j0, su[sp]);
-    __syncthreads();
-    T fz_prev = Fz_at<T>(g, su[sm], su[so], su[sp], li, lj, ic, jc, pmod(kb - 1, nz));
-    __syncthreads();
-    load_plane<T, DIM, WALL>(g, u, N, pmod(kb + 1, nz), i0, j0, su[sm]);
-    { int t = sm; sm = so; so = sp; sp = t; }
-    __syncthreads();
-    for (int k = kb; k < ke; ++k) {
-        const T(*m)[SPL] = su[sm];
-        const T(*o)[SPL] = su[so];
-        const T(*p)[SPL] = su[sp];
-        const T fx = Fx_at<T, 3>(g, m, o, p, li, lj, ic, jc, k);
-        T fy = Fy_at<T, 3>(g, m, o, p, li, lj, ic, jc, k);
-        if (WALL && j == ny - 1) fy = (T)0;
-        const T fz = Fz_at<T>(g, m, o, p, li, lj, ic, jc, k);
-        sFx[ty][tx + 1] = fx;
-        sFy[ty + 1][tx] = fy;
-        if (tx == 0) sFx[ty][0] = Fx_at<T, 3>(g, m, o, p, 1, lj, ih, jc, k);
-        if (ty == 0) sFy[0][tx] = bottom_wall_halo ? (T)0 : Fy_at<T, 3>(g, m, o, p, li, 1, ic, jh, k);
-        __syncthreads();
-        if (inside) {
-            const long a = ((long)k * ny + j) * nx + i;
-            if (F) {
-                F[a] = fx;
-                F[N + a] = fy;
-                F[2 * N + a] = fz;
-            }
-            r[a] = (fx - sFx[ty][tx]) * iDx + (fy - sFy[ty][tx]) * iDy + (fz - fz_prev) * g.coef(2, C_INV_D, k);
-        }
-        fz_prev = fz;
-        if (k + 1 < ke) load_plane<T, DIM, WALL>(g, u, N, pmod(k + 2, nz), i0, j0, su[sm]);
-        { int t = sm; sm = so; so = sp; sp = t; }
-        __syncthreads();
-    }
-}
 
 // phi = D u (used by the projection).
 template <typename T, int DIM, bool WALL>

@@ -32,6 +32,15 @@ def case(name):
                     force=None)
     if name == "p3tiny":
         return dict(faces=[U(6, 0, 1.0), U(10, 0, 2.0), U(14, 0, 1.5)], bc=["periodic"] * 3, nu=0.01, force=None)
+    if name == "p3reg":     # register-path FFT lengths 32 (8x4), 16 (4x4), 64 (8x8)
+        return dict(faces=[U(32, 0, 2 * PI), U(16, 0, 1.0), U(64, 0, 3.0)], bc=["periodic"] * 3, nu=0.02,
+                    force=None)
+    if name == "p3reg2":    # 256 (16x16) and 128 (16x8)
+        return dict(faces=[U(256, 0, 2 * PI), U(8, 0, 1.0), U(128, 0, 2 * PI)], bc=["periodic"] * 3, nu=0.01,
+                    force=None)
+    if name == "c3reg":     # channel with register-path x and z
+        return dict(faces=[U(64, 0, 4 * PI), inputs.tanh_faces(20, 0, 2, 1.5), U(32, 0, 4 * PI / 3)],
+                    bc=["periodic", "wall", "periodic"], nu=1 / 180, force=[1.0, 0.0, 0.0])
     if name == "c3":
         return dict(faces=inputs.channel_faces(36, 20, 28), bc=["periodic", "wall", "periodic"], nu=1 / 180,
                     force=[1.0, 0.0, 0.0])
@@ -41,7 +50,7 @@ def case(name):
     raise KeyError(name)
 
 
-CASES = ["p2", "p3", "p3tiny", "c3", "c2"]
+CASES = ["p2", "p3", "p3tiny", "p3reg", "p3reg2", "c3", "c3reg", "c2"]
 DTYPES = [torch.float64, torch.float32]
 
 
