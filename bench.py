@@ -235,6 +235,28 @@ def run_ours(args):
                "gpu_launches": launches, "clocks": clocks,
                "step_hbm_frac": step_model_bytes(n, s) / step_s / 1e9 / hbm_peak,
                "final_ke": diag["ke"], "final_max_div": diag["max_div"], "workspace_bytes": g.workspace_bytes()}
+        # adjoint/forward ratio: ins_step_vjp (stage recompute + reverse sweep) vs ins_step
+        kv = max(3, args.steps // 4)
+        ybar = u.detach().clone()
+        ubar = g.new_velocity()
+        nub = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar, nubar=nub)
+        torch.cuda.synchronize()
+        g.profile(True)
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(kv):
+            g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar, nubar=nub)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vprof = g.profile_read()
+        g.profile(False)
+        vms = max_over_ranks(v0.elapsed_time(v1)) / kv
+        res["adjoint"] = {"ms_per_vjp": vms, "ratio": vms / (ms_max / args.steps), "vjps": kv,
+                          "kernels": {k: {"launches": v[0], "avg_us": round(v[1] / v[0] * 1e3, 2)}
+                                      for k, v in sorted(vprof.items(), key=lambda kv_: -kv_[1][1])}}
+        del ybar, ubar
         # end to end through the public API with host buffers (pinned), copies inside the timed region
         if not args.no_e2e:
             uh = u.detach().cpu().pin_memory()
@@ -271,12 +293,12 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": prim["roofline"], "e2e": prim.get("e2e"), "gpu_launches": prim["gpu_launches"],
             "clocks": prim["clocks"], "step_hbm_frac": prim["step_hbm_frac"], "kernels": prim["kernels"],
-            "adjoint_forward_ratio": None,
+            "adjoint_forward_ratio": prim["adjoint"]["ratio"], "adjoint": prim["adjoint"],
         }
         if "f32" in results and "f64" in results:
             f = results["f32"]
             line["fp32"] = {k: f[k] for k in ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
-                                               "step_hbm_frac", "kernels", "clocks") if k in f}
+                                               "step_hbm_frac", "kernels", "clocks", "adjoint") if k in f}
             line["fp32"]["speedup_vs_fp64"] = f["value"] / prim["value"]
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(steps=1)

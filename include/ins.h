@@ -123,6 +123,24 @@ ins_status ins_divergence(ins_grid* g, const void* u, void* phi);
 ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host,
                     double* next_dt_dev, double cfl);
 
+/* Vector-Jacobian product of one ins_step (Sec. 3.4, pullback of a composition;
+ * App. B operator pullbacks; the Poisson solve is self-adjoint, Sec. 2.6.1).
+ * With u_{n+1} = step(u_n) for a frozen dt, returns
+ *   ubar_n = (d u_{n+1} / d u_n)^T ubar_np1   and   *nubar_dev += (d u_{n+1}/d nu) . ubar_np1.
+ * The stage states are recomputed from u_n (per-step checkpointing: the caller keeps
+ * only the step inputs), then the stages run in reverse: w_s = P kbar_s (P = P^T),
+ * ubar_s = J_F(u_s)^T w_s, ubar_n = ubar_np1 + sum_s ubar_s,
+ * kbar_{s-1} = dt b_{s-1} ubar_np1 + dt a_{s,s-1} ubar_s.
+ * u_n, ubar_np1: DEVICE, dim fields, not modified. ubar_n: DEVICE, dim fields, must not
+ * alias the inputs. dt_dev/dt_host: as in ins_step. nubar_dev: DEVICE double that the
+ * result is added to (so it can accumulate over steps), or NULL.
+ * Periodic uniform grids only (INS_ERR_UNSUPPORTED otherwise). The first call allocates the
+ * step-VJP workspace (3 stage states, one field, nu partial sums: about 4 velocity fields),
+ * kept until ins_grid_destroy; make the first call before any stream capture.
+ * The grid's F, r/p and RK accumulator buffers are reused as scratch. */
+ins_status ins_step_vjp(ins_grid* g, const void* u_n, const double* dt_dev, double dt_host,
+                        const void* ubar_np1, void* ubar_n, double* nubar_dev);
+
 /* Adaptive time step (Sec. 2.6.2, convective and diffusive limits):
  * dt = cfl * min(1 / max_{a,I} |u^a_I| / h_a[i], min_{a,i} d_a[i]^2 / nu)
  * where d are cell widths and h centre-to-centre distances, every operation

@@ -21,6 +21,7 @@
 #include "rhs.cuh"
 #include "stencil.cuh"
 #include "rk.cuh"
+#include "adjoint.cuh"
 
 using namespace ins;
 
@@ -114,6 +115,10 @@ struct ins_grid {
     unsigned long long* diag_max = nullptr; // [2]
     int lg_tw_x = 0, lg_tw_y = 0, lg_tw_z = 0;
     int kchunk = 32;
+    // step-VJP workspace (stage states u_2..u_4, the projected cotangent, nu partials),
+    // allocated by the first ins_step_vjp call
+    void* vjp = nullptr;
+    size_t vjp_bytes = 0;
     // launch accounting and opt-in per-kernel CUDA-event timing
     unsigned long long launches = 0;
     bool prof = false;
@@ -427,6 +432,83 @@ struct Impl {
         if (next_dt) {
             KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz, g->dmin2_nu, cfl,
                                                     next_dt));
+        }
+        return INS_OK;
+    }
+    // Pullback of one RK4 step (uniform periodic grids): recompute the stage states from the
+    // checkpoint u_n, then run the stages in reverse (see ins.h, ins_step_vjp).
+    static ins_status step_vjp(ins_grid* g, const T* un, const double* dt_dev, double dt_host, const T* ybar,
+                               T* ubar, double* nubar) {
+        static const double A[3] = {0.5, 0.5, 1.0};
+        static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+        const long N = g->N;
+        const size_t fld = (size_t)g->dim * N * sizeof(T);
+        const dim3 cg = cell_grid(g);
+        const long nblk = (long)cg.x * cg.y * cg.z;
+        const size_t need = 4 * ((fld + 255) & ~size_t(255)) + (size_t)nblk * 8;
+        if (g->vjp_bytes < need) {
+            if (g->vjp) cudaFree(g->vjp);
+            g->vjp = nullptr;
+            g->vjp_bytes = 0;
+            cudaError_t e = cudaMalloc(&g->vjp, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(INS_ERR_OOM, std::string("step-VJP workspace: ") + cudaGetErrorString(e));
+            }
+            g->vjp_bytes = need;
+        }
+        char* vb = reinterpret_cast<char*>(g->vjp);
+        const size_t fa = (fld + 255) & ~size_t(255);
+        T* U[4] = {const_cast<T*>(un), reinterpret_cast<T*>(vb), reinterpret_cast<T*>(vb + fa),
+                   reinterpret_cast<T*>(vb + 2 * fa)};
+        T* W = reinterpret_cast<T*>(vb + 3 * fa);
+        double* part = reinterpret_cast<double*>(vb + 4 * fa);
+        T* F = reinterpret_cast<T*>(g->F);
+        T* rp = reinterpret_cast<T*>(g->rp);
+        T* scratch = reinterpret_cast<T*>(g->acc);
+        ins_status s;
+        // forward: u_{s+1} = u_n + dt a_{s+1,s} k_s, s = 0, 1, 2
+        for (int st = 0; st < 3; ++st) {
+            if ((s = launch_rhs_div<T, DIM, WALL>(g, U[st], F, rp)) != INS_OK) return s;
+            if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+            RkArgs ra;
+            ra.dt_dev = dt_dev;
+            ra.dt_host = dt_host;
+            ra.a_next = A[st];
+            ra.b = 0.0;
+            ra.stage = 0;     // writes us = u0 + dt a k (and a scratch acc), leaves u0 untouched
+            ra.mx = nullptr;
+            ra.err_flag = g->err_flag;
+            KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(
+                                        make_geo<T>(g), F, rp, U[0], scratch, U[st + 1], ra));
+        }
+        // reverse
+        INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
+        const long n = (long)g->dim * N;
+        KLAUNCH(g, "scale", k_scale_dt<T><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host, B[3], n));
+        AdjCoef<T> ac;
+        ac.nx = g->nx;
+        ac.ny = g->ny;
+        ac.nz = g->nz;
+        for (int a = 0; a < 3; ++a) {
+            const double D = g->d[a][0];
+            ac.c1[a] = (T)(0.5 / D);
+            ac.c2[a] = (T)(0.25 / D);
+            ac.l2[a] = (T)(1.0 / (D * D));
+        }
+        ac.nu = (T)g->nu;
+        ac.dt_dev = dt_dev;
+        ac.dt_host = dt_host;
+        for (int st = 3; st >= 0; --st) {
+            // w = P kbar_s (P is symmetric on a uniform periodic grid)
+            KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp));
+            if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+            KLAUNCH(g, "sub_grad", k_sub_grad<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, W));
+            ac.bn = st > 0 ? B[st - 1] : 0.0;
+            ac.an = st > 0 ? A[st - 1] : 0.0;
+            KLAUNCH(g, "adj_rhs", k_adj_rhs<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
+                                      ac, U[st], W, ybar, ubar, st > 0 ? F : nullptr, part));
+            if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, nblk, nubar));
         }
         return INS_OK;
     }
@@ -841,6 +923,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
 ins_status ins_grid_destroy(ins_grid* g) {
     if (!g) return INS_OK;
     cudaStreamSynchronize(g->stream);
+    if (g->vjp) cudaFree(g->vjp);
     cudaError_t e = cudaFree(g->base);
     delete g;
     if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
@@ -921,6 +1004,25 @@ ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host, 
         using T = decltype(z);
         return dispatch<T>(g, [&](auto impl) {
             return decltype(impl)::step(g, (T*)u, dt_dev, dt_host, next_dt_dev, cfl);
+        });
+    });
+}
+
+ins_status ins_step_vjp(ins_grid* g, const void* u_n, const double* dt_dev, double dt_host, const void* ubar_np1,
+                        void* ubar_n, double* nubar_dev) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u_n, "u_n"));
+    CHECK(check_ptr(g, ubar_np1, "ubar_np1"));
+    CHECK(check_ptr(g, ubar_n, "ubar_n"));
+    if (ubar_n == ubar_np1 || ubar_n == u_n) return fail(INS_ERR_ARG, "ubar_n must not alias u_n or ubar_np1");
+    if (!dt_dev && !(std::isfinite(dt_host) && dt_host >= 0.0)) return fail(INS_ERR_ARG, "dt_host must be finite, >= 0");
+    if (g->wall_y) return fail(INS_ERR_UNSUPPORTED, "ins_step_vjp: wall directions are not supported (periodic grids only)");
+    return dispatch_dtype(g, [&](auto z) {
+        using T = decltype(z);
+        return dispatch<T>(g, [&](auto impl) {
+            return decltype(impl)::step_vjp(g, (const T*)u_n, dt_dev, dt_host, (const T*)ubar_np1, (T*)ubar_n,
+                                            nubar_dev);
         });
     });
 }

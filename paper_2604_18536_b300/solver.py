@@ -150,6 +150,21 @@ class Grid:
                              _ptr(next_dt_dev), float(cfl)), "ins_step")
         return u
 
+    def step_vjp(self, u_n, ubar_np1, dt=None, dt_dev=None, ubar_n=None, nubar=None):
+        """Pullback of one step (ins_step_vjp): returns (ubar_n, nubar) with nubar a CUDA float64
+        tensor of one element that the nu-derivative is added to (a new zero tensor if None)."""
+        self._check_u(u_n, "u_n")
+        self._check_u(ubar_np1, "ubar_np1")
+        if dt_dev is None and dt is None:
+            raise ValueError("give dt or dt_dev")
+        ubar_n = self.new_velocity() if ubar_n is None else ubar_n
+        self._check_u(ubar_n, "ubar_n")
+        nubar = torch.zeros(1, dtype=torch.float64, device=self.device) if nubar is None else nubar
+        self._sync_stream()
+        check(lib().ins_step_vjp(self._h, _ptr(u_n), _ptr(dt_dev), float(dt if dt is not None else 0.0),
+                                 _ptr(ubar_np1), _ptr(ubar_n), _ptr(nubar)), "ins_step_vjp")
+        return ubar_n, nubar
+
     def cfl_dt(self, u, cfl, out=None):
         self._check_u(u)
         out = torch.zeros(1, dtype=torch.float64, device=self.device) if out is None else out
