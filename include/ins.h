@@ -153,6 +153,22 @@ ins_status ins_cfl_dt(ins_grid* g, const void* u, double cfl, double* dt_dev);
  * Returns INS_ERR_NONFINITE (after filling out) if out[3] > 0. */
 ins_status ins_diag(ins_grid* g, const void* u, double out[4]);
 
+/* Shell energy spectrum (the closure's error measure; filtered-DNS comparison, Sec. 4):
+ * E[k] = sum over wavevectors with floor(|kvec| + 1/2) = k of
+ *        1/2 sum_a |uhat_a(kvec)|^2 / Ncells^2, k = 0 .. kmax, uhat the unnormalised DFT,
+ * |kvec| in integer wavenumbers (FP64 shell decisions). E_dev: DEVICE, kmax+1 doubles,
+ * overwritten. Periodic grids only. Uses the grid's spectral workspace. */
+ins_status ins_spectrum(ins_grid* g, const void* u, double* E_dev, int kmax);
+
+/* Face-averaging filter from a fine grid to one `ratio` times coarser in every
+ * direction (filtered DNS for closure training, Sec. 4): the coarse u^a on the face to
+ * the right of coarse cell I is the mean of the ratio^(dim-1) fine u^a on the fine faces
+ * that tile it. A divergence-free fine field stays divergence free on the coarse grid.
+ * n_coarse: coarse cells per direction (host); u_fine: DEVICE, dim fine fields
+ * (n_coarse*ratio cells each); u_coarse: DEVICE, dim coarse fields; FP64 sums. */
+ins_status ins_filter_face_average(int dim, const int n_coarse[3], int ratio, int dtype, const void* u_fine,
+                                   void* u_coarse, void* stream);
+
 /* Reads and clears the grid's device error flag (synchronous).
  * INS_ERR_NONFINITE if a step produced a NaN/Inf since the last check. */
 ins_status ins_check_finite(ins_grid* g);

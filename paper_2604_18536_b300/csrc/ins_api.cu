@@ -22,6 +22,7 @@
 #include "stencil.cuh"
 #include "rk.cuh"
 #include "adjoint.cuh"
+#include "filter_spectrum.cuh"
 
 using namespace ins;
 
@@ -509,6 +510,55 @@ struct Impl {
             KLAUNCH(g, "adj_rhs", k_adj_rhs<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
                                       ac, U[st], W, ybar, ubar, st > 0 ? F : nullptr, part));
             if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, nblk, nubar));
+        }
+        return INS_OK;
+    }
+    // Shell energy spectrum of a periodic field (see ins.h, ins_spectrum).
+    static ins_status spectrum(ins_grid* g, const T* u, double* E, int kmax) {
+        cudaStream_t st = g->stream;
+        const int nx = g->nx, ny = g->ny, nz = g->nz, nxh = g->nxh;
+        const long lines = (long)ny * nz;
+        cplx<T>* S = reinterpret_cast<cplx<T>*>(g->S);
+        INS_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * (kmax + 1), st));
+        const double ntot = (double)g->N;
+        for (int a = 0; a < g->dim; ++a) {
+            const T* comp = u + (size_t)a * g->N;
+            FftLine<T> lx = make_line<T>(g, 0);
+            if (reg_fft_len(nx)) {
+                KLAUNCH(g, "fft_x_r2c", x_reg<T>(nx, true, st, lx.tw, comp, S, nullptr, (int)lines, nxh));
+            } else {
+                const int lg = g->lg_tw_x;
+                const long pairs = (lines + 1) / 2;
+                const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);
+                KLAUNCH(g, "fft_x_r2c", k_fft_x_r2c<T><<<blocks, FFT_THREADS, fft_smem<T>(nx, lg), st>>>(
+                                            lx, comp, S, (int)lines, nxh, lg));
+            }
+            for (int d = 1; d < g->dim; ++d) {
+                FftLine<T> pl = make_line<T>(g, d);
+                long ncol, cdiv, outer, lstride;
+                if (d == 1) {
+                    ncol = (long)nz * nxh;
+                    cdiv = nxh;
+                    outer = (long)ny * nxh;
+                    lstride = nxh;
+                } else {
+                    ncol = (long)ny * nxh;
+                    cdiv = ncol;
+                    outer = 0;
+                    lstride = (long)ny * nxh;
+                }
+                if (reg_fft_len(pl.L)) {
+                    KLAUNCH(g, "fft_strided", strided_reg<T>(pl.L, st, pl.tw, S, ncol, cdiv, outer, lstride, 0,
+                                                             (const T*)nullptr));
+                } else {
+                    const int lg = d == 1 ? g->lg_tw_y : g->lg_tw_z;
+                    const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
+                    KLAUNCH(g, "fft_strided", k_fft_strided<T><<<blocks, FFT_THREADS, fft_smem<T>(pl.L, lg), st>>>(
+                                                  pl, S, ncol, cdiv, outer, lstride, 0, (const T*)nullptr, lg));
+                }
+            }
+            KLAUNCH(g, "shell_bin", k_shell_bin<T><<<592, 256, (kmax + 1) * sizeof(double), st>>>(
+                                        S, nx, ny, nz, nxh, kmax, E, 1.0 / (ntot * ntot)));
         }
         return INS_OK;
     }
@@ -1025,6 +1075,44 @@ ins_status ins_step_vjp(ins_grid* g, const void* u_n, const double* dt_dev, doub
                                             nubar_dev);
         });
     });
+}
+
+ins_status ins_spectrum(ins_grid* g, const void* u, double* E_dev, int kmax) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u, "u"));
+    if (!E_dev) return fail(INS_ERR_ARG, "E_dev is null");
+    if (kmax < 0 || kmax > 4096) return fail(INS_ERR_ARG, "kmax must be in [0, 4096]");
+    if (g->wall_y) return fail(INS_ERR_UNSUPPORTED, "ins_spectrum: periodic grids only");
+    return dispatch_dtype(g, [&](auto z) {
+        using T = decltype(z);
+        return dispatch<T>(g, [&](auto impl) { return decltype(impl)::spectrum(g, (const T*)u, E_dev, kmax); });
+    });
+}
+
+ins_status ins_filter_face_average(int dim, const int n_coarse[3], int ratio, int dtype, const void* u_fine,
+                                   void* u_coarse, void* stream) {
+    g_err.clear();
+    if (!n_coarse || !u_fine || !u_coarse) return fail(INS_ERR_ARG, "null argument");
+    if (dim != 2 && dim != 3) return fail(INS_ERR_ARG, "dim must be 2 or 3");
+    if (ratio < 1 || ratio > 64) return fail(INS_ERR_ARG, "ratio must be in [1, 64]");
+    if (dtype != INS_F32 && dtype != INS_F64) return fail(INS_ERR_ARG, "bad dtype");
+    const int cx = n_coarse[0], cy = n_coarse[1], cz = dim == 3 ? n_coarse[2] : 1;
+    if (cx < 1 || cy < 1 || cz < 1) return fail(INS_ERR_ARG, "coarse sizes must be >= 1");
+    const long total = (long)dim * cx * cy * cz;
+    if ((long)cx * ratio * cy * ratio * (dim == 3 ? (long)cz * ratio : 1) > (1L << 31))
+        return fail(INS_ERR_UNSUPPORTED, "fine grid above 2^31 cells");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (dtype == INS_F64) {
+        if (dim == 3) k_filter_face<double, 3><<<blocks, 256, 0, st>>>((const double*)u_fine, (double*)u_coarse, cx, cy, cz, ratio);
+        else k_filter_face<double, 2><<<blocks, 256, 0, st>>>((const double*)u_fine, (double*)u_coarse, cx, cy, cz, ratio);
+    } else {
+        if (dim == 3) k_filter_face<float, 3><<<blocks, 256, 0, st>>>((const float*)u_fine, (float*)u_coarse, cx, cy, cz, ratio);
+        else k_filter_face<float, 2><<<blocks, 256, 0, st>>>((const float*)u_fine, (float*)u_coarse, cx, cy, cz, ratio);
+    }
+    INS_LAUNCHED("filter_face");
+    return INS_OK;
 }
 
 ins_status ins_cfl_dt(ins_grid* g, const void* u, double cfl, double* dt_dev) {

@@ -30,6 +30,24 @@ def measure_fma_rate(dtype=torch.float64, device=None):
     return out.value
 
 
+def filter_face_average(u_fine, ratio):
+    """Face-averaging filter to a grid `ratio` times coarser (ins_filter_face_average).
+
+    u_fine: CUDA tensor (dim, [nz,] ny, nx), float32 or float64; returns the coarse field."""
+    dim = u_fine.shape[0]
+    fine = tuple(reversed(u_fine.shape[1:]))
+    if any(n % ratio for n in fine) or not u_fine.is_contiguous() or not u_fine.is_cuda:
+        raise ValueError("fine sizes must be multiples of ratio; contiguous CUDA tensor expected")
+    nc = [n // ratio for n in fine] + [1] * (3 - len(fine))
+    out = torch.empty((dim,) + tuple(reversed(nc[:dim])), dtype=u_fine.dtype, device=u_fine.device)
+    arr = (ctypes.c_int * 3)(*nc)
+    dt = _lib.INS_F64 if u_fine.dtype == torch.float64 else _lib.INS_F32
+    st = torch.cuda.current_stream(u_fine.device).cuda_stream
+    check(lib().ins_filter_face_average(dim, arr, int(ratio), dt, _ptr(u_fine), _ptr(out), ctypes.c_void_p(st)),
+          "ins_filter_face_average")
+    return out
+
+
 class Grid:
     """A staggered grid and its device workspace (``ins_grid_create``).
 
@@ -164,6 +182,15 @@ class Grid:
         check(lib().ins_step_vjp(self._h, _ptr(u_n), _ptr(dt_dev), float(dt if dt is not None else 0.0),
                                  _ptr(ubar_np1), _ptr(ubar_n), _ptr(nubar)), "ins_step_vjp")
         return ubar_n, nubar
+
+    def spectrum(self, u, kmax=None):
+        """Shell energy spectrum E[0..kmax] as a CUDA float64 tensor (ins_spectrum)."""
+        self._check_u(u)
+        kmax = min(self.n) // 2 if kmax is None else int(kmax)
+        E = torch.empty(kmax + 1, dtype=torch.float64, device=self.device)
+        self._sync_stream()
+        check(lib().ins_spectrum(self._h, _ptr(u), _ptr(E), kmax), "ins_spectrum")
+        return E
 
     def cfl_dt(self, u, cfl, out=None):
         self._check_u(u)
