@@ -131,11 +131,17 @@ def convection_vjp(g, u, w):
     return ab + tb
 
 
-def F_vjp(g, u, w):
-    """Pullback of F(u) = C(u) + nu diffusion(u) + f, and d<w,F>/dnu = <w, diffusion(u)>."""
+def F_vjp(g, u, w, closure=None):
+    """Pullback of F(u) = C(u) + nu diffusion(u) + f (+ m(u)), and d<w,F>/dnu = <w, diffusion(u)>.
+
+    With a closure (``oracle.closure.Closure``) also returns its per-layer (dW, db)."""
     ubar = convection_vjp(g, u, w) + g.nu * diffusion_T(g, w)
     nubar = float(np.sum(w * op.diffusion(g, u)))
-    return ubar, nubar
+    if closure is None:
+        return ubar, nubar
+    from . import closure as cl
+    cu, grads = cl.backward(closure.params, u, w, closure.quantize)
+    return ubar + cu, nubar, grads
 
 
 def project_T(g, kbar):
@@ -146,8 +152,9 @@ def project_T(g, kbar):
     return w
 
 
-def rk4_step_vjp(g, u0, dt, ybar):
-    """Pullback of one RK4 step u0 -> u1 (dt frozen): returns (u0bar, nubar).
+def rk4_step_vjp(g, u0, dt, ybar, closure=None):
+    """Pullback of one RK4 step u0 -> u1 (dt frozen): returns (u0bar, nubar), and with a
+    closure also the closure's per-layer (dW, db) summed over the four stages.
 
     Forward (``timestep.rk4_step``): k_s = P F(u_s), u_s = u0 + dt a_{s,s-1} k_{s-1},
     u1 = u0 + dt sum_s b_s k_s. Reverse: kbar_s = dt b_s ybar + dt a_{s+1,s} ubar_{s+1},
@@ -159,16 +166,23 @@ def rk4_step_vjp(g, u0, dt, ybar):
     us = [u0]
     for s in range(3):
         from .timestep import stage_derivative
-        k = stage_derivative(g, us[s])
+        k = stage_derivative(g, us[s], closure)
         us.append(u0 + dt * RK4_A[s + 1] * k)
     u0bar = ybar.copy()
     nubar = 0.0
+    wgrads = None
     kbar = [dt * RK4_B[s] * ybar for s in range(4)]
     for s in range(3, -1, -1):
         w = project_T(g, kbar[s])
-        ubar_s, nb = F_vjp(g, us[s], w)
+        if closure is None:
+            ubar_s, nb = F_vjp(g, us[s], w)
+        else:
+            ubar_s, nb, gr = F_vjp(g, us[s], w, closure)
+            wgrads = gr if wgrads is None else [(a[0] + b[0], a[1] + b[1]) for a, b in zip(wgrads, gr)]
         nubar += nb
         u0bar = u0bar + ubar_s
         if s > 0:
             kbar[s - 1] = kbar[s - 1] + dt * RK4_A[s] * ubar_s
+    if closure is not None:
+        return u0bar, nubar, wgrads
     return u0bar, nubar
