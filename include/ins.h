@@ -195,6 +195,51 @@ ins_status ins_check_finite(ins_grid* g);
 ins_status ins_cfl_dt_noalloc(const ins_grid_desc* desc, const void* u, double cfl, double* dt_dev,
                               void* stream);
 
+/* ---------------------------------------------------------------- CNN closure
+ * A learned closure term m(u) inside F (Sec. 4: neural-network closure models in the
+ * right-hand side, trained a posteriori through the unrolled solver). Architecture
+ * (a choice; the paper names none): 4 circular 3x3x3 convolutions 3->32->32->32->3,
+ * GELU (erf form) after the first three; input channels u^x, u^y, u^z at one storage
+ * index, output channel a added to F^a. BF16 weights and activations, FP32 accumulation
+ * on the tensor cores (tcgen05); the weight gradient runs on CUDA cores (FP32).
+ * Grids: 3-D, periodic, nx % 8 == 0, ny % 16 == 0, nz >= 2 (else INS_ERR_UNSUPPORTED). */
+typedef struct ins_closure ins_closure;
+
+/* Allocate a closure's workspace for grid g (weights blobs, activations). */
+ins_status ins_closure_create(ins_grid* g, ins_closure** out);
+ins_status ins_closure_destroy(ins_closure* c);
+
+/* Weights W[l]: DEVICE float [27][cin][cout] (tap t = 9(dz+1) + 3(dy+1) + (dx+1),
+ * y[co](v) = b[co] + sum_t sum_ci W[t][ci][co] x[ci](v + (dx, dy, dz))), rounded to BF16
+ * here; biases b[l]: DEVICE float [cout], read at every use. Call again after every
+ * weight update. */
+ins_status ins_closure_set_params(ins_closure* c, const float* const W[4], const float* const b[4]);
+
+/* m = closure(u): u and m DEVICE, dim fields of the grid dtype. save != 0 keeps the
+ * pre-activations for a following ins_closure_bwd. */
+ins_status ins_closure_fwd(ins_grid* g, ins_closure* c, const void* u, void* m, int save);
+
+/* ubar_accum += (dm/du)^T mbar; dW[l] += dL/dW[l], db[l] += dL/db[l] (DEVICE float arrays
+ * shaped like W and b; arrays or entries may be NULL). Uses the activations of the last
+ * ins_closure_fwd with save != 0. */
+ins_status ins_closure_bwd(ins_grid* g, ins_closure* c, const void* mbar, void* ubar_accum, float* const dW[4],
+                           float* const db[4]);
+
+/* Where ins_step_vjp accumulates the closure's weight and bias gradients (NULL: not kept). */
+ins_status ins_closure_set_grads(ins_closure* c, float* const dW[4], float* const db[4]);
+
+/* Copies (synchronously) the saved BF16 input of layer l (channels-last, 8 channels for
+ * l = 0, else 32) and its FP32 pre-activation (32 channels, l < 3) into DEVICE buffers
+ * given by the caller (either may be NULL), for inspection. */
+ins_status ins_closure_saved(ins_closure* c, int layer, void* x_bf16, float* z);
+
+/* INS_ERR_TIMEOUT if a bounded tensor-core wait gave up since the last check (synchronous). */
+ins_status ins_closure_check(ins_closure* c);
+
+/* Attach a closure to g (NULL detaches): ins_rhs, ins_step and ins_step_vjp then use
+ * F(u) + m(u). The first attachment allocates one velocity field for m. */
+ins_status ins_set_closure(ins_grid* g, ins_closure* c);
+
 /* ---------------------------------------------------------------- measurement
  * Tracing support (the paper describes none; these calls serve benchmarking). */
 

@@ -17,8 +17,8 @@ architecture. Reading taken (a choice of this build):
   biases; products of BF16 values are exact here and sums are FP64 (the GPU
   accumulates in FP32);
 * the backward pass treats the BF16 roundings as identity and rounds each
-  layer's incoming gradient to BF16 before the transposed convolution, as the
-  GPU does.
+  layer's incoming gradient to BF16; that rounded gradient feeds the transposed
+  convolution, the weight gradient and the bias gradient alike.
 
 ``quantize=False`` switches every rounding off (a smooth FP64 network for
 finite-difference pins).
@@ -126,7 +126,7 @@ def backward(params, u, mbar, quantize=True):
         if l < len(params) - 1:
             g = g * gelu_grad(z)
         gq = q(g)
-        grads[l] = (conv_wgrad(x, gq), np.sum(g, axis=(1, 2, 3)))
+        grads[l] = (conv_wgrad(x, gq), np.sum(gq, axis=(1, 2, 3)))
         g = conv_T(gq, q(W))
     return g, grads
 

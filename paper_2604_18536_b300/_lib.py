@@ -68,6 +68,15 @@ SIGNATURES = {
     "ins_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "ins_profile_read": (_c.c_int, [_vp, _c.POINTER(KernelStat), _c.c_int, _c.POINTER(_c.c_int)]),
     "ins_measure_fma_rate": (_c.c_int, [_c.c_int, _vp, _dp]),
+    "ins_closure_create": (_c.c_int, [_vp, _c.POINTER(_vp)]),
+    "ins_closure_destroy": (_c.c_int, [_vp]),
+    "ins_closure_set_params": (_c.c_int, [_vp, _c.POINTER(_vp), _c.POINTER(_vp)]),
+    "ins_closure_fwd": (_c.c_int, [_vp, _vp, _vp, _vp, _c.c_int]),
+    "ins_closure_bwd": (_c.c_int, [_vp, _vp, _vp, _vp, _c.POINTER(_vp), _c.POINTER(_vp)]),
+    "ins_closure_set_grads": (_c.c_int, [_vp, _c.POINTER(_vp), _c.POINTER(_vp)]),
+    "ins_closure_saved": (_c.c_int, [_vp, _c.c_int, _vp, _vp]),
+    "ins_closure_check": (_c.c_int, [_vp]),
+    "ins_set_closure": (_c.c_int, [_vp, _vp]),
     "ins_cfl_dt_noalloc": (_c.c_int, [_c.POINTER(GridDesc), _vp, _c.c_double, _vp, _vp]),
 }
 

@@ -42,7 +42,8 @@ struct AdjCoef {
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_adj_rhs(AdjCoef<T> c, const T* __restrict__ u, const T* __restrict__ w,
                                                  const T* __restrict__ ybar, T* __restrict__ ubar0,
-                                                 T* __restrict__ kb, double* __restrict__ nu_part) {
+                                                 T* __restrict__ kb, double* __restrict__ nu_part,
+                                                 const T* __restrict__ extra) {
     const int nx = c.nx, ny = c.ny, nz = c.nz;
     const long N = (long)nx * ny * nz;
     const int i = blockIdx.x * 32 + threadIdx.x;
@@ -91,7 +92,8 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjCoef<T> c, const T* __restri
                 acc = fma(c.c2[a], fma(S0, wb[Jpa] - wb[J], S1 * (wb[Jpamb] - wb[Jmb])), acc);
                 lap = fma(c.l2[b], wabp + wabm - (T)2 * wa0, lap);
             }
-            const T ubs = fma(c.nu, lap, acc);
+            T ubs = fma(c.nu, lap, acc);
+            if (extra) ubs += extra[a * N + J];   // closure pullback J_m^T w
             nup += (double)ua0 * (double)lap;
             const long e = a * N + J;
             ubar0[e] = ubar0[e] + ubs;

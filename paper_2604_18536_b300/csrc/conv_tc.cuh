@@ -1,0 +1,371 @@
+// 3x3x3 circular convolutions of the CNN closure on the 5th-generation tensor
+// cores (tcgen05, kind::f16: BF16 operands, FP32 accumulation in TMEM).
+//
+// Implicit GEMM without an im2col buffer. One MMA tile = 128 output voxels
+// (8 in x by 16 in y of one z plane) by N output channels. Input planes (with
+// a one-voxel periodic halo) are staged in shared memory as 16-byte entries of
+// 8 channels, laid out [channel group][plane slot][y (18)][x (10)]. For tap
+// (dx, dy, dz) the A operand of the MMA is a shared-memory descriptor pointing
+// at entry (slot(z+dz), 1+dy, 1+dx): its 8-row core matrices are 8 consecutive
+// x voxels (16 B apart) and consecutive core matrices are consecutive y rows
+// (SBO = one padded row, 160 B); the two core matrices of a K=16 step are two
+// channel groups (LBO = one channel-group block). The B operand is the tap's
+// weight block [N rows x K channels], K-major. D (128 lanes x N FP32 columns)
+// lives in TMEM; the epilogue reads it with tcgen05.ld (one voxel per thread).
+//
+// A CTA of 128 threads owns one 8 x 16 column of one z chunk. Planes go through
+// a 4-slot ring: while the MMAs of plane z read slots z-1, z, z+1, the loads of
+// plane z+2 are already in flight (cp.async). Thread 0 issues the MMAs and
+// commits them to an mbarrier; every wait is bounded and reports through an
+// error flag instead of hanging.
+//
+// The same kernel runs the backward data gradient (a convolution with the taps
+// reversed and the channel roles swapped) with a different epilogue.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace ins {
+
+constexpr int CV_TX = 8, CV_TY = 16;           // output tile: 8 x 16 voxels = 128 rows
+constexpr int CV_PX = CV_TX + 2, CV_PY = CV_TY + 2;
+constexpr int CV_ROW = CV_PX * 16;              // bytes per padded row of 16-byte entries
+constexpr int CV_PLANE = CV_PY * CV_ROW;        // bytes per staged plane of one channel group
+constexpr int CV_SLOTS = 4;
+constexpr int CV_CGS = CV_SLOTS * CV_PLANE;     // bytes per channel group (all slots)
+constexpr int CV_THREADS = 128;
+constexpr long CV_SPIN = 1L << 24;              // bound on every mbarrier wait
+
+enum ConvEpi {
+    EPI_GELU = 0,      // y = bf16(gelu(acc + b)) channels-last; z = acc + b (FP32) if zout
+    EPI_OUT = 1,       // out_T[c][v] = acc + b for c < nreal (the closure output m, SoA)
+    EPI_DGELU = 2,     // y = bf16(acc * gelu'(zin)) channels-last (data gradient through GELU)
+    EPI_ACCUM = 3      // out_T[c][v] += acc for c < nreal (data gradient of the input, SoA)
+};
+
+struct ConvArgs {
+    const void* x;          // input activations, bf16 channels-last [vox][8 * cin_g]
+    const void* wblob;      // packed weights (bf16), CV taps x N x (8 * kg) in the B layout
+    const float* bias;      // [N] (EPI_GELU / EPI_OUT), may be null
+    void* y;                // EPI_GELU / EPI_DGELU: bf16 channels-last [vox][N]
+    float* zout;            // EPI_GELU: FP32 pre-activation [vox][N] or null
+    const float* zin;       // EPI_DGELU: FP32 pre-activation of the layer below [vox][N]
+    void* out;              // EPI_OUT / EPI_ACCUM: SoA field (float or double) [nreal][vox]
+    int out_f64;            // out holds doubles
+    int nreal;              // real output channels for EPI_OUT / EPI_ACCUM
+    int nx, ny, nz;         // grid (periodic in all directions)
+    int zchunk;
+    unsigned int* err;      // bit 1: an mbarrier wait gave up
+};
+
+__device__ __forceinline__ uint32_t cv_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: no swizzle, K-major canonical layout.
+__device__ __forceinline__ uint64_t cv_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void cv_cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ float cv_gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752440f)); }
+__device__ __forceinline__ float cv_gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752440f)) + z * 0.39894228040143267794f * expf(-0.5f * z * z);
+}
+
+// Stage plane gz (periodic) of the column into ring slot `slot` with cp.async.
+template <int CG>
+__device__ __forceinline__ void cv_load_plane(const ConvArgs& a, unsigned char* sA, int slot, int gz, int x0, int y0) {
+    const int nx = a.nx, ny = a.ny;
+    const unsigned char* xb = reinterpret_cast<const unsigned char*>(a.x);
+    constexpr int VB = CG * 16;   // bytes per voxel
+    for (int e = threadIdx.x; e < CG * CV_PY * CV_PX; e += CV_THREADS) {
+        const int cg = e / (CV_PY * CV_PX);
+        const int r = e - cg * (CV_PY * CV_PX);
+        const int yy = r / CV_PX, xx = r - yy * CV_PX;
+        int gx = x0 - 1 + xx, gy = y0 - 1 + yy;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+        const long vox = ((long)gz * ny + gy) * nx + gx;
+        cv_cp_async16(cv_smem(sA + cg * CV_CGS + slot * CV_PLANE + yy * CV_ROW + xx * 16), xb + vox * VB + cg * 16);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// CG: channel groups of 8 in the input (1 or 4); N: MMA N (16 or 32); KG: K channel groups in
+// the weight blob (2 when CG == 1, the second group being zero; else CG).
+template <int CG, int N, int EPI>
+__global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
+    constexpr int KG = CG == 1 ? 2 : CG;
+    constexpr int KSTEPS = KG / 2;                   // MMAs (K = 16) per tap
+    constexpr int TAPB = N * KG * 16;                // weight bytes per tap
+    constexpr int SBO_B = KG * 128;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                        // CG * CV_CGS bytes
+    unsigned char* sB = smem + CG * CV_CGS;          // 27 * TAPB bytes
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x0 = blockIdx.x * CV_TX, y0 = blockIdx.y * CV_TY;
+    const int zb = blockIdx.z * a.zchunk, ze = min(zb + a.zchunk, nz);
+    const long nvox = (long)nx * ny * nz;
+
+    // weights: 27 taps of the B layout, copied as-is
+    {
+        const unsigned char* wb = reinterpret_cast<const unsigned char*>(a.wblob);
+        for (int e = tid; e < 27 * TAPB / 16; e += CV_THREADS) cv_cp_async16(cv_smem(sB + e * 16), wb + e * 16);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cv_smem(&tbase)),
+                     "r"(N < 32 ? 32 : N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&mbar)));
+    // prologue planes zb-1, zb, zb+1 into slots of (z mod 4)
+    auto slot_of = [](int z) { return ((z % CV_SLOTS) + CV_SLOTS) % CV_SLOTS; };
+    auto wrapz = [nz](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
+    cv_load_plane<CG>(a, sA, slot_of(zb - 1), wrapz(zb - 1), x0, y0);
+    cv_load_plane<CG>(a, sA, slot_of(zb), wrapz(zb), x0, y0);
+    cv_load_plane<CG>(a, sA, slot_of(zb + 1), wrapz(zb + 1), x0, y0);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tbase;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+    uint32_t phase = 0;
+    bool alive = true;
+    // this thread's output voxel within the tile (D row = TMEM lane)
+    const int m = warp * 32 + lane;
+    const int vx = x0 + (m & 7), vy = y0 + (m >> 3);
+    const bool inside = vx < nx && vy < ny;
+
+    for (int z = zb; z < ze && alive; ++z) {
+        // prefetch plane z+2 (needed by the next tile) into the free slot
+        const bool pre = z + 1 < ze;
+        if (pre) cv_load_plane<CG>(a, sA, slot_of(z + 2), wrapz(z + 2), x0, y0);
+        if (tid == 0) {
+            int first = 1;
+            for (int t = 0; t < 27; ++t) {
+                const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                const uint32_t abase = cv_smem(sA) + slot_of(z + dz) * CV_PLANE + (1 + dy) * CV_ROW + (1 + dx) * 16;
+                const uint32_t bbase = cv_smem(sB) + t * TAPB;
+#pragma unroll
+                for (int s = 0; s < KSTEPS; ++s) {
+                    const uint64_t ad = cv_desc(abase + 2 * s * CV_CGS, CG == 1 ? 0 : CV_CGS, CV_ROW);
+                    const uint64_t bd = cv_desc(bbase + 2 * s * 128, 128, SBO_B);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0 : 1));
+                    first = 0;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             cv_smem(&mbar))
+                         : "memory");
+        }
+        // wait for the MMAs of this tile (bounded)
+        uint32_t done = 0;
+        for (long it = 0; it < CV_SPIN && !done; ++it) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(cv_smem(&mbar)), "r"(phase)
+                : "memory");
+        }
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!done) {
+            if (tid == 0) atomicOr(a.err, 2u);
+            alive = false;
+        }
+        if (__syncthreads_or(!alive)) {
+            alive = false;
+            break;
+        }
+        // epilogue: D row m -> voxel (vx, vy, z)
+        uint32_t r[32];
+        {
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            if (N == 32) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+            } else {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+        if (inside) {
+            const long v = ((long)z * ny + vy) * nx + vx;
+            if (EPI == EPI_GELU) {
+                __align__(16) __nv_bfloat16 o[N];
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    const float zz = __uint_as_float(r[c]) + (a.bias ? a.bias[c] : 0.f);
+                    if (a.zout) a.zout[v * N + c] = zz;
+                    o[c] = __float2bfloat16_rn(cv_gelu(zz));
+                }
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N);
+#pragma unroll
+                for (int q = 0; q < N / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
+            } else if (EPI == EPI_DGELU) {
+                __align__(16) __nv_bfloat16 o[N];
+#pragma unroll
+                for (int c = 0; c < N; ++c)
+                    o[c] = __float2bfloat16_rn(__uint_as_float(r[c]) * cv_gelu_grad(a.zin[v * N + c]));
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N);
+#pragma unroll
+                for (int q = 0; q < N / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
+            } else {
+                for (int c = 0; c < a.nreal; ++c) {
+                    float val = __uint_as_float(r[c]);
+                    if (EPI == EPI_OUT && a.bias) val += a.bias[c];
+                    if (a.out_f64) {
+                        double* o = reinterpret_cast<double*>(a.out) + c * nvox + v;
+                        *o = EPI == EPI_ACCUM ? *o + (double)val : (double)val;
+                    } else {
+                        float* o = reinterpret_cast<float*>(a.out) + c * nvox + v;
+                        *o = EPI == EPI_ACCUM ? *o + val : val;
+                    }
+                }
+            }
+        }
+        // all TMEM reads of this tile are done before the next tile's MMAs overwrite D;
+        // the prefetched plane must have landed before the next tile reads it
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(N < 32 ? 32 : N));
+}
+
+// Pack weights W[27][cin][cout] (FP32 master copy) into the B layout of k_conv3d_tc as BF16.
+// forward: row n = co, channel k = ci, tap t; data gradient: row n = ci, channel k = co, tap 26 - t.
+__global__ void k_pack_weights(const float* __restrict__ W, int cin, int cout, int N, int KG, int transpose,
+                               __nv_bfloat16* __restrict__ blob) {
+    const int K = 8 * KG;
+    const int total = 27 * N * K;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int t = e / (N * K);
+        const int rem = e - t * N * K;
+        const int n = rem / K, k = rem - n * K;
+        float v = 0.f;
+        if (!transpose) {
+            if (n < cout && k < cin) v = W[((long)t * cin + k) * cout + n];
+        } else {
+            if (n < cin && k < cout) v = W[((long)(26 - t) * cin + n) * cout + k];
+        }
+        const long off = (long)t * N * K + (n / 8) * (KG * 64) + (k / 8) * 64 + (n % 8) * 8 + (k % 8);
+        blob[off] = __float2bfloat16_rn(v);
+    }
+}
+
+// Velocity (SoA, float or double) -> BF16 channels-last with 8 channels (3 used, 5 zero).
+template <typename T>
+__global__ void k_pack_input(const T* __restrict__ u, long nvox, __nv_bfloat16* __restrict__ x) {
+    for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < nvox; v += (long)gridDim.x * blockDim.x) {
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16_rn(c < 3 ? (float)u[c * nvox + v] : 0.f);
+        reinterpret_cast<uint4*>(x)[v] = *reinterpret_cast<const uint4*>(o);
+    }
+}
+
+// Weight and bias gradients on CUDA cores (FP32 accumulation):
+//   dW[t][ci][co] += sum_v X[v + o_t][ci] dY[v][co],  db[co] += sum_v dY[v][co] (tap 13 blocks only).
+// X, dY: BF16 channels-last with CX and CY channels (cin, cout real). Grid (27, nblk), 256 threads;
+// each block sweeps a strided set of 64-voxel chunks and adds its partial sums with one atomic per output.
+template <int CX, int CY>
+__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
+                                               int nx, int ny, int nz, int cin, int cout, float* __restrict__ dW,
+                                               float* __restrict__ db) {
+    constexpr int V = 64;
+    constexpr int PER = (CX * CY + 255) / 256;
+    __shared__ float xs[V][CX + 1];
+    __shared__ float ys[V][CY + 1];
+    const int t = blockIdx.x;
+    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+    const long nvox = (long)nx * ny * nz;
+    float acc[PER], bacc = 0.f;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) acc[q] = 0.f;
+    for (long c0 = (long)blockIdx.y * V; c0 < nvox; c0 += (long)gridDim.y * V) {
+        for (int e = threadIdx.x; e < V * CX; e += 256) {
+            const int vv = e / CX, ch = e - vv * CX;
+            const long v = c0 + vv;
+            float val = 0.f;
+            if (v < nvox) {
+                int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long)nx * ny));
+                x += dx; y += dy; z += dz;
+                x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+                z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+                val = __bfloat162float(X[(((long)z * ny + y) * nx + x) * CX + ch]);
+            }
+            xs[vv][ch] = val;
+        }
+        for (int e = threadIdx.x; e < V * CY; e += 256) {
+            const int vv = e / CY, ch = e - vv * CY;
+            const long v = c0 + vv;
+            ys[vv][ch] = v < nvox ? __bfloat162float(dY[v * CY + ch]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int o = threadIdx.x + q * 256;
+            if (o < CX * CY) {
+                const int ci = o / CY, co = o - ci * CY;
+                float s = 0.f;
+                for (int vv = 0; vv < V; ++vv) s = fmaf(xs[vv][ci], ys[vv][co], s);
+                acc[q] += s;
+            }
+        }
+        if (t == 13 && threadIdx.x < CY) {
+            float s = 0.f;
+            for (int vv = 0; vv < V; ++vv) s += ys[vv][threadIdx.x];
+            bacc += s;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int o = threadIdx.x + q * 256;
+        if (o < CX * CY) {
+            const int ci = o / CY, co = o - ci * CY;
+            if (ci < cin && co < cout) atomicAdd(&dW[((long)t * cin + ci) * cout + co], acc[q]);
+        }
+    }
+    if (t == 13 && db && threadIdx.x < cout) atomicAdd(&db[threadIdx.x], bacc);
+}
+
+}  // namespace ins

@@ -245,9 +245,11 @@ __device__ __forceinline__ void plane_commit(const PlaneMap<WALL>& pm, Plane<T> 
 }
 
 // F (dim fields, may be null) and r = D F. Grid: (ceil(nx/32), ceil(ny/8), ceil(nz/kchunk)), block (32, 8).
+// m (dim fields, may be null): a closure term added to F on every face, including the halo
+// faces the divergence reads.
 template <typename T, int DIM, bool WALL>
 __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restrict__ u, T* __restrict__ F,
-                                                 T* __restrict__ r, int kchunk) {
+                                                 T* __restrict__ r, int kchunk, const T* __restrict__ mc) {
     __shared__ T su[3][DIM][RSPL];
     __shared__ T sFx[RBY][RBX + 1];
     __shared__ T sFy[RBY + 1][RBX];
@@ -276,13 +278,27 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
         plane_commit<T, DIM, WALL>(pm, su[0], v);
         __syncthreads();
         CPlane<T> o = su[0];
-        const T fx = eval_Fx<T, 2, WALL>(c, yr, o, o, o, c0);
+        const int ic = i < nx ? i : nx - 1;
+        const long am = (long)(j < ny ? j : ny - 1) * nx + ic;
+        T fx = eval_Fx<T, 2, WALL>(c, yr, o, o, o, c0);
         T fy = eval_Fy<T, 2, WALL>(c, yr, o, o, o, c0);
+        if (mc) {
+            fx += mc[am];
+            fy += mc[N + am];
+        }
         if (WALL && j == ny - 1) fy = (T)0;
         sFx[ty][tx + 1] = fx;
         sFy[ty + 1][tx] = fy;
-        if (hy) sFy[0][tx] = hy_wall ? (T)0 : eval_Fy<T, 2, WALL>(c, yrow<T, WALL>(c, jhy), o, o, o, c0hy);
-        if (hx) sFx[tx][0] = eval_Fx<T, 2, WALL>(c, yrow<T, WALL>(c, jhx), o, o, o, c0hx);
+        if (hy) {
+            T h = hy_wall ? (T)0 : eval_Fy<T, 2, WALL>(c, yrow<T, WALL>(c, jhy), o, o, o, c0hy);
+            if (mc && !hy_wall) h += mc[N + (long)jhy * nx + ic];
+            sFy[0][tx] = h;
+        }
+        if (hx) {
+            T h = eval_Fx<T, 2, WALL>(c, yrow<T, WALL>(c, jhx), o, o, o, c0hx);
+            if (mc) h += mc[(long)jhx * nx + (i0 - 1 < 0 ? nx - 1 : i0 - 1)];
+            sFx[tx][0] = h;
+        }
         __syncthreads();
         if (inside) {
             const long a = (long)j * nx + i;
@@ -306,7 +322,11 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
         plane_commit<T, DIM, WALL>(pm, su[sp], v);
         plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(kb + 1) * plane, v);
         __syncthreads();
+        const int ic = i < nx ? i : nx - 1;
+        const int jc = j < ny ? j : ny - 1;
+        const int ihm = i0 - 1 < 0 ? nx - 1 : i0 - 1;
         T fz_prev = eval_Fz<T, WALL>(c, yr, su[sm], su[so], su[sp], c0);
+        if (mc) fz_prev += mc[2 * N + (long)wrapz(kb - 1) * plane + (long)jc * nx + ic];
         __syncthreads();
         plane_commit<T, DIM, WALL>(pm, su[sm], v);
         {
@@ -322,14 +342,28 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
             CPlane<T> m = su[sm];
             CPlane<T> o = su[so];
             CPlane<T> p = su[sp];
-            const T fx = eval_Fx<T, 3, WALL>(c, yr, m, o, p, c0);
+            T fx = eval_Fx<T, 3, WALL>(c, yr, m, o, p, c0);
             T fy = eval_Fy<T, 3, WALL>(c, yr, m, o, p, c0);
+            T fz = eval_Fz<T, WALL>(c, yr, m, o, p, c0);
+            if (mc) {
+                const long am = (long)k * plane + (long)jc * nx + ic;
+                fx += mc[am];
+                fy += mc[N + am];
+                fz += mc[2 * N + am];
+            }
             if (WALL && j == ny - 1) fy = (T)0;
-            const T fz = eval_Fz<T, WALL>(c, yr, m, o, p, c0);
             sFx[ty][tx + 1] = fx;
             sFy[ty + 1][tx] = fy;
-            if (hy) sFy[0][tx] = hy_wall ? (T)0 : eval_Fy<T, 3, WALL>(c, yrow<T, WALL>(c, jhy), m, o, p, c0hy);
-            if (hx) sFx[tx][0] = eval_Fx<T, 3, WALL>(c, yrow<T, WALL>(c, jhx), m, o, p, c0hx);
+            if (hy) {
+                T h = hy_wall ? (T)0 : eval_Fy<T, 3, WALL>(c, yrow<T, WALL>(c, jhy), m, o, p, c0hy);
+                if (mc && !hy_wall) h += mc[N + (long)k * plane + (long)jhy * nx + ic];
+                sFy[0][tx] = h;
+            }
+            if (hx) {
+                T h = eval_Fx<T, 3, WALL>(c, yrow<T, WALL>(c, jhx), m, o, p, c0hx);
+                if (mc) h += mc[(long)k * plane + (long)jhx * nx + ihm];
+                sFx[tx][0] = h;
+            }
             __syncthreads();
             if (inside) {
                 const long a = (long)k * plane + (long)j * nx + i;

@@ -209,6 +209,18 @@ class Grid:
             check(st, "ins_diag")
         return {"ke": out[0], "max_div": out[1], "max_u_over_h": out[2], "nonfinite": int(out[3])}
 
+    @property
+    def N(self):
+        n = 1
+        for v in self.n:
+            n *= v
+        return n
+
+    def set_closure(self, closure):
+        """Attach a closure (F(u) + m(u) in rhs, step, step_vjp); None detaches."""
+        check(lib().ins_set_closure(self._h, closure._h if closure is not None else None), "ins_set_closure")
+        self._closure = closure
+
     # ------------------------------------------------------------ measurement
     def launch_count(self):
         n = ctypes.c_ulonglong()
