@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtypes", default="f64,f32")
+    ap.add_argument("--no-closure", action="store_true")
     return ap.parse_args()
 
 
@@ -300,11 +301,64 @@ def run_ours(args):
             line["fp32"] = {k: f[k] for k in ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
                                                "step_hbm_frac", "kernels", "clocks", "adjoint") if k in f}
             line["fp32"]["speedup_vs_fp64"] = f["value"] / prim["value"]
+        if not args.no_closure:
+            line["closure"] = bench_closure()
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(steps=1)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ closure (tensor cores)
+def bench_closure(n=64, reps=10):
+    """CNN closure forward and backward at the LES size n^3 (FP32 grid, BF16 tensor cores)."""
+    import torch
+    from paper_2604_18536_b300 import inputs
+    from paper_2604_18536_b300.closure import Closure, init_params, SHAPES
+    from paper_2604_18536_b300.solver import Grid
+    g = Grid(inputs.periodic_box(n, 3), ["periodic"] * 3, 1.0 / 2000, dtype=torch.float32)
+    c = Closure(g)
+    W, b = init_params(0, 1.0)
+    c.set_params(W, b)
+    u = torch.tensor(inputs.random_field((3, n, n, n), 1), dtype=torch.float32, device="cuda")
+    m = g.new_velocity()
+    ub = g.new_velocity()
+    dW = [torch.zeros_like(w) for w in W]
+    db = [torch.zeros_like(x) for x in b]
+    c.forward(u, m, save=True)
+    c.backward(m, ub, dW, db)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    g.profile(True)
+    e[0].record(st)
+    for _ in range(reps):
+        c.forward(u, m, save=True)
+    e[1].record(st)
+    for _ in range(reps):
+        c.backward(m, ub, dW, db)
+    e[2].record(st)
+    torch.cuda.synchronize()
+    prof = g.profile_read()
+    g.profile(False)
+    c.check()
+    N = n ** 3
+    flops_fwd = sum(2.0 * N * 27 * ci * co for ci, co in SHAPES)
+    conv = prof.get("conv3d_tc", (1, 0.0))
+    # conv launches per rep: 4 forward + 4 backward (data gradient) with the same algorithmic flops
+    conv_s = conv[1] / 1e3 / reps / 2
+    peaks = measured_peaks()
+    pk = peaks.get("bf16_tflops", 1800.0)
+    res = {"n": n, "fwd_ms": e[0].elapsed_time(e[1]) / reps, "bwd_ms": e[1].elapsed_time(e[2]) / reps,
+           "flops_fwd": flops_fwd, "conv_tflops": flops_fwd / conv_s / 1e12,
+           "roofline": {"bound": "tensor", "kernel": "conv3d_tc", "achieved": flops_fwd / conv_s / 1e12,
+                        "peak": pk, "unit": "TFLOP/s", "frac": flops_fwd / conv_s / 1e12 / pk, "traffic": None,
+                        "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)"},
+           "kernels": {k: {"launches": v[0], "avg_us": round(v[1] / v[0] * 1e3, 2)} for k, v in prof.items()}}
+    c.close()
+    g.close()
+    return res
 
 
 # ------------------------------------------------------------------ oracle on the host

@@ -303,68 +303,88 @@ __global__ void k_pack_input(const T* __restrict__ u, long nvox, __nv_bfloat16* 
 
 // Weight and bias gradients on CUDA cores (FP32 accumulation):
 //   dW[t][ci][co] += sum_v X[v + o_t][ci] dY[v][co],  db[co] += sum_v dY[v][co] (tap 13 blocks only).
-// X, dY: BF16 channels-last with CX and CY channels (cin, cout real). Grid (27, nblk), 256 threads;
-// each block sweeps a strided set of 64-voxel chunks and adds its partial sums with one atomic per output.
+// X, dY: BF16 channels-last with CX and CY channels (cin, cout real). Grid (27, nblk), 256 threads.
+// A block stages 128 voxels of the shifted X and of dY in shared memory (FP32); the threads
+// form groups of (CX/4)(CY/4), each thread accumulating a 4 x 4 tile of (ci, co) over the
+// voxels of its group (16 FMAs per two float4 shared loads). Partial sums go out with one
+// atomic per output per group.
 template <int CX, int CY>
 __global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
                                                int nx, int ny, int nz, int cin, int cout, float* __restrict__ dW,
                                                float* __restrict__ db) {
-    constexpr int V = 64;
-    constexpr int PER = (CX * CY + 255) / 256;
-    __shared__ float xs[V][CX + 1];
-    __shared__ float ys[V][CY + 1];
+    constexpr int V = 128;
+    constexpr int TPG = (CX / 4) * (CY / 4);     // threads per group
+    constexpr int NG = 256 / TPG;                // groups
+    constexpr int VG = V / NG;                   // voxels per group and chunk
+    __shared__ __align__(16) float xs[V][CX + 4];
+    __shared__ __align__(16) float ys[V][CY + 4];
     const int t = blockIdx.x;
     const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
     const long nvox = (long)nx * ny * nz;
-    float acc[PER], bacc = 0.f;
+    const int grp = threadIdx.x / TPG, q = threadIdx.x % TPG;
+    const int ciq = q / (CY / 4), coq = q % (CY / 4);
+    float acc[4][4];
 #pragma unroll
-    for (int q = 0; q < PER; ++q) acc[q] = 0.f;
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    float bacc = 0.f;
     for (long c0 = (long)blockIdx.y * V; c0 < nvox; c0 += (long)gridDim.y * V) {
-        for (int e = threadIdx.x; e < V * CX; e += 256) {
-            const int vv = e / CX, ch = e - vv * CX;
+        for (int e = threadIdx.x; e < V * (CX / 8); e += 256) {
+            const int vv = e / (CX / 8), cg = e - vv * (CX / 8);
             const long v = c0 + vv;
-            float val = 0.f;
+            float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (v < nvox) {
                 int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long)nx * ny));
                 x += dx; y += dy; z += dz;
                 x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
                 y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
                 z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-                val = __bfloat162float(X[(((long)z * ny + y) * nx + x) * CX + ch]);
+                const uint4 raw = *reinterpret_cast<const uint4*>(X + (((long)z * ny + y) * nx + x) * CX + cg * 8);
+                const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&raw);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(h[k]);
             }
-            xs[vv][ch] = val;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) xs[vv][cg * 8 + k] = f[k];
         }
-        for (int e = threadIdx.x; e < V * CY; e += 256) {
-            const int vv = e / CY, ch = e - vv * CY;
+        for (int e = threadIdx.x; e < V * (CY / 8); e += 256) {
+            const int vv = e / (CY / 8), cg = e - vv * (CY / 8);
             const long v = c0 + vv;
-            ys[vv][ch] = v < nvox ? __bfloat162float(dY[v * CY + ch]) : 0.f;
+            float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (v < nvox) {
+                const uint4 raw = *reinterpret_cast<const uint4*>(dY + v * CY + cg * 8);
+                const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&raw);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(h[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ys[vv][cg * 8 + k] = f[k];
         }
         __syncthreads();
+        for (int vv = grp * VG; vv < (grp + 1) * VG; ++vv) {
+            const float4 xv = *reinterpret_cast<const float4*>(&xs[vv][4 * ciq]);
+            const float4 yv = *reinterpret_cast<const float4*>(&ys[vv][4 * coq]);
+            const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int o = threadIdx.x + q * 256;
-            if (o < CX * CY) {
-                const int ci = o / CY, co = o - ci * CY;
-                float s = 0.f;
-                for (int vv = 0; vv < V; ++vv) s = fmaf(xs[vv][ci], ys[vv][co], s);
-                acc[q] += s;
-            }
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], ya[b], acc[a][b]);
         }
         if (t == 13 && threadIdx.x < CY) {
-            float s = 0.f;
-            for (int vv = 0; vv < V; ++vv) s += ys[vv][threadIdx.x];
-            bacc += s;
+            float sacc = 0.f;
+            for (int vv = 0; vv < V; ++vv) sacc += ys[vv][threadIdx.x];
+            bacc += sacc;
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int o = threadIdx.x + q * 256;
-        if (o < CX * CY) {
-            const int ci = o / CY, co = o - ci * CY;
-            if (ci < cin && co < cout) atomicAdd(&dW[((long)t * cin + ci) * cout + co], acc[q]);
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int ci = 4 * ciq + a, co = 4 * coq + b;
+            if (ci < cin && co < cout) atomicAdd(&dW[((long)t * cin + ci) * cout + co], acc[a][b]);
         }
-    }
     if (t == 13 && db && threadIdx.x < cout) atomicAdd(&db[threadIdx.x], bacc);
 }
 

@@ -1341,8 +1341,8 @@ ins_status wgrad_launch(ins_grid* g, const __nv_bfloat16* X, const __nv_bfloat16
                         float* db) {
     if (!dW) return INS_OK;
     const long nvox = g->N;
-    int nblk = (int)((nvox / 64 + 26) / 27);
-    nblk = nblk < 1 ? 1 : (nblk > 148 ? 148 : nblk);
+    int nblk = (int)((nvox / 128 + 3) / 4);          // ~4 chunks of 128 voxels per block
+    nblk = nblk < 1 ? 1 : (nblk > 296 ? 296 : nblk);
     KLAUNCH(g, "wgrad", k_wgrad<CX, CY><<<dim3(27, nblk), 256, 0, g->stream>>>(X, dY, g->nx, g->ny, g->nz, cin, cout,
                                                                               dW, db));
     return INS_OK;

@@ -101,37 +101,45 @@ def random_field(shape, seed, scale=1.0):
     return scale * (2.0 * rng.random(shape) - 1.0)
 
 
-def spectrum_velocity_raw(n, dim, seed, k0=4.0):
+def spectrum_velocity_raw(n, dim, seed, k0=4.0, kmax=None):
     """Random Fourier velocity with energy spectrum E(k) ~ k^4 exp(-2 (k/k0)^2).
 
-    For every integer wavevector with 0 < |k| <= N/2 - 1 (N the smallest
-    resolution) and every component a the coefficient is
-    sqrt(E(|k|) / S(|k|)) (g1 + i g2) / sqrt(2), with S the shell area
-    (4 pi k^2 in 3-D, 2 pi k in 2-D) and (g1, g2) the Box-Muller pair of
-    counter ((a * Nz + iz) * Ny + iy) * Nx + ix under key ``seed``. The field is
-    the real part of the inverse DFT, read as face values. It is NOT yet
-    divergence free and NOT normalised: project it, then scale to unit energy.
+    For every integer wavevector with 0 < |k| <= kc (kc = N/2 - 1 with N the smallest
+    resolution, or the given kmax if smaller) and every component a the coefficient is
+    sqrt(E(|k|) / S(|k|)) (g1 + i g2) / sqrt(2), with S the shell area (4 pi k^2 in 3-D,
+    2 pi k in 2-D) and (g1, g2) the Box-Muller pair of counter
+    ((a * Nz + iz) * Ny + iy) * Nx + ix under key ``seed``. Only wavevectors inside the
+    cutoff draw numbers (the counter makes every value independent of the others, so this
+    changes nothing). The field is the real part of the inverse DFT, read as face values.
+    It is NOT yet divergence free and NOT normalised: project it, then scale to unit energy.
     """
+    import scipy.fft
     if isinstance(n, int):
         n = (n,) * dim
     n = tuple(n)
     shape = tuple(reversed(n))
     kax = [np.fft.fftfreq(nn, d=1.0 / nn) for nn in n]          # integer wavenumbers
-    grids = np.meshgrid(*[kax[a] for a in reversed(range(dim))], indexing="ij")
-    kmag = np.sqrt(sum(gk ** 2 for gk in grids))
+    k2 = np.zeros(shape)
+    for a in range(dim):
+        shp = [1] * dim
+        shp[dim - 1 - a] = -1
+        k2 = k2 + (kax[a] ** 2).reshape(shp)
     kcut = min(n) // 2 - 1
-    mask = (kmag > 0) & (kmag <= kcut)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        E = kmag ** 4 * np.exp(-2.0 * (kmag / k0) ** 2)
-        shell = 4.0 * np.pi * kmag ** 2 if dim == 3 else 2.0 * np.pi * kmag
-        amp = np.where(mask, np.sqrt(E / np.where(mask, shell, 1.0)), 0.0)
-    lin = np.arange(int(np.prod(shape)), dtype=np.uint64).reshape(shape)
+    if kmax is not None:
+        kcut = min(kcut, kmax)
+    idx = np.nonzero((k2 > 0) & (k2 <= kcut * kcut))     # |k| <= kc exactly (integer k)
+    km = np.sqrt(k2[idx])
+    E = km ** 4 * np.exp(-2.0 * (km / k0) ** 2)
+    shell = 4.0 * np.pi * km ** 2 if dim == 3 else 2.0 * np.pi * km
+    amp = np.sqrt(E / shell)
+    size = int(np.prod(shape))
+    lin = np.ravel_multi_index(idx, shape).astype(np.uint64)
     u = np.zeros((dim,) + shape)
     for a in range(dim):
-        counter = np.uint64(a) * np.uint64(lin.size) + lin
-        g1, g2 = normal_pair(seed, counter)
-        coef = amp * (g1 + 1j * g2) / np.sqrt(2.0)
-        u[a] = np.real(np.fft.ifftn(coef)) * float(np.prod(shape))
+        g1, g2 = normal_pair(seed, np.uint64(a) * np.uint64(size) + lin)
+        coef = np.zeros(shape, dtype=np.complex128)
+        coef[idx] = amp * (g1 + 1j * g2) / np.sqrt(2.0)
+        u[a] = np.real(scipy.fft.ifftn(coef, workers=-1)) * float(size)
     return u
 
 
