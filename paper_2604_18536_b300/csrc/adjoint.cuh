@@ -136,3 +136,142 @@ __global__ void k_sum_partials(const double* __restrict__ part, long n, double* 
 }
 
 }  // namespace ins
+
+namespace ins {
+
+// The same pullback as k_adj_rhs for 3-D periodic grids, with the z march of k_rhs_div:
+// a CTA of 32 x 8 threads owns a 32 x 8 column and a chunk of planes; the planes k-1, k,
+// k+1 of u and w (all three components, one-cell halo in x and y, which covers every
+// diagonal neighbour J + e_a - e_b the gather form reads) sit in dynamic shared memory as a
+// ring, and plane k+2 is loaded into registers while plane k is computed.
+constexpr int AJX = 32, AJY = 8;
+constexpr int AJSX = AJX + 2, AJSY = AJY + 2, AJSP = AJSX * AJSY;
+constexpr int AJNT = AJX * AJY;
+constexpr int AJPF = (AJSP + AJNT - 1) / AJNT;
+
+template <typename T>
+__global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __restrict__ u, const T* __restrict__ w,
+                                                   const T* __restrict__ ybar, T* __restrict__ ubar0,
+                                                   T* __restrict__ kb, double* __restrict__ nu_part,
+                                                   const T* __restrict__ extra, int kchunk) {
+    extern __shared__ __align__(16) unsigned char ajsm[];
+    T(*s)[6][AJSP] = reinterpret_cast<T(*)[6][AJSP]>(ajsm);   // s[slot][comp: u 0-2, w 3-5][cell]
+    const int nx = c.nx, ny = c.ny, nz = c.nz;
+    const long N = (long)nx * ny * nz;
+    const long plane = (long)nx * ny;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * AJX;
+    const int i0 = blockIdx.x * AJX, j0 = blockIdx.y * AJY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool ok = i < nx && j < ny;
+    const int kb0 = blockIdx.z * kchunk, ke = min(kb0 + kchunk, nz);
+    const double dt = c.dt_dev ? *c.dt_dev : c.dt_host;
+    const T dtb = (T)(dt * c.bn), dta = (T)(dt * c.an);
+    // in-plane source offsets of this thread's share of a plane
+    int off[AJPF];
+#pragma unroll
+    for (int q = 0; q < AJPF; ++q) {
+        const int e = tid + q * AJNT;
+        off[q] = -1;
+        if (e < AJSP) {
+            const int li = e % AJSX, lj = e / AJSX;
+            int gi = (i0 - 1 + li) % nx, gj = (j0 - 1 + lj) % ny;
+            gi += gi < 0 ? nx : 0;
+            gj += gj < 0 ? ny : 0;
+            off[q] = gj * nx + gi;
+        }
+    }
+    T v[6][AJPF];
+    auto fetch = [&](int kk) {
+        const long base = (long)kk * plane;
+#pragma unroll
+        for (int q = 0; q < AJPF; ++q)
+            if (off[q] >= 0) {
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    v[cc][q] = u[cc * N + base + off[q]];
+                    v[3 + cc][q] = w[cc * N + base + off[q]];
+                }
+            }
+    };
+    auto commit = [&](int slot) {
+#pragma unroll
+        for (int q = 0; q < AJPF; ++q)
+            if (off[q] >= 0) {
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) s[slot][cc][tid + q * AJNT] = v[cc][q];
+            }
+    };
+    auto wz = [nz](int k) { return k < 0 ? k + nz : (k >= nz ? k - nz : k); };
+    int sm = 0, so = 1, sp = 2;
+    fetch(wz(kb0 - 1));
+    commit(sm);
+    fetch(wz(kb0));
+    commit(so);
+    fetch(wz(kb0 + 1));
+    commit(sp);
+    __syncthreads();
+    const int c0 = (ty + 1) * AJSX + (tx + 1);
+    // offsets within a plane: +x = 1, +y = AJSX
+    double nup = 0.0;
+    for (int k = kb0; k < ke; ++k) {
+        const bool more = k + 1 < ke;
+        if (more) fetch(wz(k + 2));
+        if (ok) {
+            const T* P[3] = {s[sm][0], s[so][0], s[sp][0]};   // base pointers of planes k-1, k, k+1
+            // value of field f (0-2 u, 3-5 w) at J + (dx, dy, dz)
+            auto at = [&](int f, int dx, int dy, int dz) { return P[dz + 1][f * AJSP + c0 + dx + dy * AJSX]; };
+            const long J = (long)k * plane + (long)j * nx + i;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int ea[3] = {0, 0, 0};
+                ea[a] = 1;
+                const T ua0 = at(a, 0, 0, 0), uap = at(a, ea[0], ea[1], ea[2]), uam = at(a, -ea[0], -ea[1], -ea[2]);
+                const T wa0 = at(3 + a, 0, 0, 0), wap = at(3 + a, ea[0], ea[1], ea[2]),
+                        wam = at(3 + a, -ea[0], -ea[1], -ea[2]);
+                T acc = c.c1[a] * fma(ua0 + uap, wap - wa0, (uam + ua0) * (wa0 - wam));
+                T lap = c.l2[a] * (wap + wam - (T)2 * wa0);
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    if (b == a) continue;
+                    int eb[3] = {0, 0, 0};
+                    eb[b] = 1;
+                    const T S0 = at(b, 0, 0, 0) + at(b, ea[0], ea[1], ea[2]);
+                    const T S1 = at(b, -eb[0], -eb[1], -eb[2]) + at(b, ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]);
+                    const T wabp = at(3 + a, eb[0], eb[1], eb[2]), wabm = at(3 + a, -eb[0], -eb[1], -eb[2]);
+                    const T wb0 = at(3 + b, 0, 0, 0), wbpa = at(3 + b, ea[0], ea[1], ea[2]);
+                    const T wbm = at(3 + b, -eb[0], -eb[1], -eb[2]);
+                    const T wbpam = at(3 + b, ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]);
+                    acc = fma(c.c2[b], fma(S0, wabp - wa0, S1 * (wa0 - wabm)), acc);
+                    acc = fma(c.c2[a], fma(S0, wbpa - wb0, S1 * (wbpam - wbm)), acc);
+                    lap = fma(c.l2[b], wabp + wabm - (T)2 * wa0, lap);
+                }
+                T ubs = fma(c.nu, lap, acc);
+                if (extra) ubs += extra[a * N + J];
+                nup += (double)ua0 * (double)lap;
+                const long e = a * N + J;
+                ubar0[e] = ubar0[e] + ubs;
+                if (kb) kb[e] = fma(dtb, ybar[e], dta * ubs);
+            }
+        }
+        __syncthreads();
+        if (more) commit(sm);
+        {
+            const int t = sm;
+            sm = so;
+            so = sp;
+            sp = t;
+        }
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) nup += __shfl_xor_sync(0xffffffffu, nup, o);
+    __shared__ double red[AJY];
+    if (tx == 0) red[ty] = nup;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int r = 0; r < AJY; ++r) t += red[r];
+        nu_part[((long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+}  // namespace ins

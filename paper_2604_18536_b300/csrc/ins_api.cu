@@ -458,7 +458,14 @@ struct Impl {
         const long N = g->N;
         const size_t fld = (size_t)g->dim * N * sizeof(T);
         const dim3 cg = cell_grid(g);
-        const long nblk = (long)cg.x * cg.y * cg.z;
+        // z-marching adjoint stencil (3-D): chunks of planes per CTA
+        const int abx = (g->nx + AJX - 1) / AJX, aby = (g->ny + AJY - 1) / AJY;
+        int akc = (int)(((long)abx * aby * g->nz) / 1184);
+        akc = akc < 1 ? 1 : (akc > g->nz ? g->nz : akc);
+        const dim3 ag(abx, aby, (g->nz + akc - 1) / akc);
+        const size_t adj_smem = 3 * 6 * AJSP * sizeof(T);
+        if (DIM == 3) INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem));
+        const long nblk = DIM == 3 ? (long)ag.x * ag.y * ag.z : (long)cg.x * cg.y * cg.z;
         const size_t need = 5 * ((fld + 255) & ~size_t(255)) + (size_t)nblk * 8;
         if (g->vjp_bytes < need) {
             if (g->vjp) cudaFree(g->vjp);
@@ -531,8 +538,13 @@ struct Impl {
                 if ((s = closure_pullback<T>(g, W, Cb)) != INS_OK) return s;
                 extra = Cb;
             }
-            KLAUNCH(g, "adj_rhs", k_adj_rhs<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
-                                      ac, U[st], W, ybar, ubar, st > 0 ? F : nullptr, part, extra));
+            if (DIM == 3) {
+                KLAUNCH(g, "adj_rhs", k_adj_rhs_z<T><<<ag, dim3(AJX, AJY), adj_smem, g->stream>>>(
+                                          ac, U[st], W, ybar, ubar, st > 0 ? F : nullptr, part, extra, akc));
+            } else {
+                KLAUNCH(g, "adj_rhs", k_adj_rhs<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
+                                          ac, U[st], W, ybar, ubar, st > 0 ? F : nullptr, part, extra));
+            }
             if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, nblk, nubar));
         }
         return INS_OK;
@@ -1327,8 +1339,9 @@ ins_status conv_launch(ins_grid* g, ConvArgs a) {
     a.nx = g->nx;
     a.ny = g->ny;
     a.nz = g->nz;
+    // about one wave of two CTAs per SM: each CTA loads the weights once for ~nz*cols/296 tiles
     const int cols = (g->nx / CV_TX) * (g->ny / CV_TY);
-    int zc = (int)(((long)cols * g->nz) / 592);
+    int zc = (int)(((long)cols * g->nz + 295) / 296);
     zc = zc < 2 ? 2 : (zc > g->nz ? g->nz : zc);
     a.zchunk = zc;
     const dim3 grd(g->nx / CV_TX, g->ny / CV_TY, (g->nz + zc - 1) / zc);
