@@ -136,6 +136,11 @@ def kernel_model(name, n, s, launches_by_stage=None):
     return None, None
 
 
+# DRAM bytes per launch of the dominant kernels from ncu captures of the current kernels
+# (profiles/rhs_div_hit256.md, profiles/rk_update_hit256.md); n = 256 only.
+TRAFFIC = {("f64", "rhs_div"): 909.93e6, ("f32", "rk_update"): 942.9e6}
+
+
 def step_model_bytes(n, s):
     """Model bytes of one RK4 step with F stored: 126 values per cell."""
     return 126 * n ** 3 * s
@@ -219,14 +224,15 @@ def run_ours(args):
         dname, (dl, dms) = dom
         b, ops = kernel_model(dname, n, s)
         avg_s = dms / dl / 1e3
+        traffic = TRAFFIC.get((tag, dname)) if n == 256 else None
         if tag == "f64" and ops is not None:
             roof = {"bound": "alu", "kernel": dname, "achieved": ops / avg_s / 1e9, "peak": fp64_ops_peak / 1e9,
-                    "unit": "Gop/s (FP64 pipe ops)", "frac": ops / avg_s / fp64_ops_peak, "traffic": None,
+                    "unit": "Gop/s (FP64 pipe ops)", "frac": ops / avg_s / fp64_ops_peak, "traffic": traffic,
                     "peak_source": "measured live: dependent-FMA kernel, %.3f TFLOP/s / 2" % (fp64_flops / 1e12),
                     "hbm_frac_of_kernel": (b / avg_s / 1e9) / hbm_peak}
         else:
             roof = {"bound": "hbm", "kernel": dname, "achieved": b / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": (b / avg_s / 1e9) / hbm_peak, "traffic": None,
+                    "frac": (b / avg_s / 1e9) / hbm_peak, "traffic": traffic,
                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % hbm_src}
         kernels = {k: {"launches": v[0], "total_ms": round(v[1], 4), "share": round(v[1] / tot, 4),
                        "avg_us": round(v[1] / v[0] * 1e3, 2)} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
