@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtypes", default="f64,f32")
     ap.add_argument("--no-closure", action="store_true")
+    ap.add_argument("--no-channel", action="store_true")
     return ap.parse_args()
 
 
@@ -309,11 +310,51 @@ def run_ours(args):
             line["fp32"]["speedup_vs_fp64"] = f["value"] / prim["value"]
         if not args.no_closure:
             line["closure"] = bench_closure()
+        if not args.no_channel:
+            line["channel"] = bench_channel()
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(steps=1)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ turbulent channel
+def bench_channel(n=(192, 128, 192), steps=10, warmup=3):
+    """Re_tau = 180 channel on 4 pi x 2 x 4 pi/3 (tanh y, gamma 1.5), nu = 1/180, f = (1, 0, 0):
+    FP64 and FP32 RK4 steps with the device-side CFL 0.3 time step (x/z FFT + FP64 Thomas in y)."""
+    import torch
+    from paper_2604_18536_b300 import inputs
+    from paper_2604_18536_b300.solver import Grid
+    faces = inputs.channel_faces(*n)
+    raw = inputs.channel_velocity_raw(faces, seed=0)
+    out = {"workload": "turbulent channel %dx%dx%d, tanh-stretched y, nu=1/180, RK4, CFL 0.3" % n}
+    cells = n[0] * n[1] * n[2]
+    for tag, dtype in (("f64", torch.float64), ("f32", torch.float32)):
+        g = Grid(faces, ["periodic", "wall", "periodic"], 1.0 / 180, [1.0, 0.0, 0.0], dtype=dtype)
+        u = torch.tensor(raw, dtype=dtype, device="cuda")
+        g.project(u, out=u)
+        dt = g.cfl_dt(u, CFL)
+        for _ in range(warmup):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        g.profile(True)
+        e0.record(st)
+        for _ in range(steps):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        e1.record(st)
+        torch.cuda.synchronize()
+        prof = g.profile_read()
+        g.profile(False)
+        ms = e0.elapsed_time(e1) / steps
+        out[tag] = {"ms_per_step": ms, "value": cells / (ms / 1e3), "unit": UNIT,
+                    "kernels": {k: {"launches": v[0], "avg_us": round(v[1] / v[0] * 1e3, 2)}
+                                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+        g.check_finite()
+        g.close()
+    return out
 
 
 # ------------------------------------------------------------------ closure (tensor cores)

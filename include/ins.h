@@ -160,6 +160,14 @@ ins_status ins_diag(ins_grid* g, const void* u, double out[4]);
  * overwritten. Periodic grids only. Uses the grid's spectral workspace. */
 ins_status ins_spectrum(ins_grid* g, const void* u, double* E_dev, int kmax);
 
+/* Channel statistics along the wall-normal y (Sec. 6.2: mean velocity and Reynolds stresses
+ * from velocities interpolated to the volume centres, uc_a = (u^a_I + u^a_{I-e_a})/2, the
+ * wall value 0 below the first cell for u^y): plane averages over x and z in FP64.
+ * out_dev: DEVICE, 9*ny doubles, out[q*ny + j]: q = 0..2 mean u^x, u^y, u^z; q = 3..8 the
+ * covariances <uc_a uc_b> - <uc_a><uc_b> for (a,b) = xx, xy, xz, yy, yz, zz.
+ * 3-D grids with a wall in y only. */
+ins_status ins_wall_profiles(ins_grid* g, const void* u, double* out_dev);
+
 /* Face-averaging filter from a fine grid to one `ratio` times coarser in every
  * direction (filtered DNS for closure training, Sec. 4): the coarse u^a on the face to
  * the right of coarse cell I is the mean of the ratio^(dim-1) fine u^a on the fine faces

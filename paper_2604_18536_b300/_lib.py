@@ -61,6 +61,7 @@ SIGNATURES = {
     "ins_cfl_dt": (_c.c_int, [_vp, _vp, _c.c_double, _vp]),
     "ins_step_vjp": (_c.c_int, [_vp, _vp, _vp, _c.c_double, _vp, _vp, _vp]),
     "ins_spectrum": (_c.c_int, [_vp, _vp, _vp, _c.c_int]),
+    "ins_wall_profiles": (_c.c_int, [_vp, _vp, _vp]),
     "ins_filter_face_average": (_c.c_int, [_c.c_int, _c.POINTER(_c.c_int), _c.c_int, _c.c_int, _vp, _vp, _vp]),
     "ins_diag": (_c.c_int, [_vp, _vp, _dp]),
     "ins_check_finite": (_c.c_int, [_vp]),

@@ -326,31 +326,62 @@ template <typename T>
 __global__ void k_thomas(cplx<T>* __restrict__ S, const double* __restrict__ lo, const double* __restrict__ invm,
                          const double* __restrict__ cp, cplx<double>* __restrict__ dscr, int nxh, int ny, long ncol,
                          double norm) {
+    // The loads do not depend on the recurrence: rows are fetched in batches of CH before
+    // each CH-step stretch of the (sequential) sweep, so CH loads per array are in flight.
+    constexpr int CH = 8;
     const long col = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (col >= ncol) return;
     const long base = (col / nxh) * (long)ny * nxh + (col % nxh);
     double dre = 0.0, dim_ = 0.0;
-    for (int j = 0; j < ny; ++j) {
-        cplx<T> r = S[base + (long)j * nxh];
-        double rre = (double)r.re, rim = (double)r.im;
-        if (j == 0 && col == 0) {
-            rre = 0.0;
-            rim = 0.0;
+    for (int j0 = 0; j0 < ny; j0 += CH) {
+        cplx<T> r[CH];
+        double a[CH], im[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int j = j0 + q;
+            if (j < ny) {
+                r[q] = S[base + (long)j * nxh];
+                a[q] = __ldg(&lo[j]);
+                im[q] = __ldg(&invm[(long)j * ncol + col]);
+            }
         }
-        const double a = lo[j];
-        const double im = invm[(long)j * ncol + col];
-        dre = (rre - a * dre) * im;
-        dim_ = (rim - a * dim_) * im;
-        dscr[(long)j * ncol + col] = {dre, dim_};
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int j = j0 + q;
+            if (j < ny) {
+                double rre = (double)r[q].re, rim = (double)r[q].im;
+                if (j == 0 && col == 0) {
+                    rre = 0.0;
+                    rim = 0.0;
+                }
+                dre = (rre - a[q] * dre) * im[q];
+                dim_ = (rim - a[q] * dim_) * im[q];
+                dscr[(long)j * ncol + col] = {dre, dim_};
+            }
+        }
     }
     double xre = dre, xim = dim_;
     S[base + (long)(ny - 1) * nxh] = {(T)(xre * norm), (T)(xim * norm)};
-    for (int j = ny - 2; j >= 0; --j) {
-        const cplx<double> d = dscr[(long)j * ncol + col];
-        const double c = cp[(long)j * ncol + col];
-        xre = d.re - c * xre;
-        xim = d.im - c * xim;
-        S[base + (long)j * nxh] = {(T)(xre * norm), (T)(xim * norm)};
+    for (int j1 = ny - 2; j1 >= 0; j1 -= CH) {
+        cplx<double> d[CH];
+        double c[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int j = j1 - q;
+            if (j >= 0) {
+                d[q] = dscr[(long)j * ncol + col];
+                c[q] = __ldg(&cp[(long)j * ncol + col]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int j = j1 - q;
+            if (j >= 0) {
+                xre = d[q].re - c[q] * xre;
+                xim = d[q].im - c[q] * xim;
+                S[base + (long)j * nxh] = {(T)(xre * norm), (T)(xim * norm)};
+            }
+        }
     }
 }
 

@@ -76,3 +76,49 @@ __global__ void k_shell_bin(const cplx<T>* __restrict__ S, int nx, int ny, int n
 }
 
 }  // namespace ins
+
+namespace ins {
+
+// Plane statistics along the wall-normal y of a channel (paper Sec. 6.2: mean velocity and
+// Reynolds stresses from velocities interpolated to the volume centres). One block per row j;
+// FP64 sums over (i, k) of uc_a and uc_a uc_b, uc_a = (u^a_I + u^a_{I-e_a}) / 2 with the wall
+// value 0 below the first cell for u^y. out[q * ny + j]: q = 0..2 means, 3..8 covariances
+// (xx, xy, xz, yy, yz, zz).
+template <typename T>
+__global__ void k_wall_profiles(const T* __restrict__ u, int nx, int ny, int nz, double* __restrict__ out) {
+    const int j = blockIdx.x;
+    const long N = (long)nx * ny * nz;
+    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (long t = threadIdx.x; t < (long)nx * nz; t += blockDim.x) {
+        const int i = (int)(t % nx), k = (int)(t / nx);
+        const long a = ((long)k * ny + j) * nx + i;
+        const int im = i == 0 ? nx - 1 : i - 1;
+        const int km = k == 0 ? nz - 1 : k - 1;
+        const double cx = 0.5 * ((double)u[a] + (double)u[a - i + im]);
+        const double cy = 0.5 * ((double)u[N + a] + (j == 0 ? 0.0 : (double)u[N + a - nx]));
+        const double cz = 0.5 * ((double)u[2 * N + a] + (double)u[2 * N + ((long)km * ny + j) * nx + i]);
+        s[0] += cx; s[1] += cy; s[2] += cz;
+        s[3] += cx * cx; s[4] += cx * cy; s[5] += cx * cz;
+        s[6] += cy * cy; s[7] += cy * cz; s[8] += cz * cz;
+    }
+    __shared__ double red[9][256];
+    for (int q = 0; q < 9; ++q) red[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int q = 0; q < 9; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double inv = 1.0 / ((double)nx * nz);
+        double m[3];
+        for (int q = 0; q < 3; ++q) {
+            m[q] = red[q][0] * inv;
+            out[q * ny + j] = m[q];
+        }
+        const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+        for (int q = 0; q < 6; ++q) out[(3 + q) * ny + j] = red[3 + q][0] * inv - m[pa[q]] * m[pb[q]];
+    }
+}
+
+}  // namespace ins

@@ -1127,6 +1127,19 @@ ins_status ins_spectrum(ins_grid* g, const void* u, double* E_dev, int kmax) {
     });
 }
 
+ins_status ins_wall_profiles(ins_grid* g, const void* u, double* out_dev) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u, "u"));
+    if (!out_dev) return fail(INS_ERR_ARG, "out_dev is null");
+    if (!g->wall_y || g->dim != 3) return fail(INS_ERR_UNSUPPORTED, "ins_wall_profiles: 3-D grids with a wall in y");
+    if (g->dtype == INS_F64)
+        KLAUNCH(g, "wall_profiles", k_wall_profiles<double><<<g->ny, 256, 0, g->stream>>>((const double*)u, g->nx, g->ny, g->nz, out_dev));
+    else
+        KLAUNCH(g, "wall_profiles", k_wall_profiles<float><<<g->ny, 256, 0, g->stream>>>((const float*)u, g->nx, g->ny, g->nz, out_dev));
+    return INS_OK;
+}
+
 ins_status ins_filter_face_average(int dim, const int n_coarse[3], int ratio, int dtype, const void* u_fine,
                                    void* u_coarse, void* stream) {
     g_err.clear();

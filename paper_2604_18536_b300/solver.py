@@ -192,6 +192,14 @@ class Grid:
         check(lib().ins_spectrum(self._h, _ptr(u), _ptr(E), kmax), "ins_spectrum")
         return E
 
+    def wall_profiles(self, u):
+        """Channel statistics (ins_wall_profiles): (mean (3, ny), cov (6, ny)) float64 CUDA tensors."""
+        self._check_u(u)
+        out = torch.empty((9, self.n[1]), dtype=torch.float64, device=self.device)
+        self._sync_stream()
+        check(lib().ins_wall_profiles(self._h, _ptr(u), _ptr(out)), "ins_wall_profiles")
+        return out[:3], out[3:]
+
     def cfl_dt(self, u, cfl, out=None):
         self._check_u(u)
         out = torch.zeros(1, dtype=torch.float64, device=self.device) if out is None else out
