@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--dtypes", default="f64,f32")
     ap.add_argument("--no-closure", action="store_true")
     ap.add_argument("--no-channel", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="FP64 size sweep 128^3..840^3 only (one JSON line)")
     return ap.parse_args()
 
 
@@ -319,6 +320,49 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ size sweep (FP64)
+def run_sweep(sizes=(128, 256, 512, 840), steps=5, warmup=2):
+    """FP64 RK4 step time and device memory at several periodic sizes (one JSON line).
+
+    The initial field is the 3-D Taylor-Green vortex built on the device from separable sines
+    (the step's cost does not depend on the field), projected by ins_project."""
+    import torch
+    from paper_2604_18536_b300 import inputs
+    from paper_2604_18536_b300.solver import Grid
+    out = []
+    for n in sizes:
+        torch.cuda.empty_cache()
+        free0, total = torch.cuda.mem_get_info()
+        g = Grid(inputs.periodic_box(n, 3), ["periodic"] * 3, NU, dtype=torch.float64)
+        x = (torch.arange(n, dtype=torch.float64, device="cuda") + 0.5) * (2 * math.pi / n)
+        xf = (torch.arange(n, dtype=torch.float64, device="cuda") + 1.0) * (2 * math.pi / n)
+        u = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+        u[0] = torch.sin(xf)[None, None, :] * torch.cos(x)[None, :, None] * torch.cos(x)[:, None, None]
+        u[1] = -torch.cos(x)[None, None, :] * torch.sin(xf)[None, :, None] * torch.cos(x)[:, None, None]
+        u[2] = 0.0
+        g.project(u, out=u)
+        dt = g.cfl_dt(u, CFL)
+        for _ in range(warmup):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        e1.record(st)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        ms = e0.elapsed_time(e1) / steps
+        out.append({"n": n, "ms_per_step": ms, "cell_updates_per_s": n ** 3 / (ms / 1e3),
+                    "workspace_gb": g.workspace_bytes() / 1e9, "velocity_gb": u.numel() * 8 / 1e9,
+                    "device_used_gb": (free0 - free1) / 1e9})
+        g.check_finite()
+        g.close()
+        del u, x, xf
+    print(json.dumps({"sweep": "3-D periodic RK4 step, FP64, CFL 0.3", "results": out}))
+
+
 # ------------------------------------------------------------------ turbulent channel
 def bench_channel(n=(192, 128, 192), steps=10, warmup=3):
     """Re_tau = 180 channel on 4 pi x 2 x 4 pi/3 (tanh y, gamma 1.5), nu = 1/180, f = (1, 0, 0):
@@ -466,7 +510,9 @@ def run_reference(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
