@@ -197,7 +197,13 @@ def main():
     t1 = time.time()
     train_set, test_set = data[: a.seeds - a.test], data[a.seeds - a.test:]
     base, _ = evaluate(test_set, a.n_les, nu, nsteps=a.nsteps)
-    W, b, hist = train(train_set, a.n_les, nu, a.iters, a.batch, a.lr, a.nsteps)
+    import sys
+
+    def log(it, loss):
+        if it % 10 == 0 or it == a.iters - 1:
+            print(f"iter {it} loss {loss:.6e} t {time.time() - t1:.1f}s", file=sys.stderr, flush=True)
+
+    W, b, hist = train(train_set, a.n_les, nu, a.iters, a.batch, a.lr, a.nsteps, log=log)
     t2 = time.time()
     err, fb = evaluate(test_set, a.n_les, nu, W, b, nsteps=a.nsteps)
     print(json.dumps({"no_closure_spectrum_error": base, "closure_spectrum_error": err, "fallbacks": fb,
