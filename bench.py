@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--dtypes", default="f64,f32")
     ap.add_argument("--no-closure", action="store_true")
     ap.add_argument("--no-channel", action="store_true")
+    ap.add_argument("--no-wray3", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="FP64 size sweep 128^3..840^3 only (one JSON line)")
     return ap.parse_args()
 
@@ -313,6 +314,8 @@ def run_ours(args):
             line["closure"] = bench_closure()
         if not args.no_channel:
             line["channel"] = bench_channel()
+        if not args.no_wray3:
+            line["wray3"] = bench_wray3(n, seed=args.seed)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(steps=1)
         print(json.dumps(line))
@@ -321,7 +324,7 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ size sweep (FP64)
-def run_sweep(sizes=(128, 256, 512, 840), steps=5, warmup=2):
+def run_sweep(sizes=(128, 256, 512, 840), steps=5, warmup=2, extra=(("wray3", 840),)):
     """FP64 RK4 step time and device memory at several periodic sizes (one JSON line).
 
     The initial field is the 3-D Taylor-Green vortex built on the device from separable sines
@@ -330,10 +333,10 @@ def run_sweep(sizes=(128, 256, 512, 840), steps=5, warmup=2):
     from paper_2604_18536_b300 import inputs
     from paper_2604_18536_b300.solver import Grid
     out = []
-    for n in sizes:
+    for scheme, n in [("rk4", n) for n in sizes] + list(extra):
         torch.cuda.empty_cache()
         free0, total = torch.cuda.mem_get_info()
-        g = Grid(inputs.periodic_box(n, 3), ["periodic"] * 3, NU, dtype=torch.float64)
+        g = Grid(inputs.periodic_box(n, 3), ["periodic"] * 3, NU, dtype=torch.float64, scheme=scheme)
         x = (torch.arange(n, dtype=torch.float64, device="cuda") + 0.5) * (2 * math.pi / n)
         xf = (torch.arange(n, dtype=torch.float64, device="cuda") + 1.0) * (2 * math.pi / n)
         u = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
@@ -354,13 +357,14 @@ def run_sweep(sizes=(128, 256, 512, 840), steps=5, warmup=2):
         torch.cuda.synchronize()
         free1, _ = torch.cuda.mem_get_info()
         ms = e0.elapsed_time(e1) / steps
-        out.append({"n": n, "ms_per_step": ms, "cell_updates_per_s": n ** 3 / (ms / 1e3),
+        out.append({"n": n, "scheme": scheme, "ms_per_step": ms, "cell_updates_per_s": n ** 3 / (ms / 1e3),
                     "workspace_gb": g.workspace_bytes() / 1e9, "velocity_gb": u.numel() * 8 / 1e9,
                     "device_used_gb": (free0 - free1) / 1e9})
         g.check_finite()
         g.close()
         del u, x, xf
-    print(json.dumps({"sweep": "3-D periodic RK4 step, FP64, CFL 0.3", "results": out}))
+    print(json.dumps({"sweep": "3-D periodic step (RK4; Wray low-storage RK3 at the end), FP64, CFL 0.3",
+                      "results": out}))
 
 
 # ------------------------------------------------------------------ turbulent channel
@@ -398,6 +402,53 @@ def bench_channel(n=(192, 128, 192), steps=10, warmup=3):
                                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
         g.check_finite()
         g.close()
+    return out
+
+
+# ------------------------------------------------------------------ low-storage scheme
+def bench_wray3(n=256, steps=10, warmup=3, seed=0):
+    """Wray's low-storage 3-stage RK on the isotropic-turbulence workload: step and step-VJP
+    times, workspace (one velocity register less than RK4)."""
+    import torch
+    from paper_2604_18536_b300 import inputs
+    from paper_2604_18536_b300.solver import Grid
+    faces = inputs.periodic_box(n, 3)
+    raw = inputs.spectrum_velocity_raw(n, 3, seed=seed, k0=4.0)
+    out = {"workload": "3-D decaying isotropic turbulence %d^3, nu=1/1600, Wray low-storage RK3, CFL 0.3" % n}
+    for tag, dtype in (("f64", torch.float64), ("f32", torch.float32)):
+        g = Grid(faces, ["periodic"] * 3, NU, dtype=dtype, scheme="wray3")
+        u = torch.tensor(raw, dtype=dtype, device="cuda")
+        g.project(u, out=u)
+        u.mul_(1.0 / math.sqrt(g.diag(u)["ke"]))
+        dt = g.cfl_dt(u, CFL)
+        for _ in range(warmup):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(steps):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ybar = u.detach().clone()
+        ubar = g.new_velocity()
+        g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(3):
+            g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar)
+        e1.record(st)
+        torch.cuda.synchronize()
+        vms = e0.elapsed_time(e1) / 3
+        out[tag] = {"ms_per_step": ms, "value": n ** 3 / (ms / 1e3), "unit": UNIT,
+                    "ms_per_vjp": vms, "adjoint_forward_ratio": vms / ms,
+                    "workspace_bytes": g.workspace_bytes()}
+        g.check_finite()
+        g.close()
+        del u, ybar, ubar
+        torch.cuda.empty_cache()
     return out
 
 

@@ -48,6 +48,7 @@ typedef enum {
 
 typedef enum { INS_PERIODIC = 0, INS_WALL = 1 } ins_bc;
 typedef enum { INS_F32 = 0, INS_F64 = 1 } ins_dtype;
+typedef enum { INS_RK4 = 0, INS_WRAY3 = 1 } ins_scheme;
 
 /* Grid description (Sec. 2.1, 2.4, 2.5).
  * dim            2 or 3.
@@ -62,7 +63,12 @@ typedef enum { INS_F32 = 0, INS_F64 = 1 } ins_dtype;
  *                stretched (e.g. the tanh grid of Sec. 2.5).
  * dtype          storage and arithmetic type of the fields.
  * nu             kinematic viscosity (> 0 not required; >= 0).
- * force[a]       constant body force f^a (App. A momentum equation). */
+ * force[a]       constant body force f^a (App. A momentum equation).
+ * scheme         time integrator of ins_step (Sec. 2.6.2; 0 = INS_RK4 when the struct is
+ *                zero-initialised): INS_RK4, the classic 4-stage RK (three velocity
+ *                registers of workspace: F, stage state, accumulator), or INS_WRAY3, Wray's
+ *                3-stage third-order low-storage RK (Sec. 3.3, low-storage methods; two
+ *                registers: F and the previous stage derivative). */
 typedef struct {
     int dim;
     int n[3];
@@ -71,6 +77,7 @@ typedef struct {
     int dtype;
     double nu;
     double force[3];
+    int scheme;
 } ins_grid_desc;
 
 typedef struct ins_grid ins_grid;
@@ -84,7 +91,7 @@ const char* ins_version(void);
 /* Create a grid: validates *desc, copies the geometry to the device, builds the
  * FFT twiddle tables, the spectral inverse-Laplacian table (periodic) or the
  * Thomas factors (wall direction), and allocates the workspace (about 11 scalar
- * fields of the grid dtype). stream is a cudaStream_t (NULL = legacy default
+ * fields of the grid dtype in 3-D with INS_RK4, 8 with INS_WRAY3). stream is a cudaStream_t (NULL = legacy default
  * stream) on which every later call enqueues its work; the current CUDA device
  * must be the one the fields live on. This call synchronises the device. */
 ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** out);
@@ -110,9 +117,12 @@ ins_status ins_project(ins_grid* g, const void* u_in, void* u_out, void* p);
 /* Divergence (App. B divergence kernel): phi = D u. */
 ins_status ins_divergence(ins_grid* g, const void* u, void* phi);
 
-/* One classic RK4 step with a projection at every stage (Sec. 2.6.2):
- * k_s = F(u_s) - G p_s, u_s = u_0 + dt a_{s,s-1} k_{s-1},
- * u_{n+1} = u_0 + dt (k_1/6 + k_2/3 + k_3/3 + k_4/6).
+/* One time step of the grid's scheme with a projection at every stage (Sec. 2.6.2);
+ * every stage derivative is k_s = F(u_s) - G p_s with L p_s = D F(u_s).
+ * INS_RK4: u_s = u_0 + dt a_{s,s-1} k_{s-1}, u_{n+1} = u_0 + dt (k_1/6 + k_2/3 + k_3/3 + k_4/6).
+ * INS_WRAY3 (Butcher tableau a21 = 8/15, a31 = 1/4, a32 = 5/12, b = (1/4, 0, 3/4)), run in its
+ * two-register form u_{s+1} = u_s + dt (gamma_s k_s + zeta_s k_{s-1}) with
+ * gamma = (8/15, 5/12, 3/4), zeta = (0, -17/60, -5/12).
  * u           in/out, dim fields (the step is done in place).
  * dt_dev      DEVICE pointer to one double holding dt, read by the kernels
  *             (no host synchronisation); NULL: dt_host is used.
@@ -130,12 +140,14 @@ ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host,
  * The stage states are recomputed from u_n (per-step checkpointing: the caller keeps
  * only the step inputs), then the stages run in reverse: w_s = P kbar_s (P = P^T),
  * ubar_s = J_F(u_s)^T w_s, ubar_n = ubar_np1 + sum_s ubar_s,
- * kbar_{s-1} = dt b_{s-1} ubar_np1 + dt a_{s,s-1} ubar_s.
+ * kbar_{s-1} = dt b_{s-1} ubar_np1 + dt a_{s,s-1} ubar_s (INS_RK4). For INS_WRAY3 the
+ * state cotangents chain, Ubar_s = Ubar_{s+1} + ubar_s, and
+ * kbar_{s-1} = dt gamma_{s-1} Ubar_s + dt zeta_s Ubar_{s+1} (Ubar_4 = ubar_np1).
  * u_n, ubar_np1: DEVICE, dim fields, not modified. ubar_n: DEVICE, dim fields, must not
  * alias the inputs. dt_dev/dt_host: as in ins_step. nubar_dev: DEVICE double that the
  * result is added to (so it can accumulate over steps), or NULL.
  * Periodic uniform grids only (INS_ERR_UNSUPPORTED otherwise). The first call allocates the
- * step-VJP workspace (3 stage states, one field, nu partial sums: about 4 velocity fields),
+ * step-VJP workspace (3 stage states, two fields, nu partial sums: about 5 velocity fields),
  * kept until ins_grid_destroy; make the first call before any stream capture.
  * The grid's F, r/p and RK accumulator buffers are reused as scratch. */
 ins_status ins_step_vjp(ins_grid* g, const void* u_n, const double* dt_dev, double dt_host,

@@ -1,4 +1,4 @@
-"""Pullbacks (vector-Jacobian products) of the operators and of one RK4 step.
+"""Pullbacks (vector-Jacobian products) of the operators and of one RK step.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -23,7 +23,7 @@ import numpy as np
 from .grid import PERIODIC
 from . import operators as op
 from . import poisson
-from .timestep import RK4_A, RK4_B
+from .timestep import RK4_A, RK4_B, WRAY3_A, WRAY3_B
 
 
 def _check_periodic(g):
@@ -186,3 +186,40 @@ def rk4_step_vjp(g, u0, dt, ybar, closure=None):
     if closure is not None:
         return u0bar, nubar, wgrads
     return u0bar, nubar
+
+
+def erk_step_vjp(g, u0, dt, ybar, A, b):
+    """Pullback of one explicit RK step in Butcher form (``timestep.erk_step``), dt frozen:
+    returns (u0bar, nubar).
+
+    Forward: u_s = u0 + dt sum_{t<s} a_{s,t} k_t, k_s = P F(u_s), u1 = u0 + dt sum_s b_s k_s.
+    Reverse (s from the last stage down): kbar_s = dt b_s ybar + dt sum_{r>s} a_{r,s} ubar_r,
+    w_s = P^T kbar_s, ubar_s = J_F(u_s)^T w_s, u0bar = ybar + sum_s ubar_s,
+    nubar = sum_s <w_s, diffusion(u_s)>.
+    """
+    from .timestep import stage_derivative
+    _check_periodic(g)
+    ns = len(b)
+    us, ks = [], []
+    for s in range(ns):
+        x = u0.copy()
+        for t, a in enumerate(A[s]):
+            x = x + dt * a * ks[t]
+        us.append(x)
+        ks.append(stage_derivative(g, x))
+    kbar = [dt * b[s] * ybar for s in range(ns)]
+    u0bar = ybar.copy()
+    nubar = 0.0
+    for s in range(ns - 1, -1, -1):
+        w = project_T(g, kbar[s])
+        ubar_s, nb = F_vjp(g, us[s], w)
+        nubar += nb
+        u0bar = u0bar + ubar_s
+        for t, a in enumerate(A[s]):
+            kbar[t] = kbar[t] + dt * a * ubar_s
+    return u0bar, nubar
+
+
+def wray3_step_vjp(g, u0, dt, ybar):
+    """Pullback of one step of Wray's scheme (``timestep.wray3_step``)."""
+    return erk_step_vjp(g, u0, dt, ybar, WRAY3_A, WRAY3_B)

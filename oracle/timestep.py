@@ -13,6 +13,12 @@ Readings taken where the paper is silent:
   side k_s = F(u_s) - G p_s with L p_s = D F(u_s); the stage states are
   u_s = u_0 + dt a_{s,s-1} k_{s-1}. Because u_0 and every k_s are divergence
   free, this equals projecting the stage velocities.
+* Low-storage scheme: the paper lists Wray3 among its explicit RK methods and as its
+  low-storage method (Sec. 2.6.2, Sec. 3.3) without printing it. Reading: Wray's
+  third-order three-stage scheme, Butcher tableau a21 = 8/15, a31 = 1/4, a32 = 5/12,
+  b = (1/4, 0, 3/4), c = (0, 8/15, 2/3), with the same projected stage derivatives.
+  The oracle evaluates it in plain Butcher form (``erk_step``), not in the two-register
+  form a low-storage implementation uses.
 * CFL rule (the paper gives no formula):
   dt = cfl * min( 1 / max_{a,I} |u^a_I| / h_a[i],  min_{a,i} d_a[i]^2 / nu ).
   Every operation is one IEEE-rounded FP64 operation (abs, divide, max, min,
@@ -52,6 +58,30 @@ def rk4_step(g, u0, dt, closure=None, return_stages=False):
     return u1
 
 
+WRAY3_A = ((), (8.0 / 15.0,), (1.0 / 4.0, 5.0 / 12.0))   # row s: a_{s,t}, t < s
+WRAY3_B = (1.0 / 4.0, 0.0, 3.0 / 4.0)
+
+
+def erk_step(g, u0, dt, A, b, closure=None):
+    """One explicit RK step in Butcher form with projected stage derivatives:
+    u_s = u0 + dt sum_{t<s} a_{s,t} k_t, k_s = P F(u_s), u1 = u0 + dt sum_s b_s k_s."""
+    ks = []
+    for s in range(len(b)):
+        us = u0.copy()
+        for t, a in enumerate(A[s]):
+            us = us + dt * a * ks[t]
+        ks.append(stage_derivative(g, us, closure))
+    u1 = u0.copy()
+    for s, bs in enumerate(b):
+        u1 = u1 + dt * bs * ks[s]
+    return u1
+
+
+def wray3_step(g, u0, dt, closure=None):
+    """One step of Wray's low-storage third-order scheme (tableau in the module docstring)."""
+    return erk_step(g, u0, dt, WRAY3_A, WRAY3_B, closure)
+
+
 def max_u_over_h(g, u):
     """max_{a,I} |u^a_I| / h_a[i] in FP64 (wall faces hold 0 and do not contribute)."""
     m = 0.0
@@ -70,9 +100,10 @@ def cfl_dt(g, u, cfl):
     return cfl * min(conv, diff)
 
 
-def integrate(g, u0, dt, nsteps, closure=None):
-    """nsteps fixed-dt RK4 steps."""
+def integrate(g, u0, dt, nsteps, closure=None, scheme="rk4"):
+    """nsteps fixed-dt steps of the classic RK4 ("rk4") or Wray's scheme ("wray3")."""
+    step = {"rk4": rk4_step, "wray3": wray3_step}[scheme]
     u = u0
     for _ in range(nsteps):
-        u = rk4_step(g, u, dt, closure)
+        u = step(g, u, dt, closure)
     return u

@@ -24,6 +24,8 @@ INS_PERIODIC = 0
 INS_WALL = 1
 INS_F32 = 0
 INS_F64 = 1
+INS_RK4 = 0
+INS_WRAY3 = 1
 
 # every entry point the header declares, with (restype, argtypes)
 _c = ctypes
@@ -40,6 +42,7 @@ class GridDesc(_c.Structure):
         ("dtype", _c.c_int),
         ("nu", _c.c_double),
         ("force", _c.c_double * 3),
+        ("scheme", _c.c_int),
     ]
 
 

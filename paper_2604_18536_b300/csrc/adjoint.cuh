@@ -18,7 +18,8 @@
 //
 // The same kernel finishes the reverse stage of the RK4 step pullback:
 // ubar0 += ubar_s, and (when kb is given) the next stage cotangent
-// kbar_{s-1} = dt b_{s-1} ybar + dt a_{s,s-1} ubar_s.
+// kbar_{s-1} = dt b_{s-1} ybar + dt a_{s,s-1} ubar_s; with ybar null the value of ubar0
+// before the update takes ybar's place (the chained state cotangent of a low-storage scheme).
 #pragma once
 
 #include "common.cuh"
@@ -96,8 +97,9 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjCoef<T> c, const T* __restri
             if (extra) ubs += extra[a * N + J];   // closure pullback J_m^T w
             nup += (double)ua0 * (double)lap;
             const long e = a * N + J;
-            ubar0[e] = ubar0[e] + ubs;
-            if (kb) kb[e] = fma(dtb, ybar[e], dta * ubs);
+            const T old = ubar0[e];
+            ubar0[e] = old + ubs;
+            if (kb) kb[e] = fma(dtb, ybar ? ybar[e] : old, dta * ubs);
         }
     }
     // block partial of <u, diffusion(w)>
@@ -249,8 +251,9 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
                 if (extra) ubs += extra[a * N + J];
                 nup += (double)ua0 * (double)lap;
                 const long e = a * N + J;
-                ubar0[e] = ubar0[e] + ubs;
-                if (kb) kb[e] = fma(dtb, ybar[e], dta * ubs);
+                const T old = ubar0[e];
+                ubar0[e] = old + ubs;
+                if (kb) kb[e] = fma(dtb, ybar ? ybar[e] : old, dta * ubs);
             }
         }
         __syncthreads();

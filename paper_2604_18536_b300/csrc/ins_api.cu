@@ -82,7 +82,7 @@ struct DevBuf {
 }  // namespace
 
 struct ins_grid {
-    int dim = 0, nx = 1, ny = 1, nz = 1, wall_y = 0, dtype = 0;
+    int dim = 0, nx = 1, ny = 1, nz = 1, wall_y = 0, dtype = 0, scheme = INS_RK4;
     double nu = 0.0, force[3] = {0, 0, 0};
     cudaStream_t stream = nullptr;
     long N = 0;             // cells
@@ -374,6 +374,11 @@ bool rk_vec_ok(const ins_grid* g, const void* u) {
     return g->nx % VecT<T>::N == 0 && reinterpret_cast<uintptr_t>(u) % 16 == 0;
 }
 
+// Wray's low-storage third-order scheme in two-register form (Butcher tableau a21 = 8/15,
+// a31 = 1/4, a32 = 5/12, b = (1/4, 0, 3/4)): u_{s+1} = u_s + dt (gamma_s k_s + zeta_s k_{s-1}).
+constexpr double WRAY3_GAMMA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+constexpr double WRAY3_ZETA[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+
 template <typename T, int DIM, bool WALL>
 struct Impl {
     static ins_status rhs(ins_grid* g, const T* u, T* dudt, T* p) {
@@ -401,7 +406,60 @@ struct Impl {
         KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi));
         return INS_OK;
     }
+    // Launch the stage update (vector z-march kernel when the rows allow it).
+    template <bool LS>
+    static ins_status rk_update(ins_grid* g, const T* F, const T* rp, T* u0, T* acc, T* us, const RkArgs& ra) {
+        if (rk_vec_ok<T>(g, u0) && (!LS || us == nullptr)) {
+            constexpr int VEC = VecT<T>::N;
+            RkCoef<T> rc;
+            rc.nx = g->nx;
+            rc.ny = g->ny;
+            rc.nz = g->nz;
+            rc.ihx = (T)(1.0 / g->h[0][0]);
+            rc.ihz = (T)(1.0 / g->h[2][0]);
+            rc.ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
+            const int bx = (g->nx / VEC + 31) / 32, by = (g->ny + 7) / 8;
+            int kc = (int)(((long)bx * by * g->nz) / 2368);
+            kc = kc < 1 ? 1 : (kc > g->nz ? g->nz : kc);
+            const dim3 grd(bx, by, (g->nz + kc - 1) / kc);
+            KLAUNCH(g, "rk_update", k_rk_update_vec<T, DIM, WALL, LS><<<grd, dim3(32, 8), 0, g->stream>>>(
+                                        rc, F, rp, u0, acc, us, ra, kc));
+        } else {
+            KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL, LS><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(
+                                        make_geo<T>(g), F, rp, u0, acc, us, ra));
+        }
+        return INS_OK;
+    }
+    // Wray's low-storage 3-stage RK (two registers: F and k_{s-1}); u is updated in place.
+    static ins_status step_wray3(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
+        T* F = reinterpret_cast<T*>(g->F);
+        T* rp = reinterpret_cast<T*>(g->rp);
+        T* kprev = reinterpret_cast<T*>(g->acc);
+        ins_status s;
+        for (int st = 0; st < 3; ++st) {
+            T* m = nullptr;
+            if ((s = closure_term<T>(g, u, &m, false)) != INS_OK) return s;
+            if ((s = launch_rhs_div<T, DIM, WALL>(g, u, F, rp, m)) != INS_OK) return s;
+            if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+            RkArgs ra;
+            ra.dt_dev = dt_dev;
+            ra.dt_host = dt_host;
+            ra.a_next = WRAY3_GAMMA[st];
+            ra.b = WRAY3_ZETA[st];
+            ra.stage = st;
+            ra.last = st == 2;
+            ra.mx = (st == 2 && next_dt) ? g->cfl_max : nullptr;
+            ra.err_flag = g->err_flag;
+            if ((s = rk_update<true>(g, F, rp, u, kprev, nullptr, ra)) != INS_OK) return s;
+        }
+        if (next_dt) {
+            KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz, g->dmin2_nu, cfl,
+                                                    next_dt));
+        }
+        return INS_OK;
+    }
     static ins_status step(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
+        if (g->scheme == INS_WRAY3) return step_wray3(g, u, dt_dev, dt_host, next_dt, cfl);
         static const double A[4] = {0.5, 0.5, 1.0, 0.0};
         static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
         T* F = reinterpret_cast<T*>(g->F);
@@ -421,27 +479,10 @@ struct Impl {
             ra.a_next = A[st];
             ra.b = B[st];
             ra.stage = st;
+            ra.last = st == 3;
             ra.mx = (st == 3 && next_dt) ? g->cfl_max : nullptr;
             ra.err_flag = g->err_flag;
-            if (rk_vec_ok<T>(g, u)) {
-                constexpr int VEC = VecT<T>::N;
-                RkCoef<T> rc;
-                rc.nx = g->nx;
-                rc.ny = g->ny;
-                rc.nz = g->nz;
-                rc.ihx = (T)(1.0 / g->h[0][0]);
-                rc.ihz = (T)(1.0 / g->h[2][0]);
-                rc.ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
-                const int bx = (g->nx / VEC + 31) / 32, by = (g->ny + 7) / 8;
-                int kc = (int)(((long)bx * by * g->nz) / 2368);
-                kc = kc < 1 ? 1 : (kc > g->nz ? g->nz : kc);
-                const dim3 grd(bx, by, (g->nz + kc - 1) / kc);
-                KLAUNCH(g, "rk_update", k_rk_update_vec<T, DIM, WALL><<<grd, dim3(32, 8), 0, g->stream>>>(
-                                            rc, F, rp, u, acc, us, ra, kc));
-            } else {
-                KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, u, acc,
-                                                                                       us, ra));
-            }
+            if ((s = rk_update<false>(g, F, rp, u, acc, us, ra)) != INS_OK) return s;
         }
         if (next_dt) {
             KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz, g->dmin2_nu, cfl,
@@ -489,8 +530,28 @@ struct Impl {
         T* rp = reinterpret_cast<T*>(g->rp);
         T* scratch = reinterpret_cast<T*>(g->acc);
         ins_status s;
-        // forward: u_{s+1} = u_n + dt a_{s+1,s} k_s, s = 0, 1, 2
-        for (int st = 0; st < 3; ++st) {
+        const bool lowst = g->scheme == INS_WRAY3;
+        const int nst = lowst ? 3 : 4;
+        // forward: RK4 u_{s+1} = u_n + dt a_{s+1,s} k_s, s = 0, 1, 2; Wray
+        // u_{s+1} = u_s + dt (gamma_s k_s + zeta_s k_{s-1}), s = 0, 1 (k_{s-1} kept in scratch)
+        for (int st = 0; lowst && st < 2; ++st) {
+            T* m = nullptr;
+            if ((s = closure_term<T>(g, U[st], &m, false)) != INS_OK) return s;
+            if ((s = launch_rhs_div<T, DIM, WALL>(g, U[st], F, rp, m)) != INS_OK) return s;
+            if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+            RkArgs ra;
+            ra.dt_dev = dt_dev;
+            ra.dt_host = dt_host;
+            ra.a_next = WRAY3_GAMMA[st];
+            ra.b = WRAY3_ZETA[st];
+            ra.stage = st;
+            ra.last = 0;
+            ra.mx = nullptr;
+            ra.err_flag = g->err_flag;
+            KLAUNCH(g, "rk_update", (k_rk_update<T, DIM, WALL, true><<<cg, dim3(32, 8), 0, g->stream>>>(
+                                        make_geo<T>(g), F, rp, U[st], scratch, U[st + 1], ra)));
+        }
+        for (int st = 0; !lowst && st < 3; ++st) {
             T* m = nullptr;
             if ((s = closure_term<T>(g, U[st], &m, false)) != INS_OK) return s;
             if ((s = launch_rhs_div<T, DIM, WALL>(g, U[st], F, rp, m)) != INS_OK) return s;
@@ -501,6 +562,7 @@ struct Impl {
             ra.a_next = A[st];
             ra.b = 0.0;
             ra.stage = 0;     // writes us = u0 + dt a k (and a scratch acc), leaves u0 untouched
+            ra.last = 0;
             ra.mx = nullptr;
             ra.err_flag = g->err_flag;
             KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(
@@ -509,7 +571,8 @@ struct Impl {
         // reverse
         INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
         const long n = (long)g->dim * N;
-        KLAUNCH(g, "scale", k_scale_dt<T><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host, B[3], n));
+        KLAUNCH(g, "scale", k_scale_dt<T><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host,
+                                                                      lowst ? WRAY3_GAMMA[2] : B[3], n));
         AdjCoef<T> ac;
         ac.nx = g->nx;
         ac.ny = g->ny;
@@ -523,13 +586,20 @@ struct Impl {
         ac.nu = (T)g->nu;
         ac.dt_dev = dt_dev;
         ac.dt_host = dt_host;
-        for (int st = 3; st >= 0; --st) {
+        for (int st = nst - 1; st >= 0; --st) {
             // w = P kbar_s (P is symmetric on a uniform periodic grid)
             KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp));
             if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
             KLAUNCH(g, "sub_grad", k_sub_grad<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, W));
-            ac.bn = st > 0 ? B[st - 1] : 0.0;
-            ac.an = st > 0 ? A[st - 1] : 0.0;
+            if (lowst) {
+                // kbar_{s-1} = dt gamma_{s-1} (Ubar_{s+1} + ubar_s) + dt zeta_s Ubar_{s+1}
+                ac.bn = st > 0 ? WRAY3_GAMMA[st - 1] + WRAY3_ZETA[st] : 0.0;
+                ac.an = st > 0 ? WRAY3_GAMMA[st - 1] : 0.0;
+            } else {
+                ac.bn = st > 0 ? B[st - 1] : 0.0;
+                ac.an = st > 0 ? A[st - 1] : 0.0;
+            }
+            const T* ysrc = lowst ? nullptr : ybar;   // null: the kernel chains ubar itself
             const T* extra = nullptr;
             if (g->closure) {
                 T* m = nullptr;
@@ -540,10 +610,10 @@ struct Impl {
             }
             if (DIM == 3) {
                 KLAUNCH(g, "adj_rhs", k_adj_rhs_z<T><<<ag, dim3(AJX, AJY), adj_smem, g->stream>>>(
-                                          ac, U[st], W, ybar, ubar, st > 0 ? F : nullptr, part, extra, akc));
+                                          ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra, akc));
             } else {
                 KLAUNCH(g, "adj_rhs", k_adj_rhs<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
-                                          ac, U[st], W, ybar, ubar, st > 0 ? F : nullptr, part, extra));
+                                          ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra));
             }
             if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, nblk, nubar));
         }
@@ -721,6 +791,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     if (D.dim != 2 && D.dim != 3) return fail(INS_ERR_ARG, "dim must be 2 or 3");
     if (D.dtype != INS_F32 && D.dtype != INS_F64) return fail(INS_ERR_ARG, "dtype must be INS_F32 or INS_F64");
     if (!(D.nu >= 0.0) || !std::isfinite(D.nu)) return fail(INS_ERR_ARG, "nu must be finite and >= 0");
+    if (D.scheme != INS_RK4 && D.scheme != INS_WRAY3) return fail(INS_ERR_ARG, "scheme must be INS_RK4 or INS_WRAY3");
     for (int a = 0; a < D.dim; ++a) {
         if (D.n[a] < 2 || D.n[a] > 4096) return fail(INS_ERR_ARG, "n[a] must be in [2, 4096]");
         if (D.bc[a] != INS_PERIODIC && D.bc[a] != INS_WALL) return fail(INS_ERR_ARG, "bc must be PERIODIC or WALL");
@@ -742,6 +813,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     g->nz = D.dim == 3 ? D.n[2] : 1;
     g->wall_y = wall_y ? 1 : 0;
     g->dtype = D.dtype;
+    g->scheme = D.scheme;
     g->nu = D.nu;
     for (int a = 0; a < 3; ++a) g->force[a] = a < D.dim ? D.force[a] : 0.0;
     g->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -825,7 +897,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     }
     o_F = off; off += al((size_t)dim * N * ts);
     o_acc = off; off += al((size_t)dim * N * ts);
-    o_us = off; off += al((size_t)dim * N * ts);
+    o_us = off; off += D.scheme == INS_RK4 ? al((size_t)dim * N * ts) : 0;   // the low-storage scheme needs no stage state
     o_rp = off; off += al((size_t)N * ts);
     o_S = off; off += al((size_t)spec * 2 * ts);
     o_cfl = off; off += al(nsum * 8);
@@ -856,7 +928,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     }
     g->F = b + o_F;
     g->acc = b + o_acc;
-    g->us = b + o_us;
+    g->us = D.scheme == INS_RK4 ? b + o_us : nullptr;
     g->rp = b + o_rp;
     g->S = b + o_S;
     g->cfl_max = reinterpret_cast<unsigned long long*>(b + o_cfl);

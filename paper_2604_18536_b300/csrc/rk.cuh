@@ -1,11 +1,14 @@
-// Projection + classic RK4 stage update with 16-byte vector accesses and a z march
+// Projection + RK stage update with 16-byte vector accesses and a z march
 // (paper Sec. 2.6.2; pressure gradient of App. B).
 //
-// k = F - G p, (G p)^a = (p_{I+e_a} - p_I) / h_a, then
+// k = F - G p, (G p)^a = (p_{I+e_a} - p_I) / h_a, then for the classic RK4 scheme
 //   stage 0: acc = b0 k;    us = u0 + dt a1 k
 //   stage 1,2: acc += b k;  us = u0 + dt a k
 //   stage 3: u0 = u0 + dt (acc + b3 k) in place, the CFL per-index maxima of
-//            |u_{n+1}| and the non-finite flag.
+//            |u_{n+1}| and the non-finite flag;
+// and for the low-storage Wray scheme (LS; two registers u and k_{s-1}, Sec. 3.3)
+//   u0 = u0 + dt (gamma_s k + zeta_s acc) in place, acc = k (not on the last stage),
+//   the maxima and the flag on the last stage.
 // Each thread owns VEC consecutive cells in x (one float4 / double2) of one row
 // j and marches through a chunk of z planes: the pressure of plane k+1 loaded
 // for G p in z is the centre pressure of the next plane, and the x neighbour of
@@ -55,7 +58,7 @@ struct RkCoef {
 
 // Block (32, 8); grid (ceil(nx/VEC/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx % VEC == 0 and
 // 16-byte aligned field pointers.
-template <typename T, int DIM, bool WALL>
+template <typename T, int DIM, bool WALL, bool LS = false>
 __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __restrict__ F, const T* __restrict__ p,
                                                        T* __restrict__ u0, T* __restrict__ acc, T* __restrict__ us,
                                                        RkArgs ra, int kchunk) {
@@ -74,6 +77,8 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
     const int ke = min(kb + kchunk, nz);
     const double dt = ra.dt_dev ? *ra.dt_dev : ra.dt_host;
     const T dta = (T)(dt * ra.a_next), bb = (T)ra.b, dtt = (T)dt;
+    const T dtz = (T)(dt * ra.b);
+    const bool fin = LS ? ra.last != 0 : ra.stage == 3;
     const T ihy = __ldg(&c.ihy[j < ny ? j : ny - 1]);
     const bool top = WALL && j == ny - 1;
     const bool last_vec = iv == nvx - 1;
@@ -118,7 +123,28 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
                 const long ea = cc * N + a;
                 T uv[VEC], av[VEC];
                 VT::ld(u0 + ea, uv);
-                if (ra.stage == 0) {
+                if (LS) {
+                    if (ra.stage > 0) {
+                        VT::ld(acc + ea, av);
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) uv[e] += fma(dtz, av[e], dta * kk[cc][e]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) uv[e] += dta * kk[cc][e];
+                    }
+                    if (!ra.last) VT::st(acc + ea, kk[cc]);
+                    if (ra.last) {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) {
+                            bad |= !isfinite(uv[e]);
+                            const double q = fabs((double)uv[e]);
+                            if (cc == 0) mxx[e] = fmax(mxx[e], q);
+                            else if (cc == 1) mxy = fmax(mxy, q);
+                            else qz = fmax(qz, q);
+                        }
+                    }
+                    VT::st(u0 + ea, uv);
+                } else if (ra.stage == 0) {
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) {
                         av[e] = bb * kk[cc][e];
@@ -153,14 +179,14 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
 #pragma unroll
             for (int e = 0; e < VEC; ++e) Pt[e] = (T)0;
         }
-        if (ra.stage == 3 && ra.mx && DIM == 3) {
+        if (fin && ra.mx && DIM == 3) {
             for (int o = 16; o > 0; o >>= 1) qz = fmax(qz, __shfl_xor_sync(0xffffffffu, qz, o));
             if (lane == 0 && qz > 0.0) atomicMax(&ra.mx[nx + ny + k], (unsigned long long)__double_as_longlong(qz));
         }
 #pragma unroll
         for (int e = 0; e < VEC; ++e) P0[e] = Pt[e];
     }
-    if (ra.stage == 3) {
+    if (fin) {
         if (ra.mx) {
             __shared__ double sx[8][32 * VEC + 1];
 #pragma unroll

@@ -2,7 +2,8 @@
 // equation, App. B kernels) and the fused projection + RK update.
 //
 // k_divergence, k_sub_grad: D u and src - G p (projection, right-hand side).
-// k_rk_update: k = F - G p and the classic RK4 stage update; k_cfl_finalize: the
+// k_rk_update: k = F - G p and the stage update of the classic RK4 scheme or (LS) of
+// the low-storage 3-stage Wray scheme; k_cfl_finalize: the
 // CFL time step from per-index maxima; k_diag: energy, divergence, CFL maxima.
 // (F and D F are computed by k_rhs_div in rhs.cuh.)
 #pragma once
@@ -72,15 +73,22 @@ __global__ void k_sub_grad(Geo<T> g, const T* __restrict__ src, const T* __restr
 struct RkArgs {
     const double* dt_dev;
     double dt_host;
-    double a_next;   // a_{s+1,s}
-    double b;        // b_s
+    double a_next;   // RK4: a_{s+1,s}; low-storage: gamma_s
+    double b;        // RK4: b_s; low-storage: zeta_s (weight of the previous stage's k)
     int stage;
+    int last;        // low-storage: this is the last stage (CFL maxima, finite check)
     unsigned long long* mx;   // [nx + ny + nz] per-index maxima of |u^a|; null: skip
     unsigned int* err_flag;   // bit 0: non-finite value seen
 };
 
 // Block shape must be (32, 8): x rows of one warp each.
-template <typename T, int DIM, bool WALL>
+//
+// RK4 (LS = false): stage 0 acc = b k, us = u0 + dt a k; stages 1, 2 acc += b k,
+// us = u0 + dt a k; stage 3 u0 += dt (acc + b k).
+// Low storage (LS = true, the two-register form u_{s+1} = u_s + dt (gamma_s k_s +
+// zeta_s k_{s-1})): u0 holds u_s, acc holds k_{s-1} (read for stage > 0) and receives k_s
+// (unless last); the result goes to us, or back into u0 when us is null.
+template <typename T, int DIM, bool WALL, bool LS = false>
 __global__ void __launch_bounds__(256) k_rk_update(Geo<T> g, const T* __restrict__ F, const T* __restrict__ p,
                                                    T* __restrict__ u0, T* __restrict__ acc, T* __restrict__ us,
                                                    RkArgs ra) {
@@ -92,6 +100,8 @@ __global__ void __launch_bounds__(256) k_rk_update(Geo<T> g, const T* __restrict
     const bool in = i < nx && j < ny;
     const double dt = ra.dt_dev ? *ra.dt_dev : ra.dt_host;
     const T dta = (T)(dt * ra.a_next), bb = (T)ra.b, dtt = (T)dt;
+    const T dtz = (T)(dt * ra.b);
+    const bool fin = LS ? ra.last != 0 : ra.stage == 3;
     double q[3] = {0.0, 0.0, 0.0};
     bool bad = false;
     if (in) {
@@ -110,7 +120,18 @@ __global__ void __launch_bounds__(256) k_rk_update(Geo<T> g, const T* __restrict
         for (int c = 0; c < DIM; ++c) {
             const long e = c * N + a;
             const T u0v = u0[e];
-            if (ra.stage == 0) {
+            if (LS) {
+                T inc = dta * kk[c];
+                if (ra.stage > 0) inc = fma(dtz, acc[e], inc);
+                const T un = u0v + inc;
+                if (!ra.last) acc[e] = kk[c];
+                if (us) us[e] = un;
+                else u0[e] = un;
+                if (ra.last) {
+                    q[c] = fabs((double)un);
+                    bad |= !isfinite(un);
+                }
+            } else if (ra.stage == 0) {
                 acc[e] = bb * kk[c];
                 us[e] = u0v + dta * kk[c];
             } else if (ra.stage < 3) {
@@ -124,7 +145,7 @@ __global__ void __launch_bounds__(256) k_rk_update(Geo<T> g, const T* __restrict
             }
         }
     }
-    if (ra.stage == 3) {
+    if (fin) {
         if (ra.mx) {
             __shared__ double sx[8][33];
             const int lane = threadIdx.x, row = threadIdx.y;

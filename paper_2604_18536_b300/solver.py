@@ -55,10 +55,16 @@ class Grid:
     bc:    list of "periodic" | "wall" (only y may be a wall)
     nu, force: viscosity and constant body force
     dtype: torch.float32 or torch.float64
+    scheme: "rk4" (classic RK4) or "wray3" (Wray's low-storage third-order RK)
     """
 
-    def __init__(self, faces, bc, nu, force=None, dtype=torch.float64, device=None):
+    SCHEMES = {"rk4": _lib.INS_RK4, "wray3": _lib.INS_WRAY3}
+
+    def __init__(self, faces, bc, nu, force=None, dtype=torch.float64, device=None, scheme="rk4"):
         self.dim = len(faces)
+        if scheme not in self.SCHEMES:
+            raise ValueError(f"scheme must be one of {sorted(self.SCHEMES)}")
+        self.scheme = scheme
         self.faces = [np.ascontiguousarray(f, dtype=np.float64) for f in faces]
         self.n = tuple(len(f) - 1 for f in self.faces)
         self.shape = tuple(reversed(self.n))
@@ -79,6 +85,7 @@ class Grid:
             d.force[a] = self.force[a] if a < self.dim else 0.0
         d.dtype = _lib.INS_F64 if dtype == torch.float64 else _lib.INS_F32
         d.nu = self.nu
+        d.scheme = self.SCHEMES[scheme]
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib().ins_grid_create(ctypes.byref(d), ctypes.c_void_p(self._stream()), ctypes.byref(h)),

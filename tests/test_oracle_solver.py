@@ -158,6 +158,61 @@ def test_rk4_order_in_time():
     assert 12 < e1 / e2 < 20
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_shear_wave_wray3_amplification(dim):
+    """Every three-stage third-order explicit RK has the stability function
+    R(z) = 1 + z + z^2/2 + z^3/6: on the shear wave (no convection, identity projection)
+    one Wray step multiplies the field by it."""
+    n, m, nu, dt = 16, 3, 0.2, 0.01
+    g = periodic_grid(n, dim, nu=nu)
+    D = 2 * np.pi / n
+    u = g.zeros_u()
+    y = g.face_coords(0)[1]
+    u[0] = np.sin(m * y) * np.ones(g.shape)
+    z = -dt * nu * (4 / D ** 2) * np.sin(m * D / 2) ** 2
+    R = 1 + z + z ** 2 / 2 + z ** 3 / 6
+    u1 = timestep.wray3_step(g, u, dt)
+    np.testing.assert_allclose(u1[0], R * u[0], atol=1e-14)
+    np.testing.assert_allclose(u1[1:], 0.0, atol=1e-14)
+
+
+def test_wray3_order_in_time():
+    """Temporal order 3 on a nonlinear (convective) flow: halving dt cuts the error by ~8.
+    A wrong tableau entry (for example a32 = 1/2) drops the order and fails the ratio."""
+    g = periodic_grid(8, 2, nu=0.05)
+    u0, _ = poisson.project(g, random_u(g, 12))
+    ref = timestep.integrate(g, u0, 0.2 / 64, 64)        # RK4, error far below the Wray errors
+    e1 = np.max(np.abs(timestep.integrate(g, u0, 0.2 / 4, 4, scheme="wray3") - ref))
+    e2 = np.max(np.abs(timestep.integrate(g, u0, 0.2 / 8, 8, scheme="wray3") - ref))
+    assert 6.5 < e1 / e2 < 9.5
+
+
+def test_wray3_tableau_low_storage_form():
+    """The tableau equals the two-register recurrence u_{s+1} = u_s + dt (g_s k_s + z_s k_{s-1})
+    with g = (8/15, 5/12, 3/4), z = (0, -17/60, -5/12): a_{s+1,t} = a_{s,t} for t < s - 1,
+    a_{s+1,s-1} = a_{s,s-1} + z_s, a_{s+1,s} = g_s (b as the fourth row)."""
+    from fractions import Fraction as Fr
+    gam = (Fr(8, 15), Fr(5, 12), Fr(3, 4))
+    zet = (Fr(0), Fr(-17, 60), Fr(-5, 12))
+    rows = [[]]
+    for s in range(3):
+        prev = rows[-1] + [Fr(0)]
+        new = list(prev)
+        new[s] = gam[s]
+        if s > 0:
+            new[s - 1] = prev[s - 1] + zet[s]
+        rows.append(new)
+    A = [[Fr(x).limit_denominator(1000) for x in r] for r in timestep.WRAY3_A]
+    assert rows[1][:1] == A[1] and rows[2][:2] == A[2]
+    assert rows[3] == [Fr(x).limit_denominator(1000) for x in timestep.WRAY3_B]
+    # third-order conditions
+    b = rows[3]
+    c = [Fr(0), sum(A[1]), sum(A[2])]
+    assert sum(b) == 1 and sum(bi * ci for bi, ci in zip(b, c)) == Fr(1, 2)
+    assert sum(bi * ci * ci for bi, ci in zip(b, c)) == Fr(1, 3)
+    assert b[2] * A[2][1] * c[1] == Fr(1, 6)
+
+
 # ------------------------------------------------------------------ adjoints
 def _dot(a, b):
     return float(np.sum(a * b))
@@ -209,6 +264,38 @@ def test_step_vjp_dot_product_and_fd():
     eps = 1e-6
     for seed in range(3):
         du = random_u(g, 100 + seed)
+        fd = (loss(u0 + eps * du, g.nu) - loss(u0 - eps * du, g.nu)) / (2 * eps)
+        assert abs(fd - _dot(ubar, du)) < 1e-7 * max(1, abs(fd))
+    fdn = (loss(u0, g.nu + eps) - loss(u0, g.nu - eps)) / (2 * eps)
+    assert abs(fdn - nubar) < 1e-6 * max(1, abs(fdn))
+
+
+def test_erk_vjp_reduces_to_rk4_vjp():
+    """The generic Butcher-form pullback with the RK4 tableau is the RK4 step pullback."""
+    g = periodic_grid(6, 3, nu=0.05)
+    u0, _ = poisson.project(g, random_u(g, 31))
+    c = random_u(g, 32)
+    A = ((), (0.5,), (0.0, 0.5), (0.0, 0.0, 1.0))
+    ub1, nb1 = adjoint.erk_step_vjp(g, u0, 0.05, c, A, timestep.RK4_B)
+    ub2, nb2 = adjoint.rk4_step_vjp(g, u0, 0.05, c)
+    np.testing.assert_allclose(ub1, ub2, rtol=0, atol=1e-13 * np.max(np.abs(ub2)))
+    assert abs(nb1 - nb2) <= 1e-12 * abs(nb2)
+
+
+def test_wray3_step_vjp_fd():
+    """Wray step VJP against central finite differences (eps = 1e-6) in u0 and nu."""
+    g = periodic_grid(6, 3, nu=0.05)
+    u0, _ = poisson.project(g, random_u(g, 41))
+    dt = 0.05
+    c = random_u(g, 42)
+
+    def loss(u, nu):
+        return _dot(c, timestep.wray3_step(periodic_grid(6, 3, nu=nu), u, dt))
+
+    ubar, nubar = adjoint.wray3_step_vjp(g, u0, dt, c)
+    eps = 1e-6
+    for seed in range(3):
+        du = random_u(g, 140 + seed)
         fd = (loss(u0 + eps * du, g.nu) - loss(u0 - eps * du, g.nu)) / (2 * eps)
         assert abs(fd - _dot(ubar, du)) < 1e-7 * max(1, abs(fd))
     fdn = (loss(u0, g.nu + eps) - loss(u0, g.nu - eps)) / (2 * eps)
