@@ -159,6 +159,250 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_fft_strided_reg
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Pipelined strided pass (FP32): persistent CTAs walk the tiles of TW columns; the tile
+// after the current one is copied global -> shared with cp.async while the current one is
+// transformed, so the HBM latency is hidden behind the butterflies. The tile's shared
+// buffer (L rows of TW padded columns) also serves as the exchange buffer once stage A has
+// read it. Mode 2 prefetches the spectral scale of the tile the same way.
+__device__ __forceinline__ void fr_cp_async(void* smem, const void* gmem, int bytes, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void fr_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void fr_cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void fr_cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int R1, int R2>
+struct PipeShape {
+    static constexpr int L = R1 * R2;
+    static constexpr int RM = R1 > R2 ? R1 : R2;
+    static constexpr int NT = 256;
+    static constexpr int TW = NT / RM;
+    static constexpr int SP = TW + 1;
+    static constexpr int PER = L * TW / NT;   // copies per thread per tile
+    static constexpr size_t smem(bool scaled) {
+        return 2 * (size_t)L * SP * sizeof(cplx<float>) + (scaled ? 2 * (size_t)L * TW * sizeof(float) : 0);
+    }
+};
+
+// Same modes, addressing and results as k_fft_strided_reg<float, R1, R2>; grid = any number of
+// CTAs (persistent), dynamic shared memory PipeShape::smem(mode == 2).
+template <int R1, int R2>
+__global__ void __launch_bounds__(256, 2) k_fft_strided_pipe(const cplx<float>* __restrict__ tw, cplx<float>* __restrict__ S,
+                                                            long ncol, long cdiv, long outer, long lstride, int mode,
+                                                            const float* __restrict__ scale) {
+    using T = float;
+    using Sh = PipeShape<R1, R2>;
+    constexpr int L = Sh::L, TW = Sh::TW, SP = Sh::SP;
+    extern __shared__ __align__(16) unsigned char fr_smem[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(fr_smem);              // [2][L * SP]
+    T* sc = reinterpret_cast<T*>(buf + 2 * L * SP);                    // [2][L * TW] (mode 2)
+    const long ntiles = (ncol + TW - 1) / TW;
+    const int c = threadIdx.x % TW;
+    const int q = threadIdx.x / TW;
+    // copy e = threadIdx.x + NT t of a tile is element (column e % TW, row e / TW); NT is a
+    // multiple of TW, so a thread's column is the same for all its copies: one address
+    // computation per tile, then row steps of (NT / TW) lstride
+    static_assert(Sh::NT % TW == 0, "tile columns must divide the CTA size");
+    constexpr int MSTEP = Sh::NT / TW;
+    auto issue = [&](long tile, int b) {
+        cplx<T>* dst = buf + b * L * SP;
+        const long col = tile * TW + c;
+        const bool ok = col < ncol;
+        const int nb = ok ? 8 : 0;
+        const long base = ok ? (col / cdiv) * outer + (col % cdiv) + (long)q * lstride : 0;
+        const long step = ok ? (long)MSTEP * lstride : 0;
+#pragma unroll
+        for (int t = 0; t < Sh::PER; ++t) {
+            const int m = q + MSTEP * t;
+            fr_cp_async(dst + m * SP + c, S + base + t * step, 8, nb);
+            if (mode == 2) fr_cp_async(sc + b * L * TW + m * TW + c, scale + base + t * step, 4, nb / 2);
+        }
+        fr_cp_commit();
+    };
+    long tile = blockIdx.x;
+    int b = 0;
+    if (tile < ntiles) issue(tile, 0);
+    for (; tile < ntiles; tile += gridDim.x, b ^= 1) {
+        const long next = tile + gridDim.x;
+        if (next < ntiles) issue(next, b ^ 1);
+        else fr_cp_commit();   // empty group: the wait below always leaves one group pending
+        fr_cp_wait1();
+        __syncthreads();
+        cplx<T>* X = buf + b * L * SP;
+        const long col = tile * TW + c;
+        const bool ok = col < ncol;
+        const long cb = ok ? (col / cdiv) * outer + (col % cdiv) : 0;
+        cplx<T> v[Sh::RM];
+        // forward stage A: thread (c, j = q < R2)
+        if (q < R2) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                cplx<T> z = X[(q + R2 * r) * SP + c];
+                if (mode == 1) z = cconj(z);
+                v[r] = z;
+            }
+            stage_a<T, R1>(v, q, tw);
+        }
+        __syncthreads();   // the tile has been read: X becomes the exchange buffer
+        if (q < R2) {
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) X[(q * R1 + k1) * SP + c] = v[k1];
+        }
+        __syncthreads();
+        if (q < R1) {
+#pragma unroll
+            for (int j = 0; j < R2; ++j) v[j] = X[(j * R1 + q) * SP + c];
+            DftR<T, R2>::run(v);   // v[k2] = X[q + R1 k2]
+        }
+        if (mode == 2) {
+            const T* scb = sc + b * L * TW;
+            if (q < R1) {
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2) {
+                    const T s = scb[(q + R1 * k2) * TW + c];
+                    v[k2] = {v[k2].re * s, -v[k2].im * s};
+                }
+                stage_a<T, R2>(v, q, tw);
+            }
+            __syncthreads();
+            if (q < R1) {
+#pragma unroll
+                for (int k1 = 0; k1 < R2; ++k1) X[(q * R2 + k1) * SP + c] = v[k1];
+            }
+            __syncthreads();
+            if (q < R2) {
+#pragma unroll
+                for (int j = 0; j < R1; ++j) v[j] = X[(j * R2 + q) * SP + c];
+                DftR<T, R1>::run(v);
+                if (ok) {
+#pragma unroll
+                    for (int k2 = 0; k2 < R1; ++k2) S[cb + (long)(q + R2 * k2) * lstride] = cconj(v[k2]);
+                }
+            }
+        } else if (q < R1 && ok) {
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) {
+                cplx<T> z = v[k2];
+                if (mode == 1) z = cconj(z);
+                S[cb + (long)(q + R1 * k2) * lstride] = z;
+            }
+        }
+        __syncthreads();   // buffer b is refilled two tiles ahead
+    }
+    fr_cp_wait0();
+}
+
+// Pipelined inverse x pass (FP32): a tile of TW line pairs is one contiguous block of the
+// half spectrum (2 TW rows of nxh complex), copied with 16-byte cp.async into a double
+// buffer while the previous tile is transformed. Needs a 16-byte aligned spectrum (checked
+// by the caller); the tail of the last tile is zero-filled (src-size operand). (The same
+// staging for the forward pass measured slower than its direct register loads.)
+__device__ __forceinline__ void fr_cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+
+template <int R1, int R2>
+struct PipeX {
+    static constexpr int L = R1 * R2;
+    static constexpr int RM = R1 > R2 ? R1 : R2;
+    static constexpr int NT = 256;
+    static constexpr int TW = NT / RM;          // line pairs per tile
+    static constexpr int SR = L + L / 16 + 1;   // padded exchange row
+    static constexpr size_t smem_c2r(int nxh) {
+        return 2 * (((size_t)2 * TW * nxh * sizeof(cplx<float>) + 15) & ~size_t(15)) + (size_t)TW * SR * sizeof(cplx<float>);
+    }
+};
+
+template <int R1, int R2>
+__global__ void __launch_bounds__(256, 2) k_fft_x_c2r_pipe(const cplx<float>* __restrict__ tw, const cplx<float>* __restrict__ S,
+                                                          float* __restrict__ out, int lines, int nxh) {
+    using T = float;
+    using Sh = PipeX<R1, R2>;
+    constexpr int L = Sh::L, TW = Sh::TW, RM = Sh::RM, SR = Sh::SR;
+    extern __shared__ __align__(16) unsigned char fx_smem[];
+    const int rawc = (int)(((size_t)2 * TW * nxh * sizeof(cplx<T>) + 15) / 16) * 2;   // complex per buffer
+    cplx<T>* raw = reinterpret_cast<cplx<T>*>(fx_smem);           // [2][rawc]
+    cplx<T>* ex = raw + 2 * rawc;                                 // [TW][SR]
+    const long npairs = ((long)lines + 1) / 2;
+    const long ntiles = (npairs + TW - 1) / TW;
+    const long total = (long)lines * nxh;      // complex values in the half spectrum
+    const int nch = TW * nxh;                  // 16-byte chunks (two complex values) per tile
+    auto sidx = [](int m) { return m + (m >> 4); };
+    auto issue = [&](long tile, int b) {
+        const long c0 = tile * 2 * TW * nxh;
+        for (int ch = threadIdx.x; ch < nch; ch += Sh::NT) {
+            const long e = c0 + 2 * (long)ch;
+            const long left = total - e;
+            const int nb = left >= 2 ? 16 : (left > 0 ? 8 : 0);
+            fr_cp_async16(raw + b * rawc + 2 * ch, nb > 0 ? S + e : S, nb);
+        }
+        fr_cp_commit();
+    };
+    const int q = threadIdx.x % RM;
+    const int c = threadIdx.x / RM;
+    long tile = blockIdx.x;
+    int b = 0;
+    if (tile < ntiles) issue(tile, 0);
+    for (; tile < ntiles; tile += gridDim.x, b ^= 1) {
+        const long next = tile + gridDim.x;
+        if (next < ntiles) issue(next, b ^ 1);
+        else fr_cp_commit();
+        fr_cp_wait1();
+        __syncthreads();
+        const cplx<T>* rw = raw + b * rawc;
+        // Z = A + i B over the full line (Hermitian extension), conjugated for the inverse
+        for (int item = threadIdx.x; item < TW * L; item += Sh::NT) {
+            const int cc = item / L, m = item - cc * L;
+            const bool upper = m >= nxh;
+            const int src = upper ? L - m : m;
+            cplx<T> A = rw[(2 * cc) * nxh + src];
+            cplx<T> B = rw[(2 * cc + 1) * nxh + src];
+            if (upper) {
+                A = cconj(A);
+                B = cconj(B);
+            }
+            if (m == 0 || 2 * m == L) {
+                A.im = (T)0;
+                B.im = (T)0;
+            }
+            ex[cc * SR + sidx(m)] = {A.re - B.im, -(A.im + B.re)};
+        }
+        __syncthreads();
+        cplx<T> v[RM];
+        if (q < R2) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v[r] = ex[c * SR + sidx(q + R2 * r)];
+            stage_a<T, R1>(v, q, tw);
+        }
+        __syncthreads();
+        if (q < R2) {
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) ex[c * SR + sidx(q * R1 + k1)] = v[k1];
+        }
+        __syncthreads();
+        if (q < R1) {
+            const long la = 2 * (tile * TW + c), lb = la + 1;
+#pragma unroll
+            for (int j = 0; j < R2; ++j) v[j] = ex[c * SR + sidx(j * R1 + q)];
+            DftR<T, R2>::run(v);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) {
+                const int m = q + R1 * k2;
+                if (la < lines) out[la * L + m] = v[k2].re;
+                if (lb < lines) out[lb * L + m] = -v[k2].im;
+            }
+        }
+        __syncthreads();   // ex and raw[b] are free
+    }
+    fr_cp_wait0();
+}
+
 // x pass, real lines -> half spectra. CTA handles TW line pairs packed as a + i b.
 // Thread mapping (j fastest) keeps the loads along a line contiguous.
 template <typename T, int R1, int R2>

@@ -182,6 +182,138 @@ __device__ __forceinline__ T eval_Fz(const RhsCoef<T>& c, const YRow<T>& y, CPla
     return fma(-y.f, Y, acc);
 }
 
+// The 27 values the three F evaluations of one cell read in 3-D (planes m = k-1, o = k,
+// p = k+1; suffixes e/w/n/s = +x/-x/+y/-y). Along the z march, the m values and five of the
+// o values are the previous iteration's o and p values, kept in registers, so each plane
+// costs 17 shared loads per cell instead of 27.
+template <typename T>
+struct Nb {
+    T X0, X0e, X0w, X0n, X0s, X0wn;       // u^x, plane o
+    T Y0, Y0e, Y0w, Y0n, Y0s, Y0es;       // u^y, plane o
+    T Z0, Z0e, Z0w, Z0n, Z0s;             // u^z, plane o
+    T Xp, Xpw, Yp, Yps, Zp;               // plane p
+    T Xm, Ym, Zm, Zme, Zmn;               // plane m
+};
+
+// o-plane values not carried over from the previous iteration's p plane
+template <typename T>
+__device__ __forceinline__ void nb_load_o(Nb<T>& v, CPlane<T> o, int c0) {
+    v.X0e = o[0][c0 + 1];
+    v.X0n = o[0][c0 + RSX];
+    v.X0s = o[0][c0 - RSX];
+    v.X0wn = o[0][c0 - 1 + RSX];
+    v.Y0e = o[1][c0 + 1];
+    v.Y0w = o[1][c0 - 1];
+    v.Y0n = o[1][c0 + RSX];
+    v.Y0es = o[1][c0 + 1 - RSX];
+    v.Z0e = o[2][c0 + 1];
+    v.Z0w = o[2][c0 - 1];
+    v.Z0n = o[2][c0 + RSX];
+    v.Z0s = o[2][c0 - RSX];
+}
+
+template <typename T>
+__device__ __forceinline__ void nb_load_p(Nb<T>& v, CPlane<T> p, int c0) {
+    v.Xp = p[0][c0];
+    v.Xpw = p[0][c0 - 1];
+    v.Yp = p[1][c0];
+    v.Yps = p[1][c0 - RSX];
+    v.Zp = p[2][c0];
+}
+
+// end of an iteration: o -> m, p -> o (the carried part)
+template <typename T>
+__device__ __forceinline__ void nb_rotate(Nb<T>& v) {
+    v.Xm = v.X0;
+    v.Ym = v.Y0;
+    v.Zm = v.Z0;
+    v.Zme = v.Z0e;
+    v.Zmn = v.Z0n;
+    v.X0 = v.Xp;
+    v.X0w = v.Xpw;
+    v.Y0 = v.Yp;
+    v.Y0s = v.Yps;
+    v.Z0 = v.Zp;
+}
+
+// Same arithmetic as eval_Fx / eval_Fy / eval_Fz (DIM = 3) on register values.
+template <typename T, bool WALL>
+__device__ __forceinline__ T nb_Fx(const RhsCoef<T>& c, const YRow<T>& y, const Nb<T>& v) {
+    const T uc = v.X0, ue = v.X0e, uw = v.X0w, un = v.X0n, us = v.X0s;
+    const T s1 = uc + ue, s2 = uw + uc;
+    const T X = fma(s1, s1, -s2 * s2);
+    const T vp = v.Y0 + v.Y0e, vm = v.Y0s + v.Y0es;
+    const T Y = fma(vp, uc + un, -vm * (us + uc));
+    T acc = fma(c.dx, ue + uw, c.fx);
+    acc = fma(y.bp, un, acc);
+    acc = fma(y.bm, us, acc);
+    T dsum = (T)2 * c.dx + y.bp + y.bm;
+    const T ut = v.Xp, ub = v.Xm;
+    const T wp = v.Z0 + v.Z0e, wm = v.Zm + v.Zme;
+    const T Z = fma(wp, uc + ut, -wm * (ub + uc));
+    acc = fma(c.dz, ut + ub, acc);
+    dsum += (T)2 * c.dz;
+    acc = fma(-c.cz, Z, acc);
+    acc = fma(-dsum, uc, acc);
+    acc = fma(-c.cx, X, acc);
+    return fma(-y.f, Y, acc);
+}
+
+template <typename T, bool WALL>
+__device__ __forceinline__ T nb_Fy(const RhsCoef<T>& c, const YRow<T>& y, const Nb<T>& v) {
+    const T uc = v.Y0, un = v.Y0n, us = v.Y0s, ue = v.Y0e, uw = v.Y0w;
+    const T s1 = uc + un, s2 = us + uc;
+    const T Ys = fma(s1, s1, -s2 * s2);
+    T vp, vm, cxf, wp, wm, czf;
+    if constexpr (WALL) {
+        vp = fma(y.wl, v.X0, y.wr * v.X0n);
+        vm = fma(y.wl, v.X0w, y.wr * v.X0wn);
+        cxf = (T)2 * c.cx;
+        wp = fma(y.wl, v.Z0, y.wr * v.Z0n);
+        wm = fma(y.wl, v.Zm, y.wr * v.Zmn);
+        czf = (T)2 * c.cz;
+    } else {
+        vp = v.X0 + v.X0n;
+        vm = v.X0w + v.X0wn;
+        cxf = c.cx;
+        wp = v.Z0 + v.Z0n;
+        wm = v.Zm + v.Zmn;
+        czf = c.cz;
+    }
+    const T X = fma(vp, uc + ue, -vm * (uw + uc));
+    T acc = fma(c.dx, ue + uw, c.fy);
+    acc = fma(y.ap, un, acc);
+    acc = fma(y.am, us, acc);
+    T dsum = (T)2 * c.dx + y.ap + y.am;
+    const T ut = v.Yp, ub = v.Ym;
+    const T Z = fma(wp, uc + ut, -wm * (ub + uc));
+    acc = fma(c.dz, ut + ub, acc);
+    dsum += (T)2 * c.dz;
+    acc = fma(-czf, Z, acc);
+    acc = fma(-dsum, uc, acc);
+    acc = fma(-y.s, Ys, acc);
+    return fma(-cxf, X, acc);
+}
+
+template <typename T, bool WALL>
+__device__ __forceinline__ T nb_Fz(const RhsCoef<T>& c, const YRow<T>& y, const Nb<T>& v) {
+    const T uc = v.Z0, ut = v.Zp, ub = v.Zm, ue = v.Z0e, uw = v.Z0w, un = v.Z0n, us = v.Z0s;
+    const T s1 = uc + ut, s2 = ub + uc;
+    const T Zs = fma(s1, s1, -s2 * s2);
+    const T vp = v.X0 + v.Xp, vm = v.X0w + v.Xpw;
+    const T X = fma(vp, uc + ue, -vm * (uw + uc));
+    const T wp = v.Y0 + v.Yp, wm = v.Y0s + v.Yps;
+    const T Y = fma(wp, uc + un, -wm * (us + uc));
+    T acc = fma(c.dx, ue + uw, c.fz);
+    acc = fma(c.dz, ut + ub, acc);
+    acc = fma(y.bp, un, acc);
+    acc = fma(y.bm, us, acc);
+    acc = fma(-((T)2 * (c.dx + c.dz) + y.bp + y.bm), uc, acc);
+    acc = fma(-c.cz, Zs, acc);
+    acc = fma(-c.cx, X, acc);
+    return fma(-y.f, Y, acc);
+}
+
 // Where each thread's share of a plane comes from (the same for every plane).
 template <bool WALL>
 struct PlaneMap {
@@ -217,17 +349,25 @@ __device__ __forceinline__ PlaneMap<WALL> plane_map(int nx, int ny, int i0, int 
     return pm;
 }
 
+// Offsets are 32-bit: grids hold fewer than 2^31 cells, so every in-component index fits.
 template <typename T, int DIM, bool WALL>
-__device__ __forceinline__ void plane_fetch(const PlaneMap<WALL>& pm, const T* __restrict__ u, long N, long base,
-                                            T (&v)[DIM][RPF]) {
+__device__ __forceinline__ void plane_fetch(const PlaneMap<WALL>& pm, const T* __restrict__ u0, const T* __restrict__ u1,
+                                            const T* __restrict__ u2, int base, T (&v)[DIM][RPF]) {
 #pragma unroll
     for (int q = 0; q < RPF; ++q) {
         if (pm.off[q] >= 0) {
-#pragma unroll
-            for (int cc = 0; cc < DIM; ++cc) {
-                T x = u[cc * N + base + pm.off[q]];
-                if (WALL && pm.ghost[q]) x = (cc == 1) ? (T)0 : -x;
-                v[cc][q] = x;
+            const int o = base + pm.off[q];
+            T x0 = u0[o], x1 = u1[o];
+            if (WALL && pm.ghost[q]) {
+                x0 = -x0;
+                x1 = (T)0;
+            }
+            v[0][q] = x0;
+            v[1][q] = x1;
+            if constexpr (DIM == 3) {
+                T x2 = u2[o];
+                if (WALL && pm.ghost[q]) x2 = -x2;
+                v[2][q] = x2;
             }
         }
     }
@@ -274,7 +414,7 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
     T v[DIM][RPF];
 
     if constexpr (DIM == 2) {
-        plane_fetch<T, DIM, WALL>(pm, u, N, 0, v);
+        plane_fetch<T, DIM, WALL>(pm, u, u + N, u, 0, v);   // 2-D: no third component
         plane_commit<T, DIM, WALL>(pm, su[0], v);
         __syncthreads();
         CPlane<T> o = su[0];
@@ -312,15 +452,18 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
     } else {
         const int kb = blockIdx.z * kchunk;
         const int ke = min(kb + kchunk, nz);
+        const int iplane = nx * ny;
+        T* const F1 = F ? F + N : nullptr;
+        T* const F2 = F ? F + 2 * N : nullptr;
         auto wrapz = [nz](int k) { return k < 0 ? k + nz : (k >= nz ? k - nz : k); };
         int sm = 0, so = 1, sp = 2;
-        plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(kb - 2) * plane, v);
+        plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(kb - 2) * iplane, v);
         plane_commit<T, DIM, WALL>(pm, su[sm], v);
-        plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(kb - 1) * plane, v);
+        plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(kb - 1) * iplane, v);
         plane_commit<T, DIM, WALL>(pm, su[so], v);
-        plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(kb) * plane, v);
+        plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(kb) * iplane, v);
         plane_commit<T, DIM, WALL>(pm, su[sp], v);
-        plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(kb + 1) * plane, v);
+        plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(kb + 1) * iplane, v);
         __syncthreads();
         const int ic = i < nx ? i : nx - 1;
         const int jc = j < ny ? j : ny - 1;
@@ -336,15 +479,33 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
             sp = t;
         }
         __syncthreads();
+        // register neighbourhood: m plane and the carried o values of the first iteration
+        Nb<T> nb;
+        {
+            CPlane<T> m = su[sm];
+            CPlane<T> o = su[so];
+            nb.Xm = m[0][c0];
+            nb.Ym = m[1][c0];
+            nb.Zm = m[2][c0];
+            nb.Zme = m[2][c0 + 1];
+            nb.Zmn = m[2][c0 + RSX];
+            nb.X0 = o[0][c0];
+            nb.X0w = o[0][c0 - 1];
+            nb.Y0 = o[1][c0];
+            nb.Y0s = o[1][c0 - RSX];
+            nb.Z0 = o[2][c0];
+        }
         for (int k = kb; k < ke; ++k) {
             const bool more = k + 1 < ke;
-            if (more) plane_fetch<T, DIM, WALL>(pm, u, N, wrapz(k + 2) * plane, v);
+            if (more) plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(k + 2) * iplane, v);
             CPlane<T> m = su[sm];
             CPlane<T> o = su[so];
             CPlane<T> p = su[sp];
-            T fx = eval_Fx<T, 3, WALL>(c, yr, m, o, p, c0);
-            T fy = eval_Fy<T, 3, WALL>(c, yr, m, o, p, c0);
-            T fz = eval_Fz<T, WALL>(c, yr, m, o, p, c0);
+            nb_load_o<T>(nb, o, c0);
+            nb_load_p<T>(nb, p, c0);
+            T fx = nb_Fx<T, WALL>(c, yr, nb);
+            T fy = nb_Fy<T, WALL>(c, yr, nb);
+            T fz = nb_Fz<T, WALL>(c, yr, nb);
             if (mc) {
                 const long am = (long)k * plane + (long)jc * nx + ic;
                 fx += mc[am];
@@ -366,15 +527,16 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
             }
             __syncthreads();
             if (inside) {
-                const long a = (long)k * plane + (long)j * nx + i;
+                const int a = k * iplane + j * nx + i;
                 if (F) {
                     F[a] = fx;
-                    F[N + a] = fy;
-                    F[2 * N + a] = fz;
+                    F1[a] = fy;
+                    F2[a] = fz;
                 }
                 r[a] = (fx - sFx[ty][tx]) * c.ix + (fy - sFy[ty][tx]) * yr.i + (fz - fz_prev) * c.iz;
             }
             fz_prev = fz;
+            nb_rotate<T>(nb);
             if (more) plane_commit<T, DIM, WALL>(pm, su[sm], v);
             {
                 const int t = sm;
