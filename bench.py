@@ -118,35 +118,42 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ byte/op model
-def kernel_model(name, n, s, launches_by_stage=None):
+def kernel_model(name, n, s, fused=False):
     """Algorithmic bytes and FP64-pipe operations per launch of each kernel family.
 
     N cells, spec = (n/2+1) n^2 complex values of 2 s bytes; s = value size.
-    rhs_div: reads u (3N), writes F (3N) and r (N); 78 FP64 ops/cell for F (uniform grid, 26 per component) + 6 for D F.
+    rhs_div: reads u (3N), writes F (3N) and r (N); 78 FP64 ops/cell for F (uniform grid, 26 per
+             component) + 6 for D F.
+    update_rhs_div (FP32 fused stage boundary): reads F_s, u_0, acc (9N) and p_s (N), writes acc,
+             F_{s+1} (6N) and r (N): 17 values per cell.
     fft_*:   each pass reads and writes its data once.
-    rk_update: 13 / 16 / 16 / 13 values per cell for stages 1-4 (mean 14.5).
+    rk_update: 13 / 16 / 16 / 13 values per cell for stages 1-4 (mean 14.5); only the last stage
+             (13) when the stage boundaries are fused.
     """
     N = n ** 3
     spec = (n // 2 + 1) * n * n
     if name == "rhs_div":
         return 7 * N * s, 84 * N
+    if name == "update_rhs_div":
+        return 17 * N * s, None
     if name == "fft_x_r2c" or name == "fft_x_c2r":
         return N * s + spec * 2 * s, None
     if name == "fft_strided":
         return 2 * spec * 2 * s, None
     if name == "rk_update":
-        return 14.5 * N * s, None
+        return (13.0 if fused else 14.5) * N * s, None
     return None, None
 
 
 # DRAM bytes per launch of the dominant kernels from ncu captures of the current kernels
-# (profiles/rhs_div_hit256.md, profiles/rk_update_hit256.md); n = 256 only.
-TRAFFIC = {("f64", "rhs_div"): 909.93e6, ("f32", "rk_update"): 942.9e6}
+# (profiles/rhs_div_hit256.md); n = 256 only. None once a kernel has changed since its capture.
+TRAFFIC = {("f64", "rhs_div"): 909.93e6}
 
 
 def step_model_bytes(n, s):
-    """Model bytes of one RK4 step with F stored: 126 values per cell."""
-    return 126 * n ** 3 * s
+    """Model bytes of one RK4 step: 114 values per cell (F recomputed in the update; the minimum
+    traffic of the scheme)."""
+    return 114 * n ** 3 * s
 
 
 # ------------------------------------------------------------------ our arm
@@ -225,7 +232,7 @@ def run_ours(args):
         tot = sum(v[1] for v in prof.values())
         dom = max(prof.items(), key=lambda kv: kv[1][1])
         dname, (dl, dms) = dom
-        b, ops = kernel_model(dname, n, s)
+        b, ops = kernel_model(dname, n, s, fused=(tag == "f32" and "update_rhs_div" in prof))
         avg_s = dms / dl / 1e3
         traffic = TRAFFIC.get((tag, dname)) if n == 256 else None
         if tag == "f64" and ops is not None:

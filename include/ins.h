@@ -133,6 +133,14 @@ ins_status ins_divergence(ins_grid* g, const void* u, void* phi);
 ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host,
                     double* next_dt_dev, double cfl);
 
+/* Stage-boundary fusion of ins_step (no counterpart in the paper: an implementation
+ * choice). On FP32 3-D INS_RK4 grids without a closure, ins_step by default runs the update
+ * of stage s and the evaluation of F and D F of stage s + 1 as one kernel, so the stage
+ * state is never stored (the workspace holds one extra scalar field for it); results equal
+ * the unfused path's up to the order of FP32 roundings in F. enable = 0 selects the unfused
+ * kernels (for comparison), 1 (default) the fused ones. Other grids ignore the setting. */
+ins_status ins_set_step_fusion(ins_grid* g, int enable);
+
 /* Vector-Jacobian product of one ins_step (Sec. 3.4, pullback of a composition;
  * App. B operator pullbacks; the Poisson solve is self-adjoint, Sec. 2.6.1).
  * With u_{n+1} = step(u_n) for a frozen dt, returns

@@ -60,6 +60,7 @@ SIGNATURES = {
     "ins_rhs": (_c.c_int, [_vp, _vp, _vp, _vp]),
     "ins_project": (_c.c_int, [_vp, _vp, _vp, _vp]),
     "ins_divergence": (_c.c_int, [_vp, _vp, _vp]),
+    "ins_set_step_fusion": (_c.c_int, [_vp, _c.c_int]),
     "ins_step": (_c.c_int, [_vp, _vp, _vp, _c.c_double, _vp, _c.c_double]),
     "ins_cfl_dt": (_c.c_int, [_vp, _vp, _c.c_double, _vp]),
     "ins_step_vjp": (_c.c_int, [_vp, _vp, _vp, _c.c_double, _vp, _vp, _vp]),

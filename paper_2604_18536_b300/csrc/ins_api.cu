@@ -84,6 +84,7 @@ struct DevBuf {
 
 struct ins_grid {
     int dim = 0, nx = 1, ny = 1, nz = 1, wall_y = 0, dtype = 0, scheme = INS_RK4;
+    bool fused_step = true;   // FP32 3-D RK4: fused stage boundaries (ins_set_step_fusion)
     double nu = 0.0, force[3] = {0, 0, 0};
     cudaStream_t stream = nullptr;
     long N = 0;             // cells
@@ -111,6 +112,7 @@ struct ins_grid {
     void* acc = nullptr;
     void* us = nullptr;
     void* rp = nullptr;
+    void* pbuf = nullptr;          // FP32 3-D RK4: pressure of the fused stage boundary (r stays in rp)
     void* S = nullptr;
     unsigned long long* cfl_max = nullptr;  // [nx + ny + nz] per-index maxima of |u^a|
     unsigned int* err_flag = nullptr;       // [1]
@@ -504,8 +506,56 @@ struct Impl {
         }
         return INS_OK;
     }
+    // FP32 3-D RK4 without a closure: the update of stage s and the evaluation of stage s + 1
+    // run as one kernel (k_update_rhs_div); F alternates between two buffers, p_s and r_{s+1}
+    // live in separate buffers, no stage state is stored.
+    static ins_status step_fused(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
+        static const double A[3] = {0.5, 0.5, 1.0};
+        static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+        T* Fb[2] = {reinterpret_cast<T*>(g->F), reinterpret_cast<T*>(g->us)};
+        T* rr = reinterpret_cast<T*>(g->rp);
+        T* pp = reinterpret_cast<T*>(g->pbuf);
+        T* acc = reinterpret_cast<T*>(g->acc);
+        ins_status s;
+        if ((s = launch_rhs_div<T, DIM, WALL>(g, u, Fb[0], rr)) != INS_OK) return s;
+        if ((s = poisson<T>(g, rr, pp)) != INS_OK) return s;
+        const RhsCoef<T> rc = make_rhs_coef<T>(g);
+        const T* ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
+        const T ihx = (T)(1.0 / g->h[0][0]), ihz = (T)(1.0 / g->h[2][0]);
+        const dim3 blk(RBX, RBY, 1);
+        const dim3 grd((g->nx + RBX - 1) / RBX, (g->ny + RBY - 1) / RBY, (g->nz + g->kchunk - 1) / g->kchunk);
+        for (int st = 0; st < 3; ++st) {
+            FusedArgs fa;
+            fa.dt_dev = dt_dev;
+            fa.dt_host = dt_host;
+            fa.a_next = A[st];
+            fa.b = B[st];
+            fa.stage = st;
+            KLAUNCH(g, "update_rhs_div", k_update_rhs_div<T, WALL><<<grd, blk, 0, g->stream>>>(
+                                             rc, ihx, ihz, ihy, Fb[st & 1], pp, u, acc, Fb[(st + 1) & 1], rr, fa, g->kchunk));
+            if ((s = poisson<T>(g, rr, pp)) != INS_OK) return s;
+        }
+        RkArgs ra;
+        ra.dt_dev = dt_dev;
+        ra.dt_host = dt_host;
+        ra.a_next = 0.0;
+        ra.b = B[3];
+        ra.stage = 3;
+        ra.last = 1;
+        ra.mx = next_dt ? g->cfl_max : nullptr;
+        ra.err_flag = g->err_flag;
+        if ((s = rk_update<false>(g, Fb[1], pp, u, acc, nullptr, ra)) != INS_OK) return s;
+        if (next_dt) {
+            KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz, g->dmin2_nu, cfl,
+                                                    next_dt));
+        }
+        return INS_OK;
+    }
     static ins_status step(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
         if (g->scheme == INS_WRAY3) return step_wray3(g, u, dt_dev, dt_host, next_dt, cfl);
+        if constexpr (DIM == 3 && std::is_same<T, float>::value) {
+            if (g->pbuf && !g->closure && g->fused_step && rk_vec_ok<T>(g, u)) return step_fused(g, u, dt_dev, dt_host, next_dt, cfl);
+        }
         static const double A[4] = {0.5, 0.5, 1.0, 0.0};
         static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
         T* F = reinterpret_cast<T*>(g->F);
@@ -945,6 +995,8 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     o_acc = off; off += al((size_t)dim * N * ts);
     o_us = off; off += D.scheme == INS_RK4 ? al((size_t)dim * N * ts) : 0;   // the low-storage scheme needs no stage state
     o_rp = off; off += al((size_t)N * ts);
+    const bool fused_rk = D.dtype == INS_F32 && dim == 3 && D.scheme == INS_RK4;
+    const size_t o_pbuf = off; off += fused_rk ? al((size_t)N * ts) : 0;
     o_S = off; off += al((size_t)spec * 2 * ts);
     o_cfl = off; off += al(nsum * 8);
     o_err = off; off += al(4);
@@ -975,6 +1027,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     g->F = b + o_F;
     g->acc = b + o_acc;
     g->us = D.scheme == INS_RK4 ? b + o_us : nullptr;
+    g->pbuf = fused_rk ? b + o_pbuf : nullptr;
     g->rp = b + o_rp;
     g->S = b + o_S;
     g->cfl_max = reinterpret_cast<unsigned long long*>(b + o_cfl);
@@ -1197,6 +1250,13 @@ ins_status ins_divergence(ins_grid* g, const void* u, void* phi) {
         using T = decltype(z);
         return dispatch<T>(g, [&](auto impl) { return decltype(impl)::divergence(g, (const T*)u, (T*)phi); });
     });
+}
+
+ins_status ins_set_step_fusion(ins_grid* g, int enable) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "ins_set_step_fusion: null grid");
+    g->fused_step = enable != 0;
+    return INS_OK;
 }
 
 ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host, double* next_dt_dev, double cfl) {

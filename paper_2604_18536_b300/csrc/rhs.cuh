@@ -550,3 +550,283 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
 }
 
 }  // namespace ins
+
+namespace ins {
+
+// ---------------------------------------------------------------------------------------
+// Fused RK stage boundary (3-D): the update of stage s and the F / D F evaluation of stage
+// s + 1 in one z march, so the stage state u_{s+1} never goes to memory.
+//
+// Each plane of the halo'd tile is staged from the previous stage's F_s, p_s and u_0:
+//   k^a = F_s^a - (p_{I+e_a} - p_I) / h_a   (k^y = 0 on the stored top wall face),
+//   u_{s+1}^a = u_0^a + dt a_{s+1,s} k^a,
+// with the wall ghosts of u_{s+1} taken from the mirrored cell as in k_rhs_div. Thread t
+// stages its own cell and, for t < 129, one halo cell; at its own cell (planes of its
+// chunk only) it also updates the RK accumulator, acc = b_s k (s = 0) or acc += b_s k.
+// The evaluation of F_{s+1} and r = D F_{s+1} on the staged ring is that of k_rhs_div.
+// Reads F_s, p_s, u_0, acc and writes acc, F_{s+1}, r: 17 values per cell instead of the
+// 23 of a separate update (16) and evaluation (7).
+constexpr int FH = RSPL - RNT;   // halo cells of a plane: 129
+
+struct FusedMap {
+    int off[2];       // in-plane offset of the source cell (mirror cell for a wall ghost)
+    int sidx[2];      // position in the shared plane
+    int dxp[2];       // offset of the +x neighbour (periodic wrap)
+    int dyp[2];       // offset of the +y neighbour (periodic wrap; unused on the top wall row)
+    int gj[2];        // row of the source cell
+    bool ghost[2];    // wall ghost: u^x, u^z negated, u^y = 0
+    bool has[2];      // element 1 exists only for t < FH
+};
+
+template <bool WALL>
+__device__ __forceinline__ FusedMap fused_map(int nx, int ny, int i0, int j0) {
+    FusedMap fm;
+    const int t = threadIdx.x + threadIdx.y * RBX;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        int li, lj;
+        if (e == 0) {
+            li = threadIdx.x + 2;
+            lj = threadIdx.y + 2;
+        } else if (t < 105) {             // rows 0, 1 and RSY - 1, all RSX columns
+            const int r = t / RSX;
+            lj = r == 2 ? RSY - 1 : r;
+            li = t - r * RSX;
+        } else {                          // columns 0, 1 and RSX - 1 of rows 2 .. RSY - 2
+            const int h = t - 105;
+            lj = 2 + h / 3;
+            const int cc = h % 3;
+            li = cc == 2 ? RSX - 1 : cc;
+        }
+        fm.has[e] = e == 0 || t < FH;
+        fm.sidx[e] = lj * RSX + li;
+        int gi = (i0 - 2 + li) % nx;
+        if (gi < 0) gi += nx;
+        int gj = j0 - 2 + lj;
+        fm.ghost[e] = false;
+        if (!WALL) {
+            gj %= ny;
+            if (gj < 0) gj += ny;
+        } else if (gj < 0 || gj >= ny) {
+            const int mj = gj < 0 ? -gj - 1 : 2 * ny - 1 - gj;
+            gj = mj < 0 ? 0 : (mj >= ny ? ny - 1 : mj);
+            fm.ghost[e] = true;
+        }
+        fm.gj[e] = gj;
+        fm.off[e] = gj * nx + gi;
+        fm.dxp[e] = gi + 1 == nx ? -(nx - 1) : 1;
+        fm.dyp[e] = gj + 1 == ny ? -(ny - 1) * nx : nx;
+    }
+    return fm;
+}
+
+struct FusedArgs {
+    const double* dt_dev;
+    double dt_host;
+    double a_next;   // a_{s+1,s}
+    double b;        // b_s
+    int stage;       // s (0, 1 or 2)
+};
+
+template <typename T, bool WALL>
+__global__ void __launch_bounds__(RNT, WALL ? 2 : 3) k_update_rhs_div(RhsCoef<T> c, T ihx, T ihz, const T* __restrict__ ihy,
+                                                        const T* __restrict__ Fs, const T* __restrict__ p,
+                                                        const T* __restrict__ u0, T* __restrict__ acc,
+                                                        T* __restrict__ F, T* __restrict__ r, FusedArgs fa, int kchunk) {
+    __shared__ T su[3][3][RSPL];
+    __shared__ T sFx[RBY][RBX + 1];
+    __shared__ T sFy[RBY + 1][RBX];
+    const int nx = c.nx, ny = c.ny, nz = c.nz;
+    const size_t N = (size_t)nx * ny * nz;   // component stride (in-component offsets are 32-bit)
+    const int iplane = nx * ny;
+    const T* const Fs1 = Fs + N;
+    const T* const Fs2 = Fs + 2 * N;
+    const T* const u01 = u0 + N;
+    const T* const u02 = u0 + 2 * N;
+    T* const acc1 = acc + N;
+    T* const acc2 = acc + 2 * N;
+    T* const F1 = F + N;
+    T* const F2 = F + 2 * N;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * RBX, j0 = blockIdx.y * RBY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool inside = i < nx && j < ny;
+    const int c0 = (ty + 2) * RSX + (tx + 2);
+    const YRow<T> yr = yrow<T, WALL>(c, j < ny ? j : ny - 1);
+    const bool hy = ty == 0;
+    const bool hx = ty == 1 && tx < RBY;
+    const bool hy_wall = WALL && j0 == 0;
+    const int jhy = j0 - 1 < 0 ? ny - 1 : j0 - 1;
+    const int jhx = j0 + tx < ny ? j0 + tx : ny - 1;
+    const int c0hy = 1 * RSX + (tx + 2);
+    const int c0hx = (tx + 2) * RSX + 1;
+    const FusedMap fm = fused_map<WALL>(nx, ny, i0, j0);
+    const double dt = fa.dt_dev ? *fa.dt_dev : fa.dt_host;
+    const T dta = (T)(dt * fa.a_next), bb = (T)fa.b;
+    T ihy_e[2];
+    bool top_e[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        ihy_e[e] = __ldg(&ihy[fm.gj[e]]);
+        top_e[e] = WALL && fm.gj[e] == ny - 1;
+    }
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(kb + kchunk, nz);
+    auto wrapz = [nz](int k) { return k < 0 ? k + nz : (k >= nz ? k - nz : k); };
+    T pself[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) pself[e] = fm.has[e] ? p[wrapz(kb - 2) * iplane + fm.off[e]] : (T)0;
+    T v[3][2];
+    // staging of plane q in two halves, so the global loads of plane k + 2 are in flight
+    // while plane k is evaluated: stage_load issues them, stage_finish forms u_{s+1} in v
+    // (and the accumulator at the own cell)
+    T lF[3][2], lU[3][2], lpx[2], lpy[2], lpz[2], lA[3];
+    int la[2];
+    bool lown = false;
+    auto stage_load = [&](int q) {
+        const int base = wrapz(q) * iplane;
+        const int basez = wrapz(q + 1) * iplane;
+        lown = q >= kb && q < ke && inside;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            if (!fm.has[e]) continue;
+            const int a = base + fm.off[e];
+            la[e] = a;
+            lF[0][e] = Fs[a];
+            lF[1][e] = Fs1[a];
+            lF[2][e] = Fs2[a];
+            lU[0][e] = u0[a];
+            lU[1][e] = u01[a];
+            lU[2][e] = u02[a];
+            lpx[e] = p[a + fm.dxp[e]];
+            lpy[e] = p[a + fm.dyp[e]];
+            lpz[e] = p[basez + fm.off[e]];
+        }
+        if (lown && fa.stage > 0) {
+            lA[0] = acc[la[0]];
+            lA[1] = acc1[la[0]];
+            lA[2] = acc2[la[0]];
+        }
+    };
+    auto stage_finish = [&]() {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            if (!fm.has[e]) continue;
+            const T p0 = pself[e];
+            pself[e] = lpz[e];
+            const T kx = fma(p0 - lpx[e], ihx, lF[0][e]);
+            const T ky = top_e[e] ? (T)0 : fma(p0 - lpy[e], ihy_e[e], lF[1][e]);
+            const T kz = fma(p0 - lpz[e], ihz, lF[2][e]);
+            T ux = fma(dta, kx, lU[0][e]);
+            T uy = fma(dta, ky, lU[1][e]);
+            T uz = fma(dta, kz, lU[2][e]);
+            if (e == 0 && lown) {
+                const int a = la[0];
+                if (fa.stage == 0) {
+                    acc[a] = bb * kx;
+                    acc1[a] = bb * ky;
+                    acc2[a] = bb * kz;
+                } else {
+                    acc[a] = fma(bb, kx, lA[0]);
+                    acc1[a] = fma(bb, ky, lA[1]);
+                    acc2[a] = fma(bb, kz, lA[2]);
+                }
+            }
+            if (WALL && fm.ghost[e]) {
+                ux = -ux;
+                uy = (T)0;
+                uz = -uz;
+            }
+            v[0][e] = ux;
+            v[1][e] = uy;
+            v[2][e] = uz;
+        }
+    };
+    auto stage = [&](int q) {
+        stage_load(q);
+        stage_finish();
+    };
+    auto commit = [&](Plane<T> s) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            if (fm.has[e]) {
+                s[0][fm.sidx[e]] = v[0][e];
+                s[1][fm.sidx[e]] = v[1][e];
+                s[2][fm.sidx[e]] = v[2][e];
+            }
+    };
+    int sm = 0, so = 1, sp = 2;
+    stage(kb - 2);
+    commit(su[sm]);
+    stage(kb - 1);
+    commit(su[so]);
+    stage(kb);
+    commit(su[sp]);
+    stage(kb + 1);
+    __syncthreads();
+    T fz_prev = eval_Fz<T, WALL>(c, yr, su[sm], su[so], su[sp], c0);
+    __syncthreads();
+    commit(su[sm]);
+    {
+        const int t = sm;
+        sm = so;
+        so = sp;
+        sp = t;
+    }
+    __syncthreads();
+    Nb<T> nb;
+    {
+        CPlane<T> m = su[sm];
+        CPlane<T> o = su[so];
+        nb.Xm = m[0][c0];
+        nb.Ym = m[1][c0];
+        nb.Zm = m[2][c0];
+        nb.Zme = m[2][c0 + 1];
+        nb.Zmn = m[2][c0 + RSX];
+        nb.X0 = o[0][c0];
+        nb.X0w = o[0][c0 - 1];
+        nb.Y0 = o[1][c0];
+        nb.Y0s = o[1][c0 - RSX];
+        nb.Z0 = o[2][c0];
+    }
+    for (int k = kb; k < ke; ++k) {
+        const bool more = k + 1 < ke;
+        if (more) stage_load(k + 2);
+        CPlane<T> m = su[sm];
+        CPlane<T> o = su[so];
+        CPlane<T> pp = su[sp];
+        nb_load_o<T>(nb, o, c0);
+        nb_load_p<T>(nb, pp, c0);
+        const T fx = nb_Fx<T, WALL>(c, yr, nb);
+        T fy = nb_Fy<T, WALL>(c, yr, nb);
+        const T fz = nb_Fz<T, WALL>(c, yr, nb);
+        if (WALL && j == ny - 1) fy = (T)0;
+        sFx[ty][tx + 1] = fx;
+        sFy[ty + 1][tx] = fy;
+        if (hy) sFy[0][tx] = hy_wall ? (T)0 : eval_Fy<T, 3, WALL>(c, yrow<T, WALL>(c, jhy), m, o, pp, c0hy);
+        if (hx) sFx[tx][0] = eval_Fx<T, 3, WALL>(c, yrow<T, WALL>(c, jhx), m, o, pp, c0hx);
+        __syncthreads();
+        if (inside) {
+            const int a = k * iplane + j * nx + i;
+            F[a] = fx;
+            F1[a] = fy;
+            F2[a] = fz;
+            r[a] = (fx - sFx[ty][tx]) * c.ix + (fy - sFy[ty][tx]) * yr.i + (fz - fz_prev) * c.iz;
+        }
+        fz_prev = fz;
+        nb_rotate<T>(nb);
+        if (more) {
+            stage_finish();
+            commit(su[sm]);
+        }
+        {
+            const int t = sm;
+            sm = so;
+            so = sp;
+            sp = t;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace ins

@@ -85,9 +85,11 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
     const bool need_global_next = last_vec || lane == 31;
     const long jrow = (long)(j < ny ? j : 0) * nx;
     const long jnext = (long)(j + 1 < ny ? j + 1 : 0) * nx;   // periodic wrap in y
-    double mxx[VEC], mxy = 0.0;
+    // maxima of |u| in the field's own type (exact; one conversion to FP64 per reduction, so
+    // the FP32 path does not load the FP64 pipe)
+    T mxx[VEC], mxy = (T)0;
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) mxx[e] = 0.0;
+    for (int e = 0; e < VEC; ++e) mxx[e] = (T)0;
     bool bad = false;
     T P0[VEC], Pt[VEC];
     if (ok) VT::ld(p + (long)kb * plane + jrow + i0, P0);
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
         // x neighbour of the last element: first element of the next vector (next lane or wrap)
         T pnext = __shfl_down_sync(0xffffffffu, P0[0], 1);
         T Pn[VEC];
-        double qz = 0.0;
+        T qz = (T)0;
         if (ok) {
             if (need_global_next) pnext = p[base + jrow + (last_vec ? 0 : i0 + VEC)];
             if (DIM == 3) VT::ld(p + kt + jrow + i0, Pt);
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
 #pragma unroll
                         for (int e = 0; e < VEC; ++e) {
                             bad |= !isfinite(uv[e]);
-                            const double q = fabs((double)uv[e]);
+                            const T q = fabs(uv[e]);
                             if (cc == 0) mxx[e] = fmax(mxx[e], q);
                             else if (cc == 1) mxy = fmax(mxy, q);
                             else qz = fmax(qz, q);
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
                     for (int e = 0; e < VEC; ++e) {
                         uv[e] = fma(dtt, fma(bb, kk[cc][e], av[e]), uv[e]);
                         bad |= !isfinite(uv[e]);
-                        const double q = fabs((double)uv[e]);
+                        const T q = fabs(uv[e]);
                         if (cc == 0) mxx[e] = fmax(mxx[e], q);
                         else if (cc == 1) mxy = fmax(mxy, q);
                         else qz = fmax(qz, q);
@@ -181,26 +183,26 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
         }
         if (fin && ra.mx && DIM == 3) {
             for (int o = 16; o > 0; o >>= 1) qz = fmax(qz, __shfl_xor_sync(0xffffffffu, qz, o));
-            if (lane == 0 && qz > 0.0) atomicMax(&ra.mx[nx + ny + k], (unsigned long long)__double_as_longlong(qz));
+            if (lane == 0 && qz > (T)0) atomicMax(&ra.mx[nx + ny + k], (unsigned long long)__double_as_longlong((double)qz));
         }
 #pragma unroll
         for (int e = 0; e < VEC; ++e) P0[e] = Pt[e];
     }
     if (fin) {
         if (ra.mx) {
-            __shared__ double sx[8][32 * VEC + 1];
+            __shared__ T sx[8][32 * VEC + 1];
 #pragma unroll
             for (int e = 0; e < VEC; ++e) sx[row][lane * VEC + e] = mxx[e];
             for (int o = 16; o > 0; o >>= 1) mxy = fmax(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
-            if (lane == 0 && j < ny && mxy > 0.0)
-                atomicMax(&ra.mx[nx + j], (unsigned long long)__double_as_longlong(mxy));
+            if (lane == 0 && j < ny && mxy > (T)0)
+                atomicMax(&ra.mx[nx + j], (unsigned long long)__double_as_longlong((double)mxy));
             __syncthreads();
             if (row == 0 && iv < nvx) {
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
-                    double m = sx[0][lane * VEC + e];
+                    T m = sx[0][lane * VEC + e];
                     for (int r = 1; r < 8; ++r) m = fmax(m, sx[r][lane * VEC + e]);
-                    if (m > 0.0) atomicMax(&ra.mx[i0 + e], (unsigned long long)__double_as_longlong(m));
+                    if (m > (T)0) atomicMax(&ra.mx[i0 + e], (unsigned long long)__double_as_longlong((double)m));
                 }
             }
         }

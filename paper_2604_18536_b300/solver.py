@@ -126,6 +126,10 @@ class Grid:
     def new_scalar(self):
         return torch.zeros(self.shape, dtype=self.dtype, device=self.device)
 
+    def set_step_fusion(self, enable):
+        """FP32 3-D RK4: fused (default) or separate stage-boundary kernels (ins_set_step_fusion)."""
+        check(lib().ins_set_step_fusion(self._h, 1 if enable else 0), "ins_set_step_fusion")
+
     def workspace_bytes(self):
         b = ctypes.c_size_t()
         check(lib().ins_workspace_bytes(self._h, ctypes.byref(b)), "ins_workspace_bytes")

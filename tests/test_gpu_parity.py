@@ -233,3 +233,32 @@ def test_bad_tensor_arguments():
         gg.rhs(torch.zeros((3, 4, 4, 4), dtype=torch.float64, device="cuda"))
     with pytest.raises(ValueError):
         gg.rhs(gg.new_velocity().float())
+
+
+# ------------------------------------------------------------------ FP32 stage-boundary fusion
+@pytest.mark.parametrize("name", ["p3", "p3reg", "p3reg2", "c3", "c3reg"])
+def test_fp32_unfused_step_parity(name):
+    """The unfused FP32 kernels (ins_set_step_fusion(0)) against the oracle, like the fused default."""
+    og, gg = grids(name, torch.float32)
+    gg.set_step_fusion(False)
+    u0 = rounded(rand_u(og, 4, project=True), torch.float32)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    ut = dev(u0, torch.float32)
+    gg.step(ut, dt=dt)
+    assert rel(host(ut), timestep.rk4_step(og, u0, dt)) <= TOL[torch.float32]
+
+
+@pytest.mark.parametrize("name", ["p3reg2", "c3"])
+def test_fp32_fused_matches_unfused(name):
+    """Fused and unfused stage boundaries differ only by FP32 rounding order (10 steps)."""
+    og, gg = grids(name, torch.float32)
+    u0 = rounded(rand_u(og, 21, project=True), torch.float32)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    a = dev(u0, torch.float32)
+    b = dev(u0, torch.float32)
+    for _ in range(10):
+        gg.set_step_fusion(True)
+        gg.step(a, dt=dt)
+        gg.set_step_fusion(False)
+        gg.step(b, dt=dt)
+    assert rel(host(a), host(b)) <= 1e-6
