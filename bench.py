@@ -125,7 +125,7 @@ def kernel_model(name, n, s, fused=False):
     rhs_div: reads u (3N), writes F (3N) and r (N); 78 FP64 ops/cell for F (uniform grid, 26 per
              component) + 6 for D F.
     update_rhs_div (FP32 fused stage boundary): reads F_s, u_0, acc (9N) and p_s (N), writes acc,
-             F_{s+1} (6N) and r (N): 17 values per cell.
+             F_{s+1} (6N) and r (N): 17 values per cell (14 for the first boundary, no acc read).
     fft_*:   each pass reads and writes its data once.
     rk_update: 13 / 16 / 16 / 13 values per cell for stages 1-4 (mean 14.5); only the last stage
              (13) when the stage boundaries are fused.
@@ -135,7 +135,7 @@ def kernel_model(name, n, s, fused=False):
     if name == "rhs_div":
         return 7 * N * s, 84 * N
     if name == "update_rhs_div":
-        return 17 * N * s, None
+        return 16 * N * s, None     # stage 1 -> 2 has no accumulator read: (14 + 17 + 17) / 3
     if name == "fft_x_r2c" or name == "fft_x_c2r":
         return N * s + spec * 2 * s, None
     if name == "fft_strided":
@@ -146,8 +146,8 @@ def kernel_model(name, n, s, fused=False):
 
 
 # DRAM bytes per launch of the dominant kernels from ncu captures of the current kernels
-# (profiles/rhs_div_hit256.md); n = 256 only. None once a kernel has changed since its capture.
-TRAFFIC = {("f64", "rhs_div"): 909.93e6}
+# (profiles/rhs_div_hit256.md, profiles/update_rhs_div_hit256_f32.md); n = 256 only.
+TRAFFIC = {("f64", "rhs_div"): 909.93e6, ("f32", "update_rhs_div"): 1069.0e6}
 
 
 def step_model_bytes(n, s):
