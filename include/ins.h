@@ -268,6 +268,42 @@ ins_status ins_closure_check(ins_closure* c);
  * F(u) + m(u). The first attachment allocates one velocity field for m. */
 ins_status ins_set_closure(ins_grid* g, ins_closure* c);
 
+/* ---------------------------------------------------------------- eddy-viscosity closures
+ * Classical LES closures (App. "Eddy-viscosity models"; the baselines next to the learned
+ * closure, Sec. 4 and 6.3). With a model attached, ins_rhs and ins_step add to F the
+ * eddy-viscous stress divergence e^a = sum_b delta_b(2 nu_t S_ab), which dissipates energy.
+ * S_aa sits at the cell centres, S_ab (a != b) on the cell edges; nu_t is evaluated at the
+ * cell centres from the velocity gradient A (off-diagonal entries: mean of the four edge
+ * differences around the cell) and averaged from the four neighbouring cells onto an edge.
+ * Filter width D = (d_x d_y d_z)^(1/3). Models (S = sym A):
+ *   INS_EDDY_SMAGORINSKY  nu_t = (C D)^2 sqrt(2 S:S)                    (paper: C = 0.1)
+ *   INS_EDDY_WALE         (C D)^2 (Sd:Sd)^(3/2) / ((S:S)^(5/2) + (Sd:Sd)^(5/4)),
+ *                         Sd = sym(A A) - tr(A A)/3 I                    (C = 0.5)
+ *   INS_EDDY_QR           (C D)^2 |tr(S^3)/3| / (S:S / 2)               (C = sqrt(3/2)/pi)
+ *   INS_EDDY_VREMAN       C^2 sqrt(B_beta / (tr(A A^T)/2)),
+ *                         beta_ij = sum_m d_m^2 A_im A_jm               (C = sqrt(2.5 * 0.1^2))
+ *   INS_EDDY_CONSTANT     nu_t = C (no counterpart in the paper: a diagnostic model for which
+ *                         the term equals C (diffusion + G D) u)
+ * nu_t = 0 where the model's denominator vanishes. */
+typedef enum {
+    INS_EDDY_NONE = 0,
+    INS_EDDY_SMAGORINSKY = 1,
+    INS_EDDY_WALE = 2,
+    INS_EDDY_QR = 3,
+    INS_EDDY_VREMAN = 4,
+    INS_EDDY_CONSTANT = 5
+} ins_eddy_model;
+
+/* Attach model with constant C (INS_EDDY_NONE detaches). 3-D periodic grids with n >= 2
+ * (INS_ERR_UNSUPPORTED otherwise, and while a CNN closure is attached). The first
+ * attachment allocates four scalar fields (nu_t and the term). ins_step_vjp returns
+ * INS_ERR_UNSUPPORTED while a model is attached. */
+ins_status ins_set_eddy_viscosity(ins_grid* g, int model, double C);
+
+/* nu_t of the attached model at every cell centre: u DEVICE, dim fields; nut DEVICE, one
+ * field of the grid dtype. INS_ERR_ARG without an attached model. */
+ins_status ins_eddy_viscosity(ins_grid* g, const void* u, void* nut);
+
 /* ---------------------------------------------------------------- measurement
  * Tracing support (the paper describes none; these calls serve benchmarking). */
 

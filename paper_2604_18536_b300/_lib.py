@@ -26,6 +26,7 @@ INS_F32 = 0
 INS_F64 = 1
 INS_RK4 = 0
 INS_WRAY3 = 1
+INS_EDDY = {"none": 0, "smagorinsky": 1, "wale": 2, "qr": 3, "vreman": 4, "constant": 5}
 
 # every entry point the header declares, with (restype, argtypes)
 _c = ctypes
@@ -61,6 +62,8 @@ SIGNATURES = {
     "ins_project": (_c.c_int, [_vp, _vp, _vp, _vp]),
     "ins_divergence": (_c.c_int, [_vp, _vp, _vp]),
     "ins_set_step_fusion": (_c.c_int, [_vp, _c.c_int]),
+    "ins_set_eddy_viscosity": (_c.c_int, [_vp, _c.c_int, _c.c_double]),
+    "ins_eddy_viscosity": (_c.c_int, [_vp, _vp, _vp]),
     "ins_step": (_c.c_int, [_vp, _vp, _vp, _c.c_double, _vp, _c.c_double]),
     "ins_cfl_dt": (_c.c_int, [_vp, _vp, _c.c_double, _vp]),
     "ins_step_vjp": (_c.c_int, [_vp, _vp, _vp, _c.c_double, _vp, _vp, _vp]),

@@ -25,6 +25,7 @@
 #include "adjoint.cuh"
 #include "filter_spectrum.cuh"
 #include "conv_tc.cuh"
+#include "eddy.cuh"
 
 using namespace ins;
 
@@ -123,6 +124,10 @@ struct ins_grid {
     // attached CNN closure (m(u) joins F in rhs, step and step_vjp) and its output buffer
     struct ins_closure* closure = nullptr;
     void* mbuf = nullptr;
+    // attached eddy-viscosity model (its term joins F in rhs and step) and its buffers
+    int eddy = 0;             // EddyKind
+    double eddy_C = 0.0;
+    void* eddy_buf = nullptr; // nu_t (N) | term (3N)
     // step-VJP workspace (stage states u_2..u_4, the projected cotangent, nu partials),
     // allocated by the first ins_step_vjp call
     void* vjp = nullptr;
@@ -554,7 +559,8 @@ struct Impl {
     static ins_status step(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
         if (g->scheme == INS_WRAY3) return step_wray3(g, u, dt_dev, dt_host, next_dt, cfl);
         if constexpr (DIM == 3 && std::is_same<T, float>::value) {
-            if (g->pbuf && !g->closure && g->fused_step && rk_vec_ok<T>(g, u)) return step_fused(g, u, dt_dev, dt_host, next_dt, cfl);
+            if (g->pbuf && !g->closure && !g->eddy && g->fused_step && rk_vec_ok<T>(g, u))
+                return step_fused(g, u, dt_dev, dt_host, next_dt, cfl);
         }
         static const double A[4] = {0.5, 0.5, 1.0, 0.0};
         static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
@@ -1182,6 +1188,7 @@ ins_status ins_grid_destroy(ins_grid* g) {
     cudaStreamSynchronize(g->stream);
     if (g->vjp) cudaFree(g->vjp);
     if (g->mbuf) cudaFree(g->mbuf);
+    if (g->eddy_buf) cudaFree(g->eddy_buf);
     cudaError_t e = cudaFree(g->base);
     delete g;
     if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
@@ -1283,6 +1290,7 @@ ins_status ins_step_vjp(ins_grid* g, const void* u_n, const double* dt_dev, doub
     if (ubar_n == ubar_np1 || ubar_n == u_n) return fail(INS_ERR_ARG, "ubar_n must not alias u_n or ubar_np1");
     if (!dt_dev && !(std::isfinite(dt_host) && dt_host >= 0.0)) return fail(INS_ERR_ARG, "dt_host must be finite, >= 0");
     if (g->wall_y) return fail(INS_ERR_UNSUPPORTED, "ins_step_vjp: wall directions are not supported (periodic grids only)");
+    if (g->eddy) return fail(INS_ERR_UNSUPPORTED, "ins_step_vjp: eddy-viscosity models have no pullback here");
     return dispatch_dtype(g, [&](auto z) {
         using T = decltype(z);
         return dispatch<T>(g, [&](auto impl) {
@@ -1628,9 +1636,53 @@ ins_status ins_closure_create(ins_grid* g, ins_closure** out);
 
 namespace {
 // m(u) of the attached closure into the grid's closure buffer (*m = null when none is attached).
+dim3 eddy_grid(const ins_grid* g) { return dim3((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz); }
+
+template <typename T>
+EddyCoef<T> eddy_coef(const ins_grid* g) {
+    EddyCoef<T> c;
+    c.nx = g->nx;
+    c.ny = g->ny;
+    c.nz = g->nz;
+    double vol = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        const double d = g->d[a][0];
+        c.id[a] = (T)(1.0 / d);
+        c.w2[a] = (T)(d * d);
+        vol *= d;
+    }
+    const double D = std::cbrt(vol);
+    c.CD2 = (T)((g->eddy_C * D) * (g->eddy_C * D));
+    c.C2 = (T)(g->eddy == EDDY_CONSTANT ? g->eddy_C : g->eddy_C * g->eddy_C);
+    return c;
+}
+
+template <typename T>
+ins_status eddy_nut(ins_grid* g, const T* u, T* nut) {
+    const EddyCoef<T> c = eddy_coef<T>(g);
+    const dim3 grd = eddy_grid(g), blk(32, 8);
+    switch (g->eddy) {
+        case EDDY_SMAGORINSKY: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_SMAGORINSKY><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
+        case EDDY_WALE: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_WALE><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
+        case EDDY_QR: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_QR><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
+        case EDDY_VREMAN: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_VREMAN><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
+        default: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_CONSTANT><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
+    }
+    return INS_OK;
+}
+
 template <typename T>
 ins_status closure_term(ins_grid* g, const T* u, T** m, bool save) {
     *m = nullptr;
+    if (g->eddy) {
+        T* nut = reinterpret_cast<T*>(g->eddy_buf);
+        T* term = nut + g->N;
+        ins_status s = eddy_nut<T>(g, u, nut);
+        if (s != INS_OK) return s;
+        KLAUNCH(g, "eddy_div", k_eddy_div<T><<<eddy_grid(g), dim3(32, 8), 0, g->stream>>>(eddy_coef<T>(g), u, nut, term));
+        *m = term;
+        return INS_OK;
+    }
     if (!g->closure) return INS_OK;
     T* out = reinterpret_cast<T*>(g->mbuf);
     ins_status s = closure_forward<T>(g, g->closure, u, out, save);
@@ -1811,8 +1863,45 @@ ins_status ins_set_closure(ins_grid* g, ins_closure* c) {
             return fail(INS_ERR_OOM, "closure output buffer");
         }
     }
+    if (c && g->eddy) return fail(INS_ERR_UNSUPPORTED, "an eddy-viscosity model is attached (one closure at a time)");
     g->closure = c;
     return INS_OK;
+}
+
+ins_status ins_set_eddy_viscosity(ins_grid* g, int model, double C) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    if (model < INS_EDDY_NONE || model > INS_EDDY_CONSTANT) return fail(INS_ERR_ARG, "unknown eddy-viscosity model");
+    if (model == INS_EDDY_NONE) {
+        g->eddy = 0;
+        return INS_OK;
+    }
+    if (!(std::isfinite(C) && C >= 0.0)) return fail(INS_ERR_ARG, "C must be finite and >= 0");
+    if (g->dim != 3 || g->wall_y) return fail(INS_ERR_UNSUPPORTED, "eddy-viscosity models: 3-D periodic grids only");
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2) return fail(INS_ERR_UNSUPPORTED, "eddy-viscosity models need n >= 2");
+    if (g->closure) return fail(INS_ERR_UNSUPPORTED, "a CNN closure is attached (one closure at a time)");
+    if (!g->eddy_buf) {
+        const size_t bytes = (size_t)4 * g->N * (g->dtype == INS_F64 ? 8 : 4);
+        cudaError_t e = cudaMalloc(&g->eddy_buf, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g->eddy_buf = nullptr;
+            return fail(INS_ERR_OOM, "eddy-viscosity buffers");
+        }
+    }
+    g->eddy = model;
+    g->eddy_C = C;
+    return INS_OK;
+}
+
+ins_status ins_eddy_viscosity(ins_grid* g, const void* u, void* nut) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u, "u"));
+    if (!nut) return fail(INS_ERR_ARG, "nut is null");
+    if (!g->eddy) return fail(INS_ERR_ARG, "no eddy-viscosity model attached");
+    if (g->dtype == INS_F64) return eddy_nut<double>(g, (const double*)u, (double*)nut);
+    return eddy_nut<float>(g, (const float*)u, (float*)nut);
 }
 
 }  // extern "C"

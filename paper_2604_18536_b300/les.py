@@ -144,14 +144,17 @@ def spectrum_error(grid, u, ref):
     return float(torch.linalg.norm(la - lb) / torch.linalg.norm(lb))
 
 
-def evaluate(data, n_les, nu, W=None, b=None, nsteps=10):
-    """Mean spectrum error at step nsteps against the filtered DNS (closure if W is given)."""
+def evaluate(data, n_les, nu, W=None, b=None, nsteps=10, eddy=None):
+    """Mean spectrum error at step nsteps against the filtered DNS: with the CNN closure if W is
+    given, with an eddy-viscosity model if eddy names one (paper constants), else without closure."""
     g = _box(n_les, nu)
     c = None
     if W is not None:
         c = Closure(g)
         c.set_params(W, b)
         g.set_closure(c)
+    elif eddy is not None:
+        g.set_eddy_viscosity(eddy)
     errs = []
     fallbacks = 0
     for snaps, dt in data:
@@ -164,10 +167,13 @@ def evaluate(data, n_les, nu, W=None, b=None, nsteps=10):
             # no-closure fallback for this trajectory
             fallbacks += 1
             g.set_closure(None)
+            g.set_eddy_viscosity(None)
             u = snaps[0].clone()
             for _ in range(nsteps):
                 g.step(u, dt=dt)
             g.set_closure(c)
+            if eddy is not None and c is None:
+                g.set_eddy_viscosity(eddy)
         errs.append(spectrum_error(g, u, snaps[nsteps]))
     g.set_closure(None)
     if c is not None:
@@ -206,7 +212,10 @@ def main():
     W, b, hist = train(train_set, a.n_les, nu, a.iters, a.batch, a.lr, a.nsteps, log=log)
     t2 = time.time()
     err, fb = evaluate(test_set, a.n_les, nu, W, b, nsteps=a.nsteps)
+    eddy = {m: evaluate(test_set, a.n_les, nu, nsteps=a.nsteps, eddy=m)[0]
+            for m in ("smagorinsky", "wale", "qr", "vreman")}
     print(json.dumps({"no_closure_spectrum_error": base, "closure_spectrum_error": err, "fallbacks": fb,
+                      "eddy_viscosity_spectrum_error": eddy,
                       "loss_first": hist[0], "loss_last": hist[-1], "dns_s": t1 - t0, "train_s": t2 - t1}))
 
 

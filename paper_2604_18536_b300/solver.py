@@ -7,6 +7,7 @@ the grid's device and in the grid's dtype; a scalar field drops the first axis.
 """
 
 import ctypes
+import math
 
 import numpy as np
 import torch
@@ -125,6 +126,29 @@ class Grid:
 
     def new_scalar(self):
         return torch.zeros(self.shape, dtype=self.dtype, device=self.device)
+
+    # model constants of the paper's channel LES (Sec. 6.3)
+    EDDY_DEFAULT_C = {"smagorinsky": 0.1, "wale": 0.5, "qr": math.sqrt(1.5) / math.pi,
+                      "vreman": math.sqrt(2.5 * 0.1 ** 2)}
+
+    def set_eddy_viscosity(self, model, C=None):
+        """Attach an eddy-viscosity closure ("smagorinsky", "wale", "qr", "vreman", "constant") or
+        detach it (None / "none"); C defaults to the paper's constant (ins_set_eddy_viscosity)."""
+        name = "none" if model is None else model
+        if name not in _lib.INS_EDDY:
+            raise ValueError(f"model must be one of {sorted(_lib.INS_EDDY)}")
+        c = self.EDDY_DEFAULT_C.get(name, 0.0) if C is None else float(C)
+        check(lib().ins_set_eddy_viscosity(self._h, _lib.INS_EDDY[name], c), "ins_set_eddy_viscosity")
+        self.eddy = None if name == "none" else (name, c)
+
+    def eddy_viscosity(self, u, out=None):
+        """nu_t of the attached model at the cell centres (ins_eddy_viscosity)."""
+        self._check_u(u)
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=u.device)
+        self._sync_stream()
+        check(lib().ins_eddy_viscosity(self._h, _ptr(u), _ptr(out)), "ins_eddy_viscosity")
+        return out
 
     def set_step_fusion(self, enable):
         """FP32 3-D RK4: fused (default) or separate stage-boundary kernels (ins_set_step_fusion)."""
