@@ -321,6 +321,7 @@ def run_ours(args):
             line["closure"] = bench_closure()
         if not args.no_channel:
             line["channel"] = bench_channel()
+            line["channel_large"] = bench_channel_large()
         if not args.no_wray3:
             line["wray3"] = bench_wray3(n, seed=args.seed)
         if not args.no_cpu_baseline and world == 1:
@@ -409,6 +410,52 @@ def bench_channel(n=(192, 128, 192), steps=10, warmup=3):
                                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
         g.check_finite()
         g.close()
+    return out
+
+
+def bench_channel_large(n=(512, 1024, 256), steps=5, warmup=2):
+    """Large channel DNS throughput point (the paper's Re_tau = 180 resolution, 512 x 1024 x 256,
+    uniform in y): FP64 and FP32 RK4 steps; x/z FFT + FP64 Thomas in y. The initial field (laminar
+    parabola plus sines, projected) is built on the device; the step cost does not depend on it."""
+    import torch
+    from paper_2604_18536_b300 import inputs
+    from paper_2604_18536_b300.solver import Grid
+    lx, ly, lz = 4 * math.pi, 2.0, 4 * math.pi / 3
+    faces = [inputs.uniform_faces(n[0], 0.0, lx), inputs.uniform_faces(n[1], 0.0, ly),
+             inputs.uniform_faces(n[2], 0.0, lz)]
+    out = {"workload": "channel DNS %dx%dx%d, uniform y, nu=1/180, RK4, CFL 0.3" % n}
+    cells = n[0] * n[1] * n[2]
+    for tag, dtype in (("f64", torch.float64), ("f32", torch.float32)):
+        torch.cuda.empty_cache()
+        free0, _ = torch.cuda.mem_get_info()
+        g = Grid(faces, ["periodic", "wall", "periodic"], 1.0 / 180, [1.0, 0.0, 0.0], dtype=dtype)
+        yc = torch.tensor(inputs.centres(faces[1]), dtype=dtype, device="cuda")
+        xf = torch.tensor(faces[0][1:], dtype=dtype, device="cuda")
+        zc = torch.tensor(inputs.centres(faces[2]), dtype=dtype, device="cuda")
+        env = (yc * (2.0 - yc))[None, :, None]
+        u = torch.zeros((3, n[2], n[1], n[0]), dtype=dtype, device="cuda")
+        u[0] = 23.4 * env + 1.56 * env * torch.sin(2 * xf)[None, None, :] * torch.cos(3 * zc)[:, None, None]
+        u[2] = 1.56 * env * torch.cos(xf)[None, None, :] * torch.sin(2 * zc)[:, None, None]
+        g.project(u, out=u)
+        dt = g.cfl_dt(u, CFL)
+        for _ in range(warmup):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(steps):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        e1.record(st)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        ms = e0.elapsed_time(e1) / steps
+        out[tag] = {"ms_per_step": ms, "value": cells / (ms / 1e3), "unit": UNIT,
+                    "device_used_gb": (free0 - free1) / 1e9}
+        g.check_finite()
+        g.close()
+        del u, yc, xf, zc, env
+        torch.cuda.empty_cache()
     return out
 
 
