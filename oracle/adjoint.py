@@ -5,59 +5,93 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 Paper: Sec. 3.4 (pullback definition, eq. S:pullback: ubar_J = <phibar, d phi / d u_J>;
 linear operators pull back through their transpose; the Poisson solve is
 self-adjoint so its pullback is again a Poisson solve), App. B (pullback
-kernels of divergence, pressure gradient, diffusion, convection).
+kernels of divergence, pressure gradient, diffusion, convection), Sec. 2.6.1
+(with volume matrices, L^T = Omega_p L Omega_p^-1 on non-uniform grids).
 
-Scope: periodic directions (any spacing) for the operator transposes; the
-step VJP additionally needs a uniform grid, where the projection P = I - G L^-1 D
-is symmetric in the plain Euclidean inner product over the storage index.
+Scope: periodic directions (any spacing) and no-slip wall directions.
 
-Every transpose is written with the transpose of the shift, (S+)^T = S-,
-so it reads as the term-by-term transpose of ``oracle.operators``. The
+Every transpose is written with the transpose of the boundary-aware shift of
+``oracle.operators`` (``shift_T``): in a periodic direction (S+)^T = S-; at a wall
+the ghost rule of the forward shift (0, odd or even reflection of the first or
+last stored value) becomes an extra diagonal term at that stored index. So each
+transpose reads as the term-by-term transpose of ``oracle.operators``. The
 convection pullback is the transpose of the bilinear form B(adv, tra) in both
 arguments; its sum over the two arguments at adv = tra = u is the pullback of
 C(u) = B(u, u) (the eight contributions listed in App. B).
+
+Wall faces that are stored but are not unknowns (the top face of a wall direction,
+``Grid.face_mask``) are not degrees of freedom: the pullbacks take cotangents there as
+zero and return zero there.
+
+Reading for the projection pullback: with the face volumes Omega_u, D = Omega_p^-1 Dh and
+G = -Omega_u^-1 Dh^T on the unknowns (Dh the face-area divergence), so P^T = Omega_u P
+Omega_u^-1; on a uniform periodic grid this is P itself.
 """
 
 import numpy as np
 
 from .grid import PERIODIC
 from . import operators as op
+from .operators import NORMAL, TANGENT, EVEN
 from . import poisson
 from .timestep import RK4_A, RK4_B, WRAY3_A, WRAY3_B
 
 
-def _check_periodic(g):
+def shift_T(g, y, a, s, kind):
+    """Transpose of f -> operators.shift(g, f, a, s, kind)."""
+    ax = g.axis(a)
+    out = np.roll(y, s, axis=ax)
+    if g.bc[a] == PERIODIC:
+        return out
+    n = g.n[a]
+    idx = [slice(None)] * g.dim
+    if s == +1:
+        # shift(+1)[i] = f[i+1] for i < n-1; row n-1 holds the ghost rule in f[n-1]
+        idx[ax] = 0
+        out[tuple(idx)] = 0.0                     # nothing maps onto f[0]
+        last = [slice(None)] * g.dim
+        last[ax] = n - 1
+        if kind == TANGENT:
+            out[tuple(last)] -= y[tuple(last)]
+        elif kind == EVEN:
+            out[tuple(last)] += y[tuple(last)]
+    elif s == -1:
+        idx[ax] = n - 1
+        out[tuple(idx)] = 0.0                     # nothing maps onto f[n-1]
+        first = [slice(None)] * g.dim
+        first[ax] = 0
+        if kind == TANGENT:
+            out[tuple(first)] -= y[tuple(first)]
+        elif kind == EVEN:
+            out[tuple(first)] += y[tuple(first)]
+    else:
+        raise ValueError("shift by +1 or -1 only")
+    return out
+
+
+def mask_u(g, v):
+    """Zero the stored wall faces that are not unknowns."""
+    out = np.array(v, dtype=np.float64, copy=True)
     for a in range(g.dim):
-        assert g.bc[a] == PERIODIC, "adjoints are implemented for periodic directions"
-
-
-def _sp(g, f, a):
-    """S+ along a (periodic)."""
-    return np.roll(f, -1, axis=g.axis(a))
-
-
-def _sm(g, f, a):
-    """S- along a (periodic)."""
-    return np.roll(f, +1, axis=g.axis(a))
+        out[a] = out[a] * g.face_mask(a)
+    return out
 
 
 def divergence_T(g, phibar):
-    """D^T: ubar^a = phibar/d_a[i] - phibar_{I+e_a}/d_a[i+1]   (App. B divergence pullback)."""
-    _check_periodic(g)
+    """D^T: ubar^a = z - S-^T z with z = phibar / d_a   (App. B divergence pullback)."""
     out = g.zeros_u()
     for a in range(g.dim):
         z = phibar / g.along(g.d[a], a)
-        out[a] = z - _sp(g, z, a)
+        out[a] = z - shift_T(g, z, a, -1, NORMAL)
     return out
 
 
 def gradient_T(g, phibar):
-    """G^T: pbar = sum_a phibar^a_{I-e_a}/h_a[i-1] - phibar^a_I/h_a[i]   (App. B)."""
-    _check_periodic(g)
+    """G^T: pbar = sum_a S+^T z - z with z = mask phibar^a / h_a   (App. B)."""
     out = g.zeros_p()
     for a in range(g.dim):
-        z = phibar[a] / g.along(g.h[a], a)
-        out += _sm(g, z, a) - z
+        z = phibar[a] * g.face_mask(a) / g.along(g.h[a], a)
+        out += shift_T(g, z, a, +1, EVEN) - z
     return out
 
 
@@ -74,13 +108,13 @@ def _diff_coeffs(g, a, b):
 
 def diffusion_T(g, phibar):
     """Transpose of ``operators.diffusion`` (without nu)   (App. B diffusion pullback)."""
-    _check_periodic(g)
     out = g.zeros_u()
     for a in range(g.dim):
-        z = phibar[a]
+        z = phibar[a] * g.face_mask(a)
         for b in range(g.dim):
+            kind = NORMAL if b == a else TANGENT
             cp, cm = _diff_coeffs(g, a, b)
-            out[a] += _sm(g, cp * z, b) + _sp(g, cm * z, b) - (cp + cm) * z
+            out[a] += shift_T(g, cp * z, b, +1, kind) + shift_T(g, cm * z, b, -1, kind) - (cp + cm) * z
     return out
 
 
@@ -90,38 +124,46 @@ def convection_bilinear_T(g, adv, tra, w):
     Returns (advbar, trabar). Mirrors ``operators.convection_bilinear`` term by term:
     a term -sum z * X(adv) * Y(tra) gives advbar += -X^T(z Y) and trabar += -Y^T(z X).
     """
-    _check_periodic(g)
     advbar = g.zeros_u()
     trabar = g.zeros_u()
+
+    def sh(f, a, s, kind):
+        return op.shift(g, f, a, s, kind)
+
+    def shT(y, a, s, kind):
+        return shift_T(g, y, a, s, kind)
+
     for a in range(g.dim):
         ta = tra[a]
+        wa = w[a] * g.face_mask(a)
         for b in range(g.dim):
             if b == a:
                 aa = adv[a]
-                z = w[a] / g.along(g.h[a], a)
-                vp = 0.5 * (aa + _sp(g, aa, a))
-                vm = 0.5 * (_sm(g, aa, a) + aa)
-                tp = 0.5 * (ta + _sp(g, ta, a))
-                tm = 0.5 * (_sm(g, ta, a) + ta)
-                # avg+ (x) = (x + S+x)/2  ->  avg+^T (y) = (y + S-y)/2 ; avg- likewise with S+
-                advbar[a] += -0.5 * (z * tp + _sm(g, z * tp, a)) + 0.5 * (z * tm + _sp(g, z * tm, a))
-                trabar[a] += -0.5 * (z * vp + _sm(g, z * vp, a)) + 0.5 * (z * vm + _sp(g, z * vm, a))
+                z = wa / g.along(g.h[a], a)
+                vp = 0.5 * (aa + sh(aa, a, +1, NORMAL))
+                vm = 0.5 * (sh(aa, a, -1, NORMAL) + aa)
+                tp = 0.5 * (ta + sh(ta, a, +1, NORMAL))
+                tm = 0.5 * (sh(ta, a, -1, NORMAL) + ta)
+                # avg+ (x) = (x + S+x)/2  ->  avg+^T (y) = (y + S+^T y)/2 ; avg- likewise with S-^T
+                advbar[a] += -0.5 * (z * tp + shT(z * tp, a, +1, NORMAL)) + 0.5 * (z * tm + shT(z * tm, a, -1, NORMAL))
+                trabar[a] += -0.5 * (z * vp + shT(z * vp, a, +1, NORMAL)) + 0.5 * (z * vm + shT(z * vm, a, -1, NORMAL))
             else:
                 ab = adv[b]
                 wl, wr = op.interp_weights(g, a)
                 wl = g.along(wl, a)
                 wr = g.along(wr, a)
-                z = w[a] / g.along(g.d[b], b)
-                vp = wl * ab + wr * _sp(g, ab, a)
-                vm = _sm(g, vp, b)
-                tp = 0.5 * (ta + _sp(g, ta, b))
-                tm = 0.5 * (_sm(g, ta, b) + ta)
-                # vp = I(ab) with I(x) = wl x + wr S+_a x  ->  I^T(y) = wl y + S-_a(wr y)
-                # vm = S-_b I(ab)                          ->  (S-_b I)^T(y) = I^T(S+_b y)
+                z = wa / g.along(g.d[b], b)
+                vp = wl * ab + wr * sh(ab, a, +1, TANGENT)
+                vm = sh(vp, b, -1, NORMAL)
+                tp = 0.5 * (ta + sh(ta, b, +1, TANGENT))
+                tm = 0.5 * (sh(ta, b, -1, TANGENT) + ta)
+                # vp = I(ab) with I(x) = wl x + wr S+_a x  ->  I^T(y) = wl y + S+_a^T(wr y)
+                # vm = S-_b I(ab)                          ->  (S-_b I)^T(y) = I^T(S-_b^T y)
                 y1 = z * tp
-                y2 = _sp(g, z * tm, b)
-                advbar[b] += -(wl * y1 + _sm(g, wr * y1, a)) + (wl * y2 + _sm(g, wr * y2, a))
-                trabar[a] += -0.5 * (z * vp + _sm(g, z * vp, b)) + 0.5 * (z * vm + _sp(g, z * vm, b))
+                y2 = shT(z * tm, b, -1, NORMAL)
+                advbar[b] += -(wl * y1 + shT(wr * y1, a, +1, TANGENT)) + (wl * y2 + shT(wr * y2, a, +1, TANGENT))
+                trabar[a] += (-0.5 * (z * vp + shT(z * vp, b, +1, TANGENT))
+                              + 0.5 * (z * vm + shT(z * vm, b, -1, TANGENT)))
     return advbar, trabar
 
 
@@ -144,12 +186,24 @@ def F_vjp(g, u, w, closure=None):
     return ubar + cu, nubar, grads
 
 
-def project_T(g, kbar):
-    """P^T = P on periodic uniform grids (the Poisson solve is self-adjoint, Sec. 2.6.1)."""
+def _face_volumes(g):
+    """Omega_u^a without the wall mask (positive everywhere)."""
+    out = g.zeros_u()
     for a in range(g.dim):
-        assert g.is_uniform(a), "P is symmetric only on uniform periodic grids"
-    w, _ = poisson.project(g, kbar)
-    return w
+        v = np.ones(g.shape) * g.along(g.h[a], a)
+        for b in range(g.dim):
+            if b != a:
+                v = v * g.along(g.d[b], b)
+        out[a] = v
+    return out
+
+
+def project_T(g, kbar):
+    """P^T = M Omega_u P Omega_u^-1 M (M the mask of the unknowns; reading in the module docstring).
+    On a uniform periodic grid Omega_u is constant and P^T = P (Sec. 2.6.1)."""
+    vol = _face_volumes(g)
+    w, _ = poisson.project(g, mask_u(g, kbar) / vol)
+    return mask_u(g, vol * w)
 
 
 def rk4_step_vjp(g, u0, dt, ybar, closure=None):
@@ -159,9 +213,9 @@ def rk4_step_vjp(g, u0, dt, ybar, closure=None):
     Forward (``timestep.rk4_step``): k_s = P F(u_s), u_s = u0 + dt a_{s,s-1} k_{s-1},
     u1 = u0 + dt sum_s b_s k_s. Reverse: kbar_s = dt b_s ybar + dt a_{s+1,s} ubar_{s+1},
     w_s = P^T kbar_s, ubar_s = J_F(u_s)^T w_s, u0bar = ybar + sum_s ubar_s,
-    nubar = sum_s <w_s, diffusion(u_s)>.
+    nubar = sum_s <w_s, diffusion(u_s)>. ybar and u0bar are masked to the unknowns.
     """
-    _check_periodic(g)
+    ybar = mask_u(g, ybar)
     # recompute the stage states from the checkpoint u0
     us = [u0]
     for s in range(3):
@@ -183,6 +237,7 @@ def rk4_step_vjp(g, u0, dt, ybar, closure=None):
         u0bar = u0bar + ubar_s
         if s > 0:
             kbar[s - 1] = kbar[s - 1] + dt * RK4_A[s] * ubar_s
+    u0bar = mask_u(g, u0bar)
     if closure is not None:
         return u0bar, nubar, wgrads
     return u0bar, nubar
@@ -198,7 +253,7 @@ def erk_step_vjp(g, u0, dt, ybar, A, b):
     nubar = sum_s <w_s, diffusion(u_s)>.
     """
     from .timestep import stage_derivative
-    _check_periodic(g)
+    ybar = mask_u(g, ybar)
     ns = len(b)
     us, ks = [], []
     for s in range(ns):
@@ -217,7 +272,7 @@ def erk_step_vjp(g, u0, dt, ybar, A, b):
         u0bar = u0bar + ubar_s
         for t, a in enumerate(A[s]):
             kbar[t] = kbar[t] + dt * a * ubar_s
-    return u0bar, nubar
+    return mask_u(g, u0bar), nubar
 
 
 def wray3_step_vjp(g, u0, dt, ybar):
