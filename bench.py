@@ -405,11 +405,24 @@ def bench_channel(n=(192, 128, 192), steps=10, warmup=3):
         prof = g.profile_read()
         g.profile(False)
         ms = e0.elapsed_time(e1) / steps
+        # step VJP on the wall-bounded grid (scatter-form transposes, P^T = M Omega P Omega^-1 M)
+        ybar = u.detach().clone()
+        ubar = g.new_velocity()
+        g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(3):
+            g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar)
+        e1.record(st)
+        torch.cuda.synchronize()
+        vms = e0.elapsed_time(e1) / 3
         out[tag] = {"ms_per_step": ms, "value": cells / (ms / 1e3), "unit": UNIT,
+                    "ms_per_vjp": vms, "adjoint_forward_ratio": vms / ms,
                     "kernels": {k: {"launches": v[0], "avg_us": round(v[1] / v[0] * 1e3, 2)}
                                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
         g.check_finite()
         g.close()
+        del ybar, ubar
     return out
 
 

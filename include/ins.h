@@ -154,7 +154,11 @@ ins_status ins_set_step_fusion(ins_grid* g, int enable);
  * u_n, ubar_np1: DEVICE, dim fields, not modified. ubar_n: DEVICE, dim fields, must not
  * alias the inputs. dt_dev/dt_host: as in ins_step. nubar_dev: DEVICE double that the
  * result is added to (so it can accumulate over steps), or NULL.
- * Periodic uniform grids only (INS_ERR_UNSUPPORTED otherwise). The first call allocates the
+ * Periodic uniform grids use P^T = P and gather-form transposed stencils. Wall-bounded grids
+ * (y a no-slip wall, possibly stretched) use P^T = M Omega P Omega^-1 M (Omega the velocity
+ * volumes; M zeroes the stored top wall faces of u^y, which are not unknowns: cotangents
+ * there are ignored and ubar_n is 0 there) and scatter-form transposes with atomics (the
+ * summation order, hence the last bits, may vary between calls). The first call allocates the
  * step-VJP workspace (3 stage states, two fields, nu partial sums: about 5 velocity fields),
  * kept until ins_grid_destroy; make the first call before any stream capture.
  * The grid's F, r/p and RK accumulator buffers are reused as scratch. */

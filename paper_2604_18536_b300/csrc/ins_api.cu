@@ -23,6 +23,7 @@
 #include "stencil.cuh"
 #include "rk.cuh"
 #include "adjoint.cuh"
+#include "adjoint_wall.cuh"
 #include "filter_spectrum.cuh"
 #include "conv_tc.cuh"
 #include "eddy.cuh"
@@ -594,8 +595,102 @@ struct Impl {
     }
     // Pullback of one RK4 step (uniform periodic grids): recompute the stage states from the
     // checkpoint u_n, then run the stages in reverse (see ins.h, ins_step_vjp).
+    // Pullback of one step on a wall-bounded grid: stage recompute as below, P^T = M Omega P
+    // Omega^-1 M, J_F^T in scatter form (k_adj_rhs_wall); the stored top wall faces of u^y are not
+    // unknowns (cotangents there are ignored and returned as 0).
+    static ins_status step_vjp_wall(ins_grid* g, const T* un, const double* dt_dev, double dt_host, const T* ybar,
+                                    T* ubar, double* nubar) {
+        static const double A[3] = {0.5, 0.5, 1.0};
+        static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+        const long N = g->N;
+        const size_t fld = (size_t)g->dim * N * sizeof(T);
+        const size_t fa = (fld + 255) & ~size_t(255);
+        const dim3 cg = cell_grid(g);
+        const long nblk = (long)cg.x * cg.y * cg.z;
+        const size_t need = 5 * fa + (size_t)nblk * 8;
+        if (g->vjp_bytes < need) {
+            if (g->vjp) cudaFree(g->vjp);
+            g->vjp = nullptr;
+            g->vjp_bytes = 0;
+            cudaError_t e = cudaMalloc(&g->vjp, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(INS_ERR_OOM, std::string("step-VJP workspace: ") + cudaGetErrorString(e));
+            }
+            g->vjp_bytes = need;
+        }
+        char* vb = reinterpret_cast<char*>(g->vjp);
+        T* U[4] = {const_cast<T*>(un), reinterpret_cast<T*>(vb), reinterpret_cast<T*>(vb + fa),
+                   reinterpret_cast<T*>(vb + 2 * fa)};
+        T* W = reinterpret_cast<T*>(vb + 3 * fa);
+        T* Q = reinterpret_cast<T*>(vb + 4 * fa);
+        double* part = reinterpret_cast<double*>(vb + 5 * fa);
+        T* F = reinterpret_cast<T*>(g->F);
+        T* rp = reinterpret_cast<T*>(g->rp);
+        T* scratch = reinterpret_cast<T*>(g->acc);
+        const bool lowst = g->scheme == INS_WRAY3;
+        const int nst = lowst ? 3 : 4;
+        ins_status s;
+        for (int st = 0; st < nst - 1; ++st) {
+            if ((s = launch_rhs_div<T, DIM, WALL>(g, U[st], F, rp)) != INS_OK) return s;
+            if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+            RkArgs ra;
+            ra.dt_dev = dt_dev;
+            ra.dt_host = dt_host;
+            ra.mx = nullptr;
+            ra.err_flag = g->err_flag;
+            ra.last = 0;
+            if (lowst) {
+                ra.a_next = WRAY3_GAMMA[st];
+                ra.b = WRAY3_ZETA[st];
+                ra.stage = st;
+                KLAUNCH(g, "rk_update", (k_rk_update<T, DIM, WALL, true><<<cg, dim3(32, 8), 0, g->stream>>>(
+                                            make_geo<T>(g), F, rp, U[st], scratch, U[st + 1], ra)));
+            } else {
+                ra.a_next = A[st];
+                ra.b = 0.0;
+                ra.stage = 0;
+                KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(
+                                            make_geo<T>(g), F, rp, U[0], scratch, U[st + 1], ra));
+            }
+        }
+        const long n = (long)g->dim * N;
+        const double* hy = g->geo64 + g->nx;
+        const double* dy = g->geo64 + (g->nx + g->ny + g->nz) + g->nx;
+        INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
+        KLAUNCH(g, "scale", k_scale_dt<T><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host,
+                                                                      lowst ? WRAY3_GAMMA[2] : B[3], n));
+        WallAdj<T> wa;
+        wa.g = make_geo<T>(g);
+        wa.nu = (T)g->nu;
+        for (int st = nst - 1; st >= 0; --st) {
+            // w = P^T kbar = M Omega P (Omega^-1 M kbar)
+            KLAUNCH(g, "row_scale", k_row_scale<T><<<1184, 256, 0, g->stream>>>(F, W, hy, dy, g->nx, g->ny, N, g->dim, 1));
+            KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), W, rp));
+            if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+            KLAUNCH(g, "sub_grad", k_sub_grad<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), W, rp, W));
+            KLAUNCH(g, "row_scale", k_row_scale<T><<<1184, 256, 0, g->stream>>>(W, W, hy, dy, g->nx, g->ny, N, g->dim, 0));
+            INS_CUDA(cudaMemsetAsync(Q, 0, fld, g->stream));
+            KLAUNCH(g, "adj_rhs", k_adj_rhs_wall<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(wa, U[st], W, Q, part));
+            if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, nblk, nubar));
+            double bn, an;
+            if (lowst) {
+                bn = st > 0 ? WRAY3_GAMMA[st - 1] + WRAY3_ZETA[st] : 0.0;
+                an = st > 0 ? WRAY3_GAMMA[st - 1] : 0.0;
+            } else {
+                bn = st > 0 ? B[st - 1] : 0.0;
+                an = st > 0 ? A[st - 1] : 0.0;
+            }
+            KLAUNCH(g, "adj_finish", k_adj_finish<T><<<1184, 256, 0, g->stream>>>(
+                                         Q, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, dt_dev, dt_host, bn, an,
+                                         g->nx, g->ny, N, g->dim));
+        }
+        KLAUNCH(g, "mask_top", k_mask_top<T><<<592, 256, 0, g->stream>>>(ubar, g->nx, g->ny, g->nz, N));
+        return INS_OK;
+    }
     static ins_status step_vjp(ins_grid* g, const T* un, const double* dt_dev, double dt_host, const T* ybar,
                                T* ubar, double* nubar) {
+        if constexpr (WALL) return step_vjp_wall(g, un, dt_dev, dt_host, ybar, ubar, nubar);
         static const double A[3] = {0.5, 0.5, 1.0};
         static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
         const long N = g->N;
@@ -1289,7 +1384,6 @@ ins_status ins_step_vjp(ins_grid* g, const void* u_n, const double* dt_dev, doub
     CHECK(check_ptr(g, ubar_n, "ubar_n"));
     if (ubar_n == ubar_np1 || ubar_n == u_n) return fail(INS_ERR_ARG, "ubar_n must not alias u_n or ubar_np1");
     if (!dt_dev && !(std::isfinite(dt_host) && dt_host >= 0.0)) return fail(INS_ERR_ARG, "dt_host must be finite, >= 0");
-    if (g->wall_y) return fail(INS_ERR_UNSUPPORTED, "ins_step_vjp: wall directions are not supported (periodic grids only)");
     if (g->eddy) return fail(INS_ERR_UNSUPPORTED, "ins_step_vjp: eddy-viscosity models have no pullback here");
     return dispatch_dtype(g, [&](auto z) {
         using T = decltype(z);

@@ -115,11 +115,3 @@ def test_autograd_rollout_matches_oracle_chain():
         nub += nb
     assert rel(u.grad.cpu().numpy(), ybar) <= 1e-12
     assert abs(nu.grad.item() - nub) <= 1e-10 * abs(nub)
-
-
-def test_step_vjp_rejects_wall_grids():
-    faces = inputs.channel_faces(8, 8, 8)
-    gg = Grid(faces, ["periodic", "wall", "periodic"], 0.01, dtype=torch.float64)
-    u = gg.new_velocity()
-    with pytest.raises(InsError):
-        gg.step_vjp(u, u.clone(), dt=1e-3)
