@@ -133,6 +133,18 @@ ins_status ins_divergence(ins_grid* g, const void* u, void* phi);
 ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host,
                     double* next_dt_dev, double cfl);
 
+/* Wall-normal pressure solve of a channel grid (Sec. 2.6.1 and 6): after the x and z FFTs,
+ * INS_WALL_THOMAS solves the tridiagonal y system of every (kx, kz) mode in FP64 (any
+ * spacing); INS_WALL_DCT diagonalises it with a DCT-II (uniform spacing only: the Neumann
+ * rows' eigenvectors are cos(pi k (2j+1)/(2 ny))), computed by one complex FFT of length ny
+ * (ny = 2^p 3^q 5^r 7^s <= 2048) and divided by the eigenvalue sum in FP64. Every grid starts
+ * with INS_WALL_THOMAS (on this GPU it is faster: two O(ny) sweeps against two FFTs per line).
+ * The two give the same velocities; the pressure's mean-mode constant differs (DCT: zero
+ * mean, Thomas: p = 0 in the first row of the mean mode). INS_ERR_UNSUPPORTED: no wall
+ * direction, or DCT on a grid that does not allow it. */
+typedef enum { INS_WALL_THOMAS = 0, INS_WALL_DCT = 1 } ins_wall_solver;
+ins_status ins_set_wall_solver(ins_grid* g, int solver);
+
 /* Stage-boundary fusion of ins_step (no counterpart in the paper: an implementation
  * choice). On FP32 3-D INS_RK4 grids without a closure, ins_step by default runs the update
  * of stage s and the evaluation of F and D F of stage s + 1 as one kernel, so the stage

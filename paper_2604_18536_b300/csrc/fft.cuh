@@ -386,3 +386,80 @@ __global__ void k_thomas(cplx<T>* __restrict__ S, const double* __restrict__ lo,
 }
 
 }  // namespace ins
+
+namespace ins {
+
+// ------------------------------------------------------ DCT-II wall-normal solve
+// Uniform wall-normal spacing (paper Sec. 6: the channel DNS on a uniform grid solves the
+// pressure with FFTs): with homogeneous Neumann rows the y operator is diagonalised by the
+// DCT-II, X_k = sum_j x_j cos(pi k (2j+1) / (2N)), with eigenvalues mu_k = -4 sin^2(pi k/(2N)) / dy^2.
+// One visit per tile of TW columns (after the x and z forward FFTs): the DCT-II by one complex
+// FFT of the reordered line v = (x_0, x_2, ..., x_3, x_1) (Makhoul, IEEE TASSP 1980):
+//   X_k = (w_k V_k + conj(w_k) V_{N-k}) / 2,  w_k = exp(-i pi k / (2N)),  V_N := V_0;
+// division by lambda_x + lambda_z + mu_k (FP64; the mean mode is set to 0) times `norm`;
+// and the inverse: V_k = conj(w_k) (X_k - i X_{N-k}) (X_N := 0), v = IDFT(V) (the 1/N is in
+// `norm`), x_{2m} = v_m, x_{2(N-1-m)+1} = v_m for m >= ceil(N/2).
+// Columns as in k_fft_strided: element (col, j) at (col / cdiv) * outer + j * lstride + col % cdiv,
+// kx = col % cdiv, kz = col / cdiv.
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS) k_dct_solve_y(FftLine<T> pl, cplx<T>* __restrict__ S, long ncol,
+                                                             long cdiv, long outer, long lstride,
+                                                             const cplx<T>* __restrict__ qw,
+                                                             const double* __restrict__ lamx,
+                                                             const double* __restrict__ lamy,
+                                                             const double* __restrict__ lamz, double norm, int lgTW) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TW = 1 << lgTW, SP = TW + 1, L = pl.L;
+    const int hN = (L + 1) / 2;
+    cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* buf1 = buf0 + (size_t)L * SP;
+    const long c0 = (long)blockIdx.x * TW;
+    auto src_row = [L, hN](int m) { return m < hN ? 2 * m : 2 * (L - 1 - m) + 1; };
+    for (int item = threadIdx.x; item < L * TW; item += blockDim.x) {
+        const int c = item & (TW - 1), m = item >> lgTW;
+        const long col = c0 + c;
+        cplx<T> z = {(T)0, (T)0};
+        if (col < ncol) z = S[(col / cdiv) * outer + (long)src_row(m) * lstride + (col % cdiv)];
+        buf0[m * SP + c] = z;
+    }
+    __syncthreads();
+    cplx<T>* V = fft_tile(pl, buf0, buf1, SP, lgTW);
+    cplx<T>* X = (V == buf0) ? buf1 : buf0;
+    for (int item = threadIdx.x; item < L * TW; item += blockDim.x) {
+        const int c = item & (TW - 1), k = item >> lgTW;
+        const long col = c0 + c;
+        const cplx<T> w = ldg_c(&qw[k]);
+        const cplx<T> vk = V[k * SP + c];
+        const cplx<T> vn = V[(k == 0 ? 0 : L - k) * SP + c];
+        // (w vk + conj(w) vn) / 2
+        cplx<T> d = {(T)0.5 * (w.re * (vk.re + vn.re) - w.im * (vk.im - vn.im)),
+                     (T)0.5 * (w.re * (vk.im + vn.im) + w.im * (vk.re - vn.re))};
+        double s = 0.0;
+        if (col < ncol) {
+            const long kx = col % cdiv, kz = col / cdiv;
+            const double lam = lamx[kx] + lamz[kz] + lamy[k];
+            s = lam != 0.0 ? norm / lam : 0.0;
+        }
+        X[k * SP + c] = {(T)(s * (double)d.re), (T)(s * (double)d.im)};
+    }
+    __syncthreads();
+    for (int item = threadIdx.x; item < L * TW; item += blockDim.x) {
+        const int c = item & (TW - 1), k = item >> lgTW;
+        const cplx<T> w = ldg_c(&qw[k]);
+        const cplx<T> xk = X[k * SP + c];
+        const cplx<T> xn = k == 0 ? cplx<T>{(T)0, (T)0} : X[(L - k) * SP + c];
+        // t = xk - i xn; V = conj(w) t; stored conjugated for the inverse by a forward FFT
+        const cplx<T> t = {xk.re + xn.im, xk.im - xn.re};
+        const cplx<T> vv = {w.re * t.re + w.im * t.im, w.re * t.im - w.im * t.re};
+        V[k * SP + c] = cconj(vv);
+    }
+    __syncthreads();
+    cplx<T>* Z = fft_tile(pl, V, X, SP, lgTW);
+    for (int item = threadIdx.x; item < L * TW; item += blockDim.x) {
+        const int c = item & (TW - 1), m = item >> lgTW;
+        const long col = c0 + c;
+        if (col < ncol) S[(col / cdiv) * outer + (long)src_row(m) * lstride + (col % cdiv)] = cconj(Z[m * SP + c]);
+    }
+}
+
+}  // namespace ins

@@ -110,6 +110,10 @@ struct ins_grid {
     double* th_invm = nullptr;     // [ny][ncol]
     double* th_cp = nullptr;       // [ny][ncol]
     void* th_d = nullptr;          // cplx<double> [ny][ncol]
+    // DCT-II solve along a uniform wall-normal y (available when y is uniform and ny factorises)
+    int wall_dct = 0;              // available
+    int use_dct = 0;               // selected (ins_set_wall_solver; default Thomas)
+    void* dct_qw = nullptr;        // T complex [ny]: exp(-i pi k / (2 ny))
     void* F = nullptr;
     void* acc = nullptr;
     void* us = nullptr;
@@ -363,8 +367,17 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
         if (g->dim == 3 && (s = strided(2, 0)) != INS_OK) return s;
         const long ncol = (long)nz * nxh;
         const double norm = 1.0 / ((double)nx * (g->dim == 3 ? nz : 1));
-        KLAUNCH(g, "thomas", k_thomas<T><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(
-            S, g->th_lo, g->th_invm, g->th_cp, reinterpret_cast<cplx<double>*>(g->th_d), nxh, ny, ncol, norm));
+        if (g->use_dct) {
+            FftLine<T> py = make_line<T>(g, 1);
+            const int lg = g->lg_tw_y;
+            const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
+            KLAUNCH(g, "dct_solve", k_dct_solve_y<T><<<blocks, FFT_THREADS, fft_smem<T>(ny, lg), st>>>(
+                py, S, ncol, nxh, (long)ny * nxh, nxh, reinterpret_cast<const cplx<T>*>(g->dct_qw), g->lam,
+                g->lam + nx, g->lam + nx + ny, norm / ny, lg));
+        } else {
+            KLAUNCH(g, "thomas", k_thomas<T><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(
+                S, g->th_lo, g->th_invm, g->th_cp, reinterpret_cast<cplx<double>*>(g->th_d), nxh, ny, ncol, norm));
+        }
         if (g->dim == 3 && (s = strided(2, 1)) != INS_OK) return s;
     }
     if (reg_fft_len(nx)) {
@@ -926,6 +939,7 @@ ins_status set_smem_attrs() {
     INS_CUDA(cudaFuncSetAttribute(k_fft_x_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     INS_CUDA(cudaFuncSetAttribute(k_fft_x_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     INS_CUDA(cudaFuncSetAttribute(k_fft_strided<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    INS_CUDA(cudaFuncSetAttribute(k_dct_solve_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     return INS_OK;
 }
 
@@ -1047,6 +1061,20 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
             g->h[a][i] = 0.5 * (g->d[a][i] + dn);
         }
         g->hlo[a] = wall ? g->d[a][0] : 0.5 * (g->d[a][n - 1] + g->d[a][0]);
+        if (wall) {
+            // uniform wall-normal spacing with an FFT-friendly n: the DCT-II solve is available
+            double mean = 0.0;
+            for (double w : g->d[a]) mean += w;
+            mean /= n;
+            bool uni = n <= 2048;
+            for (double w : g->d[a]) uni = uni && std::fabs(w - mean) <= 1e-10 * mean;
+            std::vector<int> rad;
+            if (uni && factor_radices(n, rad)) {
+                g->wall_dct = 1;   // available; the Thomas solve stays the default (faster here)
+                g->nst[a] = (int)rad.size();
+                for (size_t s = 0; s < rad.size(); ++s) g->radix[a][s] = rad[s];
+            }
+        }
         if (!wall) {
             double mean = 0.0;
             for (double w : g->d[a]) mean += w;
@@ -1084,6 +1112,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
         off += al((size_t)n3[a] * 2 * ts);
     }
     o_lam = off; off += al(nsum * 8);
+    const size_t o_qw = off; off += g->wall_dct ? al((size_t)g->ny * 2 * ts) : 0;
     if (!wall_y) {
         o_scale = off; off += al((size_t)spec * ts);
     } else {
@@ -1117,6 +1146,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     g->one = reinterpret_cast<double*>(b + o_one);
     for (int a = 0; a < 3; ++a) g->tw[a] = b + o_tw[a];
     g->lam = reinterpret_cast<double*>(b + o_lam);
+    g->dct_qw = g->wall_dct ? b + o_qw : nullptr;
     if (!wall_y) {
         g->scale = b + o_scale;
     } else {
@@ -1189,7 +1219,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     }
     if (!ok) return bail(INS_ERR_CUDA, "geometry upload failed");
     for (int a = 0; a < dim; ++a) {
-        if (a == 1 && wall_y) continue;
+        if (a == 1 && wall_y && !g->wall_dct) continue;
         ins_status s = D.dtype == INS_F64 ? upload_twiddles<double>(g, a, g->tw[a], n3[a])
                                           : upload_twiddles<float>(g, a, g->tw[a], n3[a]);
         if (s != INS_OK) {
@@ -1204,11 +1234,15 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
         for (int a = 0; a < 3; ++a) {
             const int n = n3[a];
             const bool per = a < dim && !(a == 1 && wall_y);
+            const bool dct = a == 1 && g->wall_dct;
             for (int k = 0; k < n; ++k) {
                 double v = 0.0;
                 if (per) {
                     const double s = std::sin(M_PI * (double)k / (double)n);
                     v = -4.0 * s * s / (g->d[a][0] * g->h[a][0]);
+                } else if (dct) {   // Neumann rows, uniform spacing: DCT-II eigenvalues
+                    const double s = std::sin(M_PI * (double)k / (2.0 * n));
+                    v = -4.0 * s * s / (g->d[a][0] * g->d[a][0]);
                 }
                 lam[o++] = v;
             }
@@ -1248,6 +1282,19 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
                     invm[(size_t)j * ncol + col] = 1.0 / m;
                     cp[(size_t)j * ncol + col] = c;
                     cprev = c;
+                }
+            }
+            if (g->wall_dct) {
+                std::vector<double> qw(2 * (size_t)ny);
+                for (int k = 0; k < ny; ++k) {
+                    qw[2 * k] = std::cos(M_PI * k / (2.0 * ny));
+                    qw[2 * k + 1] = -std::sin(M_PI * k / (2.0 * ny));
+                }
+                if (D.dtype == INS_F64) {
+                    ok &= up(g->dct_qw, qw.data(), qw.size() * 8);
+                } else {
+                    std::vector<float> qf(qw.begin(), qw.end());
+                    ok &= up(g->dct_qw, qf.data(), qf.size() * 4);
                 }
             }
             ok &= up(g->th_lo, lo.data(), (size_t)ny * 8);
@@ -1352,6 +1399,17 @@ ins_status ins_divergence(ins_grid* g, const void* u, void* phi) {
         using T = decltype(z);
         return dispatch<T>(g, [&](auto impl) { return decltype(impl)::divergence(g, (const T*)u, (T*)phi); });
     });
+}
+
+ins_status ins_set_wall_solver(ins_grid* g, int solver) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "ins_set_wall_solver: null grid");
+    if (solver != INS_WALL_THOMAS && solver != INS_WALL_DCT) return fail(INS_ERR_ARG, "unknown wall solver");
+    if (!g->wall_y) return fail(INS_ERR_UNSUPPORTED, "ins_set_wall_solver: no wall direction");
+    if (solver == INS_WALL_DCT && !g->wall_dct)
+        return fail(INS_ERR_UNSUPPORTED, "DCT solve needs a uniform wall-normal grid with n = 2^p 3^q 5^r 7^s <= 2048");
+    g->use_dct = solver == INS_WALL_DCT;
+    return INS_OK;
 }
 
 ins_status ins_set_step_fusion(ins_grid* g, int enable) {

@@ -150,6 +150,11 @@ class Grid:
         check(lib().ins_eddy_viscosity(self._h, _ptr(u), _ptr(out)), "ins_eddy_viscosity")
         return out
 
+    def set_wall_solver(self, solver):
+        """Channel grids: "thomas" (any y spacing) or "dct" (uniform y) wall-normal pressure solve."""
+        code = {"thomas": 0, "dct": 1}[solver]
+        check(lib().ins_set_wall_solver(self._h, code), "ins_set_wall_solver")
+
     def set_step_fusion(self, enable):
         """FP32 3-D RK4: fused (default) or separate stage-boundary kernels (ins_set_step_fusion)."""
         check(lib().ins_set_step_fusion(self._h, 1 if enable else 0), "ins_set_step_fusion")

@@ -47,17 +47,25 @@ def case(name):
     if name == "c2":
         return dict(faces=[U(30, 0, 4 * PI), inputs.tanh_faces(18, 0, 2, 1.5)], bc=["periodic", "wall"], nu=0.05,
                     force=[1.0, 0.0])
+    if name == "cu3":       # uniform wall-normal spacing: the DCT-II wall solve
+        return dict(faces=[U(40, 0, 4 * PI), U(24, 0, 2.0), U(20, 0, 4 * PI / 3)],
+                    bc=["periodic", "wall", "periodic"], nu=1 / 180, force=[1.0, 0.0, 0.0])
+    if name == "cu2":
+        return dict(faces=[U(30, 0, 4 * PI), U(18, 0, 2.0)], bc=["periodic", "wall"], nu=0.05, force=[1.0, 0.0])
     raise KeyError(name)
 
 
-CASES = ["p2", "p3", "p3tiny", "p3reg", "p3reg2", "c3", "c3reg", "c2"]
+CASES = ["p2", "p3", "p3tiny", "p3reg", "p3reg2", "c3", "c3reg", "c2", "cu3", "cu2", "cu3dct", "cu2dct"]
 DTYPES = [torch.float64, torch.float32]
 
 
 def grids(name, dtype):
-    c = case(name)
+    dct = name.endswith("dct")          # the uniform-y channel cases with the DCT-II y solve
+    c = case(name[:-3] if dct else name)
     og = OGrid(c["faces"], c["bc"], c["nu"], c["force"])
     gg = Grid(c["faces"], c["bc"], c["nu"], c["force"], dtype=dtype)
+    if dct:
+        gg.set_wall_solver("dct")
     return og, gg
 
 
@@ -262,3 +270,21 @@ def test_fp32_fused_matches_unfused(name):
         gg.set_step_fusion(False)
         gg.step(b, dt=dt)
     assert rel(host(a), host(b)) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", ["cu3", "cu2"])
+def test_dct_and_thomas_wall_solves_agree(name, dtype):
+    """On a uniform wall-normal grid both y solves give the same step (velocities)."""
+    og, gg = grids(name, dtype)
+    u0 = rounded(rand_u(og, 41, project=True), dtype)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    a = dev(u0, dtype)
+    b = dev(u0, dtype)
+    gg.set_wall_solver("dct")
+    gg.step(a, dt=dt)
+    gg.set_wall_solver("thomas")
+    gg.step(b, dt=dt)
+    assert rel(host(a), host(b)) <= (1e-13 if dtype == torch.float64 else 1e-6)
+    with pytest.raises(InsError):
+        grids("c3", dtype)[1].set_wall_solver("dct")     # stretched y: no DCT
