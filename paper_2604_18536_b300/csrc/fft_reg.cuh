@@ -160,14 +160,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_fft_strided_reg
 }
 
 // ---------------------------------------------------------------------------------------
-// Pipelined strided pass (FP32): persistent CTAs walk the tiles of TW columns; the tile
+// Pipelined strided pass: persistent CTAs walk the tiles of TW columns; the tile
 // after the current one is copied global -> shared with cp.async while the current one is
 // transformed, so the HBM latency is hidden behind the butterflies. The tile's shared
 // buffer (L rows of TW padded columns) also serves as the exchange buffer once stage A has
 // read it. Mode 2 prefetches the spectral scale of the tile the same way.
-__device__ __forceinline__ void fr_cp_async(void* smem, const void* gmem, int bytes, int src_bytes) {
+template <int BYTES>
+__device__ __forceinline__ void fr_cp_async(void* smem, const void* gmem, int src_bytes) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if (bytes == 8)
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+    else if constexpr (BYTES == 8)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
@@ -176,27 +179,27 @@ __device__ __forceinline__ void fr_cp_commit() { asm volatile("cp.async.commit_g
 __device__ __forceinline__ void fr_cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void fr_cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int R1, int R2>
+template <typename T, int R1, int R2>
 struct PipeShape {
     static constexpr int L = R1 * R2;
     static constexpr int RM = R1 > R2 ? R1 : R2;
-    static constexpr int NT = 256;
+    static constexpr int NT = sizeof(T) == 8 ? 128 : 256;   // 128-byte rows of TW complex values
     static constexpr int TW = NT / RM;
     static constexpr int SP = TW + 1;
     static constexpr int PER = L * TW / NT;   // copies per thread per tile
     static constexpr size_t smem(bool scaled) {
-        return 2 * (size_t)L * SP * sizeof(cplx<float>) + (scaled ? 2 * (size_t)L * TW * sizeof(float) : 0);
+        return 2 * (size_t)L * SP * sizeof(cplx<T>) + (scaled ? 2 * (size_t)L * TW * sizeof(T) : 0);
     }
 };
 
-// Same modes, addressing and results as k_fft_strided_reg<float, R1, R2>; grid = any number of
+// Same modes, addressing and results as k_fft_strided_reg<T, R1, R2>; grid = any number of
 // CTAs (persistent), dynamic shared memory PipeShape::smem(mode == 2).
-template <int R1, int R2>
-__global__ void __launch_bounds__(256, 2) k_fft_strided_pipe(const cplx<float>* __restrict__ tw, cplx<float>* __restrict__ S,
-                                                            long ncol, long cdiv, long outer, long lstride, int mode,
-                                                            const float* __restrict__ scale) {
-    using T = float;
-    using Sh = PipeShape<R1, R2>;
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(PipeShape<T, R1, R2>::NT, 2) k_fft_strided_pipe(const cplx<T>* __restrict__ tw,
+                                                                                cplx<T>* __restrict__ S, long ncol,
+                                                                                long cdiv, long outer, long lstride,
+                                                                                int mode, const T* __restrict__ scale) {
+    using Sh = PipeShape<T, R1, R2>;
     constexpr int L = Sh::L, TW = Sh::TW, SP = Sh::SP;
     extern __shared__ __align__(16) unsigned char fr_smem[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(fr_smem);              // [2][L * SP]
@@ -213,14 +216,14 @@ __global__ void __launch_bounds__(256, 2) k_fft_strided_pipe(const cplx<float>* 
         cplx<T>* dst = buf + b * L * SP;
         const long col = tile * TW + c;
         const bool ok = col < ncol;
-        const int nb = ok ? 8 : 0;
+        const int nb = ok ? (int)sizeof(cplx<T>) : 0;
         const long base = ok ? (col / cdiv) * outer + (col % cdiv) + (long)q * lstride : 0;
         const long step = ok ? (long)MSTEP * lstride : 0;
 #pragma unroll
         for (int t = 0; t < Sh::PER; ++t) {
             const int m = q + MSTEP * t;
-            fr_cp_async(dst + m * SP + c, S + base + t * step, 8, nb);
-            if (mode == 2) fr_cp_async(sc + b * L * TW + m * TW + c, scale + base + t * step, 4, nb / 2);
+            fr_cp_async<sizeof(cplx<T>)>(dst + m * SP + c, S + base + t * step, nb);
+            if (mode == 2) fr_cp_async<sizeof(T)>(sc + b * L * TW + m * TW + c, scale + base + t * step, nb / 2);
         }
         fr_cp_commit();
     };
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(256, 2) k_fft_strided_pipe(const cplx<float>* 
     fr_cp_wait0();
 }
 
-// Pipelined inverse x pass (FP32): a tile of TW line pairs is one contiguous block of the
+// Pipelined inverse x pass: a tile of TW line pairs is one contiguous block of the
 // half spectrum (2 TW rows of nxh complex), copied with 16-byte cp.async into a double
 // buffer while the previous tile is transformed. Needs a 16-byte aligned spectrum (checked
 // by the caller); the tail of the last tile is zero-filled (src-size operand). (The same
@@ -307,40 +310,41 @@ __device__ __forceinline__ void fr_cp_async16(void* smem, const void* gmem, int 
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
 }
 
-template <int R1, int R2>
+template <typename T, int R1, int R2>
 struct PipeX {
     static constexpr int L = R1 * R2;
     static constexpr int RM = R1 > R2 ? R1 : R2;
-    static constexpr int NT = 256;
+    static constexpr int NT = sizeof(T) == 8 ? 128 : 256;
     static constexpr int TW = NT / RM;          // line pairs per tile
     static constexpr int SR = L + L / 16 + 1;   // padded exchange row
+    static constexpr int EPC = 16 / (int)sizeof(cplx<T>);   // complex values per 16-byte chunk
     static constexpr size_t smem_c2r(int nxh) {
-        return 2 * (((size_t)2 * TW * nxh * sizeof(cplx<float>) + 15) & ~size_t(15)) + (size_t)TW * SR * sizeof(cplx<float>);
+        return 2 * (((size_t)2 * TW * nxh * sizeof(cplx<T>) + 15) & ~size_t(15)) + (size_t)TW * SR * sizeof(cplx<T>);
     }
 };
 
-template <int R1, int R2>
-__global__ void __launch_bounds__(256, 2) k_fft_x_c2r_pipe(const cplx<float>* __restrict__ tw, const cplx<float>* __restrict__ S,
-                                                          float* __restrict__ out, int lines, int nxh) {
-    using T = float;
-    using Sh = PipeX<R1, R2>;
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(PipeX<T, R1, R2>::NT, 2) k_fft_x_c2r_pipe(const cplx<T>* __restrict__ tw,
+                                                                          const cplx<T>* __restrict__ S,
+                                                                          T* __restrict__ out, int lines, int nxh) {
+    using Sh = PipeX<T, R1, R2>;
     constexpr int L = Sh::L, TW = Sh::TW, RM = Sh::RM, SR = Sh::SR;
     extern __shared__ __align__(16) unsigned char fx_smem[];
-    const int rawc = (int)(((size_t)2 * TW * nxh * sizeof(cplx<T>) + 15) / 16) * 2;   // complex per buffer
+    const int rawc = (int)(((size_t)2 * TW * nxh * sizeof(cplx<T>) + 15) / 16) * Sh::EPC;   // complex per buffer
     cplx<T>* raw = reinterpret_cast<cplx<T>*>(fx_smem);           // [2][rawc]
     cplx<T>* ex = raw + 2 * rawc;                                 // [TW][SR]
     const long npairs = ((long)lines + 1) / 2;
     const long ntiles = (npairs + TW - 1) / TW;
     const long total = (long)lines * nxh;      // complex values in the half spectrum
-    const int nch = TW * nxh;                  // 16-byte chunks (two complex values) per tile
+    const int nch = (2 * TW * nxh + Sh::EPC - 1) / Sh::EPC;   // 16-byte chunks per tile
     auto sidx = [](int m) { return m + (m >> 4); };
     auto issue = [&](long tile, int b) {
         const long c0 = tile * 2 * TW * nxh;
         for (int ch = threadIdx.x; ch < nch; ch += Sh::NT) {
-            const long e = c0 + 2 * (long)ch;
+            const long e = c0 + (long)Sh::EPC * ch;
             const long left = total - e;
-            const int nb = left >= 2 ? 16 : (left > 0 ? 8 : 0);
-            fr_cp_async16(raw + b * rawc + 2 * ch, nb > 0 ? S + e : S, nb);
+            const int nb = left >= Sh::EPC ? 16 : (left > 0 ? (int)(left * sizeof(cplx<T>)) : 0);
+            fr_cp_async16(raw + b * rawc + Sh::EPC * ch, nb > 0 ? S + e : S, nb);
         }
         fr_cp_commit();
     };

@@ -240,25 +240,27 @@ int device_sm_count() {
 template <typename T, int R1, int R2>
 void launch_strided_reg(cudaStream_t st, const cplx<T>* tw, cplx<T>* S, long ncol, long cdiv, long outer,
                         long lstride, int mode, const T* scale) {
-    if constexpr (std::is_same<T, float>::value) {
-        // FP32 is bound by memory latency: persistent, double-buffered cp.async variant
-        using Ph = PipeShape<R1, R2>;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_fft_strided_pipe<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Ph::smem(true));
-            attr = true;
-        }
-        const long ntiles = (ncol + Ph::TW - 1) / Ph::TW;
-        const long cap = 2L * device_sm_count();
-        const unsigned blocks = (unsigned)(ntiles < cap ? ntiles : cap);
-        k_fft_strided_pipe<R1, R2><<<blocks, Ph::NT, Ph::smem(mode == 2), st>>>(tw, S, ncol, cdiv, outer, lstride, mode,
-                                                                              scale);
-    } else {
+    if constexpr (sizeof(T) == 8) {
+        // FP64 is bound by the FP64 pipe, not by latency: the one-tile-per-CTA kernel (the
+        // pipelined one measured 2 % slower here)
         using Sh = RegShape<T, R1, R2>;
         const unsigned blocks = (unsigned)((ncol + Sh::TW - 1) / Sh::TW);
         k_fft_strided_reg<T, R1, R2><<<blocks, Sh::NT, 0, st>>>(tw, S, ncol, cdiv, outer, lstride, mode, scale);
+        return;
     }
+    // FP32: persistent, double-buffered cp.async variant; the next tile's loads overlap the butterflies
+    using Ph = PipeShape<T, R1, R2>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_fft_strided_pipe<T, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Ph::smem(true));
+        attr = true;
+    }
+    const long ntiles = (ncol + Ph::TW - 1) / Ph::TW;
+    const long cap = 2L * device_sm_count();
+    const unsigned blocks = (unsigned)(ntiles < cap ? ntiles : cap);
+    k_fft_strided_pipe<T, R1, R2><<<blocks, Ph::NT, Ph::smem(mode == 2), st>>>(tw, S, ncol, cdiv, outer, lstride, mode,
+                                                                             scale);
 }
 
 template <typename T>
@@ -276,22 +278,21 @@ void strided_reg(int L, cudaStream_t st, const cplx<T>* tw, cplx<T>* S, long nco
 template <typename T, int R1, int R2>
 void launch_x_reg(bool forward, cudaStream_t st, const cplx<T>* tw, const T* in, cplx<T>* S, T* out, int lines,
                   int nxh) {
-    if constexpr (std::is_same<T, float>::value) {
-        // FP32 inverse: persistent double-buffered variant when the spectrum is 16-byte aligned
-        if (!forward && reinterpret_cast<uintptr_t>(S) % 16 == 0) {
-            using Px = PipeX<R1, R2>;
-            static bool attr = false;
-            if (!attr) {
-                cudaFuncSetAttribute(k_fft_x_c2r_pipe<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)Px::smem_c2r(Px::L / 2 + 1));
-                attr = true;
-            }
-            const long ntiles = (((long)lines + 1) / 2 + Px::TW - 1) / Px::TW;
-            const long cap = 2L * device_sm_count();
-            const unsigned blocks = (unsigned)(ntiles < cap ? ntiles : cap);
-            k_fft_x_c2r_pipe<R1, R2><<<blocks, Px::NT, Px::smem_c2r(nxh), st>>>(tw, S, out, lines, nxh);
-            return;
+    // FP32 inverse: persistent double-buffered variant when the spectrum is 16-byte aligned (FP64 is
+    // FP64-pipe bound and keeps the one-tile-per-CTA kernel)
+    if (sizeof(T) == 4 && !forward && reinterpret_cast<uintptr_t>(S) % 16 == 0) {
+        using Px = PipeX<T, R1, R2>;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_fft_x_c2r_pipe<T, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Px::smem_c2r(Px::L / 2 + 1));
+            attr = true;
         }
+        const long ntiles = (((long)lines + 1) / 2 + Px::TW - 1) / Px::TW;
+        const long cap = 2L * device_sm_count();
+        const unsigned blocks = (unsigned)(ntiles < cap ? ntiles : cap);
+        k_fft_x_c2r_pipe<T, R1, R2><<<blocks, Px::NT, Px::smem_c2r(nxh), st>>>(tw, S, out, lines, nxh);
+        return;
     }
     using Sh = RegShape<T, R1, R2>;
     const long pairs = (lines + 1) / 2;
