@@ -245,7 +245,7 @@ ins_status ins_cfl_dt_noalloc(const ins_grid_desc* desc, const void* u, double c
  * (a choice; the paper names none): 4 circular 3x3x3 convolutions 3->32->32->32->3,
  * GELU (erf form) after the first three; input channels u^x, u^y, u^z at one storage
  * index, output channel a added to F^a. BF16 weights and activations, FP32 accumulation
- * on the tensor cores (tcgen05); the weight gradient runs on CUDA cores (FP32).
+ * on the tensor cores (tcgen05) for the forward, the data gradient and the weight gradient.
  * Grids: 3-D, periodic, nx % 8 == 0, ny % 16 == 0, nz >= 2 (else INS_ERR_UNSUPPORTED). */
 typedef struct ins_closure ins_closure;
 

@@ -301,91 +301,232 @@ __global__ void k_pack_input(const T* __restrict__ u, long nvox, __nv_bfloat16* 
     }
 }
 
-// Weight and bias gradients on CUDA cores (FP32 accumulation):
-//   dW[t][ci][co] += sum_v X[v + o_t][ci] dY[v][co],  db[co] += sum_v dY[v][co] (tap 13 blocks only).
-// X, dY: BF16 channels-last with CX and CY channels (cin, cout real). Grid (27, nblk), 256 threads.
-// A block stages 128 voxels of the shifted X and of dY in shared memory (FP32); the threads
-// form groups of (CX/4)(CY/4), each thread accumulating a 4 x 4 tile of (ci, co) over the
-// voxels of its group (16 FMAs per two float4 shared loads). Partial sums go out with one
-// atomic per output per group.
+// ---------------------------------------------------------------------------------------
+// Weight and bias gradients on the tensor cores:
+//   dW[t][ci][co] = sum_v x[v + off_t][ci] gq[v][co],   db[co] = sum_v gq[v][co]
+// (gq = BF16 gradient of the layer's pre-activation, x = BF16 layer input, both channels-last).
+// GEMM with M = (tap, ci) (128 / CX taps per CTA), N = co, K = voxels. Channels-last rows hold
+// M (resp. N) contiguously for each voxel, so both operands are read MN-major: the canonical
+// no-swizzle MN-major layout has core matrices of 8 K-rows of 16 bytes (8 consecutive M or N
+// values); LBO = stride between core matrices along K, SBO = along M / N (checked on the
+// device against a host product). Per stage, 64 voxels of A (16 M-groups of 1 KB) and B are
+// staged with 16-byte cp.async gathers (tap shift with periodic wrap) into a 4-stage ring,
+// two stages ahead of the MMAs (a buffer is refilled once the MMAs that read it two stages
+// earlier have committed); one thread issues the 4 MMAs (K = 16 each) of a stage into the
+// TMEM accumulator. A CTA reduces
+// its voxel range and adds its 128 x N block to dW with atomics; CTAs of the first tap group
+// also sum gq for db. Zero-filled taps >= 27, voxels >= nvox and padding channels.
+constexpr int WG_S = 64;                   // voxels per stage
+constexpr int WG_NS = 4;                   // stages in the ring
+constexpr int WG_PD = 2;                   // stages loaded ahead of the MMAs
+constexpr int WG_THREADS = 256;
+
+template <int N>
+struct WgShape {
+    static constexpr int KGRP = WG_S / 8;                     // K groups (8 voxels) per stage
+    static constexpr int A_BYTES = 16 * KGRP * 128;          // 16 M-groups x KGRP x 128 B
+    static constexpr int B_BYTES = (N / 8) * KGRP * 128;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int SMEM = WG_NS * STAGE;
+};
+
 template <int CX, int CY>
-__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dY,
-                                               int nx, int ny, int nz, int cin, int cout, float* __restrict__ dW,
-                                               float* __restrict__ db) {
-    constexpr int V = 128;
-    constexpr int TPG = (CX / 4) * (CY / 4);     // threads per group
-    constexpr int NG = 256 / TPG;                // groups
-    constexpr int VG = V / NG;                   // voxels per group and chunk
-    __shared__ __align__(16) float xs[V][CX + 4];
-    __shared__ __align__(16) float ys[V][CY + 4];
-    const int t = blockIdx.x;
-    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+__global__ void __launch_bounds__(WG_THREADS) k_wgrad_tc(const __nv_bfloat16* __restrict__ X,
+                                                         const __nv_bfloat16* __restrict__ dY, int nx, int ny, int nz,
+                                                         int cin, int cout, long vchunk, float* __restrict__ dW,
+                                                         float* __restrict__ db, unsigned int* __restrict__ err) {
+    constexpr int N = CY < 16 ? 16 : CY;
+    constexpr int TAPS = 128 / CX;         // taps per CTA (M = TAPS * CX = 128)
+    constexpr int CGX = CX / 8;            // 16-byte channel groups per input voxel
+    constexpr int TPV = WG_THREADS / WG_S; // threads per staged voxel
+    using Sh = WgShape<N>;
+    constexpr int MSTR = Sh::KGRP * 128;   // byte stride between M (or N) groups
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[WG_NS];
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long nvox = (long)nx * ny * nz;
-    const int grp = threadIdx.x / TPG, q = threadIdx.x % TPG;
-    const int ciq = q / (CY / 4), coq = q % (CY / 4);
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    float bacc = 0.f;
-    for (long c0 = (long)blockIdx.y * V; c0 < nvox; c0 += (long)gridDim.y * V) {
-        for (int e = threadIdx.x; e < V * (CX / 8); e += 256) {
-            const int vv = e / (CX / 8), cg = e - vv * (CX / 8);
-            const long v = c0 + vv;
-            float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (v < nvox) {
-                int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long)nx * ny));
-                x += dx; y += dy; z += dz;
-                x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-                z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-                const uint4 raw = *reinterpret_cast<const uint4*>(X + (((long)z * ny + y) * nx + x) * CX + cg * 8);
-                const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&raw);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(h[k]);
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) xs[vv][cg * 8 + k] = f[k];
-        }
-        for (int e = threadIdx.x; e < V * (CY / 8); e += 256) {
-            const int vv = e / (CY / 8), cg = e - vv * (CY / 8);
-            const long v = c0 + vv;
-            float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (v < nvox) {
-                const uint4 raw = *reinterpret_cast<const uint4*>(dY + v * CY + cg * 8);
-                const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&raw);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(h[k]);
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) ys[vv][cg * 8 + k] = f[k];
-        }
-        __syncthreads();
-        for (int vv = grp * VG; vv < (grp + 1) * VG; ++vv) {
-            const float4 xv = *reinterpret_cast<const float4*>(&xs[vv][4 * ciq]);
-            const float4 yv = *reinterpret_cast<const float4*>(&ys[vv][4 * coq]);
-            const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], ya[b], acc[a][b]);
-        }
-        if (t == 13 && threadIdx.x < CY) {
-            float sacc = 0.f;
-            for (int vv = 0; vv < V; ++vv) sacc += ys[vv][threadIdx.x];
-            bacc += sacc;
-        }
-        __syncthreads();
+    const int tg = blockIdx.x;             // tap group
+    const long v0 = (long)blockIdx.y * vchunk;
+    const long v1 = v0 + vchunk < nvox ? v0 + vchunk : nvox;
+    const int nst = v1 > v0 ? (int)((v1 - v0 + WG_S - 1) / WG_S) : 0;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cv_smem(&tbase)), "r"(32));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    if (tid == 0)
+        for (int q = 0; q < WG_NS; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&mbar[q])));
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tbase;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+                           ((128u >> 4) << 24);
+    // staging: thread t handles voxel k = t % WG_S of the stage and every TPV-th M-group / N-group;
+    // its M-groups' tap offsets are fixed, the voxel coordinates are 32-bit (grids hold < 2^31 voxels)
+    const int kk = tid % WG_S, part = tid / WG_S;
+    constexpr int MPT = 16 / TPV;          // M-groups per thread
+    int tdx[MPT], tdy[MPT], tdz[MPT], tcg[MPT];
+    bool tok[MPT];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int j = 0; j < MPT; ++j) {
+        const int mg = part + TPV * j;
+        const int tl = mg / CGX;
+        const int t = tg * TAPS + tl;
+        tok[j] = t < 27;
+        tdz[j] = t / 9 - 1;
+        tdy[j] = (t / 3) % 3 - 1;
+        tdx[j] = t % 3 - 1;
+        tcg[j] = mg - tl * CGX;
+    }
+    const int nxy = nx * ny;
+    auto issue = [&](int st, int b) {
+        unsigned char* sa = smem + b * Sh::STAGE;
+        unsigned char* sbb = sa + Sh::A_BYTES;
+        const long vl = v0 + (long)st * WG_S + kk;
+        const bool okv = vl < v1;
+        const int v = okv ? (int)vl : 0;
+        const int z = v / nxy;
+        const int rxy = v - z * nxy;
+        const int y = rxy / nx;
+        const int x = rxy - y * nx;
+        const uint32_t kofs = (uint32_t)((kk >> 3) * 128 + (kk & 7) * 16);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int ci = 4 * ciq + a, co = 4 * coq + b;
-            if (ci < cin && co < cout) atomicAdd(&dW[((long)t * cin + ci) * cout + co], acc[a][b]);
+        for (int j = 0; j < MPT; ++j) {
+            const int mg = part + TPV * j;
+            const bool ok = okv && tok[j];
+            const unsigned char* src = reinterpret_cast<const unsigned char*>(X);
+            if (ok) {
+                int xs = x + tdx[j], ys = y + tdy[j], zs = z + tdz[j];
+                xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+                ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+                zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+                const int vs = zs * nxy + ys * nx + xs;
+                src += ((size_t)vs * CX + tcg[j] * 8) * 2;
+            }
+            const uint32_t dst = cv_smem(sa) + (uint32_t)mg * MSTR + kofs;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
         }
-    if (t == 13 && db && threadIdx.x < cout) atomicAdd(&db[threadIdx.x], bacc);
+        for (int ng = part; ng < N / 8; ng += TPV) {
+            const bool ok = okv && ng < CY / 8;
+            const unsigned char* src = reinterpret_cast<const unsigned char*>(dY);
+            if (ok) src += ((size_t)v * CY + ng * 8) * 2;
+            const uint32_t dst = cv_smem(sbb) + (uint32_t)ng * MSTR + kofs;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto wait_mbar = [&](int b, uint32_t parity) -> bool {
+        uint32_t done = 0;
+        for (long it = 0; it < CV_SPIN && !done; ++it) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(cv_smem(&mbar[b])), "r"(parity)
+                : "memory");
+        }
+        return done != 0;
+    };
+    uint32_t uses[WG_NS];                  // commits issued on each buffer's barrier
+#pragma unroll
+    for (int q = 0; q < WG_NS; ++q) uses[q] = 0u;
+    bool alive = true;
+    float bsum = 0.f;                      // db partial (first tap group; thread n < CY sums column n)
+    for (int q = 0; q < WG_PD; ++q) {      // prologue: stages 0 .. PD - 1, one commit group each
+        if (q < nst) issue(q, q);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int i = 0; i < nst && alive; ++i) {
+        const int b = i % WG_NS;
+        const int nxt = i + WG_PD;
+        if (nxt < nst) {
+            // buffer of stage i - 2: its MMAs were issued two iterations ago, its db sums are
+            // behind two barriers
+            const int nb = nxt % WG_NS;
+            if (uses[nb] > 0 && !wait_mbar(nb, (uses[nb] - 1) & 1)) {
+                if (tid == 0) atomicOr(err, 2u);
+                alive = false;
+            }
+            issue(nxt, nb);
+        } else {
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        asm volatile("cp.async.wait_group %0;" ::"n"(WG_PD) : "memory");   // stage i has landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (__syncthreads_or(!alive)) break;
+        const unsigned char* sa = smem + b * Sh::STAGE;
+        if (tg == 0 && tid < CY) {
+            const unsigned char* sbb = sa + Sh::A_BYTES;
+            const int ng = tid >> 3, w = tid & 7;
+            for (int k = 0; k < WG_S; ++k) {
+                const __nv_bfloat16 h =
+                    *reinterpret_cast<const __nv_bfloat16*>(sbb + ng * MSTR + (k >> 3) * 128 + (k & 7) * 16 + w * 2);
+                bsum += __bfloat162float(h);
+            }
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t abase = cv_smem(sa), bbase = abase + Sh::A_BYTES;
+#pragma unroll
+            for (int s2 = 0; s2 < WG_S / 16; ++s2) {
+                const uint64_t ad = cv_desc(abase + s2 * 256, 128, MSTR);
+                const uint64_t bd = cv_desc(bbase + s2 * 256, 128, MSTR);
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"((i > 0 || s2 > 0) ? 1 : 0));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             cv_smem(&mbar[b]))
+                         : "memory");
+        }
+        ++uses[b];
+    }
+    // the last stage's MMAs, then the accumulator block
+    if (alive && nst > 0) {
+        const int b = (nst - 1) % WG_NS;
+        if (!wait_mbar(b, (uses[b] - 1) & 1)) {
+            if (tid == 0) atomicOr(err, 2u);
+            alive = false;
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__syncthreads_or(!alive)) alive = false;
+    if (alive && nst > 0 && warp < 4) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        if (N == 32) {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+        } else {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int m = warp * 32 + lane;
+        const int tl = m / CX, ci = m - tl * CX;
+        const int t = tg * TAPS + tl;
+        if (t < 27 && ci < cin) {
+            for (int co = 0; co < cout; ++co) atomicAdd(&dW[((long)t * cin + ci) * cout + co], __uint_as_float(r[co]));
+        }
+    }
+    if (alive && tg == 0 && tid < cout && db) atomicAdd(&db[tid], bsum);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
 }
 
 }  // namespace ins

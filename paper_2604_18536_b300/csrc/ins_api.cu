@@ -1703,13 +1703,24 @@ ins_status conv_launch(ins_grid* g, ConvArgs a) {
 
 template <int CX, int CY>
 ins_status wgrad_launch(ins_grid* g, const __nv_bfloat16* X, const __nv_bfloat16* dY, int cin, int cout, float* dW,
-                        float* db) {
+                        float* db, unsigned int* err) {
     if (!dW) return INS_OK;
     const long nvox = g->N;
-    int nblk = (int)((nvox / 128 + 3) / 4);          // ~4 chunks of 128 voxels per block
-    nblk = nblk < 1 ? 1 : (nblk > 296 ? 296 : nblk);
-    KLAUNCH(g, "wgrad", k_wgrad<CX, CY><<<dim3(27, nblk), 256, 0, g->stream>>>(X, dY, g->nx, g->ny, g->nz, cin, cout,
-                                                                              dW, db));
+    // tensor cores: 128 / CX taps per CTA, the voxels split over about two CTAs per SM in all
+    constexpr int N = CY < 16 ? 16 : CY;
+    constexpr int ngroups = (27 + 128 / CX - 1) / (128 / CX);
+    static bool attr = false;
+    if (!attr) {
+        INS_CUDA(cudaFuncSetAttribute(k_wgrad_tc<CX, CY>, cudaFuncAttributeMaxDynamicSharedMemorySize, WgShape<N>::SMEM));
+        attr = true;
+    }
+    long nchunk = (2L * device_sm_count() + ngroups - 1) / ngroups;
+    const long stages = (nvox + WG_S - 1) / WG_S;
+    nchunk = nchunk > stages ? stages : (nchunk < 1 ? 1 : nchunk);
+    const long vchunk = ((stages + nchunk - 1) / nchunk) * WG_S;
+    nchunk = (nvox + vchunk - 1) / vchunk;
+    KLAUNCH(g, "wgrad", k_wgrad_tc<CX, CY><<<dim3(ngroups, (unsigned)nchunk), WG_THREADS, WgShape<N>::SMEM, g->stream>>>(
+                            X, dY, g->nx, g->ny, g->nz, cin, cout, vchunk, dW, db, err));
     return INS_OK;
 }
 
@@ -1748,7 +1759,7 @@ ins_status closure_backward(ins_grid* g, ins_closure* c, const T* mbar, T* ubar,
     const long nvox = g->N;
     KLAUNCH(g, "pack_input", k_pack_input<T><<<592, 256, 0, g->stream>>>(mbar, nvox, c->g4));
     ins_status s;
-    if ((s = wgrad_launch<32, 8>(g, c->x[3], c->g4, 32, 3, dW[3], db[3])) != INS_OK) return s;
+    if ((s = wgrad_launch<32, 8>(g, c->x[3], c->g4, 32, 3, dW[3], db[3], c->err)) != INS_OK) return s;
     ConvArgs a{};
     a.err = c->err;
     // layer 4 data gradient through GELU of layer 3
@@ -1760,7 +1771,7 @@ ins_status closure_backward(ins_grid* g, ins_closure* c, const T* mbar, T* ubar,
     __nv_bfloat16* gin = c->ga;
     __nv_bfloat16* gout = c->gb;
     for (int l = 2; l >= 1; --l) {
-        if ((s = wgrad_launch<32, 32>(g, c->x[l], gin, 32, 32, dW[l], db[l])) != INS_OK) return s;
+        if ((s = wgrad_launch<32, 32>(g, c->x[l], gin, 32, 32, dW[l], db[l], c->err)) != INS_OK) return s;
         a.x = gin;
         a.wblob = c->wt[l];
         a.y = gout;
@@ -1770,7 +1781,7 @@ ins_status closure_backward(ins_grid* g, ins_closure* c, const T* mbar, T* ubar,
         gin = gout;
         gout = t;
     }
-    if ((s = wgrad_launch<8, 32>(g, c->x[0], gin, 3, 32, dW[0], db[0])) != INS_OK) return s;
+    if ((s = wgrad_launch<8, 32>(g, c->x[0], gin, 3, 32, dW[0], db[0], c->err)) != INS_OK) return s;
     a.x = gin;
     a.wblob = c->wt[0];
     a.y = nullptr;

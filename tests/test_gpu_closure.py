@@ -116,3 +116,25 @@ def test_step_and_step_vjp_with_closure(dtype):
     for l in range(4):
         assert rel(dW[l].double().cpu().numpy(), wg[l][0]) <= 3e-2, l
     g.set_closure(None)
+
+
+@pytest.mark.parametrize("n", [(16, 16, 8), (24, 32, 6)])
+def test_last_layer_weight_gradient_tight(n):
+    """Tensor-core weight gradient of the output layer on the GPU's own BF16 operands: the saved
+    layer input x_3 and the BF16-rounded output cotangent. Only the FP32 summation order differs
+    from the FP64 oracle (conv_wgrad), so the relative error is at FP32 level; the bias gradient
+    is the sum of the rounded cotangent."""
+    g, og, c, W, b, params = make(n)
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal((3,) + og.shape)
+    mbar = rng.standard_normal((3,) + og.shape)
+    c.forward(torch.tensor(u, device="cuda"), save=True)
+    x3, _ = c.saved(3)
+    dW = [torch.zeros_like(w) for w in W]
+    db = [torch.zeros_like(bb) for bb in b]
+    c.backward(torch.tensor(mbar, device="cuda"), dW=dW, db=db)
+    c.check()
+    gq = oc.bf16(mbar)
+    ref = oc.conv_wgrad(to_cfirst(x3, 32, og), gq)
+    assert rel(dW[3].double().cpu().numpy(), ref) <= 1e-5
+    assert rel(db[3].double().cpu().numpy(), gq.reshape(3, -1).sum(axis=1)) <= 1e-5
