@@ -156,6 +156,32 @@ def step_model_bytes(n, s):
     return 114 * n ** 3 * s
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+# The path does not shard: N processes run independent replicas of the same
+# workload (seed + rank), synchronised by barriers around the timed region; the job time is
+# the slowest rank's and the throughput counts the cells of all ranks.
+def replica_barrier(world):
+    import torch.distributed as dist
+    if world > 1:
+        dist.barrier()
+
+
+def replica_max(x, world, device):
+    """max over ranks of a host float (a one-element tensor on `device` for the collective)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def replica_throughput(cells_per_rank, world, ms_max, steps):
+    """Whole-job cell-updates/s: the cells of all ranks over the slowest rank's step time."""
+    return cells_per_rank * world / (ms_max / steps / 1e3)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -173,15 +199,10 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replica_barrier(world)
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
+        return replica_max(x, world, "cuda")
 
     n = args.n
     N = n ** 3
@@ -247,7 +268,7 @@ def run_ours(args):
         kernels = {k: {"launches": v[0], "total_ms": round(v[1], 4), "share": round(v[1] / tot, 4),
                        "avg_us": round(v[1] / v[0] * 1e3, 2)} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
         step_s = ms_max / args.steps / 1e3
-        value = N * world / step_s
+        value = replica_throughput(N, world, ms_max, args.steps)
         res = {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roof, "kernels": kernels,
                "gpu_launches": launches, "clocks": clocks,
                "step_hbm_frac": step_model_bytes(n, s) / step_s / 1e9 / hbm_peak,
