@@ -13,11 +13,12 @@
 // weight block [N rows x K channels], K-major. D (128 lanes x N FP32 columns)
 // lives in TMEM; the epilogue reads it with tcgen05.ld (one voxel per thread).
 //
-// A CTA of 128 threads owns one 8 x 16 column of one z chunk. Planes go through
-// a 4-slot ring: while the MMAs of plane z read slots z-1, z, z+1, the loads of
-// plane z+2 are already in flight (cp.async). Thread 0 issues the MMAs and
-// commits them to an mbarrier; every wait is bounded and reports through an
-// error flag instead of hanging.
+// A CTA of 256 threads owns one 8 x 16 column of one z chunk. Two TMEM accumulators
+// alternate between tiles: while the epilogue reads tile z, the MMAs of tile z+1 run.
+// Planes go through a 5-slot ring: tile z+1 reads slots z..z+2 while plane z+3 is in
+// flight (cp.async). Thread 0 issues the MMAs and commits them to the accumulator's
+// mbarrier; every wait is bounded and reports through an error flag instead of hanging.
+// The epilogue splits a tile's channels over two warps per TMEM lane quarter.
 //
 // The same kernel runs the backward data gradient (a convolution with the taps
 // reversed and the channel roles swapped) with a different epilogue.
@@ -34,9 +35,9 @@ constexpr int CV_TX = 8, CV_TY = 16;           // output tile: 8 x 16 voxels = 1
 constexpr int CV_PX = CV_TX + 2, CV_PY = CV_TY + 2;
 constexpr int CV_ROW = CV_PX * 16;              // bytes per padded row of 16-byte entries
 constexpr int CV_PLANE = CV_PY * CV_ROW;        // bytes per staged plane of one channel group
-constexpr int CV_SLOTS = 4;
+constexpr int CV_SLOTS = 5;
 constexpr int CV_CGS = CV_SLOTS * CV_PLANE;     // bytes per channel group (all slots)
-constexpr int CV_THREADS = 128;
+constexpr int CV_THREADS = 256;
 constexpr long CV_SPIN = 1L << 24;              // bound on every mbarrier wait
 
 enum ConvEpi {
@@ -108,10 +109,12 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
     constexpr int KSTEPS = KG / 2;                   // MMAs (K = 16) per tap
     constexpr int TAPB = N * KG * 16;                // weight bytes per tap
     constexpr int SBO_B = KG * 128;
+    constexpr int NH = N / 2;                        // channels per epilogue warp
+    constexpr uint32_t TCOLS = 2 * N < 32 ? 32 : 2 * N;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                        // CG * CV_CGS bytes
     unsigned char* sB = smem + CG * CV_CGS;          // 27 * TAPB bytes
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -127,16 +130,17 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cv_smem(&tbase)),
-                     "r"(N < 32 ? 32 : N));
+                     "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&mbar)));
-    // prologue planes zb-1, zb, zb+1 into slots of (z mod 4)
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&mbar[1])));
+    }
     auto slot_of = [](int z) { return ((z % CV_SLOTS) + CV_SLOTS) % CV_SLOTS; };
     auto wrapz = [nz](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
-    cv_load_plane<CG>(a, sA, slot_of(zb - 1), wrapz(zb - 1), x0, y0);
-    cv_load_plane<CG>(a, sA, slot_of(zb), wrapz(zb), x0, y0);
-    cv_load_plane<CG>(a, sA, slot_of(zb + 1), wrapz(zb + 1), x0, y0);
+    // prologue planes zb-1 .. zb+2
+    for (int z = zb - 1; z <= zb + 2; ++z) cv_load_plane<CG>(a, sA, slot_of(z), wrapz(z), x0, y0);
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -144,48 +148,63 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tbase;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
-    uint32_t phase = 0;
+    // MMAs of tile z into accumulator acc (thread 0), committed to mbar[acc]
+    auto issue_tile = [&](int z, int acc) {
+        int first = 1;
+        const uint32_t dcol = tmem + (uint32_t)(acc * N);
+        for (int t = 0; t < 27; ++t) {
+            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+            const uint32_t abase = cv_smem(sA) + slot_of(z + dz) * CV_PLANE + (1 + dy) * CV_ROW + (1 + dx) * 16;
+            const uint32_t bbase = cv_smem(sB) + t * TAPB;
+#pragma unroll
+            for (int s = 0; s < KSTEPS; ++s) {
+                const uint64_t ad = cv_desc(abase + 2 * s * CV_CGS, CG == 1 ? 0 : CV_CGS, CV_ROW);
+                const uint64_t bd = cv_desc(bbase + 2 * s * 128, 128, SBO_B);
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0 : 1));
+                first = 0;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         cv_smem(&mbar[acc]))
+                     : "memory");
+    };
+    if (tid == 0 && zb < ze) issue_tile(zb, 0);
+    uint32_t phase[2] = {0u, 0u};
     bool alive = true;
-    // this thread's output voxel within the tile (D row = TMEM lane)
-    const int m = warp * 32 + lane;
+    // epilogue ownership: warp w reads TMEM lanes 32 (w % 4) .. +31 (voxel rows) and channels
+    // (w / 4) NH .. +NH of the tile
+    const int q4 = warp & 3, half = warp >> 2;
+    const int m = q4 * 32 + lane;
     const int vx = x0 + (m & 7), vy = y0 + (m >> 3);
     const bool inside = vx < nx && vy < ny;
+    const int c0 = half * NH;
 
     for (int z = zb; z < ze && alive; ++z) {
-        // prefetch plane z+2 (needed by the next tile) into the free slot
-        const bool pre = z + 1 < ze;
-        if (pre) cv_load_plane<CG>(a, sA, slot_of(z + 2), wrapz(z + 2), x0, y0);
-        if (tid == 0) {
-            int first = 1;
-            for (int t = 0; t < 27; ++t) {
-                const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-                const uint32_t abase = cv_smem(sA) + slot_of(z + dz) * CV_PLANE + (1 + dy) * CV_ROW + (1 + dx) * 16;
-                const uint32_t bbase = cv_smem(sB) + t * TAPB;
-#pragma unroll
-                for (int s = 0; s < KSTEPS; ++s) {
-                    const uint64_t ad = cv_desc(abase + 2 * s * CV_CGS, CG == 1 ? 0 : CV_CGS, CV_ROW);
-                    const uint64_t bd = cv_desc(bbase + 2 * s * 128, 128, SBO_B);
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0 : 1));
-                    first = 0;
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             cv_smem(&mbar))
-                         : "memory");
-        }
-        // wait for the MMAs of this tile (bounded)
+        const int b = (z - zb) & 1;
+        const bool more = z + 1 < ze;
+        // plane z+3 (tile z+2) into the slot of plane z-2, whose last reader (tile z-1) has finished
+        if (more) cv_load_plane<CG>(a, sA, slot_of(z + 3), wrapz(z + 3), x0, y0);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        // plane z+2 has landed; the epilogue of tile z-1 is done with accumulator b^1
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0 && more) issue_tile(z + 1, b ^ 1);
+        // wait for the MMAs of tile z (bounded)
         uint32_t done = 0;
         for (long it = 0; it < CV_SPIN && !done; ++it) {
             asm volatile(
                 "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                 : "=r"(done)
-                : "r"(cv_smem(&mbar)), "r"(phase)
+                : "r"(cv_smem(&mbar[b])), "r"(phase[b])
                 : "memory");
         }
-        phase ^= 1;
+        phase[b] ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!done) {
             if (tid == 0) atomicOr(a.err, 2u);
@@ -195,21 +214,11 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
             alive = false;
             break;
         }
-        // epilogue: D row m -> voxel (vx, vy, z)
-        uint32_t r[32];
+        // epilogue: D row m -> voxel (vx, vy, z), channels c0 .. c0 + NH
+        uint32_t r[NH];
         {
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-            if (N == 32) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr));
-            } else {
+            const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * N + c0);
+            if constexpr (NH == 16) {
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                     "[%16];"
@@ -217,33 +226,39 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                       "=r"(r[15])
                     : "r"(taddr));
+            } else {
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(taddr));
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         }
         if (inside) {
             const long v = ((long)z * ny + vy) * nx + vx;
             if (EPI == EPI_GELU) {
-                __align__(16) __nv_bfloat16 o[N];
+                __align__(16) __nv_bfloat16 o[NH];
 #pragma unroll
-                for (int c = 0; c < N; ++c) {
-                    const float zz = __uint_as_float(r[c]) + (a.bias ? a.bias[c] : 0.f);
-                    if (a.zout) a.zout[v * N + c] = zz;
+                for (int c = 0; c < NH; ++c) {
+                    const float zz = __uint_as_float(r[c]) + (a.bias ? a.bias[c0 + c] : 0.f);
+                    if (a.zout) a.zout[v * N + c0 + c] = zz;
                     o[c] = __float2bfloat16_rn(cv_gelu(zz));
                 }
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N);
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N + c0);
 #pragma unroll
-                for (int q = 0; q < N / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
+                for (int q = 0; q < NH / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
             } else if (EPI == EPI_DGELU) {
-                __align__(16) __nv_bfloat16 o[N];
+                __align__(16) __nv_bfloat16 o[NH];
 #pragma unroll
-                for (int c = 0; c < N; ++c)
-                    o[c] = __float2bfloat16_rn(__uint_as_float(r[c]) * cv_gelu_grad(a.zin[v * N + c]));
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N);
+                for (int c = 0; c < NH; ++c)
+                    o[c] = __float2bfloat16_rn(__uint_as_float(r[c]) * cv_gelu_grad(a.zin[v * N + c0 + c]));
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N + c0);
 #pragma unroll
-                for (int q = 0; q < N / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
+                for (int q = 0; q < NH / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
             } else {
-                for (int c = 0; c < a.nreal; ++c) {
-                    float val = __uint_as_float(r[c]);
+                const int cend = a.nreal < c0 + NH ? a.nreal : c0 + NH;
+                for (int c = c0; c < cend; ++c) {
+                    float val = __uint_as_float(r[c - c0]);
                     if (EPI == EPI_OUT && a.bias) val += a.bias[c];
                     if (a.out_f64) {
                         double* o = reinterpret_cast<double*>(a.out) + c * nvox + v;
@@ -255,18 +270,11 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
                 }
             }
         }
-        // all TMEM reads of this tile are done before the next tile's MMAs overwrite D;
-        // the prefetched plane must have landed before the next tile reads it
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(N < 32 ? 32 : N));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // Pack weights W[27][cin][cout] (FP32 master copy) into the B layout of k_conv3d_tc as BF16.
