@@ -193,7 +193,20 @@ struct Nb {
     T Z0, Z0e, Z0w, Z0n, Z0s;             // u^z, plane o
     T Xp, Xpw, Yp, Yps, Zp;               // plane p
     T Xm, Ym, Zm, Zme, Zmn;               // plane m
+    // z-face products shared by consecutive planes: the lower-face product of plane k is the
+    // upper-face product of plane k-1 (same operands, so carrying it changes no bit)
+    T cx, cy, cz;                         // F^x: w-interp * (u^x+u^x)_z, F^y: likewise, F^z: (u^z+u^z)^2
 };
+
+// carried products for the first plane of a march (from the m and o values)
+template <typename T, bool WALL>
+__device__ __forceinline__ void nb_carry_init(Nb<T>& v, const YRow<T>& y) {
+    v.cx = (v.Zm + v.Zme) * (v.Xm + v.X0);
+    const T wm = WALL ? fma(y.wl, v.Zm, y.wr * v.Zmn) : v.Zm + v.Zmn;
+    v.cy = wm * (v.Ym + v.Y0);
+    const T s2 = v.Zm + v.Z0;
+    v.cz = s2 * s2;
+}
 
 // o-plane values not carried over from the previous iteration's p plane
 template <typename T>
@@ -238,7 +251,7 @@ __device__ __forceinline__ void nb_rotate(Nb<T>& v) {
 
 // Same arithmetic as eval_Fx / eval_Fy / eval_Fz (DIM = 3) on register values.
 template <typename T, bool WALL>
-__device__ __forceinline__ T nb_Fx(const RhsCoef<T>& c, const YRow<T>& y, const Nb<T>& v) {
+__device__ __forceinline__ T nb_Fx(const RhsCoef<T>& c, const YRow<T>& y, Nb<T>& v) {
     const T uc = v.X0, ue = v.X0e, uw = v.X0w, un = v.X0n, us = v.X0s;
     const T s1 = uc + ue, s2 = uw + uc;
     const T X = fma(s1, s1, -s2 * s2);
@@ -249,8 +262,9 @@ __device__ __forceinline__ T nb_Fx(const RhsCoef<T>& c, const YRow<T>& y, const 
     acc = fma(y.bm, us, acc);
     T dsum = (T)2 * c.dx + y.bp + y.bm;
     const T ut = v.Xp, ub = v.Xm;
-    const T wp = v.Z0 + v.Z0e, wm = v.Zm + v.Zme;
-    const T Z = fma(wp, uc + ut, -wm * (ub + uc));
+    const T wp = v.Z0 + v.Z0e, sup = uc + ut;
+    const T Z = fma(wp, sup, -v.cx);
+    v.cx = wp * sup;
     acc = fma(c.dz, ut + ub, acc);
     dsum += (T)2 * c.dz;
     acc = fma(-c.cz, Z, acc);
@@ -260,24 +274,22 @@ __device__ __forceinline__ T nb_Fx(const RhsCoef<T>& c, const YRow<T>& y, const 
 }
 
 template <typename T, bool WALL>
-__device__ __forceinline__ T nb_Fy(const RhsCoef<T>& c, const YRow<T>& y, const Nb<T>& v) {
+__device__ __forceinline__ T nb_Fy(const RhsCoef<T>& c, const YRow<T>& y, Nb<T>& v) {
     const T uc = v.Y0, un = v.Y0n, us = v.Y0s, ue = v.Y0e, uw = v.Y0w;
     const T s1 = uc + un, s2 = us + uc;
     const T Ys = fma(s1, s1, -s2 * s2);
-    T vp, vm, cxf, wp, wm, czf;
+    T vp, vm, cxf, wp, czf;
     if constexpr (WALL) {
         vp = fma(y.wl, v.X0, y.wr * v.X0n);
         vm = fma(y.wl, v.X0w, y.wr * v.X0wn);
         cxf = (T)2 * c.cx;
         wp = fma(y.wl, v.Z0, y.wr * v.Z0n);
-        wm = fma(y.wl, v.Zm, y.wr * v.Zmn);
         czf = (T)2 * c.cz;
     } else {
         vp = v.X0 + v.X0n;
         vm = v.X0w + v.X0wn;
         cxf = c.cx;
         wp = v.Z0 + v.Z0n;
-        wm = v.Zm + v.Zmn;
         czf = c.cz;
     }
     const T X = fma(vp, uc + ue, -vm * (uw + uc));
@@ -286,7 +298,9 @@ __device__ __forceinline__ T nb_Fy(const RhsCoef<T>& c, const YRow<T>& y, const 
     acc = fma(y.am, us, acc);
     T dsum = (T)2 * c.dx + y.ap + y.am;
     const T ut = v.Yp, ub = v.Ym;
-    const T Z = fma(wp, uc + ut, -wm * (ub + uc));
+    const T sup = uc + ut;
+    const T Z = fma(wp, sup, -v.cy);
+    v.cy = wp * sup;
     acc = fma(c.dz, ut + ub, acc);
     dsum += (T)2 * c.dz;
     acc = fma(-czf, Z, acc);
@@ -296,10 +310,11 @@ __device__ __forceinline__ T nb_Fy(const RhsCoef<T>& c, const YRow<T>& y, const 
 }
 
 template <typename T, bool WALL>
-__device__ __forceinline__ T nb_Fz(const RhsCoef<T>& c, const YRow<T>& y, const Nb<T>& v) {
+__device__ __forceinline__ T nb_Fz(const RhsCoef<T>& c, const YRow<T>& y, Nb<T>& v) {
     const T uc = v.Z0, ut = v.Zp, ub = v.Zm, ue = v.Z0e, uw = v.Z0w, un = v.Z0n, us = v.Z0s;
-    const T s1 = uc + ut, s2 = ub + uc;
-    const T Zs = fma(s1, s1, -s2 * s2);
+    const T s1 = uc + ut;
+    const T Zs = fma(s1, s1, -v.cz);
+    v.cz = s1 * s1;
     const T vp = v.X0 + v.Xp, vm = v.X0w + v.Xpw;
     const T X = fma(vp, uc + ue, -vm * (uw + uc));
     const T wp = v.Y0 + v.Yp, wm = v.Y0s + v.Yps;
@@ -495,6 +510,7 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
             nb.Y0s = o[1][c0 - RSX];
             nb.Z0 = o[2][c0];
         }
+        nb_carry_init<T, WALL>(nb, yr);
         for (int k = kb; k < ke; ++k) {
             const bool more = k + 1 < ke;
             if (more) plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(k + 2) * iplane, v);
@@ -789,6 +805,7 @@ __global__ void __launch_bounds__(RNT, WALL ? 2 : 3) k_update_rhs_div(RhsCoef<T>
         nb.Y0s = o[1][c0 - RSX];
         nb.Z0 = o[2][c0];
     }
+    nb_carry_init<T, WALL>(nb, yr);
     for (int k = kb; k < ke; ++k) {
         const bool more = k + 1 < ke;
         if (more) stage_load(k + 2);
