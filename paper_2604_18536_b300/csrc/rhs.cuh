@@ -582,7 +582,11 @@ namespace ins {
 // The evaluation of F_{s+1} and r = D F_{s+1} on the staged ring is that of k_rhs_div.
 // Reads F_s, p_s, u_0, acc and writes acc, F_{s+1}, r: 17 values per cell instead of the
 // 23 of a separate update (16) and evaluation (7).
-constexpr int FH = RSPL - RNT;   // halo cells of a plane: 129
+// The halo cells are staged by the upper four warps, so that the halo evaluations of warps 0
+// and 1 do not fall on the same warps as a second staged cell; the three corner cells of
+// column 0 that no stencil reads ((0, 0), (0, 1) and (0, RSY - 1) of the plane) are left out,
+// which leaves 126 halo cells.
+constexpr int FH = 126;          // halo cells of a plane that are staged
 
 struct FusedMap {
     int off[2];       // in-plane offset of the source cell (mirror cell for a wall ghost)
@@ -601,20 +605,21 @@ __device__ __forceinline__ FusedMap fused_map(int nx, int ny, int i0, int j0) {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         int li, lj;
+        const int h = t - RNT / 2;        // halo index of thread t >= 128
         if (e == 0) {
             li = threadIdx.x + 2;
             lj = threadIdx.y + 2;
-        } else if (t < 105) {             // rows 0, 1 and RSY - 1, all RSX columns
-            const int r = t / RSX;
+        } else if (h >= 0 && h < 102) {   // rows 0, 1 and RSY - 1, columns 1 .. RSX - 1
+            const int r = h / (RSX - 1);
             lj = r == 2 ? RSY - 1 : r;
-            li = t - r * RSX;
+            li = 1 + h - r * (RSX - 1);
         } else {                          // columns 0, 1 and RSX - 1 of rows 2 .. RSY - 2
-            const int h = t - 105;
-            lj = 2 + h / 3;
-            const int cc = h % 3;
+            const int hh = h < 0 ? 0 : h - 102;
+            lj = 2 + hh / 3;
+            const int cc = hh % 3;
             li = cc == 2 ? RSX - 1 : cc;
         }
-        fm.has[e] = e == 0 || t < FH;
+        fm.has[e] = e == 0 || (h >= 0 && h < FH);
         fm.sidx[e] = lj * RSX + li;
         int gi = (i0 - 2 + li) % nx;
         if (gi < 0) gi += nx;
