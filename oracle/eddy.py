@@ -26,17 +26,24 @@ Readings taken where the paper is silent or its printed formula conflicts with i
 * Vreman: as printed, nu_t = C^2 sqrt(B_beta / (tr(A A^T) / 2)) with
   beta_ij = sum_m D_m^2 A_im A_jm (D_m the cell widths); 0 where A = 0.
 * QR: nu_t = -(C D)^2 |R_S| / Q_S, 0 where Q_S = 0.
-* Scope: periodic directions (the LES of decaying turbulence the learned closure is
-  compared on). Filter width D = (d_x d_y d_z)^(1/3) per cell (d_x d_y in 2-D: D = sqrt).
+* Walls (y): the velocity ghosts of ``operators`` (odd tangential, zero wall-normal); nu_t takes
+  the even ghost (the mirrored cell's value) where an edge average reaches across a wall. The
+  stored top wall face of u^y is not an unknown (no term there).
+* Filter width D = (d_x d_y d_z)^(1/3) per cell (d_x d_y in 2-D: D = sqrt).
 
 Parity: pinned by tests/test_oracle_eddy.py (a constant eddy viscosity reduces the
-operator to nu (diffusion + G D), closed forms of every model on pure shear, solid
-rotation, axisymmetric and two-component strain, and the dissipation identity).
+operator to nu (diffusion + G D) on periodic and channel grids, closed forms of every model
+on pure shear, solid rotation, axisymmetric and two-component strain, the dissipation
+identity, second-order convergence of the interpolated gradient, and on a channel the
+closed-form flux difference of a wall shear flow with a row-dependent nu_t (the wall rules
+of the velocity and of nu_t)).
 """
 
 import numpy as np
 
 from .grid import PERIODIC
+from . import operators as op
+from .operators import NORMAL, TANGENT, EVEN
 
 SMAGORINSKY = "smagorinsky"
 WALE = "wale"
@@ -54,26 +61,36 @@ DEFAULT_C = {
 
 def _check(g):
     for a in range(g.dim):
-        assert g.bc[a] == PERIODIC, "eddy-viscosity models are implemented for periodic directions"
+        assert g.bc[a] == PERIODIC or a == 1, "walls are supported in y only"
 
 
-def _sh(g, f, a, s):
-    """f at I + s e_a (periodic)."""
-    return np.roll(f, -s, axis=g.axis(a))
+def _sh(g, f, a, s, kind=TANGENT):
+    """f at I + s e_a with the boundary rule of ``operators.shift`` (kind at a wall)."""
+    return op.shift(g, f, a, s, kind)
 
 
 def _along(g, v, a):
     return g.along(v, a)
 
 
+def _h_prev(g, a):
+    return op.h_prev(g, a)
+
+
 def diag_strain(g, u, a):
-    """S_aa = A_aa at the cell centres."""
-    return (u[a] - _sh(g, u[a], a, -1)) / _along(g, g.d[a], a)
+    """S_aa = A_aa at the cell centres (u^a below a bottom wall is the wall value 0)."""
+    return (u[a] - _sh(g, u[a], a, -1, NORMAL)) / _along(g, g.d[a], a)
 
 
 def edge_grad(g, u, a, b):
-    """E_ab(I) = delta_b u^a on the (a, b) edge of cell I: (u^a_{I+e_b} - u^a_I) / h_b."""
-    return (_sh(g, u[a], b, +1) - u[a]) / _along(g, g.h[b], b)
+    """E_ab(I) = delta_b u^a on the (a, b) edge of cell I: (u^a_{I+e_b} - u^a_I) / h_b
+    (odd ghost of a tangential velocity above a top wall)."""
+    return (_sh(g, u[a], b, +1, TANGENT) - u[a]) / _along(g, g.h[b], b)
+
+
+def edge_grad_lower(g, u, a, b):
+    """E_ab(I - e_b): (u^a_I - u^a_{I-e_b}) / h_b[i-1] (odd ghost below a bottom wall)."""
+    return (u[a] - _sh(g, u[a], b, -1, TANGENT)) / _along(g, _h_prev(g, b), b)
 
 
 def gradient_at_centres(g, u):
@@ -85,9 +102,11 @@ def gradient_at_centres(g, u):
         for b in range(g.dim):
             if b == a:
                 continue
-            E = edge_grad(g, u, a, b)
-            Ea = _sh(g, E, a, -1)
-            A[a, b] = 0.25 * (E + Ea + _sh(g, E, b, -1) + _sh(g, Ea, b, -1))
+            E = edge_grad(g, u, a, b)               # edge (I; a, b)
+            El = edge_grad_lower(g, u, a, b)        # edge (I - e_b)
+            # edges (I - e_a) and (I - e_a - e_b): shift along a; below a wall in a the
+            # edge of u^a's lower neighbour carries the wall velocity 0 (NORMAL rule)
+            A[a, b] = 0.25 * (E + El + _sh(g, E, a, -1, NORMAL) + _sh(g, El, a, -1, NORMAL))
     return A
 
 
@@ -149,19 +168,29 @@ def eddy_viscosity(g, u, model, C=None):
 
 
 def stress_divergence(g, u, nu_t):
-    """e^a = sum_b delta_b (2 nu_t S_ab) on the a-faces, for a given nu_t at the cells."""
+    """e^a = sum_b delta_b (2 nu_t S_ab) on the a-faces, for a given nu_t at the cells.
+
+    Across a wall nu_t takes the even ghost (the mirrored cell's value); the strain on a wall
+    edge uses the odd ghost of the tangential velocity and the zero wall-normal velocity."""
     _check(g)
     e = g.zeros_u()
+
+    def nsh(f, b, s):
+        return op.shift(g, f, b, s, EVEN)
+
     for a in range(g.dim):
         Taa = 2.0 * nu_t * diag_strain(g, u, a)
-        e[a] += (_sh(g, Taa, a, +1) - Taa) / _along(g, g.h[a], a)
+        e[a] += (nsh(Taa, a, +1) - Taa) / _along(g, g.h[a], a)
         for b in range(g.dim):
             if b == a:
                 continue
-            nu_e = 0.25 * (nu_t + _sh(g, nu_t, a, +1) + _sh(g, nu_t, b, +1) + _sh(g, _sh(g, nu_t, a, +1), b, +1))
-            Sab = 0.5 * (edge_grad(g, u, a, b) + edge_grad(g, u, b, a))
-            Tab = 2.0 * nu_e * Sab
-            e[a] += (Tab - _sh(g, Tab, b, -1)) / _along(g, g.d[b], b)
+            nu_up = 0.25 * (nu_t + nsh(nu_t, a, +1) + nsh(nu_t, b, +1) + nsh(nsh(nu_t, a, +1), b, +1))
+            nu_lo = 0.25 * (nsh(nu_t, b, -1) + nsh(nsh(nu_t, a, +1), b, -1) + nu_t + nsh(nu_t, a, +1))
+            S_up = 0.5 * (edge_grad(g, u, a, b) + edge_grad(g, u, b, a))
+            # lower edge (I - e_b): E_ab from the odd ghost, E_ba at I - e_b (zero below a wall in b)
+            S_lo = 0.5 * (edge_grad_lower(g, u, a, b) + _sh(g, edge_grad(g, u, b, a), b, -1, NORMAL))
+            e[a] += (2.0 * nu_up * S_up - 2.0 * nu_lo * S_lo) / _along(g, g.d[b], b)
+        e[a] *= g.face_mask(a)
     return e
 
 

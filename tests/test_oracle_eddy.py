@@ -139,3 +139,43 @@ def test_closure_enters_rhs():
     F1 = op.rhs_F(g, u, eddy.closure(g, eddy.SMAGORINSKY))
     np.testing.assert_allclose(F1 - F0, eddy.closure_term(g, u, eddy.SMAGORINSKY), rtol=0, atol=1e-13)
     assert float(np.sum(u * (F1 - F0))) < 0.0
+
+
+def test_wall_constant_viscosity_identity():
+    """On a tanh channel the constant-viscosity identity holds with the wall rules too."""
+    from test_oracle_operators import channel_grid
+    g = channel_grid(6, 7, 5)
+    u = random_u(g, 3)
+    c = 0.37
+    e = eddy.stress_divergence(g, u, c * np.ones(g.shape))
+    ref = c * (op.diffusion(g, u) + op.gradient(g, op.divergence(g, u)))
+    np.testing.assert_allclose(e, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_wall_shear_with_row_viscosity_closed_form():
+    """u^x = U(y), nu_t = f(y): e^x is the 1-D flux difference
+    [nu_{j+1/2} (U_{j+1} - U_j) / h_j - nu_{j-1/2} (U_j - U_{j-1}) / h_{j-1}] / d_j with
+    nu_{j+1/2} = (f_j + f_{j+1}) / 2, the odd velocity ghost at the walls (U_{-1} = -U_0,
+    U_ny = -U_{ny-1}, h_{-1} = d_0, h_{ny-1} = d_{ny-1}) and the even viscosity ghost
+    (f_{-1} = f_0, f_ny = f_{ny-1}); e^y = e^z = 0."""
+    from test_oracle_operators import channel_grid
+    g = channel_grid(4, 9, 3)
+    ny = g.n[1]
+    rng = np.random.default_rng(7)
+    U = rng.standard_normal(ny)
+    f = 0.1 + rng.random(ny)
+    u = g.zeros_u()
+    u[0] = U.reshape(1, ny, 1) * np.ones(g.shape)
+    nu = f.reshape(1, ny, 1) * np.ones(g.shape)
+    e = eddy.stress_divergence(g, u, nu)
+    d, h = g.d[1], g.h[1]
+    want = np.zeros(ny)
+    for j in range(ny):
+        Up = U[j + 1] if j + 1 < ny else -U[j]
+        Um = U[j - 1] if j > 0 else -U[j]
+        fp = 0.5 * (f[j] + (f[j + 1] if j + 1 < ny else f[j]))
+        fm = 0.5 * (f[j] + (f[j - 1] if j > 0 else f[j]))
+        hm = h[j - 1] if j > 0 else d[0]
+        want[j] = (fp * (Up - U[j]) / h[j] - fm * (U[j] - Um) / hm) / d[j]
+    np.testing.assert_allclose(e[0][0, :, 0], want, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(e[1:], 0.0, atol=1e-13)
