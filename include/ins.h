@@ -291,7 +291,9 @@ ins_status ins_set_closure(ins_grid* g, ins_closure* c);
  * S_aa sits at the cell centres, S_ab (a != b) on the cell edges; nu_t is evaluated at the
  * cell centres from the velocity gradient A (off-diagonal entries: mean of the four edge
  * differences around the cell) and averaged from the four neighbouring cells onto an edge.
- * Filter width D = (d_x d_y d_z)^(1/3). Models (S = sym A):
+ * Filter width D = (d_x d_y d_z)^(1/3), per row on a stretched wall-normal axis. Across a
+ * wall in y the velocity takes the forward operator's ghosts (odd tangential, zero
+ * wall-normal) and nu_t the even ghost (the mirrored cell's value). Models (S = sym A):
  *   INS_EDDY_SMAGORINSKY  nu_t = (C D)^2 sqrt(2 S:S)                    (paper: C = 0.1)
  *   INS_EDDY_WALE         (C D)^2 (Sd:Sd)^(3/2) / ((S:S)^(5/2) + (Sd:Sd)^(5/4)),
  *                         Sd = sym(A A) - tr(A A)/3 I                    (C = 0.5)
@@ -310,10 +312,11 @@ typedef enum {
     INS_EDDY_CONSTANT = 5
 } ins_eddy_model;
 
-/* Attach model with constant C (INS_EDDY_NONE detaches). 3-D periodic grids with n >= 2
- * (INS_ERR_UNSUPPORTED otherwise, and while a CNN closure is attached). The first
- * attachment allocates four scalar fields (nu_t and the term). ins_step_vjp returns
- * INS_ERR_UNSUPPORTED while a model is attached. */
+/* Attach model with constant C (INS_EDDY_NONE detaches). 3-D grids (periodic, or walls in y)
+ * with n >= 2 (INS_ERR_UNSUPPORTED otherwise, and while a CNN closure is attached). The first
+ * attachment allocates four scalar fields (nu_t and the term) and, on a wall grid, four rows
+ * of ny coefficients, uploaded by a blocking copy (a set-up call: not while g's stream is
+ * being captured). ins_step_vjp returns INS_ERR_UNSUPPORTED while a model is attached. */
 ins_status ins_set_eddy_viscosity(ins_grid* g, int model, double C);
 
 /* nu_t of the attached model at every cell centre: u DEVICE, dim fields; nut DEVICE, one

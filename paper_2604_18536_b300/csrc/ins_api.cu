@@ -133,6 +133,7 @@ struct ins_grid {
     int eddy = 0;             // EddyKind
     double eddy_C = 0.0;
     void* eddy_buf = nullptr; // nu_t (N) | term (3N)
+    void* eddy_rows = nullptr; // wall y: 1/d_y | 1/h_y | (C D_j)^2 | d_y^2 (ny each, field type)
     // step-VJP workspace (stage states u_2..u_4, the projected cotangent, nu partials),
     // allocated by the first ins_step_vjp call
     void* vjp = nullptr;
@@ -1332,6 +1333,7 @@ ins_status ins_grid_destroy(ins_grid* g) {
     if (g->vjp) cudaFree(g->vjp);
     if (g->mbuf) cudaFree(g->mbuf);
     if (g->eddy_buf) cudaFree(g->eddy_buf);
+    if (g->eddy_rows) cudaFree(g->eddy_rows);
     cudaError_t e = cudaFree(g->base);
     delete g;
     if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
@@ -1820,21 +1822,54 @@ EddyCoef<T> eddy_coef(const ins_grid* g) {
     const double D = std::cbrt(vol);
     c.CD2 = (T)((g->eddy_C * D) * (g->eddy_C * D));
     c.C2 = (T)(g->eddy == EDDY_CONSTANT ? g->eddy_C : g->eddy_C * g->eddy_C);
+    const T* rows = reinterpret_cast<const T*>(g->eddy_rows);
+    c.idy = rows;
+    c.ihy = rows ? rows + g->ny : nullptr;
+    c.cd2y = rows ? rows + 2 * g->ny : nullptr;
+    c.w2y = rows ? rows + 3 * g->ny : nullptr;
     return c;
+}
+
+// The per-row wall-normal coefficients of the attached model, in the field type.
+template <typename T>
+cudaError_t eddy_upload_rows(ins_grid* g) {
+    const int ny = g->ny;
+    std::vector<T> v(4 * (size_t)ny);
+    for (int j = 0; j < ny; ++j) {
+        const double dy = g->d[1][j];
+        const double D = std::cbrt(g->d[0][0] * dy * g->d[2][0]);
+        v[j] = (T)(1.0 / dy);
+        v[ny + j] = (T)(1.0 / g->h[1][j]);
+        v[2 * ny + j] = (T)((g->eddy_C * D) * (g->eddy_C * D));
+        v[3 * ny + j] = (T)(dy * dy);
+    }
+    return cudaMemcpy(g->eddy_rows, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename T, bool WALL>
+ins_status eddy_nut_launch(ins_grid* g, const T* u, T* nut) {
+    const EddyCoef<T> c = eddy_coef<T>(g);
+    const dim3 grd = eddy_grid(g), blk(32, 8);
+    switch (g->eddy) {
+        case EDDY_SMAGORINSKY:
+            KLAUNCH(g, "eddy_nut", (k_eddy_nut<T, EDDY_SMAGORINSKY, WALL><<<grd, blk, 0, g->stream>>>(c, u, nut)));
+            break;
+        case EDDY_WALE: KLAUNCH(g, "eddy_nut", (k_eddy_nut<T, EDDY_WALE, WALL><<<grd, blk, 0, g->stream>>>(c, u, nut))); break;
+        case EDDY_QR: KLAUNCH(g, "eddy_nut", (k_eddy_nut<T, EDDY_QR, WALL><<<grd, blk, 0, g->stream>>>(c, u, nut))); break;
+        case EDDY_VREMAN:
+            KLAUNCH(g, "eddy_nut", (k_eddy_nut<T, EDDY_VREMAN, WALL><<<grd, blk, 0, g->stream>>>(c, u, nut)));
+            break;
+        default:
+            KLAUNCH(g, "eddy_nut", (k_eddy_nut<T, EDDY_CONSTANT, WALL><<<grd, blk, 0, g->stream>>>(c, u, nut)));
+            break;
+    }
+    return INS_OK;
 }
 
 template <typename T>
 ins_status eddy_nut(ins_grid* g, const T* u, T* nut) {
-    const EddyCoef<T> c = eddy_coef<T>(g);
-    const dim3 grd = eddy_grid(g), blk(32, 8);
-    switch (g->eddy) {
-        case EDDY_SMAGORINSKY: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_SMAGORINSKY><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
-        case EDDY_WALE: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_WALE><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
-        case EDDY_QR: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_QR><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
-        case EDDY_VREMAN: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_VREMAN><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
-        default: KLAUNCH(g, "eddy_nut", k_eddy_nut<T, EDDY_CONSTANT><<<grd, blk, 0, g->stream>>>(c, u, nut)); break;
-    }
-    return INS_OK;
+    if (g->wall_y) return eddy_nut_launch<T, true>(g, u, nut);
+    return eddy_nut_launch<T, false>(g, u, nut);
 }
 
 template <typename T>
@@ -1845,7 +1880,12 @@ ins_status closure_term(ins_grid* g, const T* u, T** m, bool save) {
         T* term = nut + g->N;
         ins_status s = eddy_nut<T>(g, u, nut);
         if (s != INS_OK) return s;
-        KLAUNCH(g, "eddy_div", k_eddy_div<T><<<eddy_grid(g), dim3(32, 8), 0, g->stream>>>(eddy_coef<T>(g), u, nut, term));
+        if (g->wall_y)
+            KLAUNCH(g, "eddy_div",
+                    (k_eddy_div<T, true><<<eddy_grid(g), dim3(32, 8), 0, g->stream>>>(eddy_coef<T>(g), u, nut, term)));
+        else
+            KLAUNCH(g, "eddy_div",
+                    (k_eddy_div<T, false><<<eddy_grid(g), dim3(32, 8), 0, g->stream>>>(eddy_coef<T>(g), u, nut, term)));
         *m = term;
         return INS_OK;
     }
@@ -2043,7 +2083,7 @@ ins_status ins_set_eddy_viscosity(ins_grid* g, int model, double C) {
         return INS_OK;
     }
     if (!(std::isfinite(C) && C >= 0.0)) return fail(INS_ERR_ARG, "C must be finite and >= 0");
-    if (g->dim != 3 || g->wall_y) return fail(INS_ERR_UNSUPPORTED, "eddy-viscosity models: 3-D periodic grids only");
+    if (g->dim != 3) return fail(INS_ERR_UNSUPPORTED, "eddy-viscosity models: 3-D grids only");
     if (g->nx < 2 || g->ny < 2 || g->nz < 2) return fail(INS_ERR_UNSUPPORTED, "eddy-viscosity models need n >= 2");
     if (g->closure) return fail(INS_ERR_UNSUPPORTED, "a CNN closure is attached (one closure at a time)");
     if (!g->eddy_buf) {
@@ -2054,6 +2094,19 @@ ins_status ins_set_eddy_viscosity(ins_grid* g, int model, double C) {
             g->eddy_buf = nullptr;
             return fail(INS_ERR_OOM, "eddy-viscosity buffers");
         }
+    }
+    if (g->wall_y) {
+        if (!g->eddy_rows) {
+            cudaError_t e = cudaMalloc(&g->eddy_rows, (size_t)4 * g->ny * (g->dtype == INS_F64 ? 8 : 4));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                g->eddy_rows = nullptr;
+                return fail(INS_ERR_OOM, "eddy-viscosity row coefficients");
+            }
+        }
+        g->eddy_C = C;
+        cudaError_t e = g->dtype == INS_F64 ? eddy_upload_rows<double>(g) : eddy_upload_rows<float>(g);
+        if (e != cudaSuccess) return fail(INS_ERR_CUDA, cudaGetErrorString(e));
     }
     g->eddy = model;
     g->eddy_C = C;

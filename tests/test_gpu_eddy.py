@@ -2,8 +2,9 @@
 
 nu_t fields, the right-hand side and one RK4 step with the model in F, element by element on
 seeded fields: FP64 relative L2 error <= 1e-12, FP32 (oracle on the FP32-rounded input)
-<= 2e-5 for F and the step, 1e-5 for nu_t. The grid spans several 32 x 8 tiles with ragged
-tails and unequal spacings.
+<= 2e-5 for F and the step, 1e-5 for nu_t. The grids span several 32 x 8 tiles with ragged
+tails and unequal spacings: a triply periodic box and a channel (walls in y, tanh-stretched
+rows, the wall ghost rules of the velocity and of nu_t).
 """
 
 import numpy as np
@@ -24,15 +25,24 @@ TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
 NUT_TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
 
 
-def grids(dtype, nu=0.01):
-    faces = [U(40, 0, 2 * np.pi), U(24, 0, 1.5 * np.pi), U(12, 0, 1.0)]
-    og = OGrid(faces, ["periodic"] * 3, nu)
-    gg = Grid(faces, ["periodic"] * 3, nu, dtype=dtype)
+KINDS = ["periodic", "channel"]
+
+
+def grids(dtype, nu=0.01, kind="periodic"):
+    if kind == "channel":
+        faces, bc, force = inputs.channel_faces(36, 20, 28), ["periodic", "wall", "periodic"], [1.0, 0.0, 0.0]
+    else:
+        faces, bc, force = [U(40, 0, 2 * np.pi), U(24, 0, 1.5 * np.pi), U(12, 0, 1.0)], ["periodic"] * 3, None
+    og = OGrid(faces, bc, nu, force)
+    gg = Grid(faces, bc, nu, force, dtype=dtype)
     return og, gg
 
 
 def field(og, seed, dtype):
-    u, _ = poisson.project(og, inputs.random_field((3,) + og.shape, seed))
+    u = inputs.random_field((3,) + og.shape, seed)
+    for a in range(3):
+        u[a] *= og.face_mask(a)
+    u, _ = poisson.project(og, u)
     return rounded(u, dtype)
 
 
@@ -40,10 +50,11 @@ def oc(model):
     return Grid.EDDY_DEFAULT_C.get(model, 0.02)
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("model", MODELS)
-def test_eddy_viscosity_field(model, dtype):
-    og, gg = grids(dtype)
+def test_eddy_viscosity_field(model, dtype, kind):
+    og, gg = grids(dtype, kind=kind)
     u = field(og, 31, dtype)
     gg.set_eddy_viscosity(model, oc(model))
     nu = host(gg.eddy_viscosity(dev(u, dtype)))
@@ -51,10 +62,11 @@ def test_eddy_viscosity_field(model, dtype):
     assert rel(nu, ref) <= NUT_TOL[dtype], rel(nu, ref)
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("model", MODELS)
-def test_rhs_with_eddy_model(model, dtype):
-    og, gg = grids(dtype)
+def test_rhs_with_eddy_model(model, dtype, kind):
+    og, gg = grids(dtype, kind=kind)
     u = field(og, 32, dtype)
     gg.set_eddy_viscosity(model, oc(model))
     dudt = gg.rhs(dev(u, dtype))
@@ -62,10 +74,11 @@ def test_rhs_with_eddy_model(model, dtype):
     assert rel(host(dudt), ref) <= TOL[dtype], rel(host(dudt), ref)
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("model", ["smagorinsky", "wale"])
-def test_step_with_eddy_model(model, dtype):
-    og, gg = grids(dtype)
+def test_step_with_eddy_model(model, dtype, kind):
+    og, gg = grids(dtype, kind=kind)
     u = field(og, 33, dtype)
     dt = 0.5 * timestep.cfl_dt(og, u, 0.3)
     gg.set_eddy_viscosity(model, oc(model))
@@ -92,9 +105,9 @@ def test_eddy_model_rules():
     g2 = Grid(og.faces, ["periodic"] * 3, og.nu, dtype=torch.float64)
     g2.step(c, dt=1e-3)
     assert torch.equal(b, c) and not torch.equal(a, b)
-    wall = Grid(inputs.channel_faces(8, 8, 8), ["periodic", "wall", "periodic"], 0.01, dtype=torch.float64)
+    flat = Grid([U(8, 0, 1.0), U(8, 0, 1.0)], ["periodic"] * 2, 0.01, dtype=torch.float64)
     with pytest.raises(InsError):
-        wall.set_eddy_viscosity("wale")
+        flat.set_eddy_viscosity("wale")           # 3-D grids only
 
 
 def test_eddy_models_dissipate_energy():
