@@ -147,7 +147,7 @@ def kernel_model(name, n, s, fused=False):
 
 # DRAM bytes per launch of the dominant kernels from ncu captures of the current kernels
 # (profiles/rhs_div_hit256.md, profiles/update_rhs_div_hit256_f32.md); n = 256 only.
-TRAFFIC = {("f64", "rhs_div"): 910.02e6, ("f32", "update_rhs_div"): 1069.0e6}
+TRAFFIC = {("f64", "rhs_div"): 907.1e6, ("f32", "update_rhs_div"): 1071.0e6}
 
 
 def step_model_bytes(n, s):

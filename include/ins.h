@@ -150,8 +150,16 @@ ins_status ins_set_wall_solver(ins_grid* g, int solver);
  * of stage s and the evaluation of F and D F of stage s + 1 as one kernel, so the stage
  * state is never stored (the workspace holds one extra scalar field for it); results equal
  * the unfused path's up to the order of FP32 roundings in F. enable = 0 selects the unfused
- * kernels (for comparison), 1 (default) the fused ones. Other grids ignore the setting. */
+ * kernels (for comparison), 1 the fused kernels with one cell per thread, 2 (default) the
+ * fused kernels with two neighbouring x cells per thread (8-byte accesses; same arithmetic
+ * per cell as 1). Other values: INS_ERR_ARG. Other grids ignore the setting. */
 ins_status ins_set_step_fusion(ins_grid* g, int enable);
+
+/* Launch shape of the fused two-cells-per-thread kernels (fusion level 2; no counterpart in
+ * the paper): each CTA marches `planes` consecutive z planes of its 64 x 8 column. 0 (default)
+ * chooses the chunk from the grid and the number of SMs; results do not depend on it.
+ * INS_ERR_ARG for planes < 0. */
+ins_status ins_set_march_chunk(ins_grid* g, int planes);
 
 /* Vector-Jacobian product of one ins_step (Sec. 3.4, pullback of a composition;
  * App. B operator pullbacks; the Poisson solve is self-adjoint, Sec. 2.6.1).

@@ -62,6 +62,7 @@ SIGNATURES = {
     "ins_project": (_c.c_int, [_vp, _vp, _vp, _vp]),
     "ins_divergence": (_c.c_int, [_vp, _vp, _vp]),
     "ins_set_step_fusion": (_c.c_int, [_vp, _c.c_int]),
+    "ins_set_march_chunk": (_c.c_int, [_vp, _c.c_int]),
     "ins_set_wall_solver": (_c.c_int, [_vp, _c.c_int]),
     "ins_set_eddy_viscosity": (_c.c_int, [_vp, _c.c_int, _c.c_double]),
     "ins_eddy_viscosity": (_c.c_int, [_vp, _vp, _vp]),

@@ -27,6 +27,7 @@
 #include "filter_spectrum.cuh"
 #include "conv_tc.cuh"
 #include "eddy.cuh"
+#include "rhs_x2.cuh"
 
 using namespace ins;
 
@@ -86,7 +87,9 @@ struct DevBuf {
 
 struct ins_grid {
     int dim = 0, nx = 1, ny = 1, nz = 1, wall_y = 0, dtype = 0, scheme = INS_RK4;
-    bool fused_step = true;   // FP32 3-D RK4: fused stage boundaries (ins_set_step_fusion)
+    int march_chunk = 0;      // planes per CTA of the pair kernels (0: chosen from the wave count)
+    int fusion = 2;           // FP32 3-D RK4 stage boundaries (ins_set_step_fusion): 0 separate
+                              // kernels, 1 fused, 2 fused with two cells per thread
     double nu = 0.0, force[3] = {0, 0, 0};
     cudaStream_t stream = nullptr;
     long N = 0;             // cells
@@ -437,6 +440,31 @@ ins_status launch_rhs_div(ins_grid* g, const T* u, T* F, T* r, const T* m = null
 
 dim3 cell_grid(const ins_grid* g) { return dim3((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz); }
 
+// z chunk of the pair kernels: the CTAs of a launch run in waves of 2 per SM (their launch
+// bounds); a CTA costs about its planes plus two for its prologue (five staged planes without
+// an evaluation). Take the chunk that minimises waves x cost per CTA (the last wave counts as a
+// full one), or the caller's (ins_set_march_chunk).
+int device_sm_count();
+dim3 pair_grid(const ins_grid* g) {
+    const int nbx = (g->nx + 2 * RBX - 1) / (2 * RBX), nby = (g->ny + RBY - 1) / RBY;
+    int kc = g->march_chunk;
+    if (kc <= 0) {
+        const long resident = 2L * device_sm_count();
+        long best = -1;
+        for (int c = 8; c <= 128; ++c) {
+            const long ctas = (long)nbx * nby * ((g->nz + c - 1) / c);
+            const long cost = (ctas + resident - 1) / resident * (std::min(c, g->nz) + 2);
+            if (best < 0 || cost < best) {
+                best = cost;
+                kc = c;
+            }
+            if (c >= g->nz) break;
+        }
+    }
+    kc = std::min(kc, g->nz);
+    return dim3(nbx, nby, (g->nz + kc - 1) / kc);
+}
+
 // The vector RK update needs whole 16-byte vectors per row and an aligned caller field.
 template <typename T>
 bool rk_vec_ok(const ins_grid* g, const void* u) {
@@ -538,22 +566,50 @@ struct Impl {
         T* pp = reinterpret_cast<T*>(g->pbuf);
         T* acc = reinterpret_cast<T*>(g->acc);
         ins_status s;
-        if ((s = launch_rhs_div<T, DIM, WALL>(g, u, Fb[0], rr)) != INS_OK) return s;
-        if ((s = poisson<T>(g, rr, pp)) != INS_OK) return s;
         const RhsCoef<T> rc = make_rhs_coef<T>(g);
         const T* ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
         const T ihx = (T)(1.0 / g->h[0][0]), ihz = (T)(1.0 / g->h[2][0]);
         const dim3 blk(RBX, RBY, 1);
         const dim3 grd((g->nx + RBX - 1) / RBX, (g->ny + RBY - 1) / RBY, (g->nz + g->kchunk - 1) / g->kchunk);
+        // two cells per thread: the caller's field is 16-byte aligned and nx a multiple of 4 (rk_vec_ok)
+        const bool pair = g->fusion == 2 && 3 * g->N < (1L << 31);
+        const dim3 grd2 = pair_grid(g);
+        const int kc2 = (g->nz + grd2.z - 1) / grd2.z;
+        if (pair) {
+            static bool attr = false;
+            if (!attr) {
+                INS_CUDA(cudaFuncSetAttribute(k_rhs_div_x2<WALL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              PairRegSmem::BYTES));
+                INS_CUDA(cudaFuncSetAttribute(k_rhs_div_x2<WALL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              PairRegSmem::BYTES));
+                attr = true;
+            }
+        }
+        FusedArgs fa;
+        fa.dt_dev = dt_dev;
+        fa.dt_host = dt_host;
+        fa.a_next = 0.0;
+        fa.b = 0.0;
+        fa.stage = 0;
+        static_assert(std::is_same<T, float>::value && DIM == 3, "FP32 3-D only");
+        if (pair)
+            KLAUNCH(g, "rhs_div", (k_rhs_div_x2<WALL, false><<<grd2, blk, PairRegSmem::BYTES, g->stream>>>(
+                                      rc, ihx, ihz, ihy, nullptr, nullptr, u, nullptr, Fb[0], rr, fa, kc2)));
+        else if ((s = launch_rhs_div<T, DIM, WALL>(g, u, Fb[0], rr)) != INS_OK)
+            return s;
+        if ((s = poisson<T>(g, rr, pp)) != INS_OK) return s;
         for (int st = 0; st < 3; ++st) {
-            FusedArgs fa;
-            fa.dt_dev = dt_dev;
-            fa.dt_host = dt_host;
             fa.a_next = A[st];
             fa.b = B[st];
             fa.stage = st;
-            KLAUNCH(g, "update_rhs_div", k_update_rhs_div<T, WALL><<<grd, blk, 0, g->stream>>>(
-                                             rc, ihx, ihz, ihy, Fb[st & 1], pp, u, acc, Fb[(st + 1) & 1], rr, fa, g->kchunk));
+            if (pair)
+                KLAUNCH(g, "update_rhs_div", (k_rhs_div_x2<WALL, true><<<grd2, blk, PairRegSmem::BYTES, g->stream>>>(
+                                                 rc, ihx, ihz, ihy, Fb[st & 1], pp, u, acc, Fb[(st + 1) & 1], rr, fa,
+                                                 kc2)));
+            else
+                KLAUNCH(g, "update_rhs_div", k_update_rhs_div<T, WALL><<<grd, blk, 0, g->stream>>>(
+                                                 rc, ihx, ihz, ihy, Fb[st & 1], pp, u, acc, Fb[(st + 1) & 1], rr, fa,
+                                                 g->kchunk));
             if ((s = poisson<T>(g, rr, pp)) != INS_OK) return s;
         }
         RkArgs ra;
@@ -575,7 +631,7 @@ struct Impl {
     static ins_status step(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
         if (g->scheme == INS_WRAY3) return step_wray3(g, u, dt_dev, dt_host, next_dt, cfl);
         if constexpr (DIM == 3 && std::is_same<T, float>::value) {
-            if (g->pbuf && !g->closure && !g->eddy && g->fused_step && rk_vec_ok<T>(g, u))
+            if (g->pbuf && !g->closure && !g->eddy && g->fusion > 0 && rk_vec_ok<T>(g, u))
                 return step_fused(g, u, dt_dev, dt_host, next_dt, cfl);
         }
         static const double A[4] = {0.5, 0.5, 1.0, 0.0};
@@ -1418,7 +1474,16 @@ ins_status ins_set_wall_solver(ins_grid* g, int solver) {
 ins_status ins_set_step_fusion(ins_grid* g, int enable) {
     g_err.clear();
     if (!g) return fail(INS_ERR_ARG, "ins_set_step_fusion: null grid");
-    g->fused_step = enable != 0;
+    if (enable < 0 || enable > 2) return fail(INS_ERR_ARG, "ins_set_step_fusion: level must be 0, 1 or 2");
+    g->fusion = enable;
+    return INS_OK;
+}
+
+ins_status ins_set_march_chunk(ins_grid* g, int planes) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "ins_set_march_chunk: null grid");
+    if (planes < 0) return fail(INS_ERR_ARG, "ins_set_march_chunk: planes must be >= 0");
+    g->march_chunk = planes;
     return INS_OK;
 }
 

@@ -92,14 +92,15 @@ using Plane = T (*)[RSPL];
 template <typename T>
 using CPlane = const T (*)[RSPL];
 
-template <typename T, int DIM, bool WALL>
-__device__ __forceinline__ T eval_Fx(const RhsCoef<T>& c, const YRow<T>& y, CPlane<T> m, CPlane<T> o, CPlane<T> p,
-                                     int c0) {
-    const T uc = o[0][c0], ue = o[0][c0 + 1], uw = o[0][c0 - 1], un = o[0][c0 + RSX], us = o[0][c0 - RSX];
+// Plane arguments: PL indexes [component][row * SX + column] (the ring planes of k_rhs_div by
+// default; other kernels pass their own row stride and plane type).
+template <typename T, int DIM, bool WALL, int SX = RSX, typename PL = CPlane<T>>
+__device__ __forceinline__ T eval_Fx(const RhsCoef<T>& c, const YRow<T>& y, PL m, PL o, PL p, int c0) {
+    const T uc = o[0][c0], ue = o[0][c0 + 1], uw = o[0][c0 - 1], un = o[0][c0 + SX], us = o[0][c0 - SX];
     const T s1 = uc + ue, s2 = uw + uc;
     const T X = fma(s1, s1, -s2 * s2);
     // u^y interpolated along x (uniform): weights folded into y.f
-    const T vp = o[1][c0] + o[1][c0 + 1], vm = o[1][c0 - RSX] + o[1][c0 + 1 - RSX];
+    const T vp = o[1][c0] + o[1][c0 + 1], vm = o[1][c0 - SX] + o[1][c0 + 1 - SX];
     const T Y = fma(vp, uc + un, -vm * (us + uc));
     T acc = fma(c.dx, ue + uw, c.fx);
     acc = fma(y.bp, un, acc);
@@ -118,20 +119,19 @@ __device__ __forceinline__ T eval_Fx(const RhsCoef<T>& c, const YRow<T>& y, CPla
     return fma(-y.f, Y, acc);
 }
 
-template <typename T, int DIM, bool WALL>
-__device__ __forceinline__ T eval_Fy(const RhsCoef<T>& c, const YRow<T>& y, CPlane<T> m, CPlane<T> o, CPlane<T> p,
-                                     int c0) {
-    const T uc = o[1][c0], un = o[1][c0 + RSX], us = o[1][c0 - RSX], ue = o[1][c0 + 1], uw = o[1][c0 - 1];
+template <typename T, int DIM, bool WALL, int SX = RSX, typename PL = CPlane<T>>
+__device__ __forceinline__ T eval_Fy(const RhsCoef<T>& c, const YRow<T>& y, PL m, PL o, PL p, int c0) {
+    const T uc = o[1][c0], un = o[1][c0 + SX], us = o[1][c0 - SX], ue = o[1][c0 + 1], uw = o[1][c0 - 1];
     const T s1 = uc + un, s2 = us + uc;
     const T Ys = fma(s1, s1, -s2 * s2);
     T vp, vm, cxf;
     if constexpr (WALL) {   // u^x interpolated along the stretched y with volume weights
-        vp = fma(y.wl, o[0][c0], y.wr * o[0][c0 + RSX]);
-        vm = fma(y.wl, o[0][c0 - 1], y.wr * o[0][c0 - 1 + RSX]);
+        vp = fma(y.wl, o[0][c0], y.wr * o[0][c0 + SX]);
+        vm = fma(y.wl, o[0][c0 - 1], y.wr * o[0][c0 - 1 + SX]);
         cxf = (T)2 * c.cx;
     } else {
-        vp = o[0][c0] + o[0][c0 + RSX];
-        vm = o[0][c0 - 1] + o[0][c0 - 1 + RSX];
+        vp = o[0][c0] + o[0][c0 + SX];
+        vm = o[0][c0 - 1] + o[0][c0 - 1 + SX];
         cxf = c.cx;
     }
     const T X = fma(vp, uc + ue, -vm * (uw + uc));
@@ -143,12 +143,12 @@ __device__ __forceinline__ T eval_Fy(const RhsCoef<T>& c, const YRow<T>& y, CPla
         const T ut = p[1][c0], ub = m[1][c0];
         T wp, wm, czf;
         if constexpr (WALL) {
-            wp = fma(y.wl, o[2][c0], y.wr * o[2][c0 + RSX]);
-            wm = fma(y.wl, m[2][c0], y.wr * m[2][c0 + RSX]);
+            wp = fma(y.wl, o[2][c0], y.wr * o[2][c0 + SX]);
+            wm = fma(y.wl, m[2][c0], y.wr * m[2][c0 + SX]);
             czf = (T)2 * c.cz;
         } else {
-            wp = o[2][c0] + o[2][c0 + RSX];
-            wm = m[2][c0] + m[2][c0 + RSX];
+            wp = o[2][c0] + o[2][c0 + SX];
+            wm = m[2][c0] + m[2][c0 + SX];
             czf = c.cz;
         }
         const T Z = fma(wp, uc + ut, -wm * (ub + uc));
@@ -161,16 +161,15 @@ __device__ __forceinline__ T eval_Fy(const RhsCoef<T>& c, const YRow<T>& y, CPla
     return fma(-cxf, X, acc);
 }
 
-template <typename T, bool WALL>
-__device__ __forceinline__ T eval_Fz(const RhsCoef<T>& c, const YRow<T>& y, CPlane<T> m, CPlane<T> o, CPlane<T> p,
-                                     int c0) {
-    const T uc = o[2][c0], ut = p[2][c0], ub = m[2][c0], ue = o[2][c0 + 1], uw = o[2][c0 - 1], un = o[2][c0 + RSX],
-            us = o[2][c0 - RSX];
+template <typename T, bool WALL, int SX = RSX, typename PL = CPlane<T>>
+__device__ __forceinline__ T eval_Fz(const RhsCoef<T>& c, const YRow<T>& y, PL m, PL o, PL p, int c0) {
+    const T uc = o[2][c0], ut = p[2][c0], ub = m[2][c0], ue = o[2][c0 + 1], uw = o[2][c0 - 1], un = o[2][c0 + SX],
+            us = o[2][c0 - SX];
     const T s1 = uc + ut, s2 = ub + uc;
     const T Zs = fma(s1, s1, -s2 * s2);
     const T vp = o[0][c0] + p[0][c0], vm = o[0][c0 - 1] + p[0][c0 - 1];
     const T X = fma(vp, uc + ue, -vm * (uw + uc));
-    const T wp = o[1][c0] + p[1][c0], wm = o[1][c0 - RSX] + p[1][c0 - RSX];
+    const T wp = o[1][c0] + p[1][c0], wm = o[1][c0 - SX] + p[1][c0 - SX];
     const T Y = fma(wp, uc + un, -wm * (us + uc));
     T acc = fma(c.dx, ue + uw, c.fz);
     acc = fma(c.dz, ut + ub, acc);

@@ -155,9 +155,15 @@ class Grid:
         code = {"thomas": 0, "dct": 1}[solver]
         check(lib().ins_set_wall_solver(self._h, code), "ins_set_wall_solver")
 
+    def set_march_chunk(self, planes):
+        """z planes per CTA of the fused pair kernels (ins_set_march_chunk; 0 = automatic)."""
+        check(lib().ins_set_march_chunk(self._h, int(planes)), "ins_set_march_chunk")
+
     def set_step_fusion(self, enable):
-        """FP32 3-D RK4: fused (default) or separate stage-boundary kernels (ins_set_step_fusion)."""
-        check(lib().ins_set_step_fusion(self._h, 1 if enable else 0), "ins_set_step_fusion")
+        """FP32 3-D RK4 stage boundaries (ins_set_step_fusion): False/0 separate kernels, 1 fused
+        with one cell per thread, True/2 (default) fused with two cells per thread."""
+        level = (2 if enable else 0) if isinstance(enable, bool) else int(enable)
+        check(lib().ins_set_step_fusion(self._h, level), "ins_set_step_fusion")
 
     def workspace_bytes(self):
         b = ctypes.c_size_t()

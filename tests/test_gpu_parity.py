@@ -256,8 +256,9 @@ def test_fp32_unfused_step_parity(name):
     assert rel(host(ut), timestep.rk4_step(og, u0, dt)) <= TOL[torch.float32]
 
 
+@pytest.mark.parametrize("level", [1, 2])
 @pytest.mark.parametrize("name", ["p3reg2", "c3"])
-def test_fp32_fused_matches_unfused(name):
+def test_fp32_fused_matches_unfused(name, level):
     """Fused and unfused stage boundaries differ only by FP32 rounding order (10 steps)."""
     og, gg = grids(name, torch.float32)
     u0 = rounded(rand_u(og, 21, project=True), torch.float32)
@@ -265,11 +266,35 @@ def test_fp32_fused_matches_unfused(name):
     a = dev(u0, torch.float32)
     b = dev(u0, torch.float32)
     for _ in range(10):
-        gg.set_step_fusion(True)
+        gg.set_step_fusion(level)
         gg.step(a, dt=dt)
         gg.set_step_fusion(False)
         gg.step(b, dt=dt)
     assert rel(host(a), host(b)) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["p3", "p3reg", "p3reg2", "c3", "c3reg", "cu3"])
+def test_fp32_pair_and_single_cell_fusion_agree(name):
+    """Two cells per thread (level 2) and one cell per thread (level 1) run the same arithmetic
+    per cell: one step agrees bit for bit, and both match the oracle."""
+    og, gg = grids(name, torch.float32)
+    u0 = rounded(rand_u(og, 22, project=True), torch.float32)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    out = {}
+    for level in (1, 2):
+        gg.set_step_fusion(level)
+        ut = dev(u0, torch.float32)
+        gg.step(ut, dt=dt)
+        out[level] = ut
+    assert torch.equal(out[1], out[2])
+    assert rel(host(out[2]), timestep.rk4_step(og, u0, dt)) <= TOL[torch.float32]
+
+
+def test_fusion_level_is_checked():
+    from paper_2604_18536_b300._lib import InsError
+    _, gg = grids("p3", torch.float32)
+    with pytest.raises(InsError):
+        gg.set_step_fusion(3)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -288,3 +313,22 @@ def test_dct_and_thomas_wall_solves_agree(name, dtype):
     assert rel(host(a), host(b)) <= (1e-13 if dtype == torch.float64 else 1e-6)
     with pytest.raises(InsError):
         grids("c3", dtype)[1].set_wall_solver("dct")     # stretched y: no DCT
+
+
+@pytest.mark.parametrize("name", ["p3", "c3"])
+def test_march_chunk_is_launch_shape_only(name):
+    """The z chunk of the pair kernels (ins_set_march_chunk) changes no bit of the step, including
+    chunks that split z raggedly and chunks longer than nz; negative chunks are rejected."""
+    from paper_2604_18536_b300._lib import InsError
+    og, gg = grids(name, torch.float32)
+    u0 = rounded(rand_u(og, 23, project=True), torch.float32)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    out = []
+    for kc in (0, 1, 5, 64):
+        gg.set_march_chunk(kc)
+        ut = dev(u0, torch.float32)
+        gg.step(ut, dt=dt)
+        out.append(ut)
+    assert all(torch.equal(out[0], o) for o in out[1:])
+    with pytest.raises(InsError):
+        gg.set_march_chunk(-1)
