@@ -430,21 +430,11 @@ ins_status closure_term(ins_grid* g, const T* u, T** m, bool save);
 template <typename T>
 ins_status closure_pullback(ins_grid* g, const T* w, T* ubar);
 
-template <typename T, int DIM, bool WALL>
-ins_status launch_rhs_div(ins_grid* g, const T* u, T* F, T* r, const T* m = nullptr) {
-    dim3 blk(RBX, RBY, 1);
-    dim3 grd((g->nx + RBX - 1) / RBX, (g->ny + RBY - 1) / RBY, DIM == 3 ? (g->nz + g->kchunk - 1) / g->kchunk : 1);
-    KLAUNCH(g, "rhs_div", k_rhs_div<T, DIM, WALL><<<grd, blk, 0, g->stream>>>(make_rhs_coef<T>(g), u, F, r, g->kchunk, m));
-    return INS_OK;
-}
-
-dim3 cell_grid(const ins_grid* g) { return dim3((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz); }
-
+int device_sm_count();
 // z chunk of the pair kernels: the CTAs of a launch run in waves of 2 per SM (their launch
 // bounds); a CTA costs about its planes plus two for its prologue (five staged planes without
 // an evaluation). Take the chunk that minimises waves x cost per CTA (the last wave counts as a
 // full one), or the caller's (ins_set_march_chunk).
-int device_sm_count();
 dim3 pair_grid(const ins_grid* g) {
     const int nbx = (g->nx + 2 * RBX - 1) / (2 * RBX), nby = (g->ny + RBY - 1) / RBY;
     int kc = g->march_chunk;
@@ -464,6 +454,46 @@ dim3 pair_grid(const ins_grid* g) {
     kc = std::min(kc, g->nz);
     return dim3(nbx, nby, (g->nz + kc - 1) / kc);
 }
+
+// The two-cells-per-thread FP32 kernels (fusion level 2): nx even, 8-byte aligned fields,
+// 3 x cells < 2^31.
+bool pair_ok(const ins_grid* g, const void* u) {
+    return g->fusion == 2 && g->nx % 2 == 0 && 3 * g->N < (1L << 31) && reinterpret_cast<uintptr_t>(u) % 8 == 0;
+}
+
+template <bool WALL, bool STAGE>
+ins_status launch_pair(ins_grid* g, const char* name, const float* Fs, const float* p, const float* u0, float* acc,
+                       float* F, float* r, const FusedArgs& fa) {
+    static bool attr = false;
+    if (!attr) {
+        INS_CUDA(cudaFuncSetAttribute(k_rhs_div_x2<WALL, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      PairRegSmem::BYTES));
+        attr = true;
+    }
+    const dim3 grd = pair_grid(g);
+    const int kc = (g->nz + grd.z - 1) / grd.z;
+    const float* ihy = make_geo<float>(g).c[1] + (size_t)C_INV_H * g->ny;
+    KLAUNCH(g, name, (k_rhs_div_x2<WALL, STAGE><<<grd, dim3(RBX, RBY, 1), PairRegSmem::BYTES, g->stream>>>(
+                         make_rhs_coef<float>(g), (float)(1.0 / g->h[0][0]), (float)(1.0 / g->h[2][0]), ihy, Fs, p,
+                         u0, acc, F, r, fa, kc)));
+    return INS_OK;
+}
+
+template <typename T, int DIM, bool WALL>
+ins_status launch_rhs_div(ins_grid* g, const T* u, T* F, T* r, const T* m = nullptr) {
+    if constexpr (DIM == 3 && std::is_same<T, float>::value) {
+        if (!m && pair_ok(g, u)) {
+            FusedArgs fa{};
+            return launch_pair<WALL, false>(g, "rhs_div", nullptr, nullptr, u, nullptr, F, r, fa);
+        }
+    }
+    dim3 blk(RBX, RBY, 1);
+    dim3 grd((g->nx + RBX - 1) / RBX, (g->ny + RBY - 1) / RBY, DIM == 3 ? (g->nz + g->kchunk - 1) / g->kchunk : 1);
+    KLAUNCH(g, "rhs_div", k_rhs_div<T, DIM, WALL><<<grd, blk, 0, g->stream>>>(make_rhs_coef<T>(g), u, F, r, g->kchunk, m));
+    return INS_OK;
+}
+
+dim3 cell_grid(const ins_grid* g) { return dim3((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz); }
 
 // The vector RK update needs whole 16-byte vectors per row and an aligned caller field.
 template <typename T>
@@ -571,42 +601,25 @@ struct Impl {
         const T ihx = (T)(1.0 / g->h[0][0]), ihz = (T)(1.0 / g->h[2][0]);
         const dim3 blk(RBX, RBY, 1);
         const dim3 grd((g->nx + RBX - 1) / RBX, (g->ny + RBY - 1) / RBY, (g->nz + g->kchunk - 1) / g->kchunk);
-        // two cells per thread: the caller's field is 16-byte aligned and nx a multiple of 4 (rk_vec_ok)
-        const bool pair = g->fusion == 2 && 3 * g->N < (1L << 31);
-        const dim3 grd2 = pair_grid(g);
-        const int kc2 = (g->nz + grd2.z - 1) / grd2.z;
-        if (pair) {
-            static bool attr = false;
-            if (!attr) {
-                INS_CUDA(cudaFuncSetAttribute(k_rhs_div_x2<WALL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              PairRegSmem::BYTES));
-                INS_CUDA(cudaFuncSetAttribute(k_rhs_div_x2<WALL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              PairRegSmem::BYTES));
-                attr = true;
-            }
-        }
+        static_assert(std::is_same<T, float>::value && DIM == 3, "FP32 3-D only");
+        const bool pair = pair_ok(g, u);   // the caller's field is 16-byte aligned, nx % 4 == 0 (rk_vec_ok)
         FusedArgs fa;
         fa.dt_dev = dt_dev;
         fa.dt_host = dt_host;
         fa.a_next = 0.0;
         fa.b = 0.0;
         fa.stage = 0;
-        static_assert(std::is_same<T, float>::value && DIM == 3, "FP32 3-D only");
-        if (pair)
-            KLAUNCH(g, "rhs_div", (k_rhs_div_x2<WALL, false><<<grd2, blk, PairRegSmem::BYTES, g->stream>>>(
-                                      rc, ihx, ihz, ihy, nullptr, nullptr, u, nullptr, Fb[0], rr, fa, kc2)));
-        else if ((s = launch_rhs_div<T, DIM, WALL>(g, u, Fb[0], rr)) != INS_OK)
-            return s;
+        if ((s = launch_rhs_div<T, DIM, WALL>(g, u, Fb[0], rr)) != INS_OK) return s;
         if ((s = poisson<T>(g, rr, pp)) != INS_OK) return s;
         for (int st = 0; st < 3; ++st) {
             fa.a_next = A[st];
             fa.b = B[st];
             fa.stage = st;
-            if (pair)
-                KLAUNCH(g, "update_rhs_div", (k_rhs_div_x2<WALL, true><<<grd2, blk, PairRegSmem::BYTES, g->stream>>>(
-                                                 rc, ihx, ihz, ihy, Fb[st & 1], pp, u, acc, Fb[(st + 1) & 1], rr, fa,
-                                                 kc2)));
-            else
+            if (pair) {
+                if ((s = launch_pair<WALL, true>(g, "update_rhs_div", Fb[st & 1], pp, u, acc, Fb[(st + 1) & 1], rr, fa)) !=
+                    INS_OK)
+                    return s;
+            } else
                 KLAUNCH(g, "update_rhs_div", k_update_rhs_div<T, WALL><<<grd, blk, 0, g->stream>>>(
                                                  rc, ihx, ihz, ihy, Fb[st & 1], pp, u, acc, Fb[(st + 1) & 1], rr, fa,
                                                  g->kchunk));
@@ -667,10 +680,11 @@ struct Impl {
     // Pullback of one RK4 step (uniform periodic grids): recompute the stage states from the
     // checkpoint u_n, then run the stages in reverse (see ins.h, ins_step_vjp).
     // Pullback of one step on a wall-bounded grid: stage recompute as below, P^T = M Omega P
-    // Omega^-1 M, J_F^T in scatter form (k_adj_rhs_wall); the stored top wall faces of u^y are not
+    // Omega^-1 M, J_F^T in gather form (k_adj_rhs_wall_g); the stored top wall faces of u^y are not
     // unknowns (cotangents there are ignored and returned as 0).
     static ins_status step_vjp_wall(ins_grid* g, const T* un, const double* dt_dev, double dt_host, const T* ybar,
                                     T* ubar, double* nubar) {
+        if (3 * g->N >= (1L << 31)) return fail(INS_ERR_UNSUPPORTED, "ins_step_vjp: wall grids need 3 x cells < 2^31");
         static const double A[3] = {0.5, 0.5, 1.0};
         static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
         const long N = g->N;
@@ -678,7 +692,7 @@ struct Impl {
         const size_t fa = (fld + 255) & ~size_t(255);
         const dim3 cg = cell_grid(g);
         const long nblk = (long)cg.x * cg.y * cg.z;
-        const size_t need = 5 * fa + (size_t)nblk * 8;
+        const size_t need = 4 * fa + (size_t)nblk * 8;
         if (g->vjp_bytes < need) {
             if (g->vjp) cudaFree(g->vjp);
             g->vjp = nullptr;
@@ -694,8 +708,7 @@ struct Impl {
         T* U[4] = {const_cast<T*>(un), reinterpret_cast<T*>(vb), reinterpret_cast<T*>(vb + fa),
                    reinterpret_cast<T*>(vb + 2 * fa)};
         T* W = reinterpret_cast<T*>(vb + 3 * fa);
-        T* Q = reinterpret_cast<T*>(vb + 4 * fa);
-        double* part = reinterpret_cast<double*>(vb + 5 * fa);
+        double* part = reinterpret_cast<double*>(vb + 4 * fa);
         T* F = reinterpret_cast<T*>(g->F);
         T* rp = reinterpret_cast<T*>(g->rp);
         T* scratch = reinterpret_cast<T*>(g->acc);
@@ -731,30 +744,49 @@ struct Impl {
         INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
         KLAUNCH(g, "scale", k_scale_dt<T><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host,
                                                                       lowst ? WRAY3_GAMMA[2] : B[3], n));
-        WallAdj<T> wa;
+        constexpr bool ZMARCH = DIM == 3 && std::is_same<T, float>::value;
+        // z chunks of the 3-D adjoint march: about two waves of two CTAs per SM
+        const long cols = (long)cg.x * cg.y;
+        const long nch = std::max(1L, std::min((long)g->nz, (4L * device_sm_count() + cols / 2) / cols));
+        const int zkc = ZMARCH ? (int)((g->nz + nch - 1) / nch) : 1;
+        const dim3 zg(cg.x, cg.y, ZMARCH ? (g->nz + zkc - 1) / zkc : 1);
+        const long znblk = ZMARCH ? (long)zg.x * zg.y * zg.z : nblk;
+        if constexpr (ZMARCH) {
+            static bool attr = false;
+            if (!attr) {
+                INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_wall_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              wall_adj_smem<T>()));
+                attr = true;
+            }
+        }
+        WallAdjG<T> wa;
         wa.g = make_geo<T>(g);
         wa.nu = (T)g->nu;
+        wa.dt_dev = dt_dev;
+        wa.dt_host = dt_host;
         for (int st = nst - 1; st >= 0; --st) {
             // w = P^T kbar = M Omega P (Omega^-1 M kbar)
-            KLAUNCH(g, "row_scale", k_row_scale<T><<<1184, 256, 0, g->stream>>>(F, W, hy, dy, g->nx, g->ny, N, g->dim, 1));
-            KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), W, rp));
+            KLAUNCH(g, "divergence", (k_wall_div_scaled<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp)));
             if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
-            KLAUNCH(g, "sub_grad", k_sub_grad<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), W, rp, W));
-            KLAUNCH(g, "row_scale", k_row_scale<T><<<1184, 256, 0, g->stream>>>(W, W, hy, dy, g->nx, g->ny, N, g->dim, 0));
-            INS_CUDA(cudaMemsetAsync(Q, 0, fld, g->stream));
-            KLAUNCH(g, "adj_rhs", k_adj_rhs_wall<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(wa, U[st], W, Q, part));
-            if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, nblk, nubar));
-            double bn, an;
+            KLAUNCH(g, "sub_grad",
+                    (k_wall_sub_scaled<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, W, hy, dy)));
             if (lowst) {
-                bn = st > 0 ? WRAY3_GAMMA[st - 1] + WRAY3_ZETA[st] : 0.0;
-                an = st > 0 ? WRAY3_GAMMA[st - 1] : 0.0;
+                wa.bn = st > 0 ? WRAY3_GAMMA[st - 1] + WRAY3_ZETA[st] : 0.0;
+                wa.an = st > 0 ? WRAY3_GAMMA[st - 1] : 0.0;
             } else {
-                bn = st > 0 ? B[st - 1] : 0.0;
-                an = st > 0 ? A[st - 1] : 0.0;
+                wa.bn = st > 0 ? B[st - 1] : 0.0;
+                wa.an = st > 0 ? A[st - 1] : 0.0;
             }
-            KLAUNCH(g, "adj_finish", k_adj_finish<T><<<1184, 256, 0, g->stream>>>(
-                                         Q, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, dt_dev, dt_host, bn, an,
-                                         g->nx, g->ny, N, g->dim));
+            // ubar0 += J_F^T w; the next stage cotangent into F
+            // FP32 3-D: the z march (shared-memory ring); FP64 and 2-D: neighbours from global memory
+            // (in FP64 the march's register count leaves one CTA per SM, and the global form is faster)
+            if constexpr (ZMARCH)
+                KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_z<T><<<zg, dim3(32, 8), wall_adj_smem<T>(), g->stream>>>(
+                                          wa, U[st], W, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, part, zkc)));
+            else
+                KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_g<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
+                                          wa, U[st], W, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, part)));
+            if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, znblk, nubar));
         }
         KLAUNCH(g, "mask_top", k_mask_top<T><<<592, 256, 0, g->stream>>>(ubar, g->nx, g->ny, g->nz, N));
         return INS_OK;
