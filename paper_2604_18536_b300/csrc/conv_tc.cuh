@@ -148,23 +148,28 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tbase;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
-    // MMAs of tile z into accumulator acc (thread 0), committed to mbar[acc]
+    // MMAs of tile z into accumulator acc (thread 0), committed to mbar[acc]. Descriptors are
+    // formed by adding the operand's byte offset / 16 to the address field of a base descriptor
+    // (all shared addresses stay below 256 KB, so the 14-bit field never carries); with the taps
+    // unrolled, every offset but the three plane slots is a constant.
+    const uint64_t adesc0 = cv_desc(cv_smem(sA), CG == 1 ? 0 : CV_CGS, CV_ROW);
+    const uint64_t bdesc0 = cv_desc(cv_smem(sB), 128, SBO_B);
     auto issue_tile = [&](int z, int acc) {
-        int first = 1;
         const uint32_t dcol = tmem + (uint32_t)(acc * N);
+        const uint64_t as[3] = {adesc0 + (uint64_t)((slot_of(z - 1) * CV_PLANE) >> 4),
+                                adesc0 + (uint64_t)((slot_of(z) * CV_PLANE) >> 4),
+                                adesc0 + (uint64_t)((slot_of(z + 1) * CV_PLANE) >> 4)};
+#pragma unroll
         for (int t = 0; t < 27; ++t) {
             const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-            const uint32_t abase = cv_smem(sA) + slot_of(z + dz) * CV_PLANE + (1 + dy) * CV_ROW + (1 + dx) * 16;
-            const uint32_t bbase = cv_smem(sB) + t * TAPB;
 #pragma unroll
             for (int s = 0; s < KSTEPS; ++s) {
-                const uint64_t ad = cv_desc(abase + 2 * s * CV_CGS, CG == 1 ? 0 : CV_CGS, CV_ROW);
-                const uint64_t bd = cv_desc(bbase + 2 * s * 128, 128, SBO_B);
+                const uint64_t ad = as[dz + 1] + (uint64_t)(((1 + dy) * CV_ROW + (1 + dx) * 16 + 2 * s * CV_CGS) >> 4);
+                const uint64_t bd = bdesc0 + (uint64_t)((t * TAPB + 2 * s * 128) >> 4);
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0 : 1));
-                first = 0;
+                    "l"(ad), "l"(bd), "r"(idesc), "r"((t | s) ? 1 : 0));
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
                      : "memory");
     };
     if (tid == 0 && zb < ze) issue_tile(zb, 0);
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase = 0u;   // bit b: parity of accumulator b's barrier
     bool alive = true;
     // epilogue ownership: warp w reads TMEM lanes 32 (w % 4) .. +31 (voxel rows) and channels
     // (w / 4) NH .. +NH of the tile
@@ -181,6 +186,9 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
     const int vx = x0 + (m & 7), vy = y0 + (m >> 3);
     const bool inside = vx < nx && vy < ny;
     const int c0 = half * NH;
+    float bv[NH];
+#pragma unroll
+    for (int c = 0; c < NH; ++c) bv[c] = (a.bias && (EPI == EPI_GELU || EPI == EPI_OUT)) ? a.bias[c0 + c] : 0.f;
 
     for (int z = zb; z < ze && alive; ++z) {
         const int b = (z - zb) & 1;
@@ -201,10 +209,10 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
             asm volatile(
                 "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                 : "=r"(done)
-                : "r"(cv_smem(&mbar[b])), "r"(phase[b])
+                : "r"(cv_smem(&mbar[b])), "r"((phase >> b) & 1u)
                 : "memory");
         }
-        phase[b] ^= 1;
+        phase ^= 1u << b;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!done) {
             if (tid == 0) atomicOr(a.err, 2u);
@@ -238,28 +246,38 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
             const long v = ((long)z * ny + vy) * nx + vx;
             if (EPI == EPI_GELU) {
                 __align__(16) __nv_bfloat16 o[NH];
+                __align__(16) float zz[NH];
 #pragma unroll
                 for (int c = 0; c < NH; ++c) {
-                    const float zz = __uint_as_float(r[c]) + (a.bias ? a.bias[c0 + c] : 0.f);
-                    if (a.zout) a.zout[v * N + c0 + c] = zz;
-                    o[c] = __float2bfloat16_rn(cv_gelu(zz));
+                    zz[c] = __uint_as_float(r[c]) + bv[c];
+                    o[c] = __float2bfloat16_rn(cv_gelu(zz[c]));
+                }
+                if (a.zout) {
+                    float4* zd = reinterpret_cast<float4*>(a.zout + v * N + c0);
+#pragma unroll
+                    for (int q = 0; q < NH / 4; ++q) zd[q] = reinterpret_cast<const float4*>(zz)[q];
                 }
                 uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N + c0);
 #pragma unroll
                 for (int q = 0; q < NH / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
             } else if (EPI == EPI_DGELU) {
                 __align__(16) __nv_bfloat16 o[NH];
+                __align__(16) float zi[NH];
+                const float4* zs = reinterpret_cast<const float4*>(a.zin + v * N + c0);
 #pragma unroll
-                for (int c = 0; c < NH; ++c)
-                    o[c] = __float2bfloat16_rn(__uint_as_float(r[c]) * cv_gelu_grad(a.zin[v * N + c0 + c]));
+                for (int q = 0; q < NH / 4; ++q) reinterpret_cast<float4*>(zi)[q] = zs[q];
+#pragma unroll
+                for (int c = 0; c < NH; ++c) o[c] = __float2bfloat16_rn(__uint_as_float(r[c]) * cv_gelu_grad(zi[c]));
                 uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N + c0);
 #pragma unroll
                 for (int q = 0; q < NH / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
             } else {
-                const int cend = a.nreal < c0 + NH ? a.nreal : c0 + NH;
-                for (int c = c0; c < cend; ++c) {
-                    float val = __uint_as_float(r[c - c0]);
-                    if (EPI == EPI_OUT && a.bias) val += a.bias[c];
+#pragma unroll
+                for (int cc = 0; cc < NH; ++cc) {
+                    const int c = c0 + cc;
+                    if (c >= a.nreal) continue;
+                    float val = __uint_as_float(r[cc]);
+                    if (EPI == EPI_OUT) val += bv[cc];
                     if (a.out_f64) {
                         double* o = reinterpret_cast<double*>(a.out) + c * nvox + v;
                         *o = EPI == EPI_ACCUM ? *o + (double)val : (double)val;
