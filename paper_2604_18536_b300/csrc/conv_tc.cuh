@@ -406,16 +406,32 @@ __global__ void __launch_bounds__(WG_THREADS) k_wgrad_tc(const __nv_bfloat16* __
         tcg[j] = mg - tl * CGX;
     }
     const int nxy = nx * ny;
+    // coordinates of this thread's voxel of the next stage to issue: stages are issued in
+    // order, each WG_S voxels after the previous one, so the coordinates advance without divisions
+    int cvx, cvy, cvz;
+    {
+        const long vl = v0 + kk;
+        const int v = vl < nvox ? (int)vl : 0;
+        cvz = v / nxy;
+        const int rxy = v - cvz * nxy;
+        cvy = rxy / nx;
+        cvx = rxy - cvy * nx;
+    }
     auto issue = [&](int st, int b) {
         unsigned char* sa = smem + b * Sh::STAGE;
         unsigned char* sbb = sa + Sh::A_BYTES;
         const long vl = v0 + (long)st * WG_S + kk;
         const bool okv = vl < v1;
-        const int v = okv ? (int)vl : 0;
-        const int z = v / nxy;
-        const int rxy = v - z * nxy;
-        const int y = rxy / nx;
-        const int x = rxy - y * nx;
+        const int x = cvx, y = cvy, z = cvz;
+        const int v = okv ? (z * ny + y) * nx + x : 0;
+        cvx += WG_S;
+        while (cvx >= nx) {
+            cvx -= nx;
+            if (++cvy == ny) {
+                cvy = 0;
+                ++cvz;
+            }
+        }
         const uint32_t kofs = (uint32_t)((kk >> 3) * 128 + (kk & 7) * 16);
 #pragma unroll
         for (int j = 0; j < MPT; ++j) {
