@@ -40,32 +40,71 @@ namespace ins {
 // old ubar0; the stored top wall faces of u^y keep q = 0. nu_part: one FP64 partial of
 // <w, diffusion(u) / nu> per CTA. The grid has fewer than 2^31 / 3 cells (the caller checks).
 
-// J_F^T w of the three faces of cell (i, j) (z index implicit in the accessor). A.u(c, di,
-// dj, dk) and A.w(c, di, dj, dk) give u^c and w^c at the offset with the wall rules applied:
-// u^x, u^z odd ghosts beyond the walls; u^y 0 beyond the walls and on the top wall faces; w^x,
-// w^z 0 beyond the walls; w^y 0 beyond the walls and on the top wall faces. q: the pullback of
-// each face (q[1] = 0 on the top wall faces), nup += w . (diffusion of u / nu) on the faces.
-template <typename T, int DIM, typename Acc>
-__device__ __forceinline__ void wall_adj_cell(const Geo<T>& G, T nu, int i, int j, const Acc& A, T (&q)[3],
-                                              double& nup) {
+// Coefficients of wall_adj_cell for cell (i, j): x and z are uniform, so they depend on the row
+// only; a z march computes them once.
+template <typename T>
+struct WallRowCoef {
+    T fym, fy0, fyp;      // 1/(4 d_y) at rows j - 1, j, j + 1 (clamped)
+    T sym, sy0, syp;      // 1/(4 h_y) at rows j - 1, j, j + 1 (clamped)
+    T wl, wr, wrm;        // volume weights of row j, wr of row j - 1 (0 at j = 0)
+    T cx, cx2, cz, cz2;   // 1/(4 d), 1/(2 d) of x and z
+    T lx, lz;             // 1/d^2 of x and z
+    T bp, bm, bpm, bmp;   // tangential y diffusion: c+_j, c-_j, c+_{j-1} (0 at j = 0), c-_{j+1} (0 at the top)
+    T ap, am, apm, amp;   // u^y diffusion: a+_j, a-_j, a+_{j-1} (0 at j = 0), a-_{j+1} (0 unless j + 1 < ny - 1)
+};
+
+template <typename T, int DIM>
+__device__ __forceinline__ WallRowCoef<T> wall_row_coef(const Geo<T>& G, int i, int j) {
     const int ny = G.ny;
-    // row coefficients: f = 1/(4 d_y), s = 1/(4 h_y), volume weights, y diffusion (nu-free)
-    auto fy = [&](int jj) { return (T)0.25 * G.coef(1, C_INV_D, jj < 0 ? 0 : (jj >= ny ? ny - 1 : jj)); };
-    auto sy = [&](int jj) { return G.coef(1, C_CONV_AA, jj < 0 ? 0 : (jj >= ny ? ny - 1 : jj)); };
-    const T wl = G.coef(1, C_WL, j), wr = G.coef(1, C_WR, j);
-    const T wrm = j > 0 ? G.coef(1, C_WR, j - 1) : (T)0;
-    const T cx = G.coef(0, C_CONV_AA, i), cx2 = G.coef(0, C_CONV_AB, i);   // 1/(4 d_x), 1/(2 d_x)
-    const T cz = DIM == 3 ? G.coef(2, C_CONV_AA, 0) : (T)0, cz2 = DIM == 3 ? G.coef(2, C_CONV_AB, 0) : (T)0;
-    const T lx = G.coef(0, C_INV_H, i) * G.coef(0, C_INV_D, i);
-    const T lz = DIM == 3 ? G.coef(2, C_INV_H, 0) * G.coef(2, C_INV_D, 0) : (T)0;
-    // y diffusion of the tangential components at row j: c+ = 1/(h_j d_j), c- = 1/(h_{j-1} d_j)
-    // (h_{-1} = d_0); of u^y: a+ = 1/(d_{j+1} h_j), a- = 1/(d_j h_j)
+    auto cl = [ny](int jj) { return jj < 0 ? 0 : (jj >= ny ? ny - 1 : jj); };
     auto bpy = [&](int jj) { return G.coef(1, C_INV_H, jj) * G.coef(1, C_INV_D, jj); };
     auto bmy = [&](int jj) {
         return (jj == 0 ? G.coef(1, C_INV_D, 0) : G.coef(1, C_INV_H, jj - 1)) * G.coef(1, C_INV_D, jj);
     };
     auto apy = [&](int jj) { return G.coef(1, C_INV_D, jj + 1) * G.coef(1, C_INV_H, jj); };
     auto amy = [&](int jj) { return G.coef(1, C_INV_D, jj) * G.coef(1, C_INV_H, jj); };
+    WallRowCoef<T> R;
+    R.fym = (T)0.25 * G.coef(1, C_INV_D, cl(j - 1));
+    R.fy0 = (T)0.25 * G.coef(1, C_INV_D, j);
+    R.fyp = (T)0.25 * G.coef(1, C_INV_D, cl(j + 1));
+    R.sym = G.coef(1, C_CONV_AA, cl(j - 1));
+    R.sy0 = G.coef(1, C_CONV_AA, j);
+    R.syp = G.coef(1, C_CONV_AA, cl(j + 1));
+    R.wl = G.coef(1, C_WL, j);
+    R.wr = G.coef(1, C_WR, j);
+    R.wrm = j > 0 ? G.coef(1, C_WR, j - 1) : (T)0;
+    R.cx = G.coef(0, C_CONV_AA, i);
+    R.cx2 = G.coef(0, C_CONV_AB, i);
+    R.cz = DIM == 3 ? G.coef(2, C_CONV_AA, 0) : (T)0;
+    R.cz2 = DIM == 3 ? G.coef(2, C_CONV_AB, 0) : (T)0;
+    R.lx = G.coef(0, C_INV_H, i) * G.coef(0, C_INV_D, i);
+    R.lz = DIM == 3 ? G.coef(2, C_INV_H, 0) * G.coef(2, C_INV_D, 0) : (T)0;
+    R.bp = bpy(j);
+    R.bm = bmy(j);
+    R.bpm = j > 0 ? bpy(j - 1) : (T)0;
+    R.bmp = j + 1 < ny ? bmy(j + 1) : (T)0;
+    if (j < ny - 1) {
+        R.ap = apy(j);
+        R.am = amy(j);
+    } else {
+        R.ap = R.am = (T)0;
+    }
+    R.apm = j > 0 ? apy(j - 1) : (T)0;
+    R.amp = j + 1 < ny - 1 ? amy(j + 1) : (T)0;
+    return R;
+}
+
+// J_F^T w of the three faces of cell (i, j) (z index implicit in the accessor). A.u(c, di,
+// dj, dk) and A.w(c, di, dj, dk) give u^c and w^c at the offset with the wall rules applied:
+// u^x, u^z odd ghosts beyond the walls; u^y 0 beyond the walls and on the top wall faces; w^x,
+// w^z 0 beyond the walls; w^y 0 beyond the walls and on the top wall faces. q: the pullback of
+// each face (q[1] = 0 on the top wall faces), nup += w . (diffusion of u / nu) on the faces.
+template <typename T, int DIM, typename Acc>
+__device__ __forceinline__ void wall_adj_cell(const WallRowCoef<T>& R, int ny, T nu, int j, const Acc& A, T (&q)[3],
+                                              double& nup) {
+    const T fym = R.fym, fy0 = R.fy0, fyp = R.fyp, sym = R.sym, sy0 = R.sy0, syp = R.syp;
+    const T wl = R.wl, wr = R.wr, wrm = R.wrm, cx = R.cx, cx2 = R.cx2, cz = R.cz, cz2 = R.cz2, lx = R.lx, lz = R.lz;
+    T lpart = (T)0;   // w . (diffusion of u / nu) over the three faces
     // ---- u^x
     {
         const T u0 = A.u(0, 0, 0, 0), ue = A.u(0, 1, 0, 0), uw = A.u(0, -1, 0, 0);
@@ -74,12 +113,12 @@ __device__ __forceinline__ void wall_adj_cell(const Geo<T>& G, T nu, int i, int 
         T a = (T)2 * cx * ((u0 + ue) * (we - w0) + (uw + u0) * (w0 - ww));
         // xy: edges P and P - y; V = u^y_E + u^y_{E+x}
         const T V0 = A.u(1, 0, 0, 0) + A.u(1, 1, 0, 0), Vs = A.u(1, 0, -1, 0) + A.u(1, 1, -1, 0);
-        a += (fy(j + 1) * wn - fy(j) * w0) * V0 + (fy(j) * w0 - fy(j - 1) * ws) * Vs;
+        a += (fyp * wn - fy0 * w0) * V0 + (fy0 * w0 - fym * ws) * Vs;
         // yx: edges P (wl) and P - y (wr)
         a += cx2 * (A.w(1, 1, 0, 0) - A.w(1, 0, 0, 0)) * wl * V0 + cx2 * (A.w(1, 1, -1, 0) - A.w(1, 0, -1, 0)) * wrm * Vs;
         // diffusion (x, y; z below), ghost folds at the walls
-        const T bp = bpy(j), bm = bmy(j);
-        T d = lx * (we + ww - (T)2 * w0) + (j > 0 ? bpy(j - 1) * ws : (T)0) + (j + 1 < ny ? bmy(j + 1) * wn : (T)0) -
+        const T bp = R.bp, bm = R.bm;
+        T d = lx * (we + ww - (T)2 * w0) + R.bpm * ws + R.bmp * wn -
               (bp + bm) * w0;
         if (j == 0) d -= bm * w0;
         if (j == ny - 1) d -= bp * w0;
@@ -96,37 +135,37 @@ __device__ __forceinline__ void wall_adj_cell(const Geo<T>& G, T nu, int i, int 
             lap += lz * (ut + ub - (T)2 * u0);
         }
         q[0] = a + nu * d;
-        nup += (double)w0 * (double)lap;
+        lpart = fma(w0, lap, lpart);
     }
     // ---- u^y (not an unknown on the top wall faces)
     if (j < ny - 1) {
         const T u0 = A.u(1, 0, 0, 0), un = A.u(1, 0, 1, 0), us = A.u(1, 0, -1, 0);
         const T w0 = A.w(1, 0, 0, 0), wn = A.w(1, 0, 1, 0), ws = A.w(1, 0, -1, 0);
         const T we = A.w(1, 1, 0, 0), ww = A.w(1, -1, 0, 0);
-        T a = (T)2 * ((u0 + un) * (sy(j + 1) * wn - sy(j) * w0) + (us + u0) * (sy(j) * w0 - sy(j - 1) * ws));
+        T a = (T)2 * ((u0 + un) * (syp * wn - sy0 * w0) + (us + u0) * (sy0 * w0 - sym * ws));
         // xy: edges P and P - x; T = u^x_E + u^x_{E+y}
         const T x0 = A.u(0, 0, 0, 0), xn = A.u(0, 0, 1, 0), xw = A.u(0, -1, 0, 0), xwn = A.u(0, -1, 1, 0);
-        a += (fy(j + 1) * A.w(0, 0, 1, 0) - fy(j) * A.w(0, 0, 0, 0)) * (x0 + xn) +
-             (fy(j + 1) * A.w(0, -1, 1, 0) - fy(j) * A.w(0, -1, 0, 0)) * (xw + xwn);
+        a += (fyp * A.w(0, 0, 1, 0) - fy0 * A.w(0, 0, 0, 0)) * (x0 + xn) +
+             (fyp * A.w(0, -1, 1, 0) - fy0 * A.w(0, -1, 0, 0)) * (xw + xwn);
         // yx: edges P and P - x; A = wl u^x_E + wr u^x_{E+y}
         a += cx2 * (we - w0) * (wl * x0 + wr * xn) + cx2 * (w0 - ww) * (wl * xw + wr * xwn);
-        const T ap = apy(j), am = amy(j);
-        T d = lx * (we + ww - (T)2 * w0) + (j > 0 ? apy(j - 1) * ws : (T)0) + (j + 1 < ny - 1 ? amy(j + 1) * wn : (T)0) -
+        const T ap = R.ap, am = R.am;
+        T d = lx * (we + ww - (T)2 * w0) + R.apm * ws + R.amp * wn -
               (ap + am) * w0;
         T lap = lx * (A.u(1, 1, 0, 0) + A.u(1, -1, 0, 0) - (T)2 * u0) + ap * un + am * us - (ap + am) * u0;
         if constexpr (DIM == 3) {
             const T wt = A.w(1, 0, 0, 1), wb = A.w(1, 0, 0, -1);
             const T z0 = A.u(2, 0, 0, 0), zn = A.u(2, 0, 1, 0), zb = A.u(2, 0, 0, -1), zbn = A.u(2, 0, 1, -1);
             // zy: edges P and P - z; T = u^z_E + u^z_{E+y}
-            a += (fy(j + 1) * A.w(2, 0, 1, 0) - fy(j) * A.w(2, 0, 0, 0)) * (z0 + zn) +
-                 (fy(j + 1) * A.w(2, 0, 1, -1) - fy(j) * A.w(2, 0, 0, -1)) * (zb + zbn);
+            a += (fyp * A.w(2, 0, 1, 0) - fy0 * A.w(2, 0, 0, 0)) * (z0 + zn) +
+                 (fyp * A.w(2, 0, 1, -1) - fy0 * A.w(2, 0, 0, -1)) * (zb + zbn);
             // yz: edges P and P - z; A = wl u^z_E + wr u^z_{E+y}
             a += cz2 * (wt - w0) * (wl * z0 + wr * zn) + cz2 * (w0 - wb) * (wl * zb + wr * zbn);
             d += lz * (wt + wb - (T)2 * w0);
             lap += lz * (A.u(1, 0, 0, 1) + A.u(1, 0, 0, -1) - (T)2 * u0);
         }
         q[1] = a + nu * d;
-        nup += (double)w0 * (double)lap;
+        lpart = fma(w0, lap, lpart);
     } else {
         q[1] = (T)0;
     }
@@ -143,19 +182,20 @@ __device__ __forceinline__ void wall_adj_cell(const Geo<T>& G, T nu, int i, int 
         a += pb0 * (A.u(0, 0, 0, 0) + A.u(0, 0, 0, 1)) + pbw * (A.u(0, -1, 0, 0) + A.u(0, -1, 0, 1));
         // zy: edges P and P - y; V = u^y_E + u^y_{E+z}
         const T V0 = A.u(1, 0, 0, 0) + A.u(1, 0, 0, 1), Vs = A.u(1, 0, -1, 0) + A.u(1, 0, -1, 1);
-        a += (fy(j + 1) * wn - fy(j) * w0) * V0 + (fy(j) * w0 - fy(j - 1) * ws) * Vs;
+        a += (fyp * wn - fy0 * w0) * V0 + (fy0 * w0 - fym * ws) * Vs;
         // yz: edges P (wl) and P - y (wr)
         a += cz2 * (A.w(1, 0, 0, 1) - A.w(1, 0, 0, 0)) * wl * V0 + cz2 * (A.w(1, 0, -1, 1) - A.w(1, 0, -1, 0)) * wrm * Vs;
-        const T bp = bpy(j), bm = bmy(j);
-        T d = lx * (we + ww - (T)2 * w0) + lz * (wt + wb - (T)2 * w0) + (j > 0 ? bpy(j - 1) * ws : (T)0) +
-              (j + 1 < ny ? bmy(j + 1) * wn : (T)0) - (bp + bm) * w0;
+        const T bp = R.bp, bm = R.bm;
+        T d = lx * (we + ww - (T)2 * w0) + lz * (wt + wb - (T)2 * w0) + R.bpm * ws +
+              R.bmp * wn - (bp + bm) * w0;
         if (j == 0) d -= bm * w0;
         if (j == ny - 1) d -= bp * w0;
         const T lap = lx * (A.u(2, 1, 0, 0) + A.u(2, -1, 0, 0) - (T)2 * u0) + lz * (ut + ub - (T)2 * u0) +
                       bp * A.u(2, 0, 1, 0) + bm * A.u(2, 0, -1, 0) - (bp + bm) * u0;
         q[2] = a + nu * d;
-        nup += (double)w0 * (double)lap;
+        lpart = fma(w0, lap, lpart);
     }
+    nup += (double)lpart;
 }
 
 // Accessor of wall_adj_cell on global memory (x, z wrap; the wall rules by row).
@@ -247,7 +287,7 @@ __global__ void __launch_bounds__(256) k_adj_rhs_wall_g(WallAdjG<T> c, const T* 
         A.kp = DIM == 3 ? (k + 1 == nz ? 0 : k + 1) : k;
         A.km = DIM == 3 ? (k == 0 ? nz - 1 : k - 1) : k;
         T q[3];
-        wall_adj_cell<T, DIM>(G, c.nu, i, j, A, q, nup);
+        wall_adj_cell<T, DIM>(wall_row_coef<T, DIM>(G, i, j), ny, c.nu, j, A, q, nup);
         const double dt = c.dt_dev ? *c.dt_dev : c.dt_host;
         wall_adj_finish<T, DIM>(c, N, (k * ny + j) * nx + i, q, ybar, ubar0, kbar, (T)(dt * c.bn), (T)(dt * c.an));
     }
@@ -279,7 +319,7 @@ struct SharedWallAcc {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_rhs_wall_z(WallAdjG<T> c, const T* __restrict__ u,
+__global__ void __launch_bounds__(256, 3) k_adj_rhs_wall_z(WallAdjG<T> c, const T* __restrict__ u,
                                                         const T* __restrict__ w, const T* __restrict__ ybar,
                                                         T* __restrict__ ubar0, T* __restrict__ kbar,
                                                         double* __restrict__ nu_part, int kchunk) {
@@ -357,6 +397,7 @@ __global__ void __launch_bounds__(256) k_adj_rhs_wall_z(WallAdjG<T> c, const T* 
     SharedWallAcc<T> A;
     A.s = ring;
     A.c0 = (ty + 1) * WZX + tx + 1;
+    const WallRowCoef<T> rc = wall_row_coef<T, 3>(G, own ? i : 0, own ? j : 0);
     for (int k = kb; k < ke; ++k) {
         const bool more = k + 2 <= ke;
         if (more) load(k + 2);
@@ -365,7 +406,7 @@ __global__ void __launch_bounds__(256) k_adj_rhs_wall_z(WallAdjG<T> c, const T* 
             A.so[1] = slot(k);
             A.so[2] = slot(k + 1);
             T q[3];
-            wall_adj_cell<T, 3>(G, c.nu, i, j, A, q, nup);
+            wall_adj_cell<T, 3>(rc, ny, c.nu, j, A, q, nup);
             wall_adj_finish<T, 3>(c, N, (k * ny + j) * nx + i, q, ybar, ubar0, kbar, dtb, dta);
         }
         if (more) store(k + 2);

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
 #pragma unroll
     for (int c = 0; c < NH; ++c) bv[c] = (a.bias && (EPI == EPI_GELU || EPI == EPI_OUT)) ? a.bias[c0 + c] : 0.f;
 
-    for (int z = zb; z < ze && alive; ++z) {
+    for (int z = zb; z < ze; ++z) {   // every thread reaches the barrier below (uniform exit)
         const int b = (z - zb) & 1;
         const bool more = z + 1 < ze;
         // plane z+3 (tile z+2) into the slot of plane z-2, whose last reader (tile z-1) has finished
@@ -200,7 +200,11 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        // one barrier per tile; it also spreads a failed wait of the previous tile to every thread
+        if (__syncthreads_or(!alive)) {
+            alive = false;
+            break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0 && more) issue_tile(z + 1, b ^ 1);
         // wait for the MMAs of tile z (bounded)
@@ -214,13 +218,12 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
         }
         phase ^= 1u << b;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!done) {
-            if (tid == 0) atomicOr(a.err, 2u);
+        // the warp reads the accumulator only when all its lanes saw the MMAs complete (the
+        // TMEM load is warp-collective); a failed wait ends the loop at the next barrier
+        if (!__all_sync(0xffffffffu, done)) {
+            if (lane == 0) atomicOr(a.err, 2u);
             alive = false;
-        }
-        if (__syncthreads_or(!alive)) {
-            alive = false;
-            break;
+            continue;
         }
         // epilogue: D row m -> voxel (vx, vy, z), channels c0 .. c0 + NH
         uint32_t r[NH];
