@@ -574,4 +574,239 @@ __global__ void __launch_bounds__(WG_THREADS) k_wgrad_tc(const __nv_bfloat16* __
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
 }
 
+// Weight and bias gradients of a layer with 32 input channels without gathers:
+//   dW[t][ci][co] = sum_v x[v + tap t][ci] dY[v][co],  db[co] = sum_v dY[v][co].
+// A CTA owns a 16 x 8 column of voxels (x, y) and a chunk of z planes. Input planes are
+// staged once, with a one-voxel halo in x and rows y0 - 1 .. y0 + 9, as 16-byte entries of
+// 8 channels laid out [row][channel group][x]; inside a row the four channel groups are
+// 288 bytes apart and consecutive rows 4 x 288 bytes apart, so the 16 M groups (channel
+// group, dy) of one MMA (M = 128 rows = (dy = -1 .. +2) x 32 channels) sit at one constant
+// stride: the tap shift in y is part of the A descriptor's M stride, the shifts in x and z
+// are its start address. Both operands are MN-major (8 voxels x 16 bytes per core matrix;
+// K = 16 voxels = one row of the tile). Per plane: 9 (dx, dz) accumulators x 8 rows = 72
+// MMAs of 128 x N x 16 into TMEM regions (dx, dz) that persist over the CTA's planes; the
+// rows dy = +2 are computed and discarded. The dY plane of the tile is staged [row][group][x]
+// (zero-filled beyond the real channels). At the end each CTA writes its accumulators as one
+// partial block part[cta][27][32][N] (k_wgrad_reduce sums the blocks into dW; an error leaves
+// the block unwritten and sets the flag).
+// Input planes z - 1 .. z + 1 come from a 5-slot ring, dY from a 3-slot ring; plane slots
+// are reused only after the MMAs of the tile two planes back have completed (one commit
+// group per tile on alternating mbarriers, bounded waits with an error flag).
+constexpr int WP_TX = 16, WP_TY = 8;
+constexpr int WP_XE = WP_TX + 2;                 // x entries of a staged row
+constexpr int WP_ROWS = WP_TY + 3;               // rows y0 - 1 .. y0 + 9
+constexpr int WP_CGS = WP_XE * 16;               // channel-group stride in a row (288 B)
+constexpr int WP_ROWB = 4 * WP_CGS;              // row stride (1152 B)
+constexpr int WP_XPLANE = WP_ROWS * WP_ROWB;     // 12672 B
+constexpr int WP_XSLOTS = 5, WP_DSLOTS = 3;
+template <int N>
+struct WpShape {
+    static constexpr int DROW = (N / 8) * 256;   // dY row: N/8 groups x 16 x-entries
+    static constexpr int DPLANE = WP_TY * DROW;
+    static constexpr int SMEM = WP_XSLOTS * WP_XPLANE + WP_DSLOTS * DPLANE;
+    static constexpr uint32_t TCOLS = 9 * N <= 256 ? 256 : 512;
+};
+
+template <int CY>
+__global__ void __launch_bounds__(256, 1) k_wgrad_plane(const __nv_bfloat16* __restrict__ X,
+                                                        const __nv_bfloat16* __restrict__ dY, int nx, int ny, int nz,
+                                                        int cout, int zchunk, float* __restrict__ part,
+                                                        float* __restrict__ db, unsigned int* __restrict__ err) {
+    constexpr int N = CY < 16 ? 16 : CY;
+    using Sh = WpShape<N>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* const sx = smem;
+    unsigned char* const sd = smem + WP_XSLOTS * WP_XPLANE;
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int x0 = blockIdx.x * WP_TX, y0 = blockIdx.y * WP_TY;
+    const int zb = blockIdx.z * zchunk, ze = min(zb + zchunk, nz);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cv_smem(&tbase)),
+                     "r"(Sh::TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&mbar[1])));
+    }
+    auto wrapz = [nz](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
+    auto xslot = [zb](int z) { return (z - zb + 1) % WP_XSLOTS; };   // z >= zb - 1
+    auto dslot = [zb](int z) { return (z - zb) % WP_DSLOTS; };       // z >= zb
+    // staging of input plane z: 11 rows x 4 groups x 18 entries
+    auto load_x = [&](int z) {
+        const unsigned char* xb = reinterpret_cast<const unsigned char*>(X);
+        const int gz = wrapz(z);
+        unsigned char* dst = sx + xslot(z) * WP_XPLANE;
+        for (int e = tid; e < WP_ROWS * 4 * WP_XE; e += 256) {
+            const int row = e / (4 * WP_XE), r2 = e - row * (4 * WP_XE);
+            const int cg = r2 / WP_XE, xe = r2 - cg * WP_XE;
+            int gx = x0 - 1 + xe, gy = y0 - 1 + row;
+            gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+            gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+            const long vox = ((long)gz * ny + gy) * nx + gx;
+            cv_cp_async16(cv_smem(dst + row * WP_ROWB + cg * WP_CGS + xe * 16), xb + vox * 64 + cg * 16);
+        }
+    };
+    // staging of dY plane z: 8 rows x N/8 groups x 16 entries (groups beyond CY zero-filled)
+    auto load_d = [&](int z) {
+        const unsigned char* db8 = reinterpret_cast<const unsigned char*>(dY);
+        unsigned char* dst = sd + dslot(z) * Sh::DPLANE;
+        for (int e = tid; e < WP_TY * (N / 8) * WP_TX; e += 256) {
+            const int row = e / ((N / 8) * WP_TX), r2 = e - row * ((N / 8) * WP_TX);
+            const int ng = r2 / WP_TX, xe = r2 - ng * WP_TX;
+            const long vox = ((long)z * ny + (y0 + row)) * nx + (x0 + xe);
+            const bool ok = ng < CY / 8;
+            const unsigned sa = cv_smem(dst + row * Sh::DROW + ng * 256 + xe * 16);
+            const void* src = ok ? (const void*)(db8 + (vox * CY + ng * 8) * 2) : (const void*)db8;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(src), "r"(ok ? 16 : 0) : "memory");
+        }
+    };
+    for (int z = zb - 1; z <= zb + 1 && z <= ze; ++z) load_x(z);
+    if (zb < ze) load_d(zb);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tbase;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+                           ((128u >> 4) << 24);
+    // descriptors: base + (byte offset / 16) in the address field (shared addresses < 256 KB)
+    const uint64_t adesc0 = cv_desc(cv_smem(sx), 128, WP_CGS);
+    const uint64_t bdesc0 = cv_desc(cv_smem(sd), 128, 256);
+    auto issue_tile = [&](int z, bool first) {
+        const uint64_t as[3] = {adesc0 + (uint64_t)((xslot(z - 1) * WP_XPLANE) >> 4),
+                                adesc0 + (uint64_t)((xslot(z) * WP_XPLANE) >> 4),
+                                adesc0 + (uint64_t)((xslot(z + 1) * WP_XPLANE) >> 4)};
+        const uint64_t bs = bdesc0 + (uint64_t)((dslot(z) * Sh::DPLANE) >> 4);
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const uint32_t dcol = tmem + (uint32_t)((dz * 3 + dx) * N);
+#pragma unroll
+                for (int r = 0; r < WP_TY; ++r) {
+                    const uint64_t ad = as[dz] + (uint64_t)((r * WP_ROWB + dx * 16) >> 4);
+                    const uint64_t bd = bs + (uint64_t)((r * Sh::DROW) >> 4);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"((first && r == 0) ? 0 : 1));
+                }
+            }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         cv_smem(&mbar[(z - zb) & 1]))
+                     : "memory");
+    };
+    auto wait_tile = [&](int t) -> bool {   // the MMAs of tile t (t >= zb) have completed
+        const uint32_t parity = (uint32_t)(((t - zb) >> 1) & 1);
+        uint32_t done = 0;
+        for (long it = 0; it < CV_SPIN && !done; ++it) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(cv_smem(&mbar[(t - zb) & 1])), "r"(parity)
+                : "memory");
+        }
+        return done != 0;
+    };
+    bool alive = true;
+    float bsum = 0.f;   // db partial: column co = tid % 32 over rows tid / 32 of every plane
+    for (int z = zb; z < ze; ++z) {
+        // slots of plane z + 2 (input) and z + 1 (dY) were last read by tile z - 2
+        if (z - 2 >= zb && !wait_tile(z - 2)) alive = false;
+        if (z + 1 < ze) {
+            load_x(z + 2);
+            load_d(z + 1);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // plane z + 1 and dY z have landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (__syncthreads_or(!alive)) {
+            alive = false;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) issue_tile(z, z == zb);
+        if (db) {
+            const int co = tid & 31, row = tid >> 5;
+            if (co < CY) {
+                const unsigned char* p = sd + dslot(z) * Sh::DPLANE + row * Sh::DROW + (co >> 3) * 256 + (co & 7) * 2;
+#pragma unroll
+                for (int xe = 0; xe < WP_TX; ++xe) bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p + xe * 16));
+            }
+        }
+    }
+    // the last two tiles
+    if (alive) {
+        for (int t = ze - 2 < zb ? zb : ze - 2; t < ze; ++t)
+            if (!wait_tile(t)) alive = false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__syncthreads_or(!alive)) alive = false;
+    if (!alive && tid == 0) atomicOr(err, 2u);
+    if (alive && zb < ze) {
+        const long cta = ((long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 of regions (w / 4) * 5 .. : 0..4 and 5..8
+        const int m = (warp & 3) * 32 + lane;
+        const int g = m >> 3, ci = (g & 3) * 8 + (m & 7), dyi = g >> 2;
+        const int rb = (warp >> 2) * 5, re = (warp >> 2) ? 9 : 5;
+        for (int reg = rb; reg < re; ++reg) {
+            uint32_t r[N];
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(reg * N);
+            if constexpr (N == 32) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+            } else {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (dyi < 3) {
+                const int dz = reg / 3, dx = reg - dz * 3;
+                const int t = dz * 9 + dyi * 3 + dx;
+                float4* dst = reinterpret_cast<float4*>(part + (cta * 27L * 32 + (long)t * 32 + ci) * N);
+#pragma unroll
+                for (int q = 0; q < N / 4; ++q)
+                    dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                         __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            }
+        }
+        if (db && (tid & 31) < cout) atomicAdd(&db[tid & 31], bsum);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::TCOLS));
+}
+
+// dW[t][ci][co] += sum over the CTAs' partial blocks part[c][t][ci][0..N) (co < cout); one
+// thread per weight, fixed summation order.
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int ncta, int N, int cout, float* __restrict__ dW) {
+    const int total = 27 * 32 * cout;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int tci = e / cout, co = e - tci * cout;
+        const float* p = part + (long)tci * N + co;
+        float sum = 0.f;
+        for (int c = 0; c < ncta; ++c) sum += p[(long)c * 27 * 32 * N];
+        dW[e] += sum;
+    }
+}
+
 }  // namespace ins

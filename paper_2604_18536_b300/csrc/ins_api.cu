@@ -1762,6 +1762,7 @@ struct ins_closure {
     float* gW[4] = {};             // gradient accumulators used by ins_step_vjp
     float* gB[4] = {};
     unsigned int* err = nullptr;
+    float* wpart = nullptr;        // partial weight-gradient blocks of k_wgrad_plane (null: not used)
     int params_set = 0;
 };
 
@@ -1802,10 +1803,41 @@ ins_status conv_launch(ins_grid* g, ConvArgs a) {
     return INS_OK;
 }
 
+// Grid of k_wgrad_plane: 16 x 8 columns, z chunks for about one CTA per SM.
+dim3 wgrad_plane_grid(const ins_grid* g, int* zchunk) {
+    const long cols = (long)(g->nx / WP_TX) * (g->ny / WP_TY);
+    const long sms = device_sm_count();
+    int zc = (int)((cols * g->nz + sms - 1) / sms);
+    zc = zc < 1 ? 1 : (zc > g->nz ? g->nz : zc);
+    *zchunk = zc;
+    return dim3(g->nx / WP_TX, g->ny / WP_TY, (g->nz + zc - 1) / zc);
+}
+
 template <int CX, int CY>
 ins_status wgrad_launch(ins_grid* g, const __nv_bfloat16* X, const __nv_bfloat16* dY, int cin, int cout, float* dW,
-                        float* db, unsigned int* err) {
+                        float* db, unsigned int* err, float* part = nullptr) {
     if (!dW) return INS_OK;
+    if constexpr (CX == 32) {
+        // 32 input channels: staged planes, the tap shifts in the MMA descriptors (no gathers);
+        // about one CTA per SM (each holds all 27 tap accumulators in TMEM)
+        if (part && g->nx % WP_TX == 0 && g->ny % WP_TY == 0) {
+            constexpr int N = CY < 16 ? 16 : CY;
+            static bool pattr = false;
+            if (!pattr) {
+                INS_CUDA(cudaFuncSetAttribute(k_wgrad_plane<CY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              WpShape<N>::SMEM));
+                pattr = true;
+            }
+            int zc;
+            const dim3 grd = wgrad_plane_grid(g, &zc);
+            KLAUNCH(g, "wgrad", (k_wgrad_plane<CY><<<grd, 256, WpShape<N>::SMEM, g->stream>>>(
+                                    X, dY, g->nx, g->ny, g->nz, cout, zc, part, db, err)));
+            const int ncta = (int)(grd.x * grd.y * grd.z);
+            KLAUNCH(g, "wgrad_reduce", k_wgrad_reduce<<<(27 * 32 * cout + 255) / 256, 256, 0, g->stream>>>(
+                                           part, ncta, N, cout, dW));
+            return INS_OK;
+        }
+    }
     const long nvox = g->N;
     // tensor cores: 128 / CX taps per CTA, the voxels split over about two CTAs per SM in all
     constexpr int N = CY < 16 ? 16 : CY;
@@ -1860,7 +1892,7 @@ ins_status closure_backward(ins_grid* g, ins_closure* c, const T* mbar, T* ubar,
     const long nvox = g->N;
     KLAUNCH(g, "pack_input", k_pack_input<T><<<592, 256, 0, g->stream>>>(mbar, nvox, c->g4));
     ins_status s;
-    if ((s = wgrad_launch<32, 8>(g, c->x[3], c->g4, 32, 3, dW[3], db[3], c->err)) != INS_OK) return s;
+    if ((s = wgrad_launch<32, 8>(g, c->x[3], c->g4, 32, 3, dW[3], db[3], c->err, c->wpart)) != INS_OK) return s;
     ConvArgs a{};
     a.err = c->err;
     // layer 4 data gradient through GELU of layer 3
@@ -1872,7 +1904,7 @@ ins_status closure_backward(ins_grid* g, ins_closure* c, const T* mbar, T* ubar,
     __nv_bfloat16* gin = c->ga;
     __nv_bfloat16* gout = c->gb;
     for (int l = 2; l >= 1; --l) {
-        if ((s = wgrad_launch<32, 32>(g, c->x[l], gin, 32, 32, dW[l], db[l], c->err)) != INS_OK) return s;
+        if ((s = wgrad_launch<32, 32>(g, c->x[l], gin, 32, 32, dW[l], db[l], c->err, c->wpart)) != INS_OK) return s;
         a.x = gin;
         a.wblob = c->wt[l];
         a.y = gout;
@@ -2035,6 +2067,14 @@ ins_status ins_closure_create(ins_grid* g, ins_closure** out) {
     o_gb = off; off += al((size_t)nv * 32 * 2);
     o_g4 = off; off += al((size_t)nv * 8 * 2);
     o_err = off; off += al(4);
+    size_t o_wp = 0;
+    const bool plane_wgrad = g->nx % WP_TX == 0 && g->ny % WP_TY == 0;
+    if (plane_wgrad) {
+        int zc;
+        const dim3 wg = wgrad_plane_grid(g, &zc);
+        o_wp = off;
+        off += al((size_t)wg.x * wg.y * wg.z * 27 * 32 * 32 * sizeof(float));
+    }
     cudaError_t e = cudaMalloc(&c->buf, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -2053,6 +2093,7 @@ ins_status ins_closure_create(ins_grid* g, ins_closure** out) {
     c->gb = reinterpret_cast<__nv_bfloat16*>(b + o_gb);
     c->g4 = reinterpret_cast<__nv_bfloat16*>(b + o_g4);
     c->err = reinterpret_cast<unsigned int*>(b + o_err);
+    c->wpart = plane_wgrad ? reinterpret_cast<float*>(b + o_wp) : nullptr;
     bool ok = cudaMemset(c->buf, 0, off) == cudaSuccess;
     ins_status st = INS_OK;
     if (ok) st = conv_attr<1, 32, EPI_GELU>();
