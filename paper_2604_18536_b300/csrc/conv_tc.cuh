@@ -714,7 +714,12 @@ __global__ void __launch_bounds__(256, 1) k_wgrad_plane(const __nv_bfloat16* __r
         return done != 0;
     };
     bool alive = true;
-    float bsum = 0.f;   // db partial: column co = tid % 32 over rows tid / 32 of every plane
+    // db partials: the dY tile of a plane is 8 rows x N/8 groups x 16 voxels of 16-byte entries;
+    // thread t sums entries t, t + 256, ..., all of channel group (t / 16) % (N / 8), into 8
+    // channel sums (16-byte shared loads, every warp an equal share)
+    float bsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    constexpr int DB_ENT = WP_TY * (N / 8) * WP_TX;   // 512 or 256
+    const int dbg = (tid >> 4) % (N / 8);
     for (int z = zb; z < ze; ++z) {
         // slots of plane z + 2 (input) and z + 1 (dY) were last read by tile z - 2
         if (z - 2 >= zb && !wait_tile(z - 2)) alive = false;
@@ -732,12 +737,20 @@ __global__ void __launch_bounds__(256, 1) k_wgrad_plane(const __nv_bfloat16* __r
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) issue_tile(z, z == zb);
-        if (db) {
-            const int co = tid & 31, row = tid >> 5;
-            if (co < CY) {
-                const unsigned char* p = sd + dslot(z) * Sh::DPLANE + row * Sh::DROW + (co >> 3) * 256 + (co & 7) * 2;
+        if (db && dbg < CY / 8) {
+            const unsigned char* p = sd + dslot(z) * Sh::DPLANE;
 #pragma unroll
-                for (int xe = 0; xe < WP_TX; ++xe) bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p + xe * 16));
+            for (int e = tid; e < DB_ENT; e += 256) {
+                const int row = e / ((N / 8) * WP_TX), r2 = e - row * ((N / 8) * WP_TX);
+                const int xe = r2 - (r2 / WP_TX) * WP_TX;
+                const uint4 q = *reinterpret_cast<const uint4*>(p + row * Sh::DROW + dbg * 256 + xe * 16);
+                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+                for (int c2 = 0; c2 < 4; ++c2) {
+                    const float2 f = __bfloat1622float2(h[c2]);
+                    bsum[2 * c2] += f.x;
+                    bsum[2 * c2 + 1] += f.y;
+                }
             }
         }
     }
@@ -788,7 +801,17 @@ __global__ void __launch_bounds__(256, 1) k_wgrad_plane(const __nv_bfloat16* __r
                                          __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
             }
         }
-        if (db && (tid & 31) < cout) atomicAdd(&db[tid & 31], bsum);
+        if (db) {
+            // lanes 0..15 and 16..31 of a warp share a channel group
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                for (int o = 8; o > 0; o >>= 1) bsum[c] += __shfl_xor_sync(0xffffffffu, bsum[c], o);
+            if ((lane & 15) == 0 && dbg < CY / 8) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (dbg * 8 + c < cout) atomicAdd(&db[dbg * 8 + c], bsum[c]);
+            }
+        }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
