@@ -98,84 +98,227 @@ __device__ __forceinline__ void st2(float* __restrict__ b, int a, float x, float
     *reinterpret_cast<float2*>(b + a) = make_float2(x, y);
 }
 
-// Register neighbourhoods of the two cells from a ring slot (pair index idx of the own pair):
-// values of the o plane not carried from the previous plane, and the p plane.
-__device__ __forceinline__ void nb2_load_o(Nb<float>& a, Nb<float>& b, const float2 (*o)[PLN], int idx) {
+// Packed FP32 pairs: the two cells of a thread run the same arithmetic, so the F evaluations
+// use the paired instructions add/sub/mul/fma.rn.f32x2 (each lane rounds like the scalar
+// instruction, so the results are those of nb_Fx / nb_Fy / nb_Fz bit for bit).
+union P2 {
+    float2 f;
+    unsigned long long u;
+};
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) {
+    P2 A, B, R;
+    A.f = a;
+    B.f = b;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(R.u) : "l"(A.u), "l"(B.u));
+    return R.f;
+}
+__device__ __forceinline__ float2 p2mul(float2 a, float2 b) {
+    P2 A, B, R;
+    A.f = a;
+    B.f = b;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(R.u) : "l"(A.u), "l"(B.u));
+    return R.f;
+}
+__device__ __forceinline__ float2 p2fma(float2 a, float2 b, float2 c) {
+    P2 A, B, C, R;
+    A.f = a;
+    B.f = b;
+    C.f = c;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(R.u) : "l"(A.u), "l"(B.u), "l"(C.u));
+    return R.f;
+}
+__device__ __forceinline__ float2 p2neg(float2 a) {   // exact: flips both sign bits
+    P2 A;
+    A.f = a;
+    A.u ^= 0x8000000080000000ull;
+    return A.f;
+}
+__device__ __forceinline__ float2 p2b(float x) { return make_float2(x, x); }
+
+// The register neighbourhood of the two cells as pairs (field f = (cell a, cell b)).
+struct NbP {
+    float2 X0, X0e, X0w, X0n, X0s, X0wn;
+    float2 Y0, Y0e, Y0w, Y0n, Y0s, Y0es;
+    float2 Z0, Z0e, Z0w, Z0n, Z0s;
+    float2 Xp, Xpw, Yp, Yps, Zp;
+    float2 Xm, Ym, Zm, Zme, Zmn;
+    float2 cx, cy, cz;
+};
+
+// Per-thread constants of the packed evaluations (the row coefficients do not change along z).
+struct NbPC {
+    float2 dx, dz, fx, fy, fz, bp, bm, ap, am, wl, wr;
+    float2 ncx, ncz, ncx2, ncz2, nyf, nys;   // negated convection coefficients
+    float2 ndsx, ndsy, ndsz;                 // negated diagonal diffusion sums of F^x, F^y, F^z
+};
+
+template <bool WALL>
+__device__ __forceinline__ NbPC nbp_consts(const RhsCoef<float>& c, const YRow<float>& y) {
+    NbPC k;
+    k.dx = p2b(c.dx);
+    k.dz = p2b(c.dz);
+    k.fx = p2b(c.fx);
+    k.fy = p2b(c.fy);
+    k.fz = p2b(c.fz);
+    k.bp = p2b(y.bp);
+    k.bm = p2b(y.bm);
+    k.ap = p2b(y.ap);
+    k.am = p2b(y.am);
+    k.wl = p2b(y.wl);
+    k.wr = p2b(y.wr);
+    k.ncx = p2b(-c.cx);
+    k.ncz = p2b(-c.cz);
+    k.ncx2 = p2b(-(WALL ? 2.f * c.cx : c.cx));
+    k.ncz2 = p2b(-(WALL ? 2.f * c.cz : c.cz));
+    k.nyf = p2b(-y.f);
+    k.nys = p2b(-y.s);
+    // the same sums as nb_Fx / nb_Fy / nb_Fz form
+    float dsx = 2.f * c.dx + y.bp + y.bm;
+    dsx += 2.f * c.dz;
+    float dsy = 2.f * c.dx + y.ap + y.am;
+    dsy += 2.f * c.dz;
+    k.ndsx = p2b(-dsx);
+    k.ndsy = p2b(-dsy);
+    k.ndsz = p2b(-(2.f * (c.dx + c.dz) + y.bp + y.bm));
+    return k;
+}
+
+__device__ __forceinline__ float2 nbp_Fx(const NbPC& k, NbP& v) {
+    const float2 uc = v.X0, ue = v.X0e, uw = v.X0w, un = v.X0n, us = v.X0s;
+    const float2 s1 = p2add(uc, ue), s2 = p2add(uw, uc);
+    const float2 X = p2fma(s1, s1, p2neg(p2mul(s2, s2)));
+    const float2 vp = p2add(v.Y0, v.Y0e), vm = p2add(v.Y0s, v.Y0es);
+    const float2 Y = p2fma(vp, p2add(uc, un), p2neg(p2mul(vm, p2add(us, uc))));
+    float2 acc = p2fma(k.dx, p2add(ue, uw), k.fx);
+    acc = p2fma(k.bp, un, acc);
+    acc = p2fma(k.bm, us, acc);
+    const float2 ut = v.Xp, ub = v.Xm;
+    const float2 wp = p2add(v.Z0, v.Z0e), sup = p2add(uc, ut);
+    const float2 Z = p2fma(wp, sup, p2neg(v.cx));
+    v.cx = p2mul(wp, sup);
+    acc = p2fma(k.dz, p2add(ut, ub), acc);
+    acc = p2fma(k.ncz, Z, acc);
+    acc = p2fma(k.ndsx, uc, acc);
+    acc = p2fma(k.ncx, X, acc);
+    return p2fma(k.nyf, Y, acc);
+}
+
+template <bool WALL>
+__device__ __forceinline__ float2 nbp_Fy(const NbPC& k, NbP& v) {
+    const float2 uc = v.Y0, un = v.Y0n, us = v.Y0s, ue = v.Y0e, uw = v.Y0w;
+    const float2 s1 = p2add(uc, un), s2 = p2add(us, uc);
+    const float2 Ys = p2fma(s1, s1, p2neg(p2mul(s2, s2)));
+    float2 vp, vm, wp;
+    if constexpr (WALL) {
+        vp = p2fma(k.wl, v.X0, p2mul(k.wr, v.X0n));
+        vm = p2fma(k.wl, v.X0w, p2mul(k.wr, v.X0wn));
+        wp = p2fma(k.wl, v.Z0, p2mul(k.wr, v.Z0n));
+    } else {
+        vp = p2add(v.X0, v.X0n);
+        vm = p2add(v.X0w, v.X0wn);
+        wp = p2add(v.Z0, v.Z0n);
+    }
+    const float2 X = p2fma(vp, p2add(uc, ue), p2neg(p2mul(vm, p2add(uw, uc))));
+    float2 acc = p2fma(k.dx, p2add(ue, uw), k.fy);
+    acc = p2fma(k.ap, un, acc);
+    acc = p2fma(k.am, us, acc);
+    const float2 ut = v.Yp, ub = v.Ym;
+    const float2 sup = p2add(uc, ut);
+    const float2 Z = p2fma(wp, sup, p2neg(v.cy));
+    v.cy = p2mul(wp, sup);
+    acc = p2fma(k.dz, p2add(ut, ub), acc);
+    acc = p2fma(k.ncz2, Z, acc);
+    acc = p2fma(k.ndsy, uc, acc);
+    acc = p2fma(k.nys, Ys, acc);
+    return p2fma(k.ncx2, X, acc);
+}
+
+__device__ __forceinline__ float2 nbp_Fz(const NbPC& k, NbP& v) {
+    const float2 uc = v.Z0, ut = v.Zp, ub = v.Zm, ue = v.Z0e, uw = v.Z0w, un = v.Z0n, us = v.Z0s;
+    const float2 s1 = p2add(uc, ut);
+    const float2 Zs = p2fma(s1, s1, p2neg(v.cz));
+    v.cz = p2mul(s1, s1);
+    const float2 vp = p2add(v.X0, v.Xp), vm = p2add(v.X0w, v.Xpw);
+    const float2 X = p2fma(vp, p2add(uc, ue), p2neg(p2mul(vm, p2add(uw, uc))));
+    const float2 wp = p2add(v.Y0, v.Yp), wm = p2add(v.Y0s, v.Yps);
+    const float2 Y = p2fma(wp, p2add(uc, un), p2neg(p2mul(wm, p2add(us, uc))));
+    float2 acc = p2fma(k.dx, p2add(ue, uw), k.fz);
+    acc = p2fma(k.dz, p2add(ut, ub), acc);
+    acc = p2fma(k.bp, un, acc);
+    acc = p2fma(k.bm, us, acc);
+    acc = p2fma(k.ndsz, uc, acc);
+    acc = p2fma(k.ncz, Zs, acc);
+    acc = p2fma(k.ncx, X, acc);
+    return p2fma(k.nyf, Y, acc);
+}
+
+// Register neighbourhood of the two cells from a ring slot (pair index idx of the own pair): the
+// o-plane values not carried from the previous plane, the p plane, and the m plane with the
+// carried o values of the first plane of a march.
+__device__ __forceinline__ void nbp_load_o(NbP& v, const float2 (*o)[PLN], int idx) {
     const float* of0 = reinterpret_cast<const float*>(o[0]);
     const float* of1 = reinterpret_cast<const float*>(o[1]);
     const float* of2 = reinterpret_cast<const float*>(o[2]);
-    const int f = 2 * idx;   // flat index of the first cell
-    const float2 xn = o[0][idx + PX], xs = o[0][idx - PX];
-    a.X0e = b.X0;
-    b.X0e = of0[f + 2];
-    a.X0n = xn.x;
-    b.X0n = xn.y;
-    a.X0s = xs.x;
-    b.X0s = xs.y;
-    a.X0wn = of0[f + PSX - 1];
-    b.X0wn = xn.x;
-    const float2 yn = o[1][idx + PX];
-    a.Y0e = b.Y0;
-    b.Y0e = of1[f + 2];
-    a.Y0w = of1[f - 1];
-    b.Y0w = a.Y0;
-    a.Y0n = yn.x;
-    b.Y0n = yn.y;
-    a.Y0es = b.Y0s;
-    b.Y0es = of1[f - PSX + 2];
-    const float2 zn = o[2][idx + PX], zs = o[2][idx - PX];
-    a.Z0e = b.Z0;
-    b.Z0e = of2[f + 2];
-    a.Z0w = of2[f - 1];
-    b.Z0w = a.Z0;
-    a.Z0n = zn.x;
-    b.Z0n = zn.y;
-    a.Z0s = zs.x;
-    b.Z0s = zs.y;
+    const int f = 2 * idx;
+    const float2 xn = o[0][idx + PX];
+    v.X0e = make_float2(v.X0.y, of0[f + 2]);
+    v.X0n = xn;
+    v.X0s = o[0][idx - PX];
+    v.X0wn = make_float2(of0[f + PSX - 1], xn.x);
+    v.Y0e = make_float2(v.Y0.y, of1[f + 2]);
+    v.Y0w = make_float2(of1[f - 1], v.Y0.x);
+    v.Y0n = o[1][idx + PX];
+    v.Y0es = make_float2(v.Y0s.y, of1[f - PSX + 2]);
+    v.Z0e = make_float2(v.Z0.y, of2[f + 2]);
+    v.Z0w = make_float2(of2[f - 1], v.Z0.x);
+    v.Z0n = o[2][idx + PX];
+    v.Z0s = o[2][idx - PX];
 }
 
-__device__ __forceinline__ void nb2_load_p(Nb<float>& a, Nb<float>& b, const float2 (*p)[PLN], int idx) {
+__device__ __forceinline__ void nbp_load_p(NbP& v, const float2 (*p)[PLN], int idx) {
     const float* pf0 = reinterpret_cast<const float*>(p[0]);
-    const float2 xp = p[0][idx], yp = p[1][idx], yps = p[1][idx - PX], zp = p[2][idx];
-    a.Xp = xp.x;
-    b.Xp = xp.y;
-    a.Xpw = pf0[2 * idx - 1];
-    b.Xpw = xp.x;
-    a.Yp = yp.x;
-    b.Yp = yp.y;
-    a.Yps = yps.x;
-    b.Yps = yps.y;
-    a.Zp = zp.x;
-    b.Zp = zp.y;
+    v.Xp = p[0][idx];
+    v.Xpw = make_float2(pf0[2 * idx - 1], v.Xp.x);
+    v.Yp = p[1][idx];
+    v.Yps = p[1][idx - PX];
+    v.Zp = p[2][idx];
 }
 
-// m plane and the carried o values of the first plane of a march
-__device__ __forceinline__ void nb2_init(Nb<float>& a, Nb<float>& b, const float2 (*m)[PLN], const float2 (*o)[PLN],
-                                         int idx) {
+__device__ __forceinline__ void nbp_init(NbP& v, const float2 (*m)[PLN], const float2 (*o)[PLN], int idx) {
     const float* mf2 = reinterpret_cast<const float*>(m[2]);
     const float* of0 = reinterpret_cast<const float*>(o[0]);
-    const float2 xm = m[0][idx], ym = m[1][idx], zm = m[2][idx], zmn = m[2][idx + PX];
-    a.Xm = xm.x;
-    b.Xm = xm.y;
-    a.Ym = ym.x;
-    b.Ym = ym.y;
-    a.Zm = zm.x;
-    b.Zm = zm.y;
-    a.Zme = zm.y;
-    b.Zme = mf2[2 * idx + 2];
-    a.Zmn = zmn.x;
-    b.Zmn = zmn.y;
-    const float2 x0 = o[0][idx], y0 = o[1][idx], y0s = o[1][idx - PX], z0 = o[2][idx];
-    a.X0 = x0.x;
-    b.X0 = x0.y;
-    a.X0w = of0[2 * idx - 1];
-    b.X0w = x0.x;
-    a.Y0 = y0.x;
-    b.Y0 = y0.y;
-    a.Y0s = y0s.x;
-    b.Y0s = y0s.y;
-    a.Z0 = z0.x;
-    b.Z0 = z0.y;
+    v.Xm = m[0][idx];
+    v.Ym = m[1][idx];
+    v.Zm = m[2][idx];
+    v.Zme = make_float2(v.Zm.y, mf2[2 * idx + 2]);
+    v.Zmn = m[2][idx + PX];
+    v.X0 = o[0][idx];
+    v.X0w = make_float2(of0[2 * idx - 1], v.X0.x);
+    v.Y0 = o[1][idx];
+    v.Y0s = o[1][idx - PX];
+    v.Z0 = o[2][idx];
+}
+
+template <bool WALL>
+__device__ __forceinline__ void nbp_carry_init(NbP& v, const NbPC& k) {
+    v.cx = p2mul(p2add(v.Zm, v.Zme), p2add(v.Xm, v.X0));
+    const float2 wm = WALL ? p2fma(k.wl, v.Zm, p2mul(k.wr, v.Zmn)) : p2add(v.Zm, v.Zmn);
+    v.cy = p2mul(wm, p2add(v.Ym, v.Y0));
+    const float2 s2 = p2add(v.Zm, v.Z0);
+    v.cz = p2mul(s2, s2);
+}
+
+__device__ __forceinline__ void nbp_rotate(NbP& v) {
+    v.Xm = v.X0;
+    v.Ym = v.Y0;
+    v.Zm = v.Z0;
+    v.Zme = v.Z0e;
+    v.Zmn = v.Z0n;
+    v.X0 = v.Xp;
+    v.X0w = v.Xpw;
+    v.Y0 = v.Yp;
+    v.Y0s = v.Yps;
+    v.Z0 = v.Zp;
 }
 
 // Grid (ceil(nx/64), ceil(ny/8), ceil(nz/kchunk)), block (32, 8), dynamic shared memory
@@ -325,10 +468,10 @@ __global__ void __launch_bounds__(RNT, 2)
         fzp0 = eval_Fz<float, WALL, PSX, PairPlane>(c, yr, m, o, pp, 2 * idx);
         fzp1 = eval_Fz<float, WALL, PSX, PairPlane>(c, yr, m, o, pp, 2 * idx + 1);
     }
-    Nb<float> na, nb;
-    nb2_init(na, nb, su[slot(kb - 1)], su[slot(kb)], idx);
-    nb_carry_init<float, WALL>(na, yr);
-    nb_carry_init<float, WALL>(nb, yr);
+    const NbPC kp = nbp_consts<WALL>(c, yr);
+    NbP nv;
+    nbp_init(nv, su[slot(kb - 1)], su[slot(kb)], idx);
+    nbp_carry_init<WALL>(nv, kp);
     __syncthreads();   // the slot of plane kb - 2 is refilled in the first iteration
 
     int buf = 0;
@@ -338,11 +481,11 @@ __global__ void __launch_bounds__(RNT, 2)
             if (k + 4 <= ke) stage_load(k + 4);
         }
         const int sm = slot(k - 1), so = slot(k), sp = slot(k + 1);
-        nb2_load_o(na, nb, su[so], idx);
-        nb2_load_p(na, nb, su[sp], idx);
-        const float fx0 = nb_Fx<float, WALL>(c, yr, na), fx1 = nb_Fx<float, WALL>(c, yr, nb);
-        float fy0 = nb_Fy<float, WALL>(c, yr, na), fy1 = nb_Fy<float, WALL>(c, yr, nb);
-        const float fz0 = nb_Fz<float, WALL>(c, yr, na), fz1 = nb_Fz<float, WALL>(c, yr, nb);
+        nbp_load_o(nv, su[so], idx);
+        nbp_load_p(nv, su[sp], idx);
+        const float2 fxp = nbp_Fx(kp, nv), fyp = nbp_Fy<WALL>(kp, nv), fzp = nbp_Fz(kp, nv);
+        const float fx0 = fxp.x, fx1 = fxp.y, fz0 = fzp.x, fz1 = fzp.y;
+        float fy0 = fyp.x, fy1 = fyp.y;
         if (WALL && j == ny - 1) fy0 = fy1 = 0.f;
         sFy[buf][ty + 1][tx] = make_float2(fy0, fy1);
         if (hy) {
@@ -369,8 +512,7 @@ __global__ void __launch_bounds__(RNT, 2)
         }
         fzp0 = fz0;
         fzp1 = fz1;
-        nb_rotate<float>(na);
-        nb_rotate<float>(nb);
+        nbp_rotate(nv);
         buf ^= 1;
     }
 }
