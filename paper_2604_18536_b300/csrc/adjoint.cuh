@@ -145,7 +145,8 @@ namespace ins {
 // a CTA of 32 x 8 threads owns a 32 x 8 column and a chunk of planes; the planes k-1, k,
 // k+1 of u and w (all three components, one-cell halo in x and y, which covers every
 // diagonal neighbour J + e_a - e_b the gather form reads) sit in dynamic shared memory as a
-// ring, and plane k+2 is loaded into registers while plane k is computed.
+// four-slot ring; plane k+2 is loaded into registers while plane k is computed and stored into
+// the slot of plane k-2 before the iteration's single barrier.
 constexpr int AJX = 32, AJY = 8;
 constexpr int AJSX = AJX + 2, AJSY = AJY + 2, AJSP = AJSX * AJSY;
 constexpr int AJNT = AJX * AJY;
@@ -204,13 +205,13 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
             }
     };
     auto wz = [nz](int k) { return k < 0 ? k + nz : (k >= nz ? k - nz : k); };
-    int sm = 0, so = 1, sp = 2;
+    auto slot = [kb0](int q) { return (q - kb0 + 1) & 3; };   // plane q >= kb0 - 1
     fetch(wz(kb0 - 1));
-    commit(sm);
+    commit(slot(kb0 - 1));
     fetch(wz(kb0));
-    commit(so);
+    commit(slot(kb0));
     fetch(wz(kb0 + 1));
-    commit(sp);
+    commit(slot(kb0 + 1));
     __syncthreads();
     const int c0 = (ty + 1) * AJSX + (tx + 1);
     // offsets within a plane: +x = 1, +y = AJSX
@@ -219,7 +220,8 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
         const bool more = k + 1 < ke;
         if (more) fetch(wz(k + 2));
         if (ok) {
-            const T* P[3] = {s[sm][0], s[so][0], s[sp][0]};   // base pointers of planes k-1, k, k+1
+            const T* P[3] = {s[slot(k - 1)][0], s[slot(k)][0], s[slot(k + 1)][0]};   // planes k-1, k, k+1
+            T lpart = (T)0;   // sum over the three faces of u . diffusion(w) / nu
             // value of field f (0-2 u, 3-5 w) at J + (dx, dy, dz)
             auto at = [&](int f, int dx, int dy, int dz) { return P[dz + 1][f * AJSP + c0 + dx + dy * AJSX]; };
             const long J = (long)k * plane + (long)j * nx + i;
@@ -249,21 +251,16 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
                 }
                 T ubs = fma(c.nu, lap, acc);
                 if (extra) ubs += extra[a * N + J];
-                nup += (double)ua0 * (double)lap;
+                lpart = fma(ua0, lap, lpart);
                 const long e = a * N + J;
                 const T old = ubar0[e];
                 ubar0[e] = old + ubs;
                 if (kb) kb[e] = fma(dtb, ybar ? ybar[e] : old, dta * ubs);
             }
+            nup += (double)lpart;
         }
-        __syncthreads();
-        if (more) commit(sm);
-        {
-            const int t = sm;
-            sm = so;
-            so = sp;
-            sp = t;
-        }
+        // plane k + 2 into the slot of plane k - 2, which no thread reads after the previous barrier
+        if (more) commit(slot(k + 2));
         __syncthreads();
     }
     for (int o = 16; o > 0; o >>= 1) nup += __shfl_xor_sync(0xffffffffu, nup, o);

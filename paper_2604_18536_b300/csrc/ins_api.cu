@@ -804,7 +804,7 @@ struct Impl {
         int akc = (int)(((long)abx * aby * g->nz) / 1184);
         akc = akc < 1 ? 1 : (akc > g->nz ? g->nz : akc);
         const dim3 ag(abx, aby, (g->nz + akc - 1) / akc);
-        const size_t adj_smem = 3 * 6 * AJSP * sizeof(T);
+        const size_t adj_smem = 4 * 6 * AJSP * sizeof(T);
         if (DIM == 3) INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem));
         const long nblk = DIM == 3 ? (long)ag.x * ag.y * ag.z : (long)cg.x * cg.y * cg.z;
         const size_t need = 5 * ((fld + 255) & ~size_t(255)) + (size_t)nblk * 8;
