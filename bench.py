@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-closure", action="store_true")
     ap.add_argument("--no-channel", action="store_true")
     ap.add_argument("--no-wray3", action="store_true")
+    ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="FP64 size sweep 128^3..840^3 only (one JSON line)")
     return ap.parse_args()
 
@@ -232,22 +233,37 @@ def run_ours(args):
         clk = ClockSampler(local)
         clk.start()
         time.sleep(0.3)
-        g.profile(True)
+        # the timed steps: ins_step_n (the steps after the first replay a CUDA graph of one step),
+        # no per-kernel events
         l0 = g.launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step_n(u, args.steps, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = g.launch_count() - l0
+        clocks = clk.stop()
+        barrier()
+        ms_max = max_over_ranks(ms)
+        # the same K steps as plain ins_step calls (the reference for the adjoint ratio), then once
+        # more with a CUDA-event pair around every kernel (per-kernel durations and shares)
         e0.record(stream)
         for _ in range(args.steps):
             g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        launches = g.launch_count() - l0
+        ms_plain = max_over_ranks(e0.elapsed_time(e1))
+        g.profile(True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_prof = max_over_ranks(e0.elapsed_time(e1))
         prof = g.profile_read()
         g.profile(False)
-        clocks = clk.stop()
-        barrier()
-        ms_max = max_over_ranks(ms)
         diag = g.diag(u)
         # roofline of the dominant kernel (largest share of event-timed time)
         tot = sum(v[1] for v in prof.values())
@@ -270,6 +286,7 @@ def run_ours(args):
         step_s = ms_max / args.steps / 1e3
         value = replica_throughput(N, world, ms_max, args.steps)
         res = {"value": value, "ms_per_step": ms_max / args.steps, "roofline": roof, "kernels": kernels,
+               "ms_per_step_plain_launches": ms_plain / args.steps, "ms_per_step_profiled": ms_prof / args.steps,
                "gpu_launches": launches, "clocks": clocks,
                "step_hbm_frac": step_model_bytes(n, s) / step_s / 1e9 / hbm_peak,
                "final_ke": diag["ke"], "final_max_div": diag["max_div"], "workspace_bytes": g.workspace_bytes()}
@@ -280,7 +297,6 @@ def run_ours(args):
         nub = torch.zeros(1, dtype=torch.float64, device="cuda")
         g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar, nubar=nub)
         torch.cuda.synchronize()
-        g.profile(True)
         v0 = torch.cuda.Event(enable_timing=True)
         v1 = torch.cuda.Event(enable_timing=True)
         v0.record(stream)
@@ -288,10 +304,16 @@ def run_ours(args):
             g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar, nubar=nub)
         v1.record(stream)
         torch.cuda.synchronize()
+        vms = max_over_ranks(v0.elapsed_time(v1)) / kv
+        g.profile(True)
+        for _ in range(kv):
+            g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar, nubar=nub)
+        torch.cuda.synchronize()
         vprof = g.profile_read()
         g.profile(False)
-        vms = max_over_ranks(v0.elapsed_time(v1)) / kv
-        res["adjoint"] = {"ms_per_vjp": vms, "ratio": vms / (ms_max / args.steps), "vjps": kv,
+        # ratio against the step with the same (plain) launches
+        res["adjoint"] = {"ms_per_vjp": vms, "ratio": vms / (ms_plain / args.steps), "vjps": kv,
+                          "ratio_vs_graph_step": vms / (ms_max / args.steps),
                           "kernels": {k: {"launches": v[0], "avg_us": round(v[1] / v[0] * 1e3, 2)}
                                       for k, v in sorted(vprof.items(), key=lambda kv_: -kv_[1][1])}}
         del ybar, ubar
@@ -328,14 +350,20 @@ def run_ours(args):
             "config": {"workload": "3-D decaying isotropic turbulence, 256^3 periodic MAC grid, nu=1/1600, "
                                    "RK4 + per-stage projection, CFL 0.3 (device-side adaptive dt)",
                        "n": n, "cells": N, "global_batch": world, "l2": "inputs larger than L2 (no flush)",
+                       "timing": "K steps through ins_step_n (CUDA-graph replay after the first step) between CUDA "
+                                 "events; per-kernel durations from a separate pass of K plain steps with an event "
+                                 "pair around every kernel",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
+            "ms_per_step_plain_launches": prim["ms_per_step_plain_launches"],
+            "ms_per_step_profiled": prim["ms_per_step_profiled"],
             "roofline": prim["roofline"], "e2e": prim.get("e2e"), "gpu_launches": prim["gpu_launches"],
             "clocks": prim["clocks"], "step_hbm_frac": prim["step_hbm_frac"], "kernels": prim["kernels"],
             "adjoint_forward_ratio": prim["adjoint"]["ratio"], "adjoint": prim["adjoint"],
         }
         if "f32" in results and "f64" in results:
             f = results["f32"]
-            line["fp32"] = {k: f[k] for k in ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
+            line["fp32"] = {k: f[k] for k in ("value", "ms_per_step", "ms_per_step_plain_launches",
+                                               "ms_per_step_profiled", "roofline", "e2e", "gpu_launches",
                                                "step_hbm_frac", "kernels", "clocks", "adjoint") if k in f}
             line["fp32"]["speedup_vs_fp64"] = f["value"] / prim["value"]
         if not args.no_closure:
@@ -345,6 +373,8 @@ def run_ours(args):
             line["channel_large"] = bench_channel_large()
         if not args.no_wray3:
             line["wray3"] = bench_wray3(n, seed=args.seed)
+        if not args.no_diff:
+            line["differentiation"] = bench_differentiation(seed=args.seed)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(steps=1)
         print(json.dumps(line))
@@ -551,6 +581,67 @@ def bench_wray3(n=256, steps=10, warmup=3, seed=0):
 
 
 # ------------------------------------------------------------------ closure (tensor cores)
+def bench_differentiation(n=128, nsteps=16, reps=3, seed=0):
+    """Gradient of a 16-step unroll at 128^3 (3-D periodic turbulence, k0 = 4, nu = 1/1000): loss =
+    mean squared difference of u_16 to a target 16 steps ahead of the seeded field; torch.autograd over
+    ins_step (per-step checkpoints, stage recomputation, ins_step_vjp) for d/du0 and d/dnu. Reports the
+    forward unroll time and the forward + backward time per gradient, FP64 and FP32."""
+    import torch
+    from paper_2604_18536_b300 import inputs
+    from paper_2604_18536_b300 import autograd as ag
+    from paper_2604_18536_b300.solver import Grid
+    out = {"workload": "gradient of a %d-step RK4 unroll, %d^3 periodic, nu=1/1000, w.r.t. u0 and nu" % (nsteps, n)}
+    raw = inputs.spectrum_velocity_raw(n, 3, seed=seed, k0=4.0, kmax=n // 4)
+    raw1 = inputs.spectrum_velocity_raw(n, 3, seed=seed + 1, k0=4.0, kmax=n // 4)
+    for tag, dtype in (("f64", torch.float64), ("f32", torch.float32)):
+        g = Grid(inputs.periodic_box(n, 3), ["periodic"] * 3, 1.0 / 1000, dtype=dtype)
+        ustar = torch.tensor(raw, dtype=dtype, device="cuda")
+        g.project(ustar, out=ustar)
+        ustar.mul_(1.0 / math.sqrt(g.diag(ustar)["ke"]))
+        pert = torch.tensor(raw1, dtype=dtype, device="cuda")
+        g.project(pert, out=pert)
+        pert.mul_(0.1 / math.sqrt(g.diag(pert)["ke"]))
+        dt = float(g.cfl_dt(ustar, CFL).item())
+        target = ustar.clone()
+        for _ in range(nsteps):
+            g.step(target, dt=dt)
+        u0 = ustar + pert
+
+        def grad_once():
+            u = u0.detach().clone().requires_grad_(True)
+            nut = torch.tensor(g.nu, dtype=torch.float64, device="cuda", requires_grad=True)
+            states = ag.rollout(u, g, dt, nsteps, nut)
+            loss = ((states[-1] - target) ** 2).mean()
+            loss.backward()
+            return u.grad, nut.grad
+
+        grad_once()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            with torch.no_grad():
+                u = u0.clone()
+                for _ in range(nsteps):
+                    g.step(u, dt=dt)
+        e1.record()
+        torch.cuda.synchronize()
+        fwd = e0.elapsed_time(e1) / reps
+        e0.record()
+        for _ in range(reps):
+            gu, gnu = grad_once()
+        e1.record()
+        torch.cuda.synchronize()
+        tot = e0.elapsed_time(e1) / reps
+        out[tag] = {"ms_forward_unroll": fwd, "ms_per_gradient": tot, "gradient_over_forward": tot / fwd,
+                    "backward_over_forward": (tot - fwd) / fwd,
+                    "grad_finite": bool(torch.isfinite(gu).all().item() and torch.isfinite(gnu).all().item())}
+        g.close()
+        del ustar, pert, target, u0
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_closure(n=64, reps=10):
     """CNN closure forward and backward at the LES size n^3 (FP32 grid, BF16 tensor cores)."""
     import torch

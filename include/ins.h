@@ -133,6 +133,16 @@ ins_status ins_divergence(ins_grid* g, const void* u, void* phi);
 ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host,
                     double* next_dt_dev, double cfl);
 
+/* nsteps consecutive ins_step calls with the same arguments (device-side dt: pass the same
+ * pointer as dt_dev and next_dt_dev to advance with the adaptive time step). The first step
+ * runs as plain launches; the following ones replay a CUDA graph of one step (captured once on
+ * a private stream and launched on g's stream; recaptured when u, the dt arguments, cfl, the
+ * stream or a setting of g changes), which removes the per-kernel launch gaps. Results equal
+ * nsteps ins_step calls bit for bit. Falls back to plain launches when the step cannot be
+ * captured. INS_ERR_ARG for nsteps < 0 and the argument errors of ins_step. */
+ins_status ins_step_n(ins_grid* g, void* u, int nsteps, const double* dt_dev, double dt_host, double* next_dt_dev,
+                      double cfl);
+
 /* Wall-normal pressure solve of a channel grid (Sec. 2.6.1 and 6): after the x and z FFTs,
  * INS_WALL_THOMAS solves the tridiagonal y system of every (kx, kz) mode in FP64 (any
  * spacing); INS_WALL_DCT diagonalises it with a DCT-II (uniform spacing only: the Neumann

@@ -67,6 +67,7 @@ SIGNATURES = {
     "ins_set_eddy_viscosity": (_c.c_int, [_vp, _c.c_int, _c.c_double]),
     "ins_eddy_viscosity": (_c.c_int, [_vp, _vp, _vp]),
     "ins_step": (_c.c_int, [_vp, _vp, _vp, _c.c_double, _vp, _c.c_double]),
+    "ins_step_n": (_c.c_int, [_vp, _vp, _c.c_int, _vp, _c.c_double, _vp, _c.c_double]),
     "ins_cfl_dt": (_c.c_int, [_vp, _vp, _c.c_double, _vp]),
     "ins_step_vjp": (_c.c_int, [_vp, _vp, _vp, _c.c_double, _vp, _vp, _vp]),
     "ins_spectrum": (_c.c_int, [_vp, _vp, _vp, _c.c_int]),

@@ -141,6 +141,12 @@ struct ins_grid {
     // allocated by the first ins_step_vjp call
     void* vjp = nullptr;
     size_t vjp_bytes = 0;
+    // CUDA graph of one ins_step, replayed by ins_step_n (captured on a private stream, launched
+    // on g->stream); recaptured when the key (pointers, dt, settings) changes
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    unsigned long long step_kernels = 0;   // kernels in the captured step
+    std::vector<double> graph_key;
     // launch accounting and opt-in per-kernel CUDA-event timing
     unsigned long long launches = 0;
     bool prof = false;
@@ -1418,6 +1424,8 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
 ins_status ins_grid_destroy(ins_grid* g) {
     if (!g) return INS_OK;
     cudaStreamSynchronize(g->stream);
+    if (g->step_exec) cudaGraphExecDestroy(g->step_exec);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     if (g->vjp) cudaFree(g->vjp);
     if (g->mbuf) cudaFree(g->mbuf);
     if (g->eddy_buf) cudaFree(g->eddy_buf);
@@ -1519,18 +1527,76 @@ ins_status ins_set_march_chunk(ins_grid* g, int planes) {
     return INS_OK;
 }
 
-ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host, double* next_dt_dev, double cfl) {
-    g_err.clear();
-    if (!g) return fail(INS_ERR_ARG, "null grid");
-    CHECK(check_ptr(g, u, "u"));
-    if (!dt_dev && !(std::isfinite(dt_host) && dt_host >= 0.0)) return fail(INS_ERR_ARG, "dt_host must be finite, >= 0");
-    if (next_dt_dev && !(std::isfinite(cfl) && cfl > 0.0)) return fail(INS_ERR_ARG, "cfl must be finite and > 0");
+static ins_status step_launch(ins_grid* g, void* u, const double* dt_dev, double dt_host, double* next_dt_dev,
+                              double cfl) {
     return dispatch_dtype(g, [&](auto z) {
         using T = decltype(z);
         return dispatch<T>(g, [&](auto impl) {
             return decltype(impl)::step(g, (T*)u, dt_dev, dt_host, next_dt_dev, cfl);
         });
     });
+}
+
+ins_status ins_step(ins_grid* g, void* u, const double* dt_dev, double dt_host, double* next_dt_dev, double cfl) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    CHECK(check_ptr(g, u, "u"));
+    if (!dt_dev && !(std::isfinite(dt_host) && dt_host >= 0.0)) return fail(INS_ERR_ARG, "dt_host must be finite, >= 0");
+    if (next_dt_dev && !(std::isfinite(cfl) && cfl > 0.0)) return fail(INS_ERR_ARG, "cfl must be finite and > 0");
+    return step_launch(g, u, dt_dev, dt_host, next_dt_dev, cfl);
+}
+
+ins_status ins_step_n(ins_grid* g, void* u, int nsteps, const double* dt_dev, double dt_host, double* next_dt_dev,
+                      double cfl) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    if (nsteps < 0) return fail(INS_ERR_ARG, "ins_step_n: nsteps must be >= 0");
+    if (nsteps == 0) return INS_OK;
+    // the first step runs as plain launches (lazy workspace, kernel attributes)
+    ins_status s = ins_step(g, u, dt_dev, dt_host, next_dt_dev, cfl);
+    if (s != INS_OK || nsteps == 1) return s;
+    const std::vector<double> key = {(double)reinterpret_cast<uintptr_t>(u), (double)reinterpret_cast<uintptr_t>(dt_dev),
+                                     dt_host, (double)reinterpret_cast<uintptr_t>(next_dt_dev), cfl,
+                                     (double)g->scheme, (double)g->fusion, (double)g->march_chunk, (double)g->use_dct,
+                                     (double)g->eddy, g->eddy_C, (double)reinterpret_cast<uintptr_t>(g->closure),
+                                     (double)reinterpret_cast<uintptr_t>(g->stream)};
+    if (!g->step_exec || key != g->graph_key) {
+        if (g->step_exec) {
+            cudaGraphExecDestroy(g->step_exec);
+            g->step_exec = nullptr;
+        }
+        if (!g->cap_stream) INS_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+        const cudaStream_t saved = g->stream;
+        const bool prof = g->prof;
+        const unsigned long long l0 = g->launches;
+        g->stream = g->cap_stream;
+        g->prof = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
+        ins_status cs = e == cudaSuccess ? step_launch(g, u, dt_dev, dt_host, next_dt_dev, cfl) : INS_ERR_CUDA;
+        if (e == cudaSuccess) e = cudaStreamEndCapture(g->cap_stream, &graph);
+        g->stream = saved;
+        g->prof = prof;
+        g->step_kernels = g->launches - l0;
+        g->launches = l0;   // captured, not run
+        if (cs == INS_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&g->step_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs != INS_OK || e != cudaSuccess || !g->step_exec) {
+            // the step cannot be captured here: plain launches
+            cudaGetLastError();
+            g->step_exec = nullptr;
+            g_err.clear();
+            for (int i = 1; i < nsteps; ++i)
+                if ((s = ins_step(g, u, dt_dev, dt_host, next_dt_dev, cfl)) != INS_OK) return s;
+            return INS_OK;
+        }
+        g->graph_key = key;
+    }
+    for (int i = 1; i < nsteps; ++i) {
+        INS_CUDA(cudaGraphLaunch(g->step_exec, g->stream));
+        g->launches += g->step_kernels;
+    }
+    return INS_OK;
 }
 
 ins_status ins_step_vjp(ins_grid* g, const void* u_n, const double* dt_dev, double dt_host, const void* ubar_np1,

@@ -214,6 +214,20 @@ class Grid:
                              _ptr(next_dt_dev), float(cfl)), "ins_step")
         return u
 
+    def step_n(self, u, nsteps, dt=None, dt_dev=None, next_dt_dev=None, cfl=0.3):
+        """nsteps RK4 steps in place (ins_step_n: the steps after the first replay a CUDA graph of one
+        step). Same arguments as step; results equal nsteps calls of step."""
+        self._check_u(u)
+        if dt_dev is None and dt is None:
+            raise ValueError("give dt or dt_dev")
+        for t in (dt_dev, next_dt_dev):
+            if t is not None and (t.dtype != torch.float64 or not t.is_cuda or t.numel() < 1):
+                raise ValueError("dt tensors must be CUDA float64")
+        self._sync_stream()
+        check(lib().ins_step_n(self._h, _ptr(u), int(nsteps), _ptr(dt_dev), float(dt if dt is not None else 0.0),
+                               _ptr(next_dt_dev), float(cfl)), "ins_step_n")
+        return u
+
     def step_vjp(self, u_n, ubar_np1, dt=None, dt_dev=None, ubar_n=None, nubar=None):
         """Pullback of one step (ins_step_vjp): returns (ubar_n, nubar) with nubar a CUDA float64
         tensor of one element that the nu-derivative is added to (a new zero tensor if None)."""
