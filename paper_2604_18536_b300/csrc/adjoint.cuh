@@ -222,6 +222,15 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
         if (ok) {
             const T* P[3] = {s[slot(k - 1)][0], s[slot(k)][0], s[slot(k + 1)][0]};   // planes k-1, k, k+1
             T lpart = (T)0;   // sum over the three faces of u . diffusion(w) / nu
+            // the finish's own-cell values first, so their loads overlap the stencil arithmetic
+            const long Jc = (long)k * plane + (long)j * nx + i;
+            T oldv[3], yv[3], xv[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                oldv[a] = ubar0[a * N + Jc];
+                yv[a] = ybar ? ybar[a * N + Jc] : oldv[a];
+                xv[a] = extra ? extra[a * N + Jc] : (T)0;
+            }
             // value of field f (0-2 u, 3-5 w) at J + (dx, dy, dz)
             auto at = [&](int f, int dx, int dy, int dz) { return P[dz + 1][f * AJSP + c0 + dx + dy * AJSX]; };
             const long J = (long)k * plane + (long)j * nx + i;
@@ -250,12 +259,11 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
                     lap = fma(c.l2[b], wabp + wabm - (T)2 * wa0, lap);
                 }
                 T ubs = fma(c.nu, lap, acc);
-                if (extra) ubs += extra[a * N + J];
+                if (extra) ubs += xv[a];
                 lpart = fma(ua0, lap, lpart);
                 const long e = a * N + J;
-                const T old = ubar0[e];
-                ubar0[e] = old + ubs;
-                if (kb) kb[e] = fma(dtb, ybar ? ybar[e] : old, dta * ubs);
+                ubar0[e] = oldv[a] + ubs;
+                if (kb) kb[e] = fma(dtb, yv[a], dta * ubs);
             }
             nup += (double)lpart;
         }

@@ -402,12 +402,24 @@ __global__ void __launch_bounds__(256, 3) k_adj_rhs_wall_z(WallAdjG<T> c, const 
         const bool more = k + 2 <= ke;
         if (more) load(k + 2);
         if (own) {
+            // the finish's own-cell values first, so their loads overlap the stencil arithmetic
+            const int P = (k * ny + j) * nx + i;
+            T old[3], yv[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                old[a] = ubar0[a * N + P];
+                yv[a] = ybar ? ybar[a * N + P] : old[a];
+            }
             A.so[0] = slot(k - 1);
             A.so[1] = slot(k);
             A.so[2] = slot(k + 1);
             T q[3];
             wall_adj_cell<T, 3>(rc, ny, c.nu, j, A, q, nup);
-            wall_adj_finish<T, 3>(c, N, (k * ny + j) * nx + i, q, ybar, ubar0, kbar, dtb, dta);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                ubar0[a * N + P] = old[a] + q[a];
+                if (kbar) kbar[a * N + P] = fma(dtb, yv[a], dta * q[a]);
+            }
         }
         if (more) store(k + 2);
         __syncthreads();
