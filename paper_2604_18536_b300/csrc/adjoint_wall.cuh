@@ -319,7 +319,7 @@ struct SharedWallAcc {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_adj_rhs_wall_z(WallAdjG<T> c, const T* __restrict__ u,
+__global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const T* __restrict__ u,
                                                         const T* __restrict__ w, const T* __restrict__ ybar,
                                                         T* __restrict__ ubar0, T* __restrict__ kbar,
                                                         double* __restrict__ nu_part, int kchunk) {
