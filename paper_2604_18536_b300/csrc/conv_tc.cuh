@@ -207,6 +207,16 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0 && more) issue_tile(z + 1, b ^ 1);
+        // the data gradient's pre-activations of tile z, loaded before the wait so that their
+        // latency overlaps the MMAs
+        __align__(16) float zi[EPI == EPI_DGELU ? NH : 1];
+        if constexpr (EPI == EPI_DGELU) {
+            if (inside) {
+                const float4* zs = reinterpret_cast<const float4*>(a.zin + (((long)z * ny + vy) * nx + vx) * N + c0);
+#pragma unroll
+                for (int q = 0; q < NH / 4; ++q) reinterpret_cast<float4*>(zi)[q] = zs[q];
+            }
+        }
         // wait for the MMAs of tile z (bounded)
         uint32_t done = 0;
         for (long it = 0; it < CV_SPIN && !done; ++it) {
@@ -265,10 +275,6 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
                 for (int q = 0; q < NH / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
             } else if (EPI == EPI_DGELU) {
                 __align__(16) __nv_bfloat16 o[NH];
-                __align__(16) float zi[NH];
-                const float4* zs = reinterpret_cast<const float4*>(a.zin + v * N + c0);
-#pragma unroll
-                for (int q = 0; q < NH / 4; ++q) reinterpret_cast<float4*>(zi)[q] = zs[q];
 #pragma unroll
                 for (int c = 0; c < NH; ++c) o[c] = __float2bfloat16_rn(__uint_as_float(r[c]) * cv_gelu_grad(zi[c]));
                 uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N + c0);
