@@ -118,10 +118,11 @@ def test_step_and_step_vjp_with_closure(dtype):
     g.set_closure(None)
 
 
-@pytest.mark.parametrize("n", [(16, 16, 8), (24, 32, 6)])
+@pytest.mark.parametrize("n", [(16, 16, 8), (24, 32, 6), (48, 32, 5)])
 def test_last_layer_weight_gradient_tight(n):
     """Tensor-core weight gradient of the output layer on the GPU's own BF16 operands: the saved
-    layer input x_3 and the BF16-rounded output cotangent. Only the FP32 summation order differs
+    layer input x_3 and the BF16-rounded output cotangent (sizes with nx % 16 = ny % 8 = 0 take the
+    staged-plane kernel, (24, 32, 6) the gathering one; nz = 5 splits z raggedly). Only the FP32 summation order differs
     from the FP64 oracle (conv_wgrad), so the relative error is at FP32 level; the bias gradient
     is the sum of the rounded cotangent."""
     g, og, c, W, b, params = make(n)

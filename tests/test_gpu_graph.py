@@ -78,3 +78,13 @@ def test_step_n_arguments_and_launch_count():
     n1 = g.launch_count()
     g.step_n(u, 4, dt=1e-3)
     assert g.launch_count() - n1 == 4 * per_step
+
+
+def test_step_n_with_eddy_viscosity_model():
+    g, u0 = setup("c3", torch.float64)
+    g.set_eddy_viscosity("wale")
+    a, b = u0.clone(), u0.clone()
+    for _ in range(3):
+        g.step(a, dt=1e-3)
+    g.step_n(b, 3, dt=1e-3)
+    assert torch.equal(a, b)

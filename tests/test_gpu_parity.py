@@ -290,6 +290,33 @@ def test_fp32_pair_and_single_cell_fusion_agree(name):
     assert rel(host(out[2]), timestep.rk4_step(og, u0, dt)) <= TOL[torch.float32]
 
 
+@pytest.mark.parametrize("shape", [(4, 3, 2), (60, 9, 5), (72, 9, 5)])
+@pytest.mark.parametrize("bc", ["periodic", "wall"])
+def test_pair_kernels_on_small_and_ragged_grids(shape, bc):
+    """The two-cells-per-thread kernels on grids narrower than one 64-wide tile, with a ragged
+    second tile, ragged rows and few planes: bit-identical to the one-cell kernels, and the
+    oracle's step within the FP32 tolerance."""
+    nx, ny, nz = shape
+    U = inputs.uniform_faces
+    if bc == "wall":
+        faces, bcs, force = [U(nx, 0, 4 * PI), inputs.tanh_faces(ny, 0, 2, 1.5), U(nz, 0, 2.0)], \
+            ["periodic", "wall", "periodic"], [1.0, 0.0, 0.0]
+    else:
+        faces, bcs, force = [U(nx, 0, 2 * PI), U(ny, 0, 1.5), U(nz, 0, 1.0)], ["periodic"] * 3, None
+    og = OGrid(faces, bcs, 0.02, force)
+    gg = Grid(faces, bcs, 0.02, force, dtype=torch.float32)
+    u0 = rounded(rand_u(og, 31, project=True), torch.float32)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    out = {}
+    for level in (1, 2):
+        gg.set_step_fusion(level)
+        ut = dev(u0, torch.float32)
+        gg.step(ut, dt=dt)
+        out[level] = ut
+    assert torch.equal(out[1], out[2])
+    assert rel(host(out[2]), timestep.rk4_step(og, u0, dt)) <= TOL[torch.float32]
+
+
 def test_fusion_level_is_checked():
     from paper_2604_18536_b300._lib import InsError
     _, gg = grids("p3", torch.float32)
