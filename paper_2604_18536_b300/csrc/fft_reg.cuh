@@ -75,6 +75,16 @@ __device__ __forceinline__ void stage_a(cplx<T>* v, int j, const cplx<T>* __rest
     }
 }
 
+// The same with the twiddles W_L^{j k1} already in registers (w[k1], k1 < R1).
+template <typename T, int R1>
+__device__ __forceinline__ void stage_a_w(cplx<T>* v, int j, const cplx<T>* w) {
+    DftR<T, R1>::run(v);
+    if (j > 0) {
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], w[k1]);
+    }
+}
+
 template <typename T, int R1, int R2>
 struct RegShape {
     static constexpr int L = R1 * R2;
@@ -190,6 +200,7 @@ struct PipeShape {
     static constexpr size_t smem(bool scaled) {
         return 2 * (size_t)L * SP * sizeof(cplx<T>) + (scaled ? 2 * (size_t)L * TW * sizeof(T) : 0);
     }
+    static constexpr size_t smem_max() { return smem(true) > smem(false) ? smem(true) : smem(false); }
 };
 
 // Same modes, addressing and results as k_fft_strided_reg<T, R1, R2>; grid = any number of
@@ -227,6 +238,16 @@ __global__ void __launch_bounds__(PipeShape<T, R1, R2>::NT, 2) k_fft_strided_pip
         }
         fr_cp_commit();
     };
+    // a thread's stage-A index j = q is the same for every tile (and for the inverse's stage A
+    // in mode 2): its twiddles W_L^{q k1} are loaded once. k1 < max(R1, R2) where q < min(R1, R2)
+    // (both stages), else k1 < min(R1, R2); q k1 < L in both cases.
+    constexpr int RMIN = R1 < R2 ? R1 : R2;
+    cplx<T> twr[Sh::RM];
+    {
+        const int kmax = q < RMIN ? Sh::RM : RMIN;
+#pragma unroll
+        for (int k1 = 0; k1 < Sh::RM; ++k1) twr[k1] = (k1 > 0 && k1 < kmax) ? ldg_c(&tw[q * k1]) : cplx<T>{(T)1, (T)0};
+    }
     long tile = blockIdx.x;
     int b = 0;
     if (tile < ntiles) issue(tile, 0);
@@ -249,7 +270,7 @@ __global__ void __launch_bounds__(PipeShape<T, R1, R2>::NT, 2) k_fft_strided_pip
                 if (mode == 1) z = cconj(z);
                 v[r] = z;
             }
-            stage_a<T, R1>(v, q, tw);
+            stage_a_w<T, R1>(v, q, twr);
         }
         __syncthreads();   // the tile has been read: X becomes the exchange buffer
         if (q < R2) {
@@ -270,7 +291,7 @@ __global__ void __launch_bounds__(PipeShape<T, R1, R2>::NT, 2) k_fft_strided_pip
                     const T s = scb[(q + R1 * k2) * TW + c];
                     v[k2] = {v[k2].re * s, -v[k2].im * s};
                 }
-                stage_a<T, R2>(v, q, tw);
+                stage_a_w<T, R2>(v, q, twr);
             }
             __syncthreads();
             if (q < R1) {
@@ -350,6 +371,9 @@ __global__ void __launch_bounds__(PipeX<T, R1, R2>::NT, 2) k_fft_x_c2r_pipe(cons
     };
     const int q = threadIdx.x % RM;
     const int c = threadIdx.x / RM;
+    cplx<T> twr[R1];   // W_L^{q k1}: the same for every tile
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) twr[k1] = (k1 > 0 && q < R2) ? ldg_c(&tw[q * k1]) : cplx<T>{(T)1, (T)0};
     long tile = blockIdx.x;
     int b = 0;
     if (tile < ntiles) issue(tile, 0);
@@ -382,7 +406,7 @@ __global__ void __launch_bounds__(PipeX<T, R1, R2>::NT, 2) k_fft_x_c2r_pipe(cons
         if (q < R2) {
 #pragma unroll
             for (int r = 0; r < R1; ++r) v[r] = ex[c * SR + sidx(q + R2 * r)];
-            stage_a<T, R1>(v, q, tw);
+            stage_a_w<T, R1>(v, q, twr);
         }
         __syncthreads();
         if (q < R2) {
@@ -407,10 +431,11 @@ __global__ void __launch_bounds__(PipeX<T, R1, R2>::NT, 2) k_fft_x_c2r_pipe(cons
     fr_cp_wait0();
 }
 
-// x pass, real lines -> half spectra. CTA handles TW line pairs packed as a + i b.
-// Thread mapping (j fastest) keeps the loads along a line contiguous.
+// x pass, real lines -> half spectra. CTA handles TW line pairs packed as a + i b per tile and
+// walks the tiles (grid = tiles, or fewer CTAs that stay resident; the twiddles of a thread's
+// stage-A index are loaded once). Thread mapping (j fastest) keeps the loads along a line contiguous.
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_fft_x_r2c_reg(const cplx<T>* __restrict__ tw, const T* __restrict__ in,
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_fft_x_r2c_reg(const cplx<T>* __restrict__ tw, const T* __restrict__ in,
                                                        cplx<T>* __restrict__ S, int lines, int nxh) {
     using Sh = RegShape<T, R1, R2>;
     constexpr int L = Sh::L, TW = Sh::TW, RM = Sh::RM;
@@ -418,39 +443,65 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_fft_x_r2c_reg(c
     __shared__ cplx<T> ex[TW * SR];
     const int q = threadIdx.x % RM;      // j (stage A) / k1 (stage B)
     const int c = threadIdx.x / RM;
-    const long la = 2 * ((long)blockIdx.x * TW + c), lb = la + 1;
     auto sidx = [](int m) { return m + (m >> 4); };
-    cplx<T> v[RM];
-    if (q < R2) {
+    // FP32: the twiddles stay in registers; FP64 (one tile per CTA, register-heavy) loads them per use
+    constexpr int NTW = sizeof(T) == 4 ? R1 : 1;
+    cplx<T> twr[NTW];
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-        for (int r = 0; r < R1; ++r) {
-            const int m = q + R2 * r;
-            v[r] = {la < lines ? in[la * L + m] : (T)0, lb < lines ? in[lb * L + m] : (T)0};
+        for (int k1 = 0; k1 < R1; ++k1) twr[k1] = (k1 > 0 && q < R2) ? ldg_c(&tw[q * k1]) : cplx<T>{(T)1, (T)0};
+    }
+    const long ntiles = (((long)lines + 1) / 2 + TW - 1) / TW;
+    for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long la = 2 * (tile * TW + c), lb = la + 1;
+        cplx<T> v[RM];
+        if (q < R2) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                const int m = q + R2 * r;
+                v[r] = {la < lines ? in[la * L + m] : (T)0, lb < lines ? in[lb * L + m] : (T)0};
+            }
+            if constexpr (sizeof(T) == 4)
+                stage_a_w<T, R1>(v, q, twr);
+            else
+                stage_a<T, R1>(v, q, tw);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) ex[c * SR + sidx(q * R1 + k1)] = v[k1];
         }
-        stage_a<T, R1>(v, q, tw);
+        __syncthreads();
+        if (q < R1) {
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) ex[c * SR + sidx(q * R1 + k1)] = v[k1];
-    }
-    __syncthreads();
-    if (q < R1) {
+            for (int j = 0; j < R2; ++j) v[j] = ex[c * SR + sidx(j * R1 + q)];
+            DftR<T, R2>::run(v);
+        }
+        __syncthreads();
+        if (q < R1) {
 #pragma unroll
-        for (int j = 0; j < R2; ++j) v[j] = ex[c * SR + sidx(j * R1 + q)];
-        DftR<T, R2>::run(v);
-    }
-    __syncthreads();
-    if (q < R1) {
+            for (int k2 = 0; k2 < R2; ++k2) ex[c * SR + sidx(q + R1 * k2)] = v[k2];   // natural order
+        }
+        __syncthreads();
+        // split Z = A + i B into the half spectra of a and b (nxh = L / 2 + 1): thread (pair cs,
+        // frequency kk < L / 2), PPI pairs per sweep; the kk = 0 thread also writes kk = L / 2
+        const T h = (T)0.5;
+        constexpr int LH = L / 2, PPI = Sh::NT / LH;
+        static_assert(TW % PPI == 0, "pairs per tile must be a multiple of the pairs per sweep");
+        const int kk = threadIdx.x % LH, cs = threadIdx.x / LH;
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) ex[c * SR + sidx(q + R1 * k2)] = v[k2];   // natural order
-    }
-    __syncthreads();
-    const T h = (T)0.5;
-    for (int item = threadIdx.x; item < TW * nxh; item += blockDim.x) {
-        const int cc = item / nxh, kk = item - cc * nxh;
-        const long a = 2 * ((long)blockIdx.x * TW + cc), b = a + 1;
-        const cplx<T> Z = ex[cc * SR + sidx(kk)];
-        const cplx<T> Zc = cconj(ex[cc * SR + sidx(kk == 0 ? 0 : L - kk)]);
-        if (a < lines) S[a * nxh + kk] = {h * (Z.re + Zc.re), h * (Z.im + Zc.im)};
-        if (b < lines) S[b * nxh + kk] = {h * (Z.im - Zc.im), -h * (Z.re - Zc.re)};
+        for (int it = 0; it < TW / PPI; ++it) {
+            const int cc = it * PPI + cs;
+            const long a = 2 * (tile * TW + cc), b = a + 1;
+            const cplx<T> Z = ex[cc * SR + sidx(kk)];
+            const cplx<T> Zc = cconj(ex[cc * SR + sidx(kk == 0 ? 0 : L - kk)]);
+            if (a < lines) S[a * nxh + kk] = {h * (Z.re + Zc.re), h * (Z.im + Zc.im)};
+            if (b < lines) S[b * nxh + kk] = {h * (Z.im - Zc.im), -h * (Z.re - Zc.re)};
+            if (kk == 0) {
+                const cplx<T> Zn = ex[cc * SR + sidx(LH)];
+                const cplx<T> Znc = cconj(Zn);
+                if (a < lines) S[a * nxh + LH] = {h * (Zn.re + Znc.re), h * (Zn.im + Znc.im)};
+                if (b < lines) S[b * nxh + LH] = {h * (Zn.im - Znc.im), -h * (Zn.re - Znc.re)};
+            }
+        }
+        __syncthreads();   // ex is rewritten by the next tile
     }
 }
 

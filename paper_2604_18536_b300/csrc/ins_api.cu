@@ -263,7 +263,7 @@ void launch_strided_reg(cudaStream_t st, const cplx<T>* tw, cplx<T>* S, long nco
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_fft_strided_pipe<T, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Ph::smem(true));
+                             (int)Ph::smem_max());
         attr = true;
     }
     const long ntiles = (ncol + Ph::TW - 1) / Ph::TW;
@@ -306,11 +306,24 @@ void launch_x_reg(bool forward, cudaStream_t st, const cplx<T>* tw, const T* in,
     }
     using Sh = RegShape<T, R1, R2>;
     const long pairs = (lines + 1) / 2;
-    const unsigned blocks = (unsigned)((pairs + Sh::TW - 1) / Sh::TW);
-    if (forward)
+    const long ntiles = (pairs + Sh::TW - 1) / Sh::TW;
+    if (forward) {
+        // FP32: as many CTAs as stay resident, each walking tiles (twiddles loaded once per CTA)
+        long cap = ntiles;
+        if (sizeof(T) == 4) {
+            static int per_sm = 0;
+            if (!per_sm) {
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_x_r2c_reg<T, R1, R2>, Sh::NT, 0);
+                if (per_sm < 1) per_sm = 1;
+            }
+            cap = (long)per_sm * device_sm_count();
+        }
+        const unsigned blocks = (unsigned)(ntiles < cap ? ntiles : cap);
         k_fft_x_r2c_reg<T, R1, R2><<<blocks, Sh::NT, 0, st>>>(tw, in, S, lines, nxh);
-    else
-        k_fft_x_c2r_reg<T, R1, R2><<<blocks, Sh::NT, 0, st>>>(tw, S, out, lines, nxh);
+        return;
+    }
+    const unsigned blocks = (unsigned)ntiles;
+    k_fft_x_c2r_reg<T, R1, R2><<<blocks, Sh::NT, 0, st>>>(tw, S, out, lines, nxh);
 }
 
 template <typename T>
