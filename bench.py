@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--dtypes", default="f64,f32")
     ap.add_argument("--no-closure", action="store_true")
     ap.add_argument("--no-channel", action="store_true")
+    ap.add_argument("--no-channel-large", action="store_true", help="skip the 512x1024x256 channel point")
     ap.add_argument("--no-wray3", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="FP64 size sweep 128^3..840^3 only (one JSON line)")
@@ -370,7 +371,8 @@ def run_ours(args):
             line["closure"] = bench_closure()
         if not args.no_channel:
             line["channel"] = bench_channel()
-            line["channel_large"] = bench_channel_large()
+            if not args.no_channel_large:
+                line["channel_large"] = bench_channel_large()
         if not args.no_wray3:
             line["wray3"] = bench_wray3(n, seed=args.seed)
         if not args.no_diff:
