@@ -752,9 +752,8 @@ struct Impl {
             } else {
                 ra.a_next = A[st];
                 ra.b = 0.0;
-                ra.stage = 0;
-                KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(
-                                            make_geo<T>(g), F, rp, U[0], scratch, U[st + 1], ra));
+                ra.stage = 0;   // us = u0 + dt a k only (no acc)
+                if ((s = rk_update<false>(g, F, rp, U[0], nullptr, U[st + 1], ra)) != INS_OK) return s;
             }
         }
         const long n = (long)g->dim * N;
@@ -880,12 +879,11 @@ struct Impl {
             ra.dt_host = dt_host;
             ra.a_next = A[st];
             ra.b = 0.0;
-            ra.stage = 0;     // writes us = u0 + dt a k (and a scratch acc), leaves u0 untouched
+            ra.stage = 0;     // writes us = u0 + dt a k only (no acc), leaves u0 untouched
             ra.last = 0;
             ra.mx = nullptr;
             ra.err_flag = g->err_flag;
-            KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(
-                                        make_geo<T>(g), F, rp, U[0], scratch, U[st + 1], ra));
+            if ((s = rk_update<false>(g, F, rp, U[0], nullptr, U[st + 1], ra)) != INS_OK) return s;
         }
         // reverse
         INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));

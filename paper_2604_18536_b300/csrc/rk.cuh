@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
                         av[e] = bb * kk[cc][e];
                         uv[e] = fma(dta, kk[cc][e], uv[e]);
                     }
-                    VT::st(acc + ea, av);
+                    if (acc) VT::st(acc + ea, av);   // null: stage state only (the step VJP's recompute)
                     VT::st(us + ea, uv);
                 } else if (ra.stage < 3) {
                     VT::ld(acc + ea, av);

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) k_rk_update(Geo<T> g, const T* __restrict
                     bad |= !isfinite(un);
                 }
             } else if (ra.stage == 0) {
-                acc[e] = bb * kk[c];
+                if (acc) acc[e] = bb * kk[c];   // null: stage state only (the step VJP's recompute)
                 us[e] = u0v + dta * kk[c];
             } else if (ra.stage < 3) {
                 acc[e] = acc[e] + bb * kk[c];
