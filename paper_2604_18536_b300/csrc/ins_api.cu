@@ -555,7 +555,7 @@ struct Impl {
     // Launch the stage update (vector z-march kernel when the rows allow it).
     template <bool LS>
     static ins_status rk_update(ins_grid* g, const T* F, const T* rp, T* u0, T* acc, T* us, const RkArgs& ra) {
-        if (rk_vec_ok<T>(g, u0) && (!LS || us == nullptr)) {
+        if (rk_vec_ok<T>(g, u0) && (us == nullptr || reinterpret_cast<uintptr_t>(us) % 16 == 0)) {
             constexpr int VEC = VecT<T>::N;
             RkCoef<T> rc;
             rc.nx = g->nx;
@@ -747,8 +747,7 @@ struct Impl {
                 ra.a_next = WRAY3_GAMMA[st];
                 ra.b = WRAY3_ZETA[st];
                 ra.stage = st;
-                KLAUNCH(g, "rk_update", (k_rk_update<T, DIM, WALL, true><<<cg, dim3(32, 8), 0, g->stream>>>(
-                                            make_geo<T>(g), F, rp, U[st], scratch, U[st + 1], ra)));
+                if ((s = rk_update<true>(g, F, rp, U[st], scratch, U[st + 1], ra)) != INS_OK) return s;
             } else {
                 ra.a_next = A[st];
                 ra.b = 0.0;
@@ -866,8 +865,7 @@ struct Impl {
             ra.last = 0;
             ra.mx = nullptr;
             ra.err_flag = g->err_flag;
-            KLAUNCH(g, "rk_update", (k_rk_update<T, DIM, WALL, true><<<cg, dim3(32, 8), 0, g->stream>>>(
-                                        make_geo<T>(g), F, rp, U[st], scratch, U[st + 1], ra)));
+            if ((s = rk_update<true>(g, F, rp, U[st], scratch, U[st + 1], ra)) != INS_OK) return s;
         }
         for (int st = 0; !lowst && st < 3; ++st) {
             T* m = nullptr;

@@ -7,8 +7,8 @@
 //   stage 3: u0 = u0 + dt (acc + b3 k) in place, the CFL per-index maxima of
 //            |u_{n+1}| and the non-finite flag;
 // and for the low-storage Wray scheme (LS; two registers u and k_{s-1}, Sec. 3.3)
-//   u0 = u0 + dt (gamma_s k + zeta_s acc) in place, acc = k (not on the last stage),
-//   the maxima and the flag on the last stage.
+//   u0 = u0 + dt (gamma_s k + zeta_s acc) in place (into us instead when us is not null),
+//   acc = k (not on the last stage), the maxima and the flag on the last stage.
 // Each thread owns VEC consecutive cells in x (one float4 / double2) of one row
 // j and marches through a chunk of z planes: the pressure of plane k+1 loaded
 // for G p in z is the centre pressure of the next plane, and the x neighbour of
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
                             else qz = fmax(qz, q);
                         }
                     }
-                    VT::st(u0 + ea, uv);
+                    VT::st((us ? us : u0) + ea, uv);
                 } else if (ra.stage == 0) {
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) {
