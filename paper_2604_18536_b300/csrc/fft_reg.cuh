@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_fft_strided_reg
 // after the current one is copied global -> shared with cp.async while the current one is
 // transformed, so the HBM latency is hidden behind the butterflies. The tile's shared
 // buffer (L rows of TW padded columns) also serves as the exchange buffer once stage A has
-// read it. Mode 2 prefetches the spectral scale of the tile the same way.
+// read it. Mode 2 computes the spectral factor from eigenvalue sums (one value per column,
+// the line's values in shared memory), so it reads nothing more than the spectrum.
 template <int BYTES>
 __device__ __forceinline__ void fr_cp_async(void* smem, const void* gmem, int src_bytes) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -189,6 +190,9 @@ __device__ __forceinline__ void fr_cp_commit() { asm volatile("cp.async.commit_g
 __device__ __forceinline__ void fr_cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void fr_cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+__device__ __forceinline__ float fr_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double fr_rcp(double x) { return 1.0 / x; }
+
 template <typename T, int R1, int R2>
 struct PipeShape {
     static constexpr int L = R1 * R2;
@@ -198,23 +202,27 @@ struct PipeShape {
     static constexpr int SP = TW + 1;
     static constexpr int PER = L * TW / NT;   // copies per thread per tile
     static constexpr size_t smem(bool scaled) {
-        return 2 * (size_t)L * SP * sizeof(cplx<T>) + (scaled ? 2 * (size_t)L * TW * sizeof(T) : 0);
+        return 2 * (size_t)L * SP * sizeof(cplx<T>) + (scaled ? (size_t)L * sizeof(T) : 0);
     }
     static constexpr size_t smem_max() { return smem(true) > smem(false) ? smem(true) : smem(false); }
 };
 
-// Same modes, addressing and results as k_fft_strided_reg<T, R1, R2>; grid = any number of
-// CTAs (persistent), dynamic shared memory PipeShape::smem(mode == 2).
+// Same modes and addressing as k_fft_strided_reg<T, R1, R2>; grid = any number of CTAs
+// (persistent), dynamic shared memory PipeShape::smem(mode == 2). Mode 2 forms the spectral
+// factor 1 / (N (lambda_col + lambda_line[m])) from N-scaled eigenvalue sums instead of
+// reading a table: eig[col] for the ncol columns, eig[ncol + m] along the line (L values),
+// eig[ncol + L] for the mean mode (column 0, m = 0); the factor's rounding differs from the
+// FP64-built table by about one unit in the last place.
 template <typename T, int R1, int R2>
 __global__ void __launch_bounds__(PipeShape<T, R1, R2>::NT, 2) k_fft_strided_pipe(const cplx<T>* __restrict__ tw,
                                                                                 cplx<T>* __restrict__ S, long ncol,
                                                                                 long cdiv, long outer, long lstride,
-                                                                                int mode, const T* __restrict__ scale) {
+                                                                                int mode, const T* __restrict__ eig) {
     using Sh = PipeShape<T, R1, R2>;
     constexpr int L = Sh::L, TW = Sh::TW, SP = Sh::SP;
     extern __shared__ __align__(16) unsigned char fr_smem[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(fr_smem);              // [2][L * SP]
-    T* sc = reinterpret_cast<T*>(buf + 2 * L * SP);                    // [2][L * TW] (mode 2)
+    T* sl = reinterpret_cast<T*>(buf + 2 * L * SP);                    // [L] line eigenvalues (mode 2)
     const long ntiles = (ncol + TW - 1) / TW;
     const int c = threadIdx.x % TW;
     const int q = threadIdx.x / TW;
@@ -234,7 +242,6 @@ __global__ void __launch_bounds__(PipeShape<T, R1, R2>::NT, 2) k_fft_strided_pip
         for (int t = 0; t < Sh::PER; ++t) {
             const int m = q + MSTEP * t;
             fr_cp_async<sizeof(cplx<T>)>(dst + m * SP + c, S + base + t * step, nb);
-            if (mode == 2) fr_cp_async<sizeof(T)>(sc + b * L * TW + m * TW + c, scale + base + t * step, nb / 2);
         }
         fr_cp_commit();
     };
@@ -247,6 +254,11 @@ __global__ void __launch_bounds__(PipeShape<T, R1, R2>::NT, 2) k_fft_strided_pip
         const int kmax = q < RMIN ? Sh::RM : RMIN;
 #pragma unroll
         for (int k1 = 0; k1 < Sh::RM; ++k1) twr[k1] = (k1 > 0 && k1 < kmax) ? ldg_c(&tw[q * k1]) : cplx<T>{(T)1, (T)0};
+    }
+    T inv_n = (T)0;
+    if (mode == 2) {
+        for (int m = threadIdx.x; m < L; m += Sh::NT) sl[m] = eig[ncol + m];   // visible after the first barrier
+        inv_n = eig[ncol + L];
     }
     long tile = blockIdx.x;
     int b = 0;
@@ -261,6 +273,7 @@ __global__ void __launch_bounds__(PipeShape<T, R1, R2>::NT, 2) k_fft_strided_pip
         const long col = tile * TW + c;
         const bool ok = col < ncol;
         const long cb = ok ? (col / cdiv) * outer + (col % cdiv) : 0;
+        const T lc = (mode == 2 && ok) ? __ldg(&eig[col]) : (T)1;
         cplx<T> v[Sh::RM];
         // forward stage A: thread (c, j = q < R2)
         if (q < R2) {
@@ -284,11 +297,11 @@ __global__ void __launch_bounds__(PipeShape<T, R1, R2>::NT, 2) k_fft_strided_pip
             DftR<T, R2>::run(v);   // v[k2] = X[q + R1 k2]
         }
         if (mode == 2) {
-            const T* scb = sc + b * L * TW;
             if (q < R1) {
 #pragma unroll
                 for (int k2 = 0; k2 < R2; ++k2) {
-                    const T s = scb[(q + R1 * k2) * TW + c];
+                    const int m = q + R1 * k2;
+                    const T s = (col == 0 && m == 0) ? inv_n : fr_rcp(lc + sl[m]);
                     v[k2] = {v[k2].re * s, -v[k2].im * s};
                 }
                 stage_a_w<T, R2>(v, q, twr);

@@ -108,6 +108,7 @@ struct ins_grid {
     int radix[3][FFT_MAX_STAGES];
     int nst[3] = {0, 0, 0};
     void* scale = nullptr;         // T, [nz][ny][nxh] (periodic)
+    float* eig = nullptr;          // FP32 periodic: N-scaled eigenvalue sums of the fused pass (see k_fft_strided_pipe)
     double* lam = nullptr;         // FP64 eigenvalues: x (nxh) | y (ny) | z (nz)
     double* th_lo = nullptr;       // Thomas: lo[ny]
     double* th_invm = nullptr;     // [ny][ncol]
@@ -369,8 +370,9 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
             lstride = (long)ny * nxh;
         }
         if (reg_fft_len(pl.L)) {
-            KLAUNCH(g, "fft_strided", strided_reg<T>(pl.L, st, pl.tw, S, ncol, cdiv, outer, lstride, mode,
-                                                     reinterpret_cast<const T*>(g->scale)));
+            // FP32: the fused pass forms its scale from the eigenvalue sums (no table read)
+            const T* sc = sizeof(T) == 4 ? reinterpret_cast<const T*>(g->eig) : reinterpret_cast<const T*>(g->scale);
+            KLAUNCH(g, "fft_strided", strided_reg<T>(pl.L, st, pl.tw, S, ncol, cdiv, outer, lstride, mode, sc));
             return INS_OK;
         }
         const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
@@ -1218,6 +1220,9 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     }
     o_lam = off; off += al(nsum * 8);
     const size_t o_qw = off; off += g->wall_dct ? al((size_t)g->ny * 2 * ts) : 0;
+    // FP32 periodic: [columns of the fused pass | its line | 1/N] (3-D: ny nxh | nz; 2-D: nxh | ny)
+    const size_t neig = (!wall_y && D.dtype == INS_F32) ? (size_t)(dim == 3 ? g->ny * nxh + g->nz : nxh + g->ny) + 1 : 0;
+    const size_t o_eig = off; off += al(neig * 4);
     if (!wall_y) {
         o_scale = off; off += al((size_t)spec * ts);
     } else {
@@ -1252,6 +1257,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     for (int a = 0; a < 3; ++a) g->tw[a] = b + o_tw[a];
     g->lam = reinterpret_cast<double*>(b + o_lam);
     g->dct_qw = g->wall_dct ? b + o_qw : nullptr;
+    g->eig = neig ? reinterpret_cast<float*>(b + o_eig) : nullptr;
     if (!wall_y) {
         g->scale = b + o_scale;
     } else {
@@ -1353,6 +1359,25 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
             }
         }
         ok &= up(g->lam, lam.data(), lam.size() * 8);
+        if (g->eig) {
+            // the fused forward/scale/inverse pass runs along z (3-D) or y (2-D); its column c is
+            // (kx, ky) = (c % nxh, c / nxh) in 3-D and kx = c in 2-D
+            const double ntot = (double)N;
+            const double* lx = lam.data();
+            const double* ly = lam.data() + g->nx;
+            const double* lz = lam.data() + g->nx + g->ny;
+            std::vector<float> ev;
+            if (dim == 3) {
+                for (int j = 0; j < g->ny; ++j)
+                    for (long i = 0; i < nxh; ++i) ev.push_back((float)(ntot * (lx[i] + ly[j])));
+                for (int k = 0; k < g->nz; ++k) ev.push_back((float)(ntot * lz[k]));
+            } else {
+                for (long i = 0; i < nxh; ++i) ev.push_back((float)(ntot * lx[i]));
+                for (int j = 0; j < g->ny; ++j) ev.push_back((float)(ntot * ly[j]));
+            }
+            ev.push_back((float)(1.0 / ntot));   // the mean mode's factor (as in the table)
+            ok &= up(g->eig, ev.data(), ev.size() * 4);
+        }
         if (!wall_y) {
             const double ntot = (double)N;
             if (D.dtype == INS_F64)
