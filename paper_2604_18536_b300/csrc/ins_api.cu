@@ -543,12 +543,11 @@ struct Impl {
     }
     static ins_status project(ins_grid* g, const T* uin, T* uout, T* p) {
         T* rp = reinterpret_cast<T*>(g->rp);
-        KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), uin, rp));
-        T* pp = p ? p : rp;
         ins_status s;
+        if ((s = div_fast(g, uin, rp)) != INS_OK) return s;
+        T* pp = p ? p : rp;
         if ((s = poisson<T>(g, rp, pp)) != INS_OK) return s;
-        KLAUNCH(g, "sub_grad", k_sub_grad<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), uin, pp, uout));
-        return INS_OK;
+        return sub_grad_fast(g, uin, pp, uout);
     }
     static ins_status divergence(ins_grid* g, const T* u, T* phi) {
         KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi));
@@ -576,6 +575,60 @@ struct Impl {
             KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL, LS><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(
                                         make_geo<T>(g), F, rp, u0, acc, us, ra));
         }
+        return INS_OK;
+    }
+    // phi = D u and out = src - G p through the vector z-march kernels when the rows allow it
+    // (the step VJP's P^T and ins_project), else the one-cell kernels.
+    static dim3 vec_grid(const ins_grid* g, int* kc) {
+        constexpr int VEC = VecT<T>::N;
+        const int bx = (g->nx / VEC + 31) / 32, by = (g->ny + 7) / 8;
+        int c = (int)(((long)bx * by * g->nz) / 2368);
+        c = c < 1 ? 1 : (c > g->nz ? g->nz : c);
+        *kc = c;
+        return dim3(bx, by, (g->nz + c - 1) / c);
+    }
+    static ins_status div_fast(ins_grid* g, const T* u, T* phi) {
+        if (rk_vec_ok<T>(g, u) && reinterpret_cast<uintptr_t>(phi) % 16 == 0) {
+            DivCoef<T> dc;
+            dc.nx = g->nx;
+            dc.ny = g->ny;
+            dc.nz = g->nz;
+            dc.idx = (T)(1.0 / g->d[0][0]);
+            dc.idz = (T)(1.0 / g->d[2][0]);
+            dc.idy = make_geo<T>(g).c[1] + (size_t)C_INV_D * g->ny;
+            int kc;
+            const dim3 grd = vec_grid(g, &kc);
+            KLAUNCH(g, "divergence", (k_divergence_vec<T, DIM, WALL><<<grd, dim3(32, 8), 0, g->stream>>>(dc, u, phi, kc)));
+            return INS_OK;
+        }
+        KLAUNCH(g, "divergence", (k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi)));
+        return INS_OK;
+    }
+    static ins_status sub_grad_fast(ins_grid* g, const T* src, const T* p, T* out) {
+        if (rk_vec_ok<T>(g, src) && reinterpret_cast<uintptr_t>(out) % 16 == 0 && reinterpret_cast<uintptr_t>(p) % 16 == 0) {
+            RkCoef<T> rc;
+            rc.nx = g->nx;
+            rc.ny = g->ny;
+            rc.nz = g->nz;
+            rc.ihx = (T)(1.0 / g->h[0][0]);
+            rc.ihz = (T)(1.0 / g->h[2][0]);
+            rc.ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
+            RkArgs ra;
+            ra.dt_dev = nullptr;
+            ra.dt_host = 0.0;
+            ra.a_next = 0.0;
+            ra.b = 0.0;
+            ra.stage = -1;   // out = src - G p only
+            ra.last = 0;
+            ra.mx = nullptr;
+            ra.err_flag = g->err_flag;
+            int kc;
+            const dim3 grd = vec_grid(g, &kc);
+            KLAUNCH(g, "sub_grad", (k_rk_update_vec<T, DIM, WALL, false><<<grd, dim3(32, 8), 0, g->stream>>>(
+                                       rc, src, p, nullptr, nullptr, out, ra, kc)));
+            return INS_OK;
+        }
+        KLAUNCH(g, "sub_grad", (k_sub_grad<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), src, p, out)));
         return INS_OK;
     }
     // Wray's low-storage 3-stage RK (two registers: F and k_{s-1}); u is updated in place.
@@ -905,9 +958,9 @@ struct Impl {
         ac.dt_host = dt_host;
         for (int st = nst - 1; st >= 0; --st) {
             // w = P kbar_s (P is symmetric on a uniform periodic grid)
-            KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp));
+            if ((s = div_fast(g, F, rp)) != INS_OK) return s;
             if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
-            KLAUNCH(g, "sub_grad", k_sub_grad<T, DIM, WALL><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, W));
+            if ((s = sub_grad_fast(g, F, rp, W)) != INS_OK) return s;
             if (lowst) {
                 // kbar_{s-1} = dt gamma_{s-1} (Ubar_{s+1} + ubar_s) + dt zeta_s Ubar_{s+1}
                 ac.bn = st > 0 ? WRAY3_GAMMA[st - 1] + WRAY3_ZETA[st] : 0.0;

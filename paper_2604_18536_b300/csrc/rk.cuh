@@ -6,6 +6,7 @@
 //   stage 1,2: acc += b k;  us = u0 + dt a k
 //   stage 3: u0 = u0 + dt (acc + b3 k) in place, the CFL per-index maxima of
 //            |u_{n+1}| and the non-finite flag;
+//   stage -1 (projection only): us = F - G p (u0 and acc are not touched);
 // and for the low-storage Wray scheme (LS; two registers u and k_{s-1}, Sec. 3.3)
 //   u0 = u0 + dt (gamma_s k + zeta_s acc) in place (into us instead when us is not null),
 //   acc = k (not on the last stage), the maxima and the flag on the last stage.
@@ -123,6 +124,10 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
 #pragma unroll
             for (int cc = 0; cc < DIM; ++cc) {
                 const long ea = cc * N + a;
+                if (!LS && ra.stage < 0) {   // projection only: us = F - G p
+                    VT::st(us + ea, kk[cc]);
+                    continue;
+                }
                 T uv[VEC], av[VEC];
                 VT::ld(u0 + ea, uv);
                 if (LS) {
@@ -207,6 +212,75 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
             }
         }
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(ra.err_flag, 1u);
+    }
+}
+
+// phi = D u (App. B divergence kernel) with the same thread layout and z march: VEC cells in x
+// per thread, the x neighbour u^x_{i-1} of the first cell from the previous lane (or global
+// memory at a warp or row start), u^z of plane k - 1 carried along the march. x and z uniform
+// and periodic; y periodic or a wall (u^y below the bottom wall is 0), 1/d_y[j] per row.
+template <typename T>
+struct DivCoef {
+    int nx, ny, nz;
+    T idx, idz;          // 1/d of the uniform x and z directions
+    const T* idy;        // 1/d_y[j]
+};
+
+// Block (32, 8); grid (ceil(nx/VEC/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx % VEC == 0 and
+// 16-byte aligned u and phi.
+template <typename T, int DIM, bool WALL>
+__global__ void __launch_bounds__(256) k_divergence_vec(DivCoef<T> c, const T* __restrict__ u, T* __restrict__ phi,
+                                                        int kchunk) {
+    using VT = VecT<T>;
+    constexpr int VEC = VT::N;
+    const int nx = c.nx, ny = c.ny, nz = c.nz;
+    const long N = (long)nx * ny * nz;
+    const long plane = (long)nx * ny;
+    const int nvx = nx / VEC;
+    const int lane = threadIdx.x, row = threadIdx.y;
+    const int iv = blockIdx.x * 32 + lane;
+    const int i0 = iv * VEC;
+    const int j = blockIdx.y * 8 + row;
+    const bool ok = iv < nvx && j < ny;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(kb + kchunk, nz);
+    const T idy = __ldg(&c.idy[j < ny ? j : ny - 1]);
+    const bool need_global_prev = iv == 0 || lane == 0;
+    const long jrow = (long)(j < ny ? j : 0) * nx;
+    const long jprev = (long)(j > 0 ? j - 1 : ny - 1) * nx;   // periodic wrap in y
+    const bool bottom = WALL && j == 0;
+    T Zm[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) Zm[e] = (T)0;
+    if (DIM == 3 && ok) VT::ld(u + 2 * N + (long)(kb == 0 ? nz - 1 : kb - 1) * plane + jrow + i0, Zm);
+    for (int k = kb; k < ke; ++k) {
+        const long base = (long)k * plane;
+        const long a = base + jrow + i0;
+        T ux[VEC], uy[VEC], uym[VEC], uz[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) ux[e] = uy[e] = uym[e] = uz[e] = (T)0;
+        if (ok) {
+            VT::ld(u + a, ux);
+            VT::ld(u + N + a, uy);
+            if (!bottom) VT::ld(u + N + base + jprev + i0, uym);
+            if (DIM == 3) VT::ld(u + 2 * N + a, uz);
+        }
+        T xprev = __shfl_up_sync(0xffffffffu, ux[VEC - 1], 1);
+        if (ok && need_global_prev) xprev = u[base + jrow + (iv == 0 ? nx - 1 : i0 - 1)];
+        if (ok) {
+            T d[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const T xm = e > 0 ? ux[e - 1] : xprev;
+                T v = (ux[e] - xm) * c.idx;
+                v += (uy[e] - uym[e]) * idy;
+                if (DIM == 3) v += (uz[e] - Zm[e]) * c.idz;
+                d[e] = v;
+            }
+            VT::st(phi + a, d);
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) Zm[e] = uz[e];
     }
 }
 
