@@ -98,7 +98,7 @@ struct RegShape {
 // (col / cdiv) * outer + m * lstride + (col % cdiv).
 // mode 0: forward, 1: inverse, 2: forward, times scale[addr], inverse.
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_fft_strided_reg(const cplx<T>* __restrict__ tw, cplx<T>* __restrict__ S,
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 256, 2) k_fft_strided_reg(const cplx<T>* __restrict__ tw, cplx<T>* __restrict__ S,
                                                          long ncol, long cdiv, long outer, long lstride, int mode,
                                                          const T* __restrict__ scale) {
     using Sh = RegShape<T, R1, R2>;
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(PipeX<T, R1, R2>::NT, 2) k_fft_x_c2r_pipe(cons
 // walks the tiles (grid = tiles, or fewer CTAs that stay resident; the twiddles of a thread's
 // stage-A index are loaded once). Thread mapping (j fastest) keeps the loads along a line contiguous.
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_fft_x_r2c_reg(const cplx<T>* __restrict__ tw, const T* __restrict__ in,
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 256, 3) k_fft_x_r2c_reg(const cplx<T>* __restrict__ tw, const T* __restrict__ in,
                                                        cplx<T>* __restrict__ S, int lines, int nxh) {
     using Sh = RegShape<T, R1, R2>;
     constexpr int L = Sh::L, TW = Sh::TW, RM = Sh::RM;
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3) k_fft_x_r2c_reg(c
 
 // x pass, half spectra -> real lines (unnormalised inverse).
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_fft_x_c2r_reg(const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ S,
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 256, sizeof(T) == 8 ? 3 : 2) k_fft_x_c2r_reg(const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ S,
                                                        T* __restrict__ out, int lines, int nxh) {
     using Sh = RegShape<T, R1, R2>;
     constexpr int L = Sh::L, TW = Sh::TW, RM = Sh::RM;
