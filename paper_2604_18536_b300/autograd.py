@@ -27,20 +27,27 @@ class _RK4Step(torch.autograd.Function):
         return ubar, nubar.reshape(()), None, None
 
 
-def step(u, grid, dt, nu=None):
-    """One differentiable RK4 step: u_{n+1} = step(u_n); gradients flow to u and nu."""
+def _nu_tensor(u, grid, nu):
+    """nu as a float64 tensor, checked against the grid's viscosity (one host read)."""
     if nu is None:
-        nu = torch.tensor(grid.nu, dtype=torch.float64, device=u.device)
+        return torch.tensor(grid.nu, dtype=torch.float64, device=u.device)
     if abs(float(nu.detach()) - grid.nu) > 1e-15 * max(1.0, abs(grid.nu)):
         raise ValueError("nu must equal the grid's viscosity (create a new grid to change it)")
-    return _RK4Step.apply(u, nu, grid, float(dt))
+    return nu
+
+
+def step(u, grid, dt, nu=None):
+    """One differentiable RK4 step: u_{n+1} = step(u_n); gradients flow to u and nu."""
+    return _RK4Step.apply(u, _nu_tensor(u, grid, nu), grid, float(dt))
 
 
 def rollout(u0, grid, dt, nsteps, nu=None):
-    """nsteps differentiable steps; returns the list of states u_1 .. u_nsteps."""
+    """nsteps differentiable steps; returns the list of states u_1 .. u_nsteps. nu is checked
+    once (its host read waits for the device), not at every step."""
+    nu = _nu_tensor(u0, grid, nu)
     out = []
     u = u0
     for _ in range(nsteps):
-        u = step(u, grid, dt, nu)
+        u = _RK4Step.apply(u, nu, grid, float(dt))
         out.append(u)
     return out
