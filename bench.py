@@ -154,12 +154,14 @@ TRAFFIC = {("f64", "rhs_div"): 907.1e6, ("f32", "update_rhs_div"): 1071.0e6}
 
 def step_model_bytes(n, s):
     """Model bytes of one RK4 step: 114 values per cell (F recomputed in the update; the minimum
-    traffic of the scheme)."""
+    traffic of the scheme: per stage u and F read and written by the fused evaluation and update, the
+    Poisson passes over the half spectrum)."""
     return 114 * n ** 3 * s
 
 
 # ------------------------------------------------------------------ replicas (N > 1)
-# The path does not shard (see DESIGN.md): N processes run independent replicas of the same
+# The path does not shard (every stencil needs a halo exchange and every Poisson solve all-to-all
+# transposes, which the single-GPU design does not do): N processes run independent replicas of the same
 # workload (seed + rank), synchronised by barriers around the timed region; the job time is
 # the slowest rank's and the throughput counts the cells of all ranks.
 def replica_barrier(world):
