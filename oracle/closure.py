@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 Paper: Sec. 4 (neural-network closure models inside the right-hand side of the
 LES solver, trained a posteriori through the unrolled solver; gradients by
 reverse-mode AD with hand-written pullbacks, Sec. 3.4). The paper names no
-architecture. Reading taken (a choice of this build):
+architecture. Reading taken (a choice, not the paper's):
 
 * input channels: u^x, u^y, u^z at the same storage index; output channel a is
   added to F^a at that index;

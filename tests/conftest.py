@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests are skipped, not failed, on a machine without a GPU only when
-    # they were selected implicitly; `-m gpu` on a GPU machine runs them.
+    # they were selected implicitly; `-m gpu` on a machine with a GPU runs them.
     try:
         import torch
         has_gpu = torch.cuda.is_available()
