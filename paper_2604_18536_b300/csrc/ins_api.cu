@@ -456,11 +456,11 @@ int device_sm_count();
 // bounds); a CTA costs about its planes plus two for its prologue (five staged planes without
 // an evaluation). Take the chunk that minimises waves x cost per CTA (the last wave counts as a
 // full one), or the caller's (ins_set_march_chunk).
-dim3 pair_grid(const ins_grid* g) {
+dim3 pair_grid(const ins_grid* g, int ctas_per_sm = 2) {
     const int nbx = (g->nx + 2 * RBX - 1) / (2 * RBX), nby = (g->ny + RBY - 1) / RBY;
     int kc = g->march_chunk;
     if (kc <= 0) {
-        const long resident = 2L * device_sm_count();
+        const long resident = (long)ctas_per_sm * device_sm_count();
         long best = -1;
         for (int c = 8; c <= 128; ++c) {
             const long ctas = (long)nbx * nby * ((g->nz + c - 1) / c);
@@ -491,7 +491,7 @@ ins_status launch_pair(ins_grid* g, const char* name, const float* Fs, const flo
                                       PairRegSmem::BYTES));
         attr = true;
     }
-    const dim3 grd = pair_grid(g);
+    const dim3 grd = pair_grid(g, pair_ctas_per_sm(WALL, STAGE));
     const int kc = (g->nz + grd.z - 1) / grd.z;
     const float* ihy = make_geo<float>(g).c[1] + (size_t)C_INV_H * g->ny;
     KLAUNCH(g, name, (k_rhs_div_x2<WALL, STAGE><<<grd, dim3(RBX, RBY, 1), PairRegSmem::BYTES, g->stream>>>(

@@ -331,8 +331,12 @@ struct PairRegSmem {
     static constexpr int BYTES = FXH * 8 + 2 * RBY * 4;
 };
 
+// Resident CTAs per SM the kernel is compiled for: the plain periodic evaluation fits 80
+// registers (three CTAs); the staged and the wall variants keep 128 (two CTAs, no spills).
+constexpr int pair_ctas_per_sm(bool wall, bool stage) { return (stage || wall) ? 2 : 3; }
+
 template <bool WALL, bool STAGE>
-__global__ void __launch_bounds__(RNT, 2)
+__global__ void __launch_bounds__(RNT, pair_ctas_per_sm(WALL, STAGE))
     k_rhs_div_x2(RhsCoef<float> c, float ihx, float ihz, const float* __restrict__ ihy, const float* __restrict__ Fs,
                   const float* __restrict__ p, const float* __restrict__ u0, float* __restrict__ acc,
                   float* __restrict__ F, float* __restrict__ r, FusedArgs fa, int kchunk) {
