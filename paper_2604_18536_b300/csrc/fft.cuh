@@ -327,8 +327,9 @@ __global__ void k_thomas(cplx<T>* __restrict__ S, const double* __restrict__ lo,
                          const double* __restrict__ cp, cplx<double>* __restrict__ dscr, int nxh, int ny, long ncol,
                          double norm) {
     // The loads do not depend on the recurrence: rows are fetched in batches of CH before
-    // each CH-step stretch of the (sequential) sweep, so CH loads per array are in flight.
-    constexpr int CH = 8;
+    // each CH-step stretch of the (sequential) sweep, so CH loads per array are in flight
+    // (one thread per column leaves few warps per SM: the batch depth carries the bandwidth).
+    constexpr int CH = 16;
     const long col = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (col >= ncol) return;
     const long base = (col / nxh) * (long)ny * nxh + (col % nxh);
