@@ -65,6 +65,70 @@ struct DftR<T, 16> {
     }
 };
 
+// 3-point DFT with constants: s = a1 + a2, d = a1 - a2, y0 = a0 + s, y1,2 = a0 - s/2 -+ i (sqrt3/2) d.
+template <typename T>
+struct DftR<T, 3> {
+    static __device__ __forceinline__ void run(cplx<T>* v) {
+        const T h3 = (T)0.86602540378443864676;   // sqrt(3)/2
+        const cplx<T> s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        const cplx<T> t = {v[0].re - (T)0.5 * s.re, v[0].im - (T)0.5 * s.im};
+        const cplx<T> e = {h3 * d.im, -h3 * d.re};   // -i (sqrt3/2) d
+        v[0] = cadd(v[0], s);
+        v[1] = cadd(t, e);
+        v[2] = csub(t, e);
+    }
+};
+
+// 6-point DFT as 3 x 2: DFT3 of (x[n2], x[n2+2], x[n2+4]) for n2 = 0, 1, twiddles W6^{n2 k1},
+// DFT2 over n2: X[k1 + 3 k2].
+template <typename T>
+struct DftR<T, 6> {
+    static __device__ __forceinline__ void run(cplx<T>* v) {
+        const T h3 = (T)0.86602540378443864676;
+        cplx<T> a[3] = {v[0], v[2], v[4]}, b[3] = {v[1], v[3], v[5]};
+        DftR<T, 3>::run(a);
+        DftR<T, 3>::run(b);
+        const cplx<T> b1 = cmul(b[1], cplx<T>{(T)0.5, -h3});    // W6
+        const cplx<T> b2 = cmul(b[2], cplx<T>{(T)-0.5, -h3});   // W6^2
+        v[0] = cadd(a[0], b[0]);
+        v[3] = csub(a[0], b[0]);
+        v[1] = cadd(a[1], b1);
+        v[4] = csub(a[1], b1);
+        v[2] = cadd(a[2], b2);
+        v[5] = csub(a[2], b2);
+    }
+};
+
+// 12-point DFT as 4 x 3: DFT4 of (x[n2], x[n2+3], x[n2+6], x[n2+9]) for n2 < 3, twiddles
+// W12^{n2 k1}, DFT3 over n2: X[k1 + 4 k2].
+template <typename T>
+struct DftR<T, 12> {
+    static __device__ __forceinline__ void run(cplx<T>* v) {
+        const T h3 = (T)0.86602540378443864676;
+        cplx<T> y[3][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 3; ++n2) {
+            cplx<T> t[4] = {v[n2], v[n2 + 3], v[n2 + 6], v[n2 + 9]};
+            Dft<T, 4>::run(t, nullptr, 0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) y[n2][k] = t[k];
+        }
+        y[1][1] = cmul(y[1][1], cplx<T>{h3, (T)-0.5});      // W12
+        y[1][2] = cmul(y[1][2], cplx<T>{(T)0.5, -h3});      // W12^2
+        y[1][3] = cmul_mi(y[1][3]);                           // W12^3 = -i
+        y[2][1] = cmul(y[2][1], cplx<T>{(T)0.5, -h3});      // W12^2
+        y[2][2] = cmul(y[2][2], cplx<T>{(T)-0.5, -h3});     // W12^4
+        y[2][3] = {-y[2][3].re, -y[2][3].im};                 // W12^6 = -1
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            cplx<T> t[3] = {y[0][k1], y[1][k1], y[2][k1]};
+            DftR<T, 3>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) v[k1 + 4 * k2] = t[k2];
+        }
+    }
+};
+
 // Stage A in registers: DFT_R1 over r of v[r] = x[j + R2 r], then v[k1] *= W_L^{j k1}.
 template <typename T, int R1>
 __device__ __forceinline__ void stage_a(cplx<T>* v, int j, const cplx<T>* __restrict__ tw) {
@@ -496,12 +560,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 256, 3) k_fft_x_r2c_reg
         // split Z = A + i B into the half spectra of a and b (nxh = L / 2 + 1): thread (pair cs,
         // frequency kk < L / 2), PPI pairs per sweep; the kk = 0 thread also writes kk = L / 2
         const T h = (T)0.5;
-        constexpr int LH = L / 2, PPI = Sh::NT / LH;
-        static_assert(TW % PPI == 0, "pairs per tile must be a multiple of the pairs per sweep");
+        constexpr int LH = L / 2, PPI = Sh::NT / LH;   // threads >= PPI LH idle here (LH not dividing NT)
         const int kk = threadIdx.x % LH, cs = threadIdx.x / LH;
 #pragma unroll
-        for (int it = 0; it < TW / PPI; ++it) {
+        for (int it = 0; it < (TW + PPI - 1) / PPI; ++it) {
             const int cc = it * PPI + cs;
+            if (cs >= PPI || cc >= TW) break;
             const long a = 2 * (tile * TW + cc), b = a + 1;
             const cplx<T> Z = ex[cc * SR + sidx(kk)];
             const cplx<T> Zc = cconj(ex[cc * SR + sidx(kk == 0 ? 0 : L - kk)]);

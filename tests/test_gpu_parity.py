@@ -4,7 +4,7 @@ Tolerances (relative L2 field error): FP64 <= 1e-12 per call/step and <= 1e-10 a
 100 steps; FP32 <= 2e-5 per call/step (the FP32 path is compared with the FP64 oracle
 run on the same FP32-rounded input). The CFL time step is compared bit for bit.
 Sizes span several 32 x 8 stencil tiles and z chunks with ragged tails, and FFT
-lengths with every radix (2, 3, 4, 5, 7, 8).
+lengths with every radix (2, 3, 4, 5, 7, 8) and the register-path lengths (16 .. 256, 48, 96, 192).
 """
 
 import numpy as np
@@ -38,6 +38,14 @@ def case(name):
     if name == "p3reg2":    # 256 (16x16) and 128 (16x8)
         return dict(faces=[U(256, 0, 2 * PI), U(8, 0, 1.0), U(128, 0, 2 * PI)], bc=["periodic"] * 3, nu=0.01,
                     force=None)
+    if name == "p3r12":     # register-path lengths with radix-3 and radix-12 butterflies: 48 (16x3), 192 (16x12)
+        return dict(faces=[U(48, 0, 2 * PI), U(8, 0, 1.0), U(192, 0, 2 * PI)], bc=["periodic"] * 3, nu=0.02,
+                    force=None)
+    if name == "p2r12":     # 192 (16x12) in x, 96 (16x6) in the fused y pass
+        return dict(faces=[U(192, 0, 2 * PI), U(96, 0, 1.5 * PI)], bc=["periodic"] * 2, nu=0.02, force=None)
+    if name == "c3r12":     # channel with x 96 (16x6) and z 48 (16x3)
+        return dict(faces=[U(96, 0, 4 * PI), inputs.tanh_faces(12, 0, 2, 1.5), U(48, 0, 4 * PI / 3)],
+                    bc=["periodic", "wall", "periodic"], nu=1 / 180, force=[1.0, 0.0, 0.0])
     if name == "c3reg":     # channel with register-path x and z
         return dict(faces=[U(64, 0, 4 * PI), inputs.tanh_faces(20, 0, 2, 1.5), U(32, 0, 4 * PI / 3)],
                     bc=["periodic", "wall", "periodic"], nu=1 / 180, force=[1.0, 0.0, 0.0])
@@ -55,7 +63,8 @@ def case(name):
     raise KeyError(name)
 
 
-CASES = ["p2", "p3", "p3tiny", "p3reg", "p3reg2", "c3", "c3reg", "c2", "cu3", "cu2", "cu3dct", "cu2dct"]
+CASES = ["p2", "p3", "p3tiny", "p3reg", "p3reg2", "p3r12", "p2r12", "c3", "c3reg", "c3r12", "c2", "cu3", "cu2",
+         "cu3dct", "cu2dct"]
 DTYPES = [torch.float64, torch.float32]
 
 
