@@ -316,71 +316,111 @@ __global__ void k_make_scale(T* __restrict__ s, const double* __restrict__ lx, c
 }
 
 // ---------------------------------------------------------- wall direction
-// FP64 Thomas solve of (D G along y + lambda_x + lambda_z) p = r for every
-// (kx, kz) mode, with precomputed factors (they do not change in time):
-//   forward  d_j = (r_j - lo_j d_{j-1}) * invm[j][col],   backward x_j = d_j - cp[j][col] x_{j+1}.
+// FP64 solve of (D G along y + lambda_x + lambda_z) p = r for every (kx, kz) mode by a twisted
+// (two-ended) factorisation with precomputed factors (they do not change in time). Rows
+// lo_j x_{j-1} + b_j x_j + up_j x_{j+1} = r_j meet at m = ny / 2:
+//   top    (j < m, downwards):  d_j = (r_j - lo_j d_{j-1}) * f_j,  row j: x_j + g_j x_{j+1} = d_j,
+//   bottom (j > m, upwards):    e_j = (r_j - up_j e_{j+1}) * f_j,  row j: g_j x_{j-1} + x_j = e_j,
+//   middle: x_m = (r_m - lo_m d_{m-1} - up_m e_{m+1}) * f_m,
+// then x_j = d_j - g_j x_{j+1} upwards from m and x_j = e_j - g_j x_{j-1} downwards from m
+// (f = th_invm, g = th_cp, per row and column). The normalisation s = 1/(nx nz) of the two
+// inverse FFTs is folded into the factors (f' = s f, lo' = lo / s, up' = up / s give s x with
+// the same operations). Two threads per column, one per end, so twice
+// the columns' parallelism of a one-sided sweep; the middle values pass through shared memory.
 // col = kz * nxh + kx; element (col, j) at (col / nxh) * ny * nxh + j * nxh + col % nxh.
 // The mean mode (col 0) has its first row replaced by p_0 = 0 (r_0 taken as 0).
-// The result is scaled by 1/(nx nz) (the normalisation of the two inverse FFTs).
+// Block 2 * TH_COLS threads: threads [0, TH_COLS) the top ends, the rest the bottom ends of
+// TH_COLS consecutive columns.
+constexpr int TH_COLS = 64;
+
 template <typename T>
-__global__ void k_thomas(cplx<T>* __restrict__ S, const double* __restrict__ lo, const double* __restrict__ invm,
-                         const double* __restrict__ cp, cplx<double>* __restrict__ dscr, int nxh, int ny, long ncol,
-                         double norm) {
+__global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S, const double* __restrict__ lo,
+                                                         const double* __restrict__ up,
+                                                         const double* __restrict__ invm,
+                                                         const double* __restrict__ cp,
+                                                         cplx<double>* __restrict__ dscr, int nxh, int ny, long ncol) {
     // The loads do not depend on the recurrence: rows are fetched in batches of CH before
-    // each CH-step stretch of the (sequential) sweep, so CH loads per array are in flight
-    // (one thread per column leaves few warps per SM: the batch depth carries the bandwidth).
+    // each CH-step stretch of the (sequential) sweep, so CH loads per array are in flight.
     constexpr int CH = 16;
-    const long col = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (col >= ncol) return;
-    const long base = (col / nxh) * (long)ny * nxh + (col % nxh);
+    __shared__ double2 mid[2][TH_COLS];   // d_{m-1} (top ends), e_{m+1} (bottom ends)
+    const int lc = threadIdx.x % TH_COLS;
+    const bool top = threadIdx.x < TH_COLS;
+    const long col = blockIdx.x * (long)TH_COLS + lc;
+    const bool ok = col < ncol;
+    const long base = ok ? (col / nxh) * (long)ny * nxh + (col % nxh) : 0;
+    const int m = ny / 2;
+    // rows handled by this end, in elimination order: top 0 .. m-1, bottom ny-1 .. m+1
+    const int nrows = top ? m : ny - 1 - m;
+    const int dir = top ? 1 : -1;
+    const int j0 = top ? 0 : ny - 1;
+    const double* cpl = top ? lo : up;   // the coupling to the previous row of the sweep
     double dre = 0.0, dim_ = 0.0;
-    for (int j0 = 0; j0 < ny; j0 += CH) {
-        cplx<T> r[CH];
-        double a[CH], im[CH];
+    if (ok) {
+        for (int s0 = 0; s0 < nrows; s0 += CH) {
+            cplx<T> r[CH];
+            double a[CH], f[CH];
 #pragma unroll
-        for (int q = 0; q < CH; ++q) {
-            const int j = j0 + q;
-            if (j < ny) {
-                r[q] = S[base + (long)j * nxh];
-                a[q] = __ldg(&lo[j]);
-                im[q] = __ldg(&invm[(long)j * ncol + col]);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < CH; ++q) {
-            const int j = j0 + q;
-            if (j < ny) {
-                double rre = (double)r[q].re, rim = (double)r[q].im;
-                if (j == 0 && col == 0) {
-                    rre = 0.0;
-                    rim = 0.0;
+            for (int q = 0; q < CH; ++q) {
+                if (s0 + q < nrows) {
+                    const int j = j0 + dir * (s0 + q);
+                    r[q] = S[base + (long)j * nxh];
+                    a[q] = __ldg(&cpl[j]);
+                    f[q] = __ldg(&invm[(long)j * ncol + col]);
                 }
-                dre = (rre - a[q] * dre) * im[q];
-                dim_ = (rim - a[q] * dim_) * im[q];
-                dscr[(long)j * ncol + col] = {dre, dim_};
+            }
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                if (s0 + q < nrows) {
+                    const int j = j0 + dir * (s0 + q);
+                    double rre = (double)r[q].re, rim = (double)r[q].im;
+                    if (j == 0 && col == 0) {
+                        rre = 0.0;
+                        rim = 0.0;
+                    }
+                    dre = (rre - a[q] * dre) * f[q];
+                    dim_ = (rim - a[q] * dim_) * f[q];
+                    dscr[(long)j * ncol + col] = {dre, dim_};
+                }
             }
         }
     }
-    double xre = dre, xim = dim_;
-    S[base + (long)(ny - 1) * nxh] = {(T)(xre * norm), (T)(xim * norm)};
-    for (int j1 = ny - 2; j1 >= 0; j1 -= CH) {
+    mid[top ? 0 : 1][lc] = make_double2(dre, dim_);   // 0 when this end has no rows
+    // row m's right-hand side is read by both ends before the barrier (the top end rewrites it)
+    cplx<T> rm = {(T)0, (T)0};
+    double fm = 0.0;
+    if (ok) {
+        rm = S[base + (long)m * nxh];
+        if (m == 0 && col == 0) rm = {(T)0, (T)0};   // ny == 1: the mean mode's p_0 = 0 row is the middle
+        fm = __ldg(&invm[(long)m * ncol + col]);
+    }
+    __syncthreads();
+    if (!ok) return;
+    // x_m, computed by both ends of the column
+    const double2 dm = mid[0][lc], em = mid[1][lc];
+    const double lom = __ldg(&lo[m]), upm = __ldg(&up[m]);
+    double xre = ((double)rm.re - lom * dm.x - upm * em.x) * fm;
+    double xim = ((double)rm.im - lom * dm.y - upm * em.y) * fm;
+    if (top) S[base + (long)m * nxh] = {(T)xre, (T)xim};
+    // back-substitution from the middle outwards: top m-1 .. 0, bottom m+1 .. ny-1
+    const int jb = top ? m - 1 : m + 1;
+    for (int s0 = 0; s0 < nrows; s0 += CH) {
         cplx<double> d[CH];
-        double c[CH];
+        double g[CH];
 #pragma unroll
         for (int q = 0; q < CH; ++q) {
-            const int j = j1 - q;
-            if (j >= 0) {
+            if (s0 + q < nrows) {
+                const int j = jb - dir * (s0 + q);
                 d[q] = dscr[(long)j * ncol + col];
-                c[q] = __ldg(&cp[(long)j * ncol + col]);
+                g[q] = __ldg(&cp[(long)j * ncol + col]);
             }
         }
 #pragma unroll
         for (int q = 0; q < CH; ++q) {
-            const int j = j1 - q;
-            if (j >= 0) {
-                xre = d[q].re - c[q] * xre;
-                xim = d[q].im - c[q] * xim;
-                S[base + (long)j * nxh] = {(T)(xre * norm), (T)(xim * norm)};
+            if (s0 + q < nrows) {
+                const int j = jb - dir * (s0 + q);
+                xre = d[q].re - g[q] * xre;
+                xim = d[q].im - g[q] * xim;
+                S[base + (long)j * nxh] = {(T)xre, (T)xim};
             }
         }
     }

@@ -110,7 +110,8 @@ struct ins_grid {
     void* scale = nullptr;         // T, [nz][ny][nxh] (periodic)
     float* eig = nullptr;          // FP32 periodic: N-scaled eigenvalue sums of the fused pass (see k_fft_strided_pipe)
     double* lam = nullptr;         // FP64 eigenvalues: x (nxh) | y (ny) | z (nz)
-    double* th_lo = nullptr;       // Thomas: lo[ny]
+    double* th_lo = nullptr;       // Thomas: lo[ny], up[ny]
+    double* th_up = nullptr;
     double* th_invm = nullptr;     // [ny][ncol]
     double* th_cp = nullptr;       // [ny][ncol]
     void* th_d = nullptr;          // cplx<double> [ny][ncol]
@@ -414,8 +415,8 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
                 py, S, ncol, nxh, (long)ny * nxh, nxh, reinterpret_cast<const cplx<T>*>(g->dct_qw), g->lam,
                 g->lam + nx, g->lam + nx + ny, norm / ny, lg));
         } else {
-            KLAUNCH(g, "thomas", k_thomas<T><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(
-                S, g->th_lo, g->th_invm, g->th_cp, reinterpret_cast<cplx<double>*>(g->th_d), nxh, ny, ncol, norm));
+            KLAUNCH(g, "thomas", k_thomas2<T><<<(unsigned)((ncol + TH_COLS - 1) / TH_COLS), 2 * TH_COLS, 0, st>>>(
+                S, g->th_lo, g->th_up, g->th_invm, g->th_cp, reinterpret_cast<cplx<double>*>(g->th_d), nxh, ny, ncol));
         }
         if (g->dim == 3 && (s = strided(2, 1)) != INS_OK) return s;
     }
@@ -1292,7 +1293,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     if (!wall_y) {
         o_scale = off; off += al((size_t)spec * ts);
     } else {
-        o_thlo = off; off += al((size_t)g->ny * 8);
+        o_thlo = off; off += al((size_t)g->ny * 2 * 8);
         o_thinv = off; off += al((size_t)g->ny * ncol * 8);
         o_thcp = off; off += al((size_t)g->ny * ncol * 8);
         o_thd = off; off += al((size_t)g->ny * ncol * 16);
@@ -1328,6 +1329,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
         g->scale = b + o_scale;
     } else {
         g->th_lo = reinterpret_cast<double*>(b + o_thlo);
+        g->th_up = g->th_lo + g->ny;
         g->th_invm = reinterpret_cast<double*>(b + o_thinv);
         g->th_cp = reinterpret_cast<double*>(b + o_thcp);
         g->th_d = b + o_thd;
@@ -1461,24 +1463,33 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
             std::vector<double> lo(ny, 0.0), upc(ny, 0.0);
             for (int j = 1; j < ny; ++j) lo[j] = 1.0 / (d[j] * h[j - 1]);
             for (int j = 0; j + 1 < ny; ++j) upc[j] = 1.0 / (d[j] * h[j]);
+            // twisted factorisation meeting at row mid = ny / 2 (see k_thomas2): top rows eliminated
+            // downwards, bottom rows upwards, the middle row's pivot from both; the inverse FFTs'
+            // normalisation sn folded in (f * sn, lo / sn, up / sn)
             std::vector<double> invm((size_t)ny * ncol), cp((size_t)ny * ncol);
+            const int mid = ny / 2;
+            const double sn = 1.0 / ((double)g->nx * (dim == 3 ? g->nz : 1));
             for (long col = 0; col < ncol; ++col) {
                 const int kx = (int)(col % nxh), kz = (int)(col / nxh);
                 const double lamxz = lam[kx] + (dim == 3 ? lam[g->nx + g->ny + kz] : 0.0);
-                double cprev = 0.0;
-                for (int j = 0; j < ny; ++j) {
-                    double diag = -lo[j] - upc[j] + lamxz;
-                    double upj = upc[j];
-                    if (col == 0 && j == 0) {
-                        diag = 1.0;
-                        upj = 0.0;
-                    }
-                    const double m = diag - lo[j] * cprev;
-                    const double c = upj / m;
-                    invm[(size_t)j * ncol + col] = 1.0 / m;
-                    cp[(size_t)j * ncol + col] = c;
-                    cprev = c;
+                auto diag = [&](int j) { return (col == 0 && j == 0) ? 1.0 : -lo[j] - upc[j] + lamxz; };
+                auto upr = [&](int j) { return (col == 0 && j == 0) ? 0.0 : upc[j]; };
+                double gtop = 0.0;   // g_{j-1} of the downward sweep
+                for (int j = 0; j < mid; ++j) {
+                    const double piv = diag(j) - lo[j] * gtop;
+                    gtop = upr(j) / piv;
+                    invm[(size_t)j * ncol + col] = sn / piv;
+                    cp[(size_t)j * ncol + col] = gtop;
                 }
+                double gbot = 0.0;   // g_{j+1} of the upward sweep
+                for (int j = ny - 1; j > mid; --j) {
+                    const double piv = diag(j) - upr(j) * gbot;
+                    gbot = lo[j] / piv;
+                    invm[(size_t)j * ncol + col] = sn / piv;
+                    cp[(size_t)j * ncol + col] = gbot;
+                }
+                invm[(size_t)mid * ncol + col] = sn / (diag(mid) - lo[mid] * gtop - upr(mid) * gbot);
+                cp[(size_t)mid * ncol + col] = 0.0;
             }
             if (g->wall_dct) {
                 std::vector<double> qw(2 * (size_t)ny);
@@ -1493,7 +1504,13 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
                     ok &= up(g->dct_qw, qf.data(), qf.size() * 4);
                 }
             }
-            ok &= up(g->th_lo, lo.data(), (size_t)ny * 8);
+            std::vector<double> los(ny), ups(ny);
+            for (int j = 0; j < ny; ++j) {
+                los[j] = lo[j] / sn;
+                ups[j] = upc[j] / sn;
+            }
+            ok &= up(g->th_lo, los.data(), (size_t)ny * 8);
+            ok &= up(g->th_up, ups.data(), (size_t)ny * 8);
             ok &= up(g->th_invm, invm.data(), invm.size() * 8);
             ok &= up(g->th_cp, cp.data(), cp.size() * 8);
         }
