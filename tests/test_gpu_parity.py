@@ -46,6 +46,12 @@ def case(name):
     if name == "c3r12":     # channel with x 96 (16x6) and z 48 (16x3)
         return dict(faces=[U(96, 0, 4 * PI), inputs.tanh_faces(12, 0, 2, 1.5), U(48, 0, 4 * PI / 3)],
                     bc=["periodic", "wall", "periodic"], nu=1 / 180, force=[1.0, 0.0, 0.0])
+    if name == "c3odd":     # odd wall-normal size: the two-ended wall solve meets at an interior row
+        return dict(faces=[U(24, 0, 4 * PI), inputs.tanh_faces(15, 0, 2, 1.5), U(20, 0, 4 * PI / 3)],
+                    bc=["periodic", "wall", "periodic"], nu=1 / 180, force=[1.0, 0.0, 0.0])
+    if name == "c2odd":
+        return dict(faces=[U(28, 0, 4 * PI), inputs.tanh_faces(7, 0, 2, 1.5)], bc=["periodic", "wall"], nu=0.05,
+                    force=[1.0, 0.0])
     if name == "c3reg":     # channel with register-path x and z
         return dict(faces=[U(64, 0, 4 * PI), inputs.tanh_faces(20, 0, 2, 1.5), U(32, 0, 4 * PI / 3)],
                     bc=["periodic", "wall", "periodic"], nu=1 / 180, force=[1.0, 0.0, 0.0])
@@ -63,8 +69,8 @@ def case(name):
     raise KeyError(name)
 
 
-CASES = ["p2", "p3", "p3tiny", "p3reg", "p3reg2", "p3r12", "p2r12", "c3", "c3reg", "c3r12", "c2", "cu3", "cu2",
-         "cu3dct", "cu2dct"]
+CASES = ["p2", "p3", "p3tiny", "p3reg", "p3reg2", "p3r12", "p2r12", "c3", "c3reg", "c3r12", "c3odd", "c2", "c2odd",
+         "cu3", "cu2", "cu3dct", "cu2dct"]
 DTYPES = [torch.float64, torch.float32]
 
 
