@@ -470,6 +470,22 @@ int device_sm_count();
 // bounds); a CTA costs about its planes plus two for its prologue (five staged planes without
 // an evaluation). Take the chunk that minimises waves x cost per CTA (the last wave counts as a
 // full one), or the caller's (ins_set_march_chunk).
+// z planes per CTA of a z-marching kernel over `cols` columns: the chunk that minimises
+// (waves of `resident` CTAs) x (planes a CTA stages: chunk + halo).
+int wave_chunk(long cols, int nz, long resident, int halo) {
+    int best_c = nz;
+    long best = -1;
+    for (int c = 1; c <= nz; ++c) {
+        const long ctas = cols * ((nz + c - 1) / c);
+        const long cost = (ctas + resident - 1) / resident * (c + halo);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_c = c;
+        }
+    }
+    return best_c;
+}
+
 dim3 pair_grid(const ins_grid* g, int ctas_per_sm = 2) {
     const int nbx = (g->nx + 2 * RBX - 1) / (2 * RBX), nby = (g->ny + RBY - 1) / RBY;
     int kc = g->march_chunk;
@@ -885,13 +901,20 @@ struct Impl {
         const long N = g->N;
         const size_t fld = (size_t)g->dim * N * sizeof(T);
         const dim3 cg = cell_grid(g);
-        // z-marching adjoint stencil (3-D): chunks of planes per CTA
+        // z-marching adjoint stencil (3-D): chunks of planes per CTA, the chunk from the wave count
+        // of the resident CTAs (each CTA stages its chunk plus two halo planes)
         const int abx = (g->nx + AJX - 1) / AJX, aby = (g->ny + AJY - 1) / AJY;
-        int akc = (int)(((long)abx * aby * g->nz) / 1184);
-        akc = akc < 1 ? 1 : (akc > g->nz ? g->nz : akc);
-        const dim3 ag(abx, aby, (g->nz + akc - 1) / akc);
         const size_t adj_smem = 4 * 6 * AJSP * sizeof(T);
-        if (DIM == 3) INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem));
+        static int adj_per_sm = 0;
+        if (DIM == 3) {
+            INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem));
+            if (!adj_per_sm) {
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&adj_per_sm, k_adj_rhs_z<T>, AJX * AJY, adj_smem);
+                if (adj_per_sm < 1) adj_per_sm = 1;
+            }
+        }
+        const int akc = DIM == 3 ? wave_chunk((long)abx * aby, g->nz, (long)adj_per_sm * device_sm_count(), 2) : 1;
+        const dim3 ag(abx, aby, (g->nz + akc - 1) / akc);
         const long nblk = DIM == 3 ? (long)ag.x * ag.y * ag.z : (long)cg.x * cg.y * cg.z;
         const size_t need = 5 * ((fld + 255) & ~size_t(255)) + (size_t)nblk * 8;
         if (g->vjp_bytes < need) {
