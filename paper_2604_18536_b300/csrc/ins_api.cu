@@ -583,66 +583,78 @@ struct Impl {
         KLAUNCH(g, "divergence", k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi));
         return INS_OK;
     }
-    // Launch the stage update (vector z-march kernel when the rows allow it).
-    template <bool LS>
-    static ins_status rk_update(ins_grid* g, const T* F, const T* rp, T* u0, T* acc, T* us, const RkArgs& ra) {
-        if (rk_vec_ok<T>(g, u0) && (us == nullptr || reinterpret_cast<uintptr_t>(us) % 16 == 0)) {
-            constexpr int VEC = VecT<T>::N;
-            RkCoef<T> rc;
-            rc.nx = g->nx;
-            rc.ny = g->ny;
-            rc.nz = g->nz;
-            rc.ihx = (T)(1.0 / g->h[0][0]);
-            rc.ihz = (T)(1.0 / g->h[2][0]);
-            rc.ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
-            const int bx = (g->nx / VEC + 31) / 32, by = (g->ny + 7) / 8;
-            int kc = (int)(((long)bx * by * g->nz) / 2368);
-            kc = kc < 1 ? 1 : (kc > g->nz ? g->nz : kc);
-            const dim3 grd(bx, by, (g->nz + kc - 1) / kc);
-            KLAUNCH(g, "rk_update", k_rk_update_vec<T, DIM, WALL, LS><<<grd, dim3(32, 8), 0, g->stream>>>(
-                                        rc, F, rp, u0, acc, us, ra, kc));
-        } else {
-            KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL, LS><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(
-                                        make_geo<T>(g), F, rp, u0, acc, us, ra));
-        }
-        return INS_OK;
+    // Vector width of the z-march kernels: VecT<T>::N, or half of it when a row's vector count
+    // would leave warps partly idle and the half width fills whole warps (FP32 nx = 192: 48
+    // float4 per row, 96 float2).
+    static int vec_width(const ins_grid* g) {
+        constexpr int V = VecT<T>::N;
+        const int nv = g->nx / V;
+        return (nv % 32 != 0 && nv < 128 && (g->nx / (V / 2)) % 32 == 0) ? V / 2 : V;
     }
-    // phi = D u and out = src - G p through the vector z-march kernels when the rows allow it
-    // (the step VJP's P^T and ins_project), else the one-cell kernels.
-    static dim3 vec_grid(const ins_grid* g, int* kc) {
-        constexpr int VEC = VecT<T>::N;
-        const int bx = (g->nx / VEC + 31) / 32, by = (g->ny + 7) / 8;
+    static dim3 vec_grid(const ins_grid* g, int vw, int* kc) {
+        const int bx = (g->nx / vw + 31) / 32, by = (g->ny + 7) / 8;
         int c = (int)(((long)bx * by * g->nz) / 2368);
         c = c < 1 ? 1 : (c > g->nz ? g->nz : c);
         *kc = c;
         return dim3(bx, by, (g->nz + c - 1) / c);
     }
+    static RkCoef<T> rk_coef(const ins_grid* g) {
+        RkCoef<T> rc;
+        rc.nx = g->nx;
+        rc.ny = g->ny;
+        rc.nz = g->nz;
+        rc.ihx = (T)(1.0 / g->h[0][0]);
+        rc.ihz = (T)(1.0 / g->h[2][0]);
+        rc.ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
+        return rc;
+    }
+    template <bool LS, int VW>
+    static ins_status rk_vec_launch(ins_grid* g, const char* name, const T* F, const T* rp, T* u0, T* acc, T* us,
+                                    const RkArgs& ra) {
+        int kc;
+        const dim3 grd = vec_grid(g, VW, &kc);
+        KLAUNCH(g, name, (k_rk_update_vec<T, DIM, WALL, LS, VW><<<grd, dim3(32, 8), 0, g->stream>>>(
+                             rk_coef(g), F, rp, u0, acc, us, ra, kc)));
+        return INS_OK;
+    }
+    // Launch the stage update (vector z-march kernel when the rows allow it).
+    template <bool LS>
+    static ins_status rk_update(ins_grid* g, const T* F, const T* rp, T* u0, T* acc, T* us, const RkArgs& ra) {
+        if (rk_vec_ok<T>(g, u0) && (us == nullptr || reinterpret_cast<uintptr_t>(us) % 16 == 0)) {
+            constexpr int V = VecT<T>::N;
+            if (vec_width(g) == V) return rk_vec_launch<LS, V>(g, "rk_update", F, rp, u0, acc, us, ra);
+            return rk_vec_launch<LS, V / 2>(g, "rk_update", F, rp, u0, acc, us, ra);
+        }
+        KLAUNCH(g, "rk_update", k_rk_update<T, DIM, WALL, LS><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(
+                                    make_geo<T>(g), F, rp, u0, acc, us, ra));
+        return INS_OK;
+    }
+    // phi = D u and out = src - G p through the vector z-march kernels when the rows allow it
+    // (the step VJP's P^T and ins_project), else the one-cell kernels.
+    template <int VW>
+    static ins_status div_vec_launch(ins_grid* g, const T* u, T* phi) {
+        DivCoef<T> dc;
+        dc.nx = g->nx;
+        dc.ny = g->ny;
+        dc.nz = g->nz;
+        dc.idx = (T)(1.0 / g->d[0][0]);
+        dc.idz = (T)(1.0 / g->d[2][0]);
+        dc.idy = make_geo<T>(g).c[1] + (size_t)C_INV_D * g->ny;
+        int kc;
+        const dim3 grd = vec_grid(g, VW, &kc);
+        KLAUNCH(g, "divergence", (k_divergence_vec<T, DIM, WALL, VW><<<grd, dim3(32, 8), 0, g->stream>>>(dc, u, phi, kc)));
+        return INS_OK;
+    }
     static ins_status div_fast(ins_grid* g, const T* u, T* phi) {
         if (rk_vec_ok<T>(g, u) && reinterpret_cast<uintptr_t>(phi) % 16 == 0) {
-            DivCoef<T> dc;
-            dc.nx = g->nx;
-            dc.ny = g->ny;
-            dc.nz = g->nz;
-            dc.idx = (T)(1.0 / g->d[0][0]);
-            dc.idz = (T)(1.0 / g->d[2][0]);
-            dc.idy = make_geo<T>(g).c[1] + (size_t)C_INV_D * g->ny;
-            int kc;
-            const dim3 grd = vec_grid(g, &kc);
-            KLAUNCH(g, "divergence", (k_divergence_vec<T, DIM, WALL><<<grd, dim3(32, 8), 0, g->stream>>>(dc, u, phi, kc)));
-            return INS_OK;
+            constexpr int V = VecT<T>::N;
+            return vec_width(g) == V ? div_vec_launch<V>(g, u, phi) : div_vec_launch<V / 2>(g, u, phi);
         }
         KLAUNCH(g, "divergence", (k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi)));
         return INS_OK;
     }
     static ins_status sub_grad_fast(ins_grid* g, const T* src, const T* p, T* out) {
         if (rk_vec_ok<T>(g, src) && reinterpret_cast<uintptr_t>(out) % 16 == 0 && reinterpret_cast<uintptr_t>(p) % 16 == 0) {
-            RkCoef<T> rc;
-            rc.nx = g->nx;
-            rc.ny = g->ny;
-            rc.nz = g->nz;
-            rc.ihx = (T)(1.0 / g->h[0][0]);
-            rc.ihz = (T)(1.0 / g->h[2][0]);
-            rc.ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
             RkArgs ra;
             ra.dt_dev = nullptr;
             ra.dt_host = 0.0;
@@ -652,11 +664,9 @@ struct Impl {
             ra.last = 0;
             ra.mx = nullptr;
             ra.err_flag = g->err_flag;
-            int kc;
-            const dim3 grd = vec_grid(g, &kc);
-            KLAUNCH(g, "sub_grad", (k_rk_update_vec<T, DIM, WALL, false><<<grd, dim3(32, 8), 0, g->stream>>>(
-                                       rc, src, p, nullptr, nullptr, out, ra, kc)));
-            return INS_OK;
+            constexpr int V = VecT<T>::N;
+            if (vec_width(g) == V) return rk_vec_launch<false, V>(g, "sub_grad", src, p, nullptr, nullptr, out, ra);
+            return rk_vec_launch<false, V / 2>(g, "sub_grad", src, p, nullptr, nullptr, out, ra);
         }
         KLAUNCH(g, "sub_grad", (k_sub_grad<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), src, p, out)));
         return INS_OK;

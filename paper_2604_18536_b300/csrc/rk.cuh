@@ -50,6 +50,28 @@ struct VecT<double> {
     }
 };
 
+// The same accesses with half the width (float2 / one double): rows whose 16-byte vector count
+// would leave a warp partly idle (nx = 192 in FP32: 48 float4 per row, 96 float2) run with these.
+template <typename T, int N>
+struct VecIO : VecT<T> {};
+template <>
+struct VecIO<float, 2> {
+    static constexpr int N = 2;
+    static __device__ __forceinline__ void ld(const float* p, float (&x)[2]) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        x[0] = v.x; x[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(float* p, const float (&x)[2]) {
+        *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+    }
+};
+template <>
+struct VecIO<double, 1> {
+    static constexpr int N = 1;
+    static __device__ __forceinline__ void ld(const double* p, double (&x)[1]) { x[0] = *p; }
+    static __device__ __forceinline__ void st(double* p, const double (&x)[1]) { *p = x[0]; }
+};
+
 template <typename T>
 struct RkCoef {
     int nx, ny, nz;
@@ -59,12 +81,12 @@ struct RkCoef {
 
 // Block (32, 8); grid (ceil(nx/VEC/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx % VEC == 0 and
 // 16-byte aligned field pointers.
-template <typename T, int DIM, bool WALL, bool LS = false>
+template <typename T, int DIM, bool WALL, bool LS = false, int VW = VecT<T>::N>
 __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __restrict__ F, const T* __restrict__ p,
                                                        T* __restrict__ u0, T* __restrict__ acc, T* __restrict__ us,
                                                        RkArgs ra, int kchunk) {
-    using VT = VecT<T>;
-    constexpr int VEC = VT::N;
+    using VT = VecIO<T, VW>;
+    constexpr int VEC = VW;
     const int nx = c.nx, ny = c.ny, nz = c.nz;
     const long N = (long)nx * ny * nz;
     const long plane = (long)nx * ny;
@@ -228,11 +250,11 @@ struct DivCoef {
 
 // Block (32, 8); grid (ceil(nx/VEC/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx % VEC == 0 and
 // 16-byte aligned u and phi.
-template <typename T, int DIM, bool WALL>
+template <typename T, int DIM, bool WALL, int VW = VecT<T>::N>
 __global__ void __launch_bounds__(256) k_divergence_vec(DivCoef<T> c, const T* __restrict__ u, T* __restrict__ phi,
                                                         int kchunk) {
-    using VT = VecT<T>;
-    constexpr int VEC = VT::N;
+    using VT = VecIO<T, VW>;
+    constexpr int VEC = VW;
     const int nx = c.nx, ny = c.ny, nz = c.nz;
     const long N = (long)nx * ny * nz;
     const long plane = (long)nx * ny;
