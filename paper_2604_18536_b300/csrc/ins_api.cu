@@ -653,6 +653,68 @@ struct Impl {
         KLAUNCH(g, "divergence", (k_divergence<T, DIM, WALL><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi)));
         return INS_OK;
     }
+    // The row-scaled P^T passes of the wall-bounded pullback (vector kernels when the rows allow it).
+    template <int VW>
+    static ins_status div_scaled_vec(ins_grid* g, const T* u, T* phi) {
+        DivCoef<T> dc;
+        dc.nx = g->nx;
+        dc.ny = g->ny;
+        dc.nz = g->nz;
+        dc.idx = (T)(1.0 / g->d[0][0]);
+        dc.idz = (T)(1.0 / g->d[2][0]);
+        dc.idy = make_geo<T>(g).c[1] + (size_t)C_INV_D * g->ny;
+        dc.ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
+        int kc;
+        const dim3 grd = vec_grid(g, VW, &kc);
+        KLAUNCH(g, "divergence", (k_divergence_vec<T, DIM, WALL, VW, true><<<grd, dim3(32, 8), 0, g->stream>>>(dc, u, phi, kc)));
+        return INS_OK;
+    }
+    static ins_status div_scaled_fast(ins_grid* g, const T* u, T* phi) {
+        if constexpr (WALL) {
+            // FP64 keeps the one-cell kernel (its row scalings cost FP64 operations the vector form
+            // does not save: 95 vs 109 us on the 192 x 128 x 192 channel)
+            if (sizeof(T) == 4 && rk_vec_ok<T>(g, u) && reinterpret_cast<uintptr_t>(phi) % 16 == 0) {
+                constexpr int V = VecT<T>::N;
+                return vec_width(g) == V ? div_scaled_vec<V>(g, u, phi) : div_scaled_vec<V / 2>(g, u, phi);
+            }
+            KLAUNCH(g, "divergence", (k_wall_div_scaled<T, DIM><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), u, phi)));
+        }
+        return INS_OK;
+    }
+    template <int VW>
+    static ins_status sub_scaled_vec(ins_grid* g, const T* src, const T* p, T* out, const double* hy, const double* dy) {
+        RkCoef<T> rc = rk_coef(g);
+        rc.idy = make_geo<T>(g).c[1] + (size_t)C_INV_D * g->ny;
+        rc.hy = hy;
+        rc.dy = dy;
+        RkArgs ra;
+        ra.dt_dev = nullptr;
+        ra.dt_host = 0.0;
+        ra.a_next = 0.0;
+        ra.b = 0.0;
+        ra.stage = -1;
+        ra.last = 0;
+        ra.mx = nullptr;
+        ra.err_flag = g->err_flag;
+        int kc;
+        const dim3 grd = vec_grid(g, VW, &kc);
+        KLAUNCH(g, "sub_grad", (k_rk_update_vec<T, DIM, WALL, false, VW, true><<<grd, dim3(32, 8), 0, g->stream>>>(
+                                   rc, src, p, nullptr, nullptr, out, ra, kc)));
+        return INS_OK;
+    }
+    static ins_status sub_scaled_fast(ins_grid* g, const T* src, const T* p, T* out, const double* hy, const double* dy) {
+        if constexpr (WALL) {
+            if (sizeof(T) == 4 && rk_vec_ok<T>(g, src) && reinterpret_cast<uintptr_t>(out) % 16 == 0 &&
+                reinterpret_cast<uintptr_t>(p) % 16 == 0) {
+                constexpr int V = VecT<T>::N;
+                return vec_width(g) == V ? sub_scaled_vec<V>(g, src, p, out, hy, dy)
+                                         : sub_scaled_vec<V / 2>(g, src, p, out, hy, dy);
+            }
+            KLAUNCH(g, "sub_grad",
+                    (k_wall_sub_scaled<T, DIM><<<cell_grid(g), dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), src, p, out, hy, dy)));
+        }
+        return INS_OK;
+    }
     static ins_status sub_grad_fast(ins_grid* g, const T* src, const T* p, T* out) {
         if (rk_vec_ok<T>(g, src) && reinterpret_cast<uintptr_t>(out) % 16 == 0 && reinterpret_cast<uintptr_t>(p) % 16 == 0) {
             RkArgs ra;
@@ -878,10 +940,9 @@ struct Impl {
         wa.dt_host = dt_host;
         for (int st = nst - 1; st >= 0; --st) {
             // w = P^T kbar = M Omega P (Omega^-1 M kbar)
-            KLAUNCH(g, "divergence", (k_wall_div_scaled<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp)));
+            if ((s = div_scaled_fast(g, F, rp)) != INS_OK) return s;
             if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
-            KLAUNCH(g, "sub_grad",
-                    (k_wall_sub_scaled<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(make_geo<T>(g), F, rp, W, hy, dy)));
+            if ((s = sub_scaled_fast(g, F, rp, W, hy, dy)) != INS_OK) return s;
             if (lowst) {
                 wa.bn = st > 0 ? WRAY3_GAMMA[st - 1] + WRAY3_ZETA[st] : 0.0;
                 wa.an = st > 0 ? WRAY3_GAMMA[st - 1] : 0.0;

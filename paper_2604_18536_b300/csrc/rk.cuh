@@ -77,11 +77,18 @@ struct RkCoef {
     int nx, ny, nz;
     T ihx, ihz;          // 1/h of the uniform x and z directions
     const T* ihy;        // 1/h_y[j]
+    // SC (row-scaled projection of the wall-bounded step VJP): 1/d_y[j], and the FP64 d_y, h_y
+    const T* idy = nullptr;
+    const double* dy = nullptr;
+    const double* hy = nullptr;
 };
 
 // Block (32, 8); grid (ceil(nx/VEC/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx % VEC == 0 and
 // 16-byte aligned field pointers.
-template <typename T, int DIM, bool WALL, bool LS = false, int VW = VecT<T>::N>
+// SC (with stage -1 only): the wall-bounded pullback's M Omega (Omega^-1 M F - G p): F^x, F^z
+// scaled by 1/d_y[j] and F^y by 1/h_y[j] before the gradient, the result by d_y[j] (x, z) and
+// h_y[j] (y) after it; the stored top wall faces of u^y are 0.
+template <typename T, int DIM, bool WALL, bool LS = false, int VW = VecT<T>::N, bool SC = false>
 __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __restrict__ F, const T* __restrict__ p,
                                                        T* __restrict__ u0, T* __restrict__ acc, T* __restrict__ us,
                                                        RkArgs ra, int kchunk) {
@@ -136,6 +143,15 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
             VT::ld(F + a, f[0]);
             VT::ld(F + N + a, f[1]);
             if (DIM == 3) VT::ld(F + 2 * N + a, f[2]);
+            if constexpr (SC) {
+                const T sd = __ldg(&c.idy[j]);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    f[0][e] *= sd;
+                    f[1][e] *= ihy;
+                    if (DIM == 3) f[2][e] *= sd;
+                }
+            }
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
                 const T pe = e + 1 < VEC ? P0[e + 1] : pnext;
@@ -147,6 +163,11 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
             for (int cc = 0; cc < DIM; ++cc) {
                 const long ea = cc * N + a;
                 if (!LS && ra.stage < 0) {   // projection only: us = F - G p
+                    if constexpr (SC) {
+                        const T post = (T)(cc == 1 ? c.hy[j] : c.dy[j]);
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) kk[cc][e] *= post;
+                    }
                     VT::st(us + ea, kk[cc]);
                     continue;
                 }
@@ -246,11 +267,14 @@ struct DivCoef {
     int nx, ny, nz;
     T idx, idz;          // 1/d of the uniform x and z directions
     const T* idy;        // 1/d_y[j]
+    const T* ihy = nullptr;   // SC: 1/h_y[j]
 };
 
 // Block (32, 8); grid (ceil(nx/VEC/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx % VEC == 0 and
 // 16-byte aligned u and phi.
-template <typename T, int DIM, bool WALL, int VW = VecT<T>::N>
+// SC: the divergence of Omega^-1 M u of the wall-bounded pullback (u^x, u^z scaled by 1/d_y[j],
+// u^y by 1/h_y[j], the stored top wall faces of u^y taken as 0).
+template <typename T, int DIM, bool WALL, int VW = VecT<T>::N, bool SC = false>
 __global__ void __launch_bounds__(256) k_divergence_vec(DivCoef<T> c, const T* __restrict__ u, T* __restrict__ phi,
                                                         int kchunk) {
     using VT = VecIO<T, VW>;
@@ -275,6 +299,16 @@ __global__ void __launch_bounds__(256) k_divergence_vec(DivCoef<T> c, const T* _
 #pragma unroll
     for (int e = 0; e < VEC; ++e) Zm[e] = (T)0;
     if (DIM == 3 && ok) VT::ld(u + 2 * N + (long)(kb == 0 ? nz - 1 : kb - 1) * plane + jrow + i0, Zm);
+    // SC row factors: x and z faces of row j, y faces of rows j and j - 1
+    T sxz = (T)1, sy = (T)1, sym = (T)1;
+    if constexpr (SC) {
+        const int jc = j < ny ? j : ny - 1;
+        sxz = idy;
+        sy = jc == ny - 1 ? (T)0 : __ldg(&c.ihy[jc]);
+        sym = jc > 0 ? __ldg(&c.ihy[jc - 1]) : (T)0;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) Zm[e] *= sxz;
+    }
     for (int k = kb; k < ke; ++k) {
         const long base = (long)k * plane;
         const long a = base + jrow + i0;
@@ -286,9 +320,18 @@ __global__ void __launch_bounds__(256) k_divergence_vec(DivCoef<T> c, const T* _
             VT::ld(u + N + a, uy);
             if (!bottom) VT::ld(u + N + base + jprev + i0, uym);
             if (DIM == 3) VT::ld(u + 2 * N + a, uz);
+            if constexpr (SC) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    ux[e] *= sxz;
+                    uy[e] *= sy;
+                    uym[e] *= sym;
+                    uz[e] *= sxz;
+                }
+            }
         }
         T xprev = __shfl_up_sync(0xffffffffu, ux[VEC - 1], 1);
-        if (ok && need_global_prev) xprev = u[base + jrow + (iv == 0 ? nx - 1 : i0 - 1)];
+        if (ok && need_global_prev) xprev = u[base + jrow + (iv == 0 ? nx - 1 : i0 - 1)] * sxz;
         if (ok) {
             T d[VEC];
 #pragma unroll
