@@ -162,7 +162,10 @@ ins_status ins_set_wall_solver(ins_grid* g, int solver);
  * the unfused path's up to the order of FP32 roundings in F. enable = 0 selects the unfused
  * kernels (for comparison), 1 the fused kernels with one cell per thread, 2 (default) the
  * fused kernels with two neighbouring x cells per thread (8-byte accesses; same arithmetic
- * per cell as 1). Other values: INS_ERR_ARG. Other grids ignore the setting. */
+ * per cell as 1). Other values: INS_ERR_ARG. Other grids ignore the setting. On FP32 3-D
+ * periodic grids with even nx, level 2 also selects the two-cells-per-thread pullback
+ * stencil of ins_step_vjp (levels 0 and 1: one cell per thread); its results equal the
+ * one-cell kernel's up to the order of FP32 roundings. */
 ins_status ins_set_step_fusion(ins_grid* g, int enable);
 
 /* Launch shape of the fused two-cells-per-thread kernels (fusion level 2; no counterpart in

@@ -24,6 +24,7 @@
 #include "rk.cuh"
 #include "adjoint.cuh"
 #include "adjoint_wall.cuh"
+#include "adjoint_x2.cuh"
 #include "filter_spectrum.cuh"
 #include "conv_tc.cuh"
 #include "eddy.cuh"
@@ -974,17 +975,34 @@ struct Impl {
         const dim3 cg = cell_grid(g);
         // z-marching adjoint stencil (3-D): chunks of planes per CTA, the chunk from the wave count
         // of the resident CTAs (each CTA stages its chunk plus two halo planes)
-        const int abx = (g->nx + AJX - 1) / AJX, aby = (g->ny + AJY - 1) / AJY;
-        const size_t adj_smem = 4 * 6 * AJSP * sizeof(T);
-        static int adj_per_sm = 0;
+        // FP32 (step fusion level 2): the two-cells-per-thread march k_adj_rhs_z2 on 64 x 8 columns
+        bool pair_adj = false;
+        if constexpr (DIM == 3 && std::is_same<T, float>::value) {
+            auto al8 = [](const void* q) { return q == nullptr || reinterpret_cast<uintptr_t>(q) % 8 == 0; };
+            pair_adj = g->fusion == 2 && g->nx % 2 == 0 && 3 * g->N < (1L << 31) && al8(un) && al8(ubar) && al8(ybar);
+        }
+        const int abx = pair_adj ? (g->nx + 63) / 64 : (g->nx + AJX - 1) / AJX, aby = (g->ny + AJY - 1) / AJY;
+        const size_t adj_smem = pair_adj ? (size_t)ax2_smem() : 4 * 6 * AJSP * sizeof(T);
+        static int adj_per_sm = 0, adj2_per_sm = 0;
         if (DIM == 3) {
-            INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem));
-            if (!adj_per_sm) {
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&adj_per_sm, k_adj_rhs_z<T>, AJX * AJY, adj_smem);
-                if (adj_per_sm < 1) adj_per_sm = 1;
+            if (pair_adj) {
+                if constexpr (std::is_same<T, float>::value) {
+                    INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_z2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem));
+                    if (!adj2_per_sm) {
+                        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&adj2_per_sm, k_adj_rhs_z2, 256, adj_smem);
+                        if (adj2_per_sm < 1) adj2_per_sm = 1;
+                    }
+                }
+            } else {
+                INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem));
+                if (!adj_per_sm) {
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&adj_per_sm, k_adj_rhs_z<T>, AJX * AJY, adj_smem);
+                    if (adj_per_sm < 1) adj_per_sm = 1;
+                }
             }
         }
-        const int akc = DIM == 3 ? wave_chunk((long)abx * aby, g->nz, (long)adj_per_sm * device_sm_count(), 2) : 1;
+        const long adj_resident = (long)(pair_adj ? adj2_per_sm : adj_per_sm) * device_sm_count();
+        const int akc = DIM == 3 ? wave_chunk((long)abx * aby, g->nz, adj_resident, 2) : 1;
         const dim3 ag(abx, aby, (g->nz + akc - 1) / akc);
         const long nblk = DIM == 3 ? (long)ag.x * ag.y * ag.z : (long)cg.x * cg.y * cg.z;
         const size_t need = 5 * ((fld + 255) & ~size_t(255)) + (size_t)nblk * 8;
@@ -1087,8 +1105,17 @@ struct Impl {
                 extra = Cb;
             }
             if (DIM == 3) {
-                KLAUNCH(g, "adj_rhs", k_adj_rhs_z<T><<<ag, dim3(AJX, AJY), adj_smem, g->stream>>>(
-                                          ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra, akc));
+                bool done = false;
+                if constexpr (std::is_same<T, float>::value) {
+                    if (pair_adj) {
+                        KLAUNCH(g, "adj_rhs", k_adj_rhs_z2<<<ag, dim3(32, 8), adj_smem, g->stream>>>(
+                                                  ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra, akc));
+                        done = true;
+                    }
+                }
+                if (!done)
+                    KLAUNCH(g, "adj_rhs", k_adj_rhs_z<T><<<ag, dim3(AJX, AJY), adj_smem, g->stream>>>(
+                                              ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra, akc));
             } else {
                 KLAUNCH(g, "adj_rhs", k_adj_rhs<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
                                           ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra));

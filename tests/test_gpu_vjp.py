@@ -28,6 +28,10 @@ def case(name):
         return [U(32, 0, 2 * PI), U(16, 0, 1.0), U(64, 0, 3.0)], 0.02
     if name == "p2":
         return [U(40, 0, 2 * PI), U(24, 0, 1.5 * PI)], 0.05
+    if name == "p3odd":     # odd nx: the one-cell-per-thread adjoint march
+        return [U(15, 0, 2 * PI), U(12, 0, 1.5 * PI), U(10, 0, 3.0)], 0.03
+    if name == "p3wide":    # nx = 140: two full 64-wide pair tiles and a ragged one
+        return [U(140, 0, 2 * PI), U(9, 0, 1.5 * PI), U(6, 0, 3.0)], 0.03
     raise KeyError(name)
 
 
@@ -63,6 +67,22 @@ def test_step_vjp_matches_oracle(name, dtype):
     ub_o, nb_o = adjoint.rk4_step_vjp(og, u0, dt, ybar)
     assert rel(ub.double().cpu().numpy(), ub_o) <= TOL[dtype]
     assert abs(nb.item() - nb_o) <= 50 * TOL[dtype] * abs(nb_o)
+
+
+@pytest.mark.parametrize("level", [0, 2])
+@pytest.mark.parametrize("name", ["p3", "p3reg", "p3odd", "p3wide"])
+def test_step_vjp_fp32_adjoint_kernels(name, level):
+    """FP32: the two-cells-per-thread adjoint march (fusion level 2, even nx) and the one-cell
+    march (level 0, or odd nx) both against the oracle, and against each other."""
+    og, gg, u0, ybar, dt = setup(name, torch.float32, seed=7)
+    gg.set_step_fusion(level)
+    ub, nb = gg.step_vjp(dev(u0, torch.float32), dev(ybar, torch.float32), dt=dt)
+    ub_o, nb_o = adjoint.rk4_step_vjp(og, u0, dt, ybar)
+    assert rel(ub.double().cpu().numpy(), ub_o) <= TOL[torch.float32]
+    assert abs(nb.item() - nb_o) <= 50 * TOL[torch.float32] * abs(nb_o)
+    gg.set_step_fusion(2 - level)
+    ub2, _ = gg.step_vjp(dev(u0, torch.float32), dev(ybar, torch.float32), dt=dt)
+    assert rel(ub2.double().cpu().numpy(), ub.double().cpu().numpy()) <= 1e-6
 
 
 def test_step_vjp_inputs_untouched_and_device_dt():
