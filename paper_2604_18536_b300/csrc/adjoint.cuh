@@ -36,6 +36,7 @@ struct AdjCoef {
     const double* dt_dev;   // dt on the device, or null: dt_host
     double dt_host;
     double bn, an;          // b_{s-1}, a_{s,s-1} for the next stage cotangent
+    const T* ubar_in = nullptr;   // z marches: the accumulator's previous value (null: ubar0 itself)
 };
 
 // Block (32, 8), grid (ceil(nx/32), ceil(ny/8), nz). nu_part[block] receives the block's
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
             T oldv[3], yv[3], xv[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                oldv[a] = ubar0[a * N + Jc];
+                oldv[a] = (c.ubar_in ? c.ubar_in : ubar0)[a * N + Jc];
                 yv[a] = ybar ? ybar[a * N + Jc] : oldv[a];
                 xv[a] = extra ? extra[a * N + Jc] : (T)0;
             }

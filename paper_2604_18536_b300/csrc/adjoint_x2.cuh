@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_rhs_z2(AdjCoef<float> c, const f
             float2 oldv[3], yv[3], xv[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                oldv[a] = ld2(ubar0, a * N + J);
+                oldv[a] = ld2(c.ubar_in ? c.ubar_in : ubar0, a * N + J);
                 yv[a] = ybar ? ld2(ybar, a * N + J) : oldv[a];
                 xv[a] = extra ? ld2(extra, a * N + J) : make_float2(0.f, 0.f);
             }

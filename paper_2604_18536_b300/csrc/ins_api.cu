@@ -716,6 +716,44 @@ struct Impl {
         }
         return INS_OK;
     }
+    // The step VJP's first P^T passes on (dt beta) ybar without forming it: vector kernels only
+    // (the caller checks rk_vec_ok on ybar and the alignment of the outputs).
+    template <int VW>
+    static ins_status div_fold_vec(ins_grid* g, const T* y, T* phi, const double* dt_dev, double dt_host, double beta) {
+        DivCoef<T> dc;
+        dc.nx = g->nx;
+        dc.ny = g->ny;
+        dc.nz = g->nz;
+        dc.idx = (T)(1.0 / g->d[0][0]);
+        dc.idz = (T)(1.0 / g->d[2][0]);
+        dc.idy = make_geo<T>(g).c[1] + (size_t)C_INV_D * g->ny;
+        dc.sdt = dt_dev;
+        dc.sdt_host = dt_host;
+        dc.sbeta = beta;
+        int kc;
+        const dim3 grd = vec_grid(g, VW, &kc);
+        KLAUNCH(g, "divergence", (k_divergence_vec<T, DIM, WALL, VW, false, true><<<grd, dim3(32, 8), 0, g->stream>>>(
+                                     dc, y, phi, kc)));
+        return INS_OK;
+    }
+    template <int VW>
+    static ins_status sub_fold_vec(ins_grid* g, const T* y, const T* p, T* out, const double* dt_dev, double dt_host,
+                                   double beta) {
+        RkArgs ra;
+        ra.dt_dev = dt_dev;
+        ra.dt_host = dt_host;
+        ra.a_next = 0.0;
+        ra.b = beta;
+        ra.stage = -1;
+        ra.last = 0;
+        ra.mx = nullptr;
+        ra.err_flag = g->err_flag;
+        int kc;
+        const dim3 grd = vec_grid(g, VW, &kc);
+        KLAUNCH(g, "sub_grad", (k_rk_update_vec<T, DIM, WALL, false, VW, false, true><<<grd, dim3(32, 8), 0, g->stream>>>(
+                                   rk_coef(g), y, p, nullptr, nullptr, out, ra, kc)));
+        return INS_OK;
+    }
     static ins_status sub_grad_fast(ins_grid* g, const T* src, const T* p, T* out) {
         if (rk_vec_ok<T>(g, src) && reinterpret_cast<uintptr_t>(out) % 16 == 0 && reinterpret_cast<uintptr_t>(p) % 16 == 0) {
             RkArgs ra;
@@ -1064,11 +1102,17 @@ struct Impl {
             ra.err_flag = g->err_flag;
             if ((s = rk_update<false>(g, F, rp, U[0], nullptr, U[st + 1], ra)) != INS_OK) return s;
         }
-        // reverse
-        INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
-        const long n = (long)g->dim * N;
-        KLAUNCH(g, "scale", k_scale_dt<T><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host,
-                                                                      lowst ? WRAY3_GAMMA[2] : B[3], n));
+        // reverse. 3-D with vector rows: the last stage's cotangent dt b ybar is formed inside its P^T
+        // passes and the first adjoint march reads ybar as the accumulator's previous value, so neither
+        // the copy ubar <- ybar nor the scaled field is materialised.
+        const double blast = lowst ? WRAY3_GAMMA[2] : B[3];
+        const bool fold = DIM == 3 && rk_vec_ok<T>(g, ybar) && reinterpret_cast<uintptr_t>(rp) % 16 == 0 &&
+                          reinterpret_cast<uintptr_t>(W) % 16 == 0;
+        if (!fold) {
+            INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
+            const long n = (long)g->dim * N;
+            KLAUNCH(g, "scale", k_scale_dt<T><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host, blast, n));
+        }
         AdjCoef<T> ac;
         ac.nx = g->nx;
         ac.ny = g->ny;
@@ -1084,9 +1128,22 @@ struct Impl {
         ac.dt_host = dt_host;
         for (int st = nst - 1; st >= 0; --st) {
             // w = P kbar_s (P is symmetric on a uniform periodic grid)
-            if ((s = div_fast(g, F, rp)) != INS_OK) return s;
-            if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
-            if ((s = sub_grad_fast(g, F, rp, W)) != INS_OK) return s;
+            const bool first = fold && st == nst - 1;
+            ac.ubar_in = first ? ybar : nullptr;
+            if (first) {
+                constexpr int V = VecT<T>::N;
+                if ((s = vec_width(g) == V ? div_fold_vec<V>(g, ybar, rp, dt_dev, dt_host, blast)
+                                           : div_fold_vec<V / 2>(g, ybar, rp, dt_dev, dt_host, blast)) != INS_OK)
+                    return s;
+                if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+                if ((s = vec_width(g) == V ? sub_fold_vec<V>(g, ybar, rp, W, dt_dev, dt_host, blast)
+                                           : sub_fold_vec<V / 2>(g, ybar, rp, W, dt_dev, dt_host, blast)) != INS_OK)
+                    return s;
+            } else {
+                if ((s = div_fast(g, F, rp)) != INS_OK) return s;
+                if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+                if ((s = sub_grad_fast(g, F, rp, W)) != INS_OK) return s;
+            }
             if (lowst) {
                 // kbar_{s-1} = dt gamma_{s-1} (Ubar_{s+1} + ubar_s) + dt zeta_s Ubar_{s+1}
                 ac.bn = st > 0 ? WRAY3_GAMMA[st - 1] + WRAY3_ZETA[st] : 0.0;

@@ -88,7 +88,9 @@ struct RkCoef {
 // SC (with stage -1 only): the wall-bounded pullback's M Omega (Omega^-1 M F - G p): F^x, F^z
 // scaled by 1/d_y[j] and F^y by 1/h_y[j] before the gradient, the result by d_y[j] (x, z) and
 // h_y[j] (y) after it; the stored top wall faces of u^y are 0.
-template <typename T, int DIM, bool WALL, bool LS = false, int VW = VecT<T>::N, bool SC = false>
+// SCL (with stage -1 only): F is read as (dt b) F (the step VJP's first cotangent dt b_last ybar,
+// formed here instead of in a separate pass).
+template <typename T, int DIM, bool WALL, bool LS = false, int VW = VecT<T>::N, bool SC = false, bool SCL = false>
 __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __restrict__ F, const T* __restrict__ p,
                                                        T* __restrict__ u0, T* __restrict__ acc, T* __restrict__ us,
                                                        RkArgs ra, int kchunk) {
@@ -143,6 +145,15 @@ __global__ void __launch_bounds__(256) k_rk_update_vec(RkCoef<T> c, const T* __r
             VT::ld(F + a, f[0]);
             VT::ld(F + N + a, f[1]);
             if (DIM == 3) VT::ld(F + 2 * N + a, f[2]);
+            if constexpr (SCL) {
+                const T al = (T)(dt * ra.b);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    f[0][e] *= al;
+                    f[1][e] *= al;
+                    if (DIM == 3) f[2][e] *= al;
+                }
+            }
             if constexpr (SC) {
                 const T sd = __ldg(&c.idy[j]);
 #pragma unroll
@@ -268,13 +279,16 @@ struct DivCoef {
     T idx, idz;          // 1/d of the uniform x and z directions
     const T* idy;        // 1/d_y[j]
     const T* ihy = nullptr;   // SC: 1/h_y[j]
+    const double* sdt = nullptr;   // SCL: u is read as (dt beta) u, dt from sdt or sdt_host
+    double sdt_host = 0.0, sbeta = 0.0;
 };
 
 // Block (32, 8); grid (ceil(nx/VEC/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx % VEC == 0 and
 // 16-byte aligned u and phi.
 // SC: the divergence of Omega^-1 M u of the wall-bounded pullback (u^x, u^z scaled by 1/d_y[j],
 // u^y by 1/h_y[j], the stored top wall faces of u^y taken as 0).
-template <typename T, int DIM, bool WALL, int VW = VecT<T>::N, bool SC = false>
+// SCL: the divergence of (dt beta) u (the step VJP's first cotangent).
+template <typename T, int DIM, bool WALL, int VW = VecT<T>::N, bool SC = false, bool SCL = false>
 __global__ void __launch_bounds__(256) k_divergence_vec(DivCoef<T> c, const T* __restrict__ u, T* __restrict__ phi,
                                                         int kchunk) {
     using VT = VecIO<T, VW>;
@@ -299,8 +313,15 @@ __global__ void __launch_bounds__(256) k_divergence_vec(DivCoef<T> c, const T* _
 #pragma unroll
     for (int e = 0; e < VEC; ++e) Zm[e] = (T)0;
     if (DIM == 3 && ok) VT::ld(u + 2 * N + (long)(kb == 0 ? nz - 1 : kb - 1) * plane + jrow + i0, Zm);
-    // SC row factors: x and z faces of row j, y faces of rows j and j - 1
+    // SC row factors: x and z faces of row j, y faces of rows j and j - 1 (SCL: times dt beta)
     T sxz = (T)1, sy = (T)1, sym = (T)1;
+    if constexpr (SCL) {
+        sxz = sy = sym = (T)((c.sdt ? *c.sdt : c.sdt_host) * c.sbeta);
+        if (DIM == 3) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) Zm[e] *= sxz;
+        }
+    }
     if constexpr (SC) {
         const int jc = j < ny ? j : ny - 1;
         sxz = idy;
@@ -320,7 +341,7 @@ __global__ void __launch_bounds__(256) k_divergence_vec(DivCoef<T> c, const T* _
             VT::ld(u + N + a, uy);
             if (!bottom) VT::ld(u + N + base + jprev + i0, uym);
             if (DIM == 3) VT::ld(u + 2 * N + a, uz);
-            if constexpr (SC) {
+            if constexpr (SC || SCL) {
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
                     ux[e] *= sxz;
