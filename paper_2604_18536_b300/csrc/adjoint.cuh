@@ -36,7 +36,6 @@ struct AdjCoef {
     const double* dt_dev;   // dt on the device, or null: dt_host
     double dt_host;
     double bn, an;          // b_{s-1}, a_{s,s-1} for the next stage cotangent
-    const T* ubar_in = nullptr;   // z marches: the accumulator's previous value (null: ubar0 itself)
 };
 
 // Block (32, 8), grid (ceil(nx/32), ceil(ny/8), nz). nu_part[block] receives the block's
@@ -157,7 +156,8 @@ template <typename T>
 __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __restrict__ u, const T* __restrict__ w,
                                                    const T* __restrict__ ybar, T* __restrict__ ubar0,
                                                    T* __restrict__ kb, double* __restrict__ nu_part,
-                                                   const T* __restrict__ extra, int kchunk) {
+                                                   const T* __restrict__ extra, int kchunk,
+                                                   const T* __restrict__ uin) {
     extern __shared__ __align__(16) unsigned char ajsm[];
     T(*s)[6][AJSP] = reinterpret_cast<T(*)[6][AJSP]>(ajsm);   // s[slot][comp: u 0-2, w 3-5][cell]
     const int nx = c.nx, ny = c.ny, nz = c.nz;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
             T oldv[3], yv[3], xv[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                oldv[a] = (c.ubar_in ? c.ubar_in : ubar0)[a * N + Jc];
+                oldv[a] = uin[a * N + Jc];   // the accumulator's previous value (ubar0, or ybar first)
                 yv[a] = ybar ? ybar[a * N + Jc] : oldv[a];
                 xv[a] = extra ? extra[a * N + Jc] : (T)0;
             }

@@ -322,7 +322,8 @@ template <typename T>
 __global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const T* __restrict__ u,
                                                         const T* __restrict__ w, const T* __restrict__ ybar,
                                                         T* __restrict__ ubar0, T* __restrict__ kbar,
-                                                        double* __restrict__ nu_part, int kchunk) {
+                                                        double* __restrict__ nu_part, int kchunk,
+                                                        const T* __restrict__ uin) {
     extern __shared__ __align__(16) unsigned char wz_smem[];
     T* const ring = reinterpret_cast<T*>(wz_smem);
     const Geo<T>& G = c.g;
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const 
             T old[3], yv[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                old[a] = ubar0[a * N + P];
+                old[a] = uin[a * N + P];   // the accumulator's previous value (ubar0, or ybar first)
                 yv[a] = ybar ? ybar[a * N + P] : old[a];
             }
             A.so[0] = slot(k - 1);

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_rhs_z2(AdjCoef<float> c, const f
                                                        const float* __restrict__ w, const float* __restrict__ ybar,
                                                        float* __restrict__ ubar0, float* __restrict__ kb,
                                                        double* __restrict__ nu_part, const float* __restrict__ extra,
-                                                       int kchunk) {
+                                                       int kchunk, const float* __restrict__ uin) {
     extern __shared__ __align__(16) float ax2s[];   // [slot 4][comp 6][AX2_PL]
     const int nx = c.nx, ny = c.ny, nz = c.nz;
     const int N = nx * ny * nz;   // 3 N < 2^31 (checked by the caller)
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_rhs_z2(AdjCoef<float> c, const f
             float2 oldv[3], yv[3], xv[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                oldv[a] = ld2(c.ubar_in ? c.ubar_in : ubar0, a * N + J);
+                oldv[a] = ld2(uin, a * N + J);   // the accumulator's previous value (ubar0, or ybar first)
                 yv[a] = ybar ? ld2(ybar, a * N + J) : oldv[a];
                 xv[a] = extra ? ld2(extra, a * N + J) : make_float2(0.f, 0.f);
             }

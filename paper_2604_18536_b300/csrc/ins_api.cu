@@ -655,8 +655,9 @@ struct Impl {
         return INS_OK;
     }
     // The row-scaled P^T passes of the wall-bounded pullback (vector kernels when the rows allow it).
-    template <int VW>
-    static ins_status div_scaled_vec(ins_grid* g, const T* u, T* phi) {
+    template <int VW, bool SCL = false>
+    static ins_status div_scaled_vec(ins_grid* g, const T* u, T* phi, const double* sdt = nullptr, double sdt_host = 0.0,
+                                     double sbeta = 0.0) {
         DivCoef<T> dc;
         dc.nx = g->nx;
         dc.ny = g->ny;
@@ -665,9 +666,12 @@ struct Impl {
         dc.idz = (T)(1.0 / g->d[2][0]);
         dc.idy = make_geo<T>(g).c[1] + (size_t)C_INV_D * g->ny;
         dc.ihy = make_geo<T>(g).c[1] + (size_t)C_INV_H * g->ny;
+        dc.sdt = sdt;
+        dc.sdt_host = sdt_host;
+        dc.sbeta = sbeta;
         int kc;
         const dim3 grd = vec_grid(g, VW, &kc);
-        KLAUNCH(g, "divergence", (k_divergence_vec<T, DIM, WALL, VW, true><<<grd, dim3(32, 8), 0, g->stream>>>(dc, u, phi, kc)));
+        KLAUNCH(g, "divergence", (k_divergence_vec<T, DIM, WALL, VW, true, SCL><<<grd, dim3(32, 8), 0, g->stream>>>(dc, u, phi, kc)));
         return INS_OK;
     }
     static ins_status div_scaled_fast(ins_grid* g, const T* u, T* phi) {
@@ -682,24 +686,25 @@ struct Impl {
         }
         return INS_OK;
     }
-    template <int VW>
-    static ins_status sub_scaled_vec(ins_grid* g, const T* src, const T* p, T* out, const double* hy, const double* dy) {
+    template <int VW, bool SCL = false>
+    static ins_status sub_scaled_vec(ins_grid* g, const T* src, const T* p, T* out, const double* hy, const double* dy,
+                                     const double* sdt = nullptr, double sdt_host = 0.0, double sbeta = 0.0) {
         RkCoef<T> rc = rk_coef(g);
         rc.idy = make_geo<T>(g).c[1] + (size_t)C_INV_D * g->ny;
         rc.hy = hy;
         rc.dy = dy;
         RkArgs ra;
-        ra.dt_dev = nullptr;
-        ra.dt_host = 0.0;
+        ra.dt_dev = sdt;
+        ra.dt_host = sdt_host;
         ra.a_next = 0.0;
-        ra.b = 0.0;
+        ra.b = sbeta;   // SCL: src is read as (dt b) src
         ra.stage = -1;
         ra.last = 0;
         ra.mx = nullptr;
         ra.err_flag = g->err_flag;
         int kc;
         const dim3 grd = vec_grid(g, VW, &kc);
-        KLAUNCH(g, "sub_grad", (k_rk_update_vec<T, DIM, WALL, false, VW, true><<<grd, dim3(32, 8), 0, g->stream>>>(
+        KLAUNCH(g, "sub_grad", (k_rk_update_vec<T, DIM, WALL, false, VW, true, SCL><<<grd, dim3(32, 8), 0, g->stream>>>(
                                    rc, src, p, nullptr, nullptr, out, ra, kc)));
         return INS_OK;
     }
@@ -954,10 +959,16 @@ struct Impl {
         const long n = (long)g->dim * N;
         const double* hy = g->geo64 + g->nx;
         const double* dy = g->geo64 + (g->nx + g->ny + g->nz) + g->nx;
-        INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
-        KLAUNCH(g, "scale", k_scale_dt<T><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host,
-                                                                      lowst ? WRAY3_GAMMA[2] : B[3], n));
         constexpr bool ZMARCH = DIM == 3 && std::is_same<T, float>::value;
+        // FP32 3-D with vector rows: the last stage's cotangent dt b ybar is formed inside its P^T passes
+        // and the first z march reads ybar as the accumulator's previous value (no copy, no scaled field)
+        const double blast = lowst ? WRAY3_GAMMA[2] : B[3];
+        const bool fold = ZMARCH && rk_vec_ok<T>(g, ybar) && reinterpret_cast<uintptr_t>(rp) % 16 == 0 &&
+                          reinterpret_cast<uintptr_t>(W) % 16 == 0;
+        if (!fold) {
+            INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
+            KLAUNCH(g, "scale", k_scale_dt<T><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host, blast, n));
+        }
         // z chunks of the 3-D adjoint march: about two waves of two CTAs per SM
         const long cols = (long)cg.x * cg.y;
         const long nch = std::max(1L, std::min((long)g->nz, (4L * device_sm_count() + cols / 2) / cols));
@@ -979,9 +990,23 @@ struct Impl {
         wa.dt_host = dt_host;
         for (int st = nst - 1; st >= 0; --st) {
             // w = P^T kbar = M Omega P (Omega^-1 M kbar)
-            if ((s = div_scaled_fast(g, F, rp)) != INS_OK) return s;
-            if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
-            if ((s = sub_scaled_fast(g, F, rp, W, hy, dy)) != INS_OK) return s;
+            const bool first = fold && st == nst - 1;
+            const T* uin = first ? ybar : ubar;   // the accumulator's previous value
+            if (first) {
+                constexpr int V = VecT<T>::N;
+                if ((s = vec_width(g) == V ? div_scaled_vec<V, true>(g, ybar, rp, dt_dev, dt_host, blast)
+                                           : div_scaled_vec<V / 2, true>(g, ybar, rp, dt_dev, dt_host, blast)) != INS_OK)
+                    return s;
+                if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+                if ((s = vec_width(g) == V ? sub_scaled_vec<V, true>(g, ybar, rp, W, hy, dy, dt_dev, dt_host, blast)
+                                           : sub_scaled_vec<V / 2, true>(g, ybar, rp, W, hy, dy, dt_dev, dt_host, blast)) !=
+                    INS_OK)
+                    return s;
+            } else {
+                if ((s = div_scaled_fast(g, F, rp)) != INS_OK) return s;
+                if ((s = poisson<T>(g, rp, rp)) != INS_OK) return s;
+                if ((s = sub_scaled_fast(g, F, rp, W, hy, dy)) != INS_OK) return s;
+            }
             if (lowst) {
                 wa.bn = st > 0 ? WRAY3_GAMMA[st - 1] + WRAY3_ZETA[st] : 0.0;
                 wa.an = st > 0 ? WRAY3_GAMMA[st - 1] : 0.0;
@@ -994,7 +1019,7 @@ struct Impl {
             // (in FP64 the march's register count leaves one CTA per SM, and the global form is faster)
             if constexpr (ZMARCH)
                 KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_z<T><<<zg, dim3(32, 8), wall_adj_smem<T>(), g->stream>>>(
-                                          wa, U[st], W, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, part, zkc)));
+                                          wa, U[st], W, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, part, zkc, uin)));
             else
                 KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_g<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
                                           wa, U[st], W, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, part)));
@@ -1129,7 +1154,7 @@ struct Impl {
         for (int st = nst - 1; st >= 0; --st) {
             // w = P kbar_s (P is symmetric on a uniform periodic grid)
             const bool first = fold && st == nst - 1;
-            ac.ubar_in = first ? ybar : nullptr;
+            const T* uin = first ? ybar : ubar;   // the accumulator's previous value
             if (first) {
                 constexpr int V = VecT<T>::N;
                 if ((s = vec_width(g) == V ? div_fold_vec<V>(g, ybar, rp, dt_dev, dt_host, blast)
@@ -1166,13 +1191,13 @@ struct Impl {
                 if constexpr (std::is_same<T, float>::value) {
                     if (pair_adj) {
                         KLAUNCH(g, "adj_rhs", k_adj_rhs_z2<<<ag, dim3(32, 8), adj_smem, g->stream>>>(
-                                                  ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra, akc));
+                                                  ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra, akc, uin));
                         done = true;
                     }
                 }
                 if (!done)
                     KLAUNCH(g, "adj_rhs", k_adj_rhs_z<T><<<ag, dim3(AJX, AJY), adj_smem, g->stream>>>(
-                                              ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra, akc));
+                                              ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra, akc, uin));
             } else {
                 KLAUNCH(g, "adj_rhs", k_adj_rhs<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
                                           ac, U[st], W, ysrc, ubar, st > 0 ? F : nullptr, part, extra));

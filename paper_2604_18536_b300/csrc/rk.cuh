@@ -313,22 +313,22 @@ __global__ void __launch_bounds__(256) k_divergence_vec(DivCoef<T> c, const T* _
 #pragma unroll
     for (int e = 0; e < VEC; ++e) Zm[e] = (T)0;
     if (DIM == 3 && ok) VT::ld(u + 2 * N + (long)(kb == 0 ? nz - 1 : kb - 1) * plane + jrow + i0, Zm);
-    // SC row factors: x and z faces of row j, y faces of rows j and j - 1 (SCL: times dt beta)
+    // SC row factors: x and z faces of row j, y faces of rows j and j - 1; SCL: times dt beta
     T sxz = (T)1, sy = (T)1, sym = (T)1;
-    if constexpr (SCL) {
-        sxz = sy = sym = (T)((c.sdt ? *c.sdt : c.sdt_host) * c.sbeta);
+    if constexpr (SC || SCL) {
+        const T al = SCL ? (T)((c.sdt ? *c.sdt : c.sdt_host) * c.sbeta) : (T)1;
+        if constexpr (SC) {
+            const int jc = j < ny ? j : ny - 1;
+            sxz = idy * al;
+            sy = jc == ny - 1 ? (T)0 : __ldg(&c.ihy[jc]) * al;
+            sym = jc > 0 ? __ldg(&c.ihy[jc - 1]) * al : (T)0;
+        } else {
+            sxz = sy = sym = al;
+        }
         if (DIM == 3) {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) Zm[e] *= sxz;
         }
-    }
-    if constexpr (SC) {
-        const int jc = j < ny ? j : ny - 1;
-        sxz = idy;
-        sy = jc == ny - 1 ? (T)0 : __ldg(&c.ihy[jc]);
-        sym = jc > 0 ? __ldg(&c.ihy[jc - 1]) : (T)0;
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) Zm[e] *= sxz;
     }
     for (int k = kb; k < ke; ++k) {
         const long base = (long)k * plane;
