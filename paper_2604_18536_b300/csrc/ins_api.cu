@@ -513,19 +513,19 @@ bool pair_ok(const ins_grid* g, const void* u) {
     return g->fusion == 2 && g->nx % 2 == 0 && 3 * g->N < (1L << 31) && reinterpret_cast<uintptr_t>(u) % 8 == 0;
 }
 
-template <bool WALL, bool STAGE>
+template <bool WALL, bool STAGE, bool STS = false>
 ins_status launch_pair(ins_grid* g, const char* name, const float* Fs, const float* p, const float* u0, float* acc,
                        float* F, float* r, const FusedArgs& fa) {
     static bool attr = false;
     if (!attr) {
-        INS_CUDA(cudaFuncSetAttribute(k_rhs_div_x2<WALL, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        INS_CUDA(cudaFuncSetAttribute(k_rhs_div_x2<WALL, STAGE, STS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       PairRegSmem::BYTES));
         attr = true;
     }
     const dim3 grd = pair_grid(g, pair_ctas_per_sm(WALL, STAGE));
     const int kc = (g->nz + grd.z - 1) / grd.z;
     const float* ihy = make_geo<float>(g).c[1] + (size_t)C_INV_H * g->ny;
-    KLAUNCH(g, name, (k_rhs_div_x2<WALL, STAGE><<<grd, dim3(RBX, RBY, 1), PairRegSmem::BYTES, g->stream>>>(
+    KLAUNCH(g, name, (k_rhs_div_x2<WALL, STAGE, STS><<<grd, dim3(RBX, RBY, 1), PairRegSmem::BYTES, g->stream>>>(
                          make_rhs_coef<float>(g), (float)(1.0 / g->h[0][0]), (float)(1.0 / g->h[2][0]), ihy, Fs, p,
                          u0, acc, F, r, fa, kc)));
     return INS_OK;
@@ -1111,7 +1111,43 @@ struct Impl {
             ra.err_flag = g->err_flag;
             if ((s = rk_update<true>(g, F, rp, U[st], scratch, U[st + 1], ra)) != INS_OK) return s;
         }
-        for (int st = 0; !lowst && st < 3; ++st) {
+        // FP32 3-D RK4 without a closure: stages 2 and 3 recomputed by the fused boundary kernel, which
+        // stores the staged u_{s+1} of its own cells (no accumulator; p and r in separate buffers)
+        bool fused_rc = false;
+        if constexpr (DIM == 3 && std::is_same<T, float>::value) {
+            fused_rc = !lowst && !g->closure && !g->eddy && g->pbuf && g->us && pair_ok(g, un) &&
+                       reinterpret_cast<uintptr_t>(un) % 16 == 0;
+            if (fused_rc) {
+                T* Fb[2] = {F, reinterpret_cast<T*>(g->us)};
+                T* pp = reinterpret_cast<T*>(g->pbuf);
+                if ((s = launch_rhs_div<T, DIM, WALL>(g, U[0], Fb[0], rp)) != INS_OK) return s;
+                if ((s = poisson<T>(g, rp, pp)) != INS_OK) return s;
+                for (int st = 0; st < 2; ++st) {
+                    FusedArgs fa;
+                    fa.dt_dev = dt_dev;
+                    fa.dt_host = dt_host;
+                    fa.a_next = A[st];
+                    fa.b = 0.0;
+                    fa.stage = st;
+                    fa.ust = U[st + 1];
+                    if ((s = launch_pair<WALL, true, true>(g, "update_rhs_div", Fb[st & 1], pp, U[0], nullptr,
+                                                           Fb[(st + 1) & 1], rp, fa)) != INS_OK)
+                        return s;
+                    if ((s = poisson<T>(g, rp, pp)) != INS_OK) return s;
+                }
+                RkArgs ra;
+                ra.dt_dev = dt_dev;
+                ra.dt_host = dt_host;
+                ra.a_next = A[2];
+                ra.b = 0.0;
+                ra.stage = 0;
+                ra.last = 0;
+                ra.mx = nullptr;
+                ra.err_flag = g->err_flag;
+                if ((s = rk_update<false>(g, Fb[0], pp, U[0], nullptr, U[3], ra)) != INS_OK) return s;
+            }
+        }
+        for (int st = 0; !lowst && !fused_rc && st < 3; ++st) {
             T* m = nullptr;
             if ((s = closure_term<T>(g, U[st], &m, false)) != INS_OK) return s;
             if ((s = launch_rhs_div<T, DIM, WALL>(g, U[st], F, rp, m)) != INS_OK) return s;

@@ -646,6 +646,7 @@ struct FusedArgs {
     double a_next;   // a_{s+1,s}
     double b;        // b_s
     int stage;       // s (0, 1 or 2)
+    float* ust = nullptr;   // pair kernel, STS: the staged u_{s+1} of the own cells
 };
 
 template <typename T, bool WALL>

@@ -24,6 +24,8 @@
 // STAGE = true:  the fused RK stage boundary: plane cells are staged from F_s, p_s and u_0 as
 //   u_{s+1} = u_0 + dt a_{s+1,s} (F_s - G p_s), and the RK accumulator is updated at the
 //   own cells (acc = b_s k or acc += b_s k), as in k_update_rhs_div.
+// STS (with STAGE): no accumulator; the staged u_{s+1} of the own cells is stored to fa.ust
+//   (the stage states of the step VJP's recomputation).
 // Requirements (checked by the caller): nx even, every field 8-byte aligned, 3 x cells < 2^31.
 #pragma once
 
@@ -335,7 +337,7 @@ struct PairRegSmem {
 // registers (three CTAs); the staged and the wall variants keep 128 (two CTAs, no spills).
 constexpr int pair_ctas_per_sm(bool wall, bool stage) { return (stage || wall) ? 2 : 3; }
 
-template <bool WALL, bool STAGE>
+template <bool WALL, bool STAGE, bool STS = false>
 __global__ void __launch_bounds__(RNT, pair_ctas_per_sm(WALL, STAGE))
     k_rhs_div_x2(RhsCoef<float> c, float ihx, float ihz, const float* __restrict__ ihy, const float* __restrict__ Fs,
                   const float* __restrict__ p, const float* __restrict__ u0, float* __restrict__ acc,
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(RNT, pair_ctas_per_sm(WALL, STAGE))
                 lpz[e] = ld2(p, wrapz(q + 1) * iplane + pm.off[e]);
             }
         }
-        if constexpr (STAGE) {
+        if constexpr (STAGE && !STS) {
             if (lown && fa.stage > 0) {
                 lA[0] = ld2(acc, la0);
                 lA[1] = ld2(acc, la0 + N);
@@ -435,7 +437,13 @@ __global__ void __launch_bounds__(RNT, pair_ctas_per_sm(WALL, STAGE))
                 ux = make_float2(fmaf(dta, kx0, ux.x), fmaf(dta, kx1, ux.y));
                 uy = make_float2(fmaf(dta, ky0, uy.x), fmaf(dta, ky1, uy.y));
                 uz = make_float2(fmaf(dta, kz0, uz.x), fmaf(dta, kz1, uz.y));
-                if (e == 0 && lown) {
+                if constexpr (STS) {
+                    if (e == 0 && lown) {
+                        st2(fa.ust, la0, ux.x, ux.y);
+                        st2(fa.ust, la0 + N, uy.x, uy.y);
+                        st2(fa.ust, la0 + 2 * N, uz.x, uz.y);
+                    }
+                } else if (e == 0 && lown) {
                     if (fa.stage == 0) {
                         st2(acc, la0, bb * kx0, bb * kx1);
                         st2(acc, la0 + N, bb * ky0, bb * ky1);
