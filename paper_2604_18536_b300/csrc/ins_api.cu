@@ -592,10 +592,11 @@ struct Impl {
         const int nv = g->nx / V;
         return (nv % 32 != 0 && nv < 128 && (g->nx / (V / 2)) % 32 == 0) ? V / 2 : V;
     }
+    // z chunk from the wave count of the resident CTAs (the vector kernels keep four 256-thread CTAs
+    // per SM; each CTA reads its chunk plus one plane of p or u^z beyond it)
     static dim3 vec_grid(const ins_grid* g, int vw, int* kc) {
         const int bx = (g->nx / vw + 31) / 32, by = (g->ny + 7) / 8;
-        int c = (int)(((long)bx * by * g->nz) / 2368);
-        c = c < 1 ? 1 : (c > g->nz ? g->nz : c);
+        const int c = wave_chunk((long)bx * by, g->nz, 4L * device_sm_count(), 1);
         *kc = c;
         return dim3(bx, by, (g->nz + c - 1) / c);
     }
