@@ -1168,8 +1168,9 @@ struct Impl {
         // passes and the first adjoint march reads ybar as the accumulator's previous value, so neither
         // the copy ubar <- ybar nor the scaled field is materialised.
         const double blast = lowst ? WRAY3_GAMMA[2] : B[3];
-        const bool fold = DIM == 3 && rk_vec_ok<T>(g, ybar) && reinterpret_cast<uintptr_t>(rp) % 16 == 0 &&
-                          reinterpret_cast<uintptr_t>(W) % 16 == 0;
+        // (FP32 only: in FP64 the folded multiplies load the FP64 pipe as much as the passes they save)
+        const bool fold = DIM == 3 && sizeof(T) == 4 && rk_vec_ok<T>(g, ybar) &&
+                          reinterpret_cast<uintptr_t>(rp) % 16 == 0 && reinterpret_cast<uintptr_t>(W) % 16 == 0;
         if (!fold) {
             INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
             const long n = (long)g->dim * N;
