@@ -318,7 +318,9 @@ struct SharedWallAcc {
     }
 };
 
-template <typename T>
+// UIN: the accumulator's previous value comes from uin (the first stage of the pullback reads
+// ybar there); otherwise from ubar0 itself (uin unused).
+template <typename T, bool UIN = false>
 __global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const T* __restrict__ u,
                                                         const T* __restrict__ w, const T* __restrict__ ybar,
                                                         T* __restrict__ ubar0, T* __restrict__ kbar,
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const 
             T old[3], yv[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                old[a] = uin[a * N + P];   // the accumulator's previous value (ubar0, or ybar first)
+                old[a] = UIN ? uin[a * N + P] : ubar0[a * N + P];   // the accumulator's previous value
                 yv[a] = ybar ? ybar[a * N + P] : old[a];
             }
             A.so[0] = slot(k - 1);

@@ -981,6 +981,8 @@ struct Impl {
             if (!attr) {
                 INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_wall_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               wall_adj_smem<T>()));
+                INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_wall_z<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              wall_adj_smem<T>()));
                 attr = true;
             }
         }
@@ -1018,10 +1020,15 @@ struct Impl {
             // ubar0 += J_F^T w; the next stage cotangent into F
             // FP32 3-D: the z march (shared-memory ring); FP64 and 2-D: neighbours from global memory
             // (in FP64 the march's register count leaves one CTA per SM, and the global form is faster)
-            if constexpr (ZMARCH)
-                KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_z<T><<<zg, dim3(32, 8), wall_adj_smem<T>(), g->stream>>>(
-                                          wa, U[st], W, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, part, zkc, uin)));
-            else
+            if constexpr (ZMARCH) {
+                if (first) {
+                    KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_z<T, true><<<zg, dim3(32, 8), wall_adj_smem<T>(), g->stream>>>(
+                                              wa, U[st], W, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, part, zkc, uin)));
+                } else {
+                    KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_z<T><<<zg, dim3(32, 8), wall_adj_smem<T>(), g->stream>>>(
+                                              wa, U[st], W, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, part, zkc, uin)));
+                }
+            } else
                 KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_g<T, DIM><<<cg, dim3(32, 8), 0, g->stream>>>(
                                           wa, U[st], W, lowst ? nullptr : ybar, ubar, st > 0 ? F : nullptr, part)));
             if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, znblk, nubar));
