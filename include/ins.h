@@ -190,8 +190,9 @@ ins_status ins_set_march_chunk(ins_grid* g, int planes);
  * Periodic uniform grids use P^T = P and gather-form transposed stencils. Wall-bounded grids
  * (y a no-slip wall, possibly stretched) use P^T = M Omega P Omega^-1 M (Omega the velocity
  * volumes; M zeroes the stored top wall faces of u^y, which are not unknowns: cotangents
- * there are ignored and ubar_n is 0 there) and scatter-form transposes with atomics (the
- * summation order, hence the last bits, may vary between calls). The first call allocates the
+ * there are ignored and ubar_n is 0 there) and gather-form transposes (each output value is
+ * summed by one thread in a fixed order, no atomics, so repeated calls return the same bits).
+ * The first call allocates the
  * step-VJP workspace (3 stage states, two fields, nu partial sums: about 5 velocity fields),
  * kept until ins_grid_destroy; make the first call before any stream capture.
  * The grid's F, r/p and RK accumulator buffers are reused as scratch. */
@@ -250,13 +251,20 @@ ins_status ins_check_finite(ins_grid* g);
  * stream: cudaStream_t the work is enqueued on.
  * Scratch: a static device array of 192 KiB inside the library (per-index
  * maxima and spacings), held by every GPU that loads the library until the
- * process exits; nothing is allocated or freed by this call. The first call on
- * each device looks up that array's device address (cudaGetSymbolAddress);
+ * process exits; the call itself allocates and frees nothing. Loading is not
+ * free, though: CUDA loads the library's device code and this array into a
+ * device's memory lazily, at the first call into the library on that device
+ * (this entry point or any other), and that load takes device memory (the
+ * code of every kernel plus the 192 KiB). A caller whose memory manager is
+ * about to reserve nearly all device memory should therefore make its first
+ * call on each device before the pool takes that memory. The first call on
+ * each device also looks up that array's device address (cudaGetSymbolAddress);
  * make this first call before any stream capture. Every call shares the array
  * and clears what must start at zero, so calls whose work overlaps on the GPU
  * (other streams, other host threads on the same device) race: serialise them.
- * The spacings are copied from pageable host memory, so the call waits for the
- * stream's earlier work before returning. */
+ * The spacings are staged in a host buffer of the calling thread and copied
+ * with cudaMemcpyAsync from that pageable memory; such a copy has consumed its
+ * source when it returns, so the next call may reuse the buffer. */
 ins_status ins_cfl_dt_noalloc(const ins_grid_desc* desc, const void* u, double cfl, double* dt_dev,
                               void* stream);
 

@@ -93,3 +93,58 @@ def test_noalloc_rejects_sizes_beyond_the_limit():
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     assert _noalloc(desc, u, 0.3, out) == _lib.INS_ERR_ARG
     assert b"4096" in _lib.lib().ins_last_error()
+
+
+_FIRST_CALL_SCRIPT = r"""
+import ctypes, json, sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2604_18536_b300 import inputs, _lib
+torch.cuda.init()
+faces = inputs.periodic_box(32, 3)
+keep = [np.ascontiguousarray(f, dtype=np.float64) for f in faces]
+d = _lib.GridDesc()
+d.dim = 3
+for a in range(3):
+    d.n[a] = 32
+    d.bc[a] = _lib.INS_PERIODIC
+    d.face_coords[a] = keep[a].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+d.dtype = _lib.INS_F64
+d.nu = 0.01
+u = torch.tensor(inputs.random_field((3, 32, 32, 32), 3), dtype=torch.float64, device="cuda")
+out = torch.zeros(1, dtype=torch.float64, device="cuda")
+lib = _lib.lib()
+st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+torch.cuda.synchronize()
+free = [torch.cuda.mem_get_info()[0]]
+for _ in range(4):
+    rc = lib.ins_cfl_dt_noalloc(ctypes.byref(d), ctypes.c_void_p(u.data_ptr()), 0.5,
+                                ctypes.c_void_p(out.data_ptr()), st)
+    assert rc == _lib.INS_OK, lib.ins_last_error()
+    torch.cuda.synchronize()
+    free.append(torch.cuda.mem_get_info()[0])
+print(json.dumps({"free": free, "dt": out.item()}))
+"""
+
+
+def test_noalloc_first_call_in_fresh_process():
+    """In a process that has not called the library yet, the first call loads the library's device
+    code and static array (CUDA loads modules lazily), which takes device memory; later calls take
+    none. The drop is recorded so that memory-constrained callers know what to set aside."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FIRST_CALL_SCRIPT, root], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    free = res["free"]
+    first_drop = free[0] - free[1]
+    print(f"first call on the device: {first_drop / 2**20:.1f} MiB of device memory (module load)")
+    assert first_drop >= 0
+    assert first_drop < 512 * 2**20
+    assert free[1] == free[2] == free[3] == free[4]
+    assert res["dt"] > 0.0
