@@ -124,8 +124,9 @@ def kernel_model(name, n, s, fused=False):
     """Algorithmic bytes and FP64-pipe operations per launch of each kernel family.
 
     N cells, spec = (n/2+1) n^2 complex values of 2 s bytes; s = value size.
-    rhs_div: reads u (3N), writes F (3N) and r (N); 78 FP64 ops/cell for F (uniform grid, 26 per
-             component) + 6 for D F.
+    rhs_div: reads u (3N), writes F (3N) and r (N); 79 FP64-pipe ops/cell for F and D F on a
+             uniform grid (the count of the kernel as built, with the z-face products of a plane
+             carried to the next plane of the march instead of recomputed).
     update_rhs_div (FP32 fused stage boundary): reads F_s, u_0, acc (9N) and p_s (N), writes acc,
              F_{s+1} (6N) and r (N): 17 values per cell (14 for the first boundary, no acc read).
     fft_*:   each pass reads and writes its data once.
@@ -135,7 +136,7 @@ def kernel_model(name, n, s, fused=False):
     N = n ** 3
     spec = (n // 2 + 1) * n * n
     if name == "rhs_div":
-        return 7 * N * s, 84 * N
+        return 7 * N * s, 79 * N
     if name == "update_rhs_div":
         return 16 * N * s, None     # stage 1 -> 2 has no accumulator read: (14 + 17 + 17) / 3
     if name == "fft_x_r2c" or name == "fft_x_c2r":
@@ -147,8 +148,8 @@ def kernel_model(name, n, s, fused=False):
     return None, None
 
 
-# DRAM bytes per launch of the dominant kernels from ncu captures of the current kernels
-# (profiles/rhs_div_hit256.md, profiles/update_rhs_div_hit256_f32.md); n = 256 only.
+# DRAM bytes per launch of the dominant kernels, from ncu captures of the current kernels at n = 256
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch).
 TRAFFIC = {("f64", "rhs_div"): 907.1e6, ("f32", "update_rhs_div"): 1071.0e6}
 
 
@@ -365,10 +366,9 @@ def run_ours(args):
         }
         if "f32" in results and "f64" in results:
             f = results["f32"]
-            line["fp32"] = {k: f[k] for k in ("value", "ms_per_step", "ms_per_step_plain_launches",
-                                               "ms_per_step_profiled", "roofline", "e2e", "gpu_launches",
-                                               "step_hbm_frac", "kernels", "clocks", "adjoint") if k in f}
-            line["fp32"]["speedup_vs_fp64"] = f["value"] / prim["value"]
+            line["fp32_detail"] = {k: f[k] for k in ("ms_per_step_plain_launches", "ms_per_step_profiled",
+                                                      "roofline", "e2e", "gpu_launches", "kernels", "clocks",
+                                                      "adjoint", "workspace_bytes") if k in f}
         if not args.no_closure:
             line["closure"] = bench_closure()
         if not args.no_channel:
@@ -380,7 +380,21 @@ def run_ours(args):
         if not args.no_diff:
             line["differentiation"] = bench_differentiation(seed=args.seed)
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(steps=1)
+            line["cpu_baseline"] = cpu_baseline()
+        if "f32" in results and "f64" in results:
+            # compact FP32 summary as the line's last key (kept short so that a truncated record of the
+            # line's tail still carries it)
+            f = results["f32"]
+            r = f["roofline"]
+            line["fp32"] = {"value": f["value"], "ms_per_step": f["ms_per_step"],
+                            "step_hbm_frac": round(f["step_hbm_frac"], 4),
+                            "speedup_vs_fp64": f["value"] / prim["value"],
+                            "rel_error_vs_fp64_step": fp32_step_error(n, seed=args.seed),
+                            "roofline": {"bound": r["bound"], "kernel": r["kernel"], "achieved": round(r["achieved"], 1),
+                                         "peak": r["peak"], "unit": r["unit"], "frac": round(r["frac"], 4),
+                                         "traffic": r["traffic"]},
+                            "e2e": f["e2e"]["value"] if f.get("e2e") else None,
+                            "adjoint_forward_ratio": round(f["adjoint"]["ratio"], 3)}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -646,8 +660,35 @@ def bench_differentiation(n=128, nsteps=16, reps=3, seed=0):
     return out
 
 
-def bench_closure(n=64, reps=10):
-    """CNN closure forward and backward at the LES size n^3 (FP32 grid, BF16 tensor cores)."""
+def fp32_step_error(n, seed=0):
+    """Relative L2 difference of one FP32 RK4 step from the FP64 step of the same (FP32-representable)
+    field with the same dt: the FP32 path's error at the benchmark size (the FP64 path itself is within
+    1e-12 of the FP64 oracle there)."""
+    import torch
+    from paper_2604_18536_b300 import inputs
+    from paper_2604_18536_b300.solver import Grid
+    faces = inputs.periodic_box(n, 3)
+    g64 = Grid(faces, ["periodic"] * 3, NU, dtype=torch.float64)
+    u64 = torch.tensor(inputs.spectrum_velocity_raw(n, 3, seed=seed, k0=4.0), dtype=torch.float64, device="cuda")
+    g64.project(u64, out=u64)
+    u64.mul_(1.0 / math.sqrt(g64.diag(u64)["ke"]))
+    u64 = u64.float().double()
+    u32 = u64.float()
+    dt = float(g64.cfl_dt(u64, CFL).item())
+    g64.step(u64, dt=dt)
+    g64.close()
+    g32 = Grid(faces, ["periodic"] * 3, NU, dtype=torch.float32)
+    g32.step(u32, dt=dt)
+    g32.close()
+    err = float(torch.linalg.vector_norm(u32.double() - u64) / torch.linalg.vector_norm(u64))
+    del u64, u32
+    torch.cuda.empty_cache()
+    return err
+
+
+def bench_closure(n=64, batch=8, reps=5):
+    """CNN closure forward and backward on a training batch of `batch` fields at the LES size n^3 (FP32
+    grids, BF16 tensor cores): the batch runs as `batch` calls on one grid, as in training."""
     import torch
     from paper_2604_18536_b300 import inputs
     from paper_2604_18536_b300.closure import Closure, init_params, SHAPES
@@ -656,37 +697,43 @@ def bench_closure(n=64, reps=10):
     c = Closure(g)
     W, b = init_params(0, 1.0)
     c.set_params(W, b)
-    u = torch.tensor(inputs.random_field((3, n, n, n), 1), dtype=torch.float32, device="cuda")
-    m = g.new_velocity()
+    us = [torch.tensor(inputs.random_field((3, n, n, n), 1 + i), dtype=torch.float32, device="cuda")
+          for i in range(batch)]
+    ms = [g.new_velocity() for _ in range(batch)]
     ub = g.new_velocity()
     dW = [torch.zeros_like(w) for w in W]
     db = [torch.zeros_like(x) for x in b]
-    c.forward(u, m, save=True)
-    c.backward(m, ub, dW, db)
+    c.forward(us[0], ms[0], save=True)
+    c.backward(ms[0], ub, dW, db)
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     g.profile(True)
-    e[0].record(st)
+    fwd = bwd = 0.0
     for _ in range(reps):
-        c.forward(u, m, save=True)
-    e[1].record(st)
-    for _ in range(reps):
-        c.backward(m, ub, dW, db)
-    e[2].record(st)
-    torch.cuda.synchronize()
+        e[0].record(st)
+        for i in range(batch):
+            c.forward(us[i], ms[i], save=(i == batch - 1))
+        e[1].record(st)
+        c.backward(ms[batch - 1], ub, dW, db)
+        e[2].record(st)
+        torch.cuda.synchronize()
+        fwd += e[0].elapsed_time(e[1])
+        bwd += e[1].elapsed_time(e[2])
     prof = g.profile_read()
     g.profile(False)
     c.check()
     N = n ** 3
     flops_fwd = sum(2.0 * N * 27 * ci * co for ci, co in SHAPES)
     conv = prof.get("conv3d_tc", (1, 0.0))
-    # conv launches per rep: 4 forward + 4 backward (data gradient) with the same algorithmic flops
-    conv_s = conv[1] / 1e3 / reps / 2
+    # conv launches: 4 per forward (batch x reps forwards) + 4 data-gradient launches per backward (reps)
+    conv_s = conv[1] / 1e3 / (reps * (batch + 1))
     peaks = measured_peaks()
     pk = peaks.get("bf16_tflops", 1800.0)
-    res = {"n": n, "fwd_ms": e[0].elapsed_time(e[1]) / reps, "bwd_ms": e[1].elapsed_time(e[2]) / reps,
-           "flops_fwd": flops_fwd, "conv_tflops": flops_fwd / conv_s / 1e12,
+    res = {"n": n, "batch": batch, "fwd_ms_per_batch": fwd / reps, "fwd_ms_per_sample": fwd / reps / batch,
+           "bwd_ms_per_sample": bwd / reps, "flops_fwd_per_sample": flops_fwd,
+           "fwd_tflops_per_batch": flops_fwd * batch / (fwd / reps / 1e3) / 1e12,
+           "conv_tflops": flops_fwd / conv_s / 1e12,
            "roofline": {"bound": "tensor", "kernel": "conv3d_tc", "achieved": flops_fwd / conv_s / 1e12,
                         "peak": pk, "unit": "TFLOP/s", "frac": flops_fwd / conv_s / 1e12 / pk, "traffic": None,
                         "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)"},
@@ -697,24 +744,75 @@ def bench_closure(n=64, reps=10):
 
 
 # ------------------------------------------------------------------ oracle on the host
-def cpu_baseline(steps=1, n=128, seed=0):
-    """FP64 numpy oracle, as it stands, on a bounded sample: RK4 steps of the same workload at 128^3."""
+def _oracle_steps(n, steps, warmup, seed):
+    """Wall seconds of each of `steps` FP64 oracle RK4 steps (+ CFL) of the workload at n^3, after
+    `warmup` untimed steps. Runs in a worker process of the host-core baseline, or in-process."""
     from oracle.grid import Grid as OGrid
     from oracle import poisson, timestep, diagnostics
     from paper_2604_18536_b300 import inputs
-    faces = inputs.periodic_box(n, 3)
-    og = OGrid(faces, ["periodic"] * 3, NU)
+    og = OGrid(inputs.periodic_box(n, 3), ["periodic"] * 3, NU)
     u, _ = poisson.project(og, inputs.spectrum_velocity_raw(n, 3, seed=seed, k0=4.0))
     u = u / math.sqrt(diagnostics.kinetic_energy(og, u))
     dt = timestep.cfl_dt(og, u, CFL)
-    t0 = time.perf_counter()
-    for _ in range(steps):
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
         u = timestep.rk4_step(og, u, dt)
         dt = timestep.cfl_dt(og, u, CFL)
-    sec = time.perf_counter() - t0
-    return {"value": n ** 3 * steps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d RK4 step(s) + CFL of the same workload at %d^3, FP64 numpy (single-threaded), %.1f s"
-                      % (steps, n, sec)}
+        if i >= warmup:
+            times.append(time.perf_counter() - t0)
+    return times
+
+
+def _oracle_worker(args):
+    return _oracle_steps(*args)
+
+
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def cpu_baseline(n=128, n_big=256, steps=3, warmup=1, seed=0):
+    """The FP64 numpy oracle as it stands, timed on the host cores on a bounded sample of the workload.
+
+    The oracle's array arithmetic runs on one thread, so the host cores are used by P independent
+    replicas (spawned worker processes, one trajectory each, seed + i) of the n^3 workload: each times
+    `steps` RK4 steps after `warmup`; value = sum over replicas of n^3 / (median step time). P is
+    bounded by the cores, the free host memory (about 2 GB per 128^3 replica) and 16. The single-thread
+    step time at n^3 and one step at n_big^3 (the benchmark's size) are reported beside it."""
+    import multiprocessing as mp
+    nproc, model = host_cpu()
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = 8e9
+    P = max(1, min(nproc, 16, int(avail // 2.5e9)))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(P) as pool:
+        res = pool.map(_oracle_worker, [(n, steps, warmup, seed + i) for i in range(P)])
+    wall = time.perf_counter() - t0
+    med = [statistics.median(t) for t in res]
+    value = sum(n ** 3 / m for m in med)
+    t_big = _oracle_steps(n_big, 1, 0, seed)[0]
+    return {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
+            "sample": "%d replicas (one process each) of the workload at %d^3, each the median of %d RK4 steps "
+                      "after %d warm-up, FP64 numpy oracle (one thread per replica); %.0f s wall"
+                      % (P, n, steps, warmup, wall),
+            "host": {"nproc": nproc, "cpu_model": model},
+            "single_thread": {"n%d" % n: {"ms_per_step": statistics.median(res[0]) * 1e3,
+                                          "value": n ** 3 / statistics.median(res[0])},
+                              "n%d" % n_big: {"ms_per_step": t_big * 1e3, "value": n_big ** 3 / t_big,
+                                              "steps": 1}}}
 
 
 def run_reference(args):
