@@ -10,11 +10,12 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libins.so")
-SOURCES = ["ins_api.cu"]
+# translation units of the library (each compiled separately, in parallel, then linked)
+SOURCES = ["ins_grid.cu", "ins_step.cu", "ins_vjp.cu", "ins_closure.cu", "ins_eddy.cu", "ins_noalloc.cu"]
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC",
     "--expt-relaxed-constexpr",
 ]
 
@@ -34,18 +35,37 @@ def up_to_date():
     return os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_source_mtime()
 
 
+def _run(cmd):
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    return r.returncode, r.stdout + r.stderr
+
+
 def build(verbose=False, force=False):
     """Compile libins.so (skips when it is newer than every source)."""
     if not force and up_to_date():
         return LIB
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
-        ["-o", LIB + ".tmp"] + [os.path.join(CSRC, s) for s in SOURCES]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
-    if verbose:
-        sys.stderr.write(r.stderr)
+    import shutil
+    import tempfile
+    from concurrent.futures import ThreadPoolExecutor
+    OBJ = tempfile.mkdtemp(prefix="libins_build_")   # object files stay out of the tree
+    extra = ["-Xptxas", "-v"] if verbose else []
+    cmds, objs = [], []
+    for src in SOURCES:
+        obj = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
+        objs.append(obj)
+        cmds.append([nvcc()] + NVCC_FLAGS + extra + ["-c", "-o", obj, os.path.join(CSRC, src)])
+    with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+        results = list(ex.map(_run, cmds))
+    for (rc, out), src in zip(results, SOURCES):
+        if rc != 0:
+            raise RuntimeError("nvcc failed on %s:\n%s" % (src, out))
+        if verbose:
+            sys.stderr.write(out)
+    rc, out = _run([nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", LIB + ".tmp"] + objs)
+    if rc != 0:
+        raise RuntimeError("link failed:\n" + out)
     os.replace(LIB + ".tmp", LIB)
+    shutil.rmtree(OBJ, ignore_errors=True)
     return LIB
 
 

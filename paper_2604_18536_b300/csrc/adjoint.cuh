@@ -124,7 +124,7 @@ __global__ void k_scale_dt(const T* __restrict__ x, T* __restrict__ out, const d
 }
 
 // *acc += sum of the partials, in a fixed order (one block of 256 threads).
-__global__ void k_sum_partials(const double* __restrict__ part, long n, double* __restrict__ acc) {
+static __global__ void k_sum_partials(const double* __restrict__ part, long n, double* __restrict__ acc) {
     __shared__ double red[256];
     double s = 0.0;
     for (long t = threadIdx.x; t < n; t += blockDim.x) s += part[t];

@@ -25,7 +25,7 @@ constexpr int ax2_smem() { return 4 * 6 * AX2_PL * (int)sizeof(float); }
 
 __device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return p2add(a, p2neg(b)); }
 
-__global__ void __launch_bounds__(256, 2) k_adj_rhs_z2(AdjCoef<float> c, const float* __restrict__ u,
+static __global__ void __launch_bounds__(256, 2) k_adj_rhs_z2(AdjCoef<float> c, const float* __restrict__ u,
                                                        const float* __restrict__ w, const float* __restrict__ ybar,
                                                        float* __restrict__ ubar0, float* __restrict__ kb,
                                                        double* __restrict__ nu_part, const float* __restrict__ extra,

@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
 
 // Pack weights W[27][cin][cout] (FP32 master copy) into the B layout of k_conv3d_tc as BF16.
 // forward: row n = co, channel k = ci, tap t; data gradient: row n = ci, channel k = co, tap 26 - t.
-__global__ void k_pack_weights(const float* __restrict__ W, int cin, int cout, int N, int KG, int transpose,
+static __global__ void k_pack_weights(const float* __restrict__ W, int cin, int cout, int N, int KG, int transpose,
                                __nv_bfloat16* __restrict__ blob) {
     const int K = 8 * KG;
     const int total = 27 * N * K;
@@ -827,7 +827,7 @@ __global__ void __launch_bounds__(256, 1) k_wgrad_plane(const __nv_bfloat16* __r
 
 // dW[t][ci][co] += sum over the CTAs' partial blocks part[c][t][ci][0..N) (co < cout); one
 // thread per weight, fixed summation order.
-__global__ void k_wgrad_reduce(const float* __restrict__ part, int ncta, int N, int cout, float* __restrict__ dW) {
+static __global__ void k_wgrad_reduce(const float* __restrict__ part, int ncta, int N, int cout, float* __restrict__ dW) {
     const int total = 27 * 32 * cout;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int tci = e / cout, co = e - tci * cout;

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_rk_update(Geo<T> g, const T* __restrict
 
 // dt = cfl * min(1 / max_{a,i} mx[off_a + i] / h_a[i], dmin^2 / nu); resets mx to 0.
 // h64 holds h_x, h_y, h_z back to back (the same layout as mx). One block of 256 threads.
-__global__ void k_cfl_finalize(unsigned long long* mx, const double* __restrict__ h64, int ntot, double dmin2_nu,
+static __global__ void k_cfl_finalize(unsigned long long* mx, const double* __restrict__ h64, int ntot, double dmin2_nu,
                                double cfl, double* dt_out) {
     __shared__ double red[256];
     double m = 0.0;
