@@ -1,7 +1,7 @@
-"""torch.autograd over ins_step: differentiable RK4 steps with per-step checkpointing.
+"""torch.autograd over ins_step: differentiable steps with per-step checkpointing.
 
-Each step saves only its input u_n; the backward pass (ins_step_vjp) recomputes the
-four stage states from it and runs the hand-written pullback kernels, so an unroll of
+The step is the grid's scheme (classic RK4 or Wray's low-storage RK3). Each step saves only
+its input u_n; the backward pass (ins_step_vjp) recomputes the stage states from it and runs the hand-written pullback kernels, so an unroll of
 T steps keeps T velocity fields plus one step's stage states. The time step dt is
 treated as a constant. The viscosity enters as a tensor so that dL/dnu is returned;
 its value must equal the grid's nu (the grid's coefficients are built from it).
@@ -10,7 +10,9 @@ its value must equal the grid's nu (the grid's coefficients are built from it).
 import torch
 
 
-class _RK4Step(torch.autograd.Function):
+class _SolverStep(torch.autograd.Function):
+    """One ins_step of the grid's scheme; backward is ins_step_vjp."""
+
     @staticmethod
     def forward(ctx, u, nu, grid, dt):
         ctx.grid = grid
@@ -37,8 +39,8 @@ def _nu_tensor(u, grid, nu):
 
 
 def step(u, grid, dt, nu=None):
-    """One differentiable RK4 step: u_{n+1} = step(u_n); gradients flow to u and nu."""
-    return _RK4Step.apply(u, _nu_tensor(u, grid, nu), grid, float(dt))
+    """One differentiable step of the grid's scheme: u_{n+1} = step(u_n); gradients flow to u and nu."""
+    return _SolverStep.apply(u, _nu_tensor(u, grid, nu), grid, float(dt))
 
 
 def rollout(u0, grid, dt, nsteps, nu=None):
@@ -48,6 +50,6 @@ def rollout(u0, grid, dt, nsteps, nu=None):
     out = []
     u = u0
     for _ in range(nsteps):
-        u = _RK4Step.apply(u, nu, grid, float(dt))
+        u = _SolverStep.apply(u, nu, grid, float(dt))
         out.append(u)
     return out
