@@ -1,8 +1,9 @@
 """torch.autograd over ins_step: differentiable steps with per-step checkpointing.
 
 The step is the grid's scheme (classic RK4 or Wray's low-storage RK3). Each step saves only
-its input u_n; the backward pass (ins_step_vjp) recomputes the stage states from it and runs the hand-written pullback kernels, so an unroll of
-T steps keeps T velocity fields plus one step's stage states. The time step dt is
+its input u_n; the backward pass (ins_step_vjp) recomputes the stage states from it and runs
+the hand-written pullback kernels, so an unroll of T steps keeps T velocity fields plus one
+step's stage states. The time step dt is
 treated as a constant. The viscosity enters as a tensor so that dL/dnu is returned;
 its value must equal the grid's nu (the grid's coefficients are built from it).
 """
