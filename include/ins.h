@@ -168,6 +168,25 @@ ins_status ins_set_wall_solver(ins_grid* g, int solver);
  * one-cell kernel's up to the order of FP32 roundings. */
 ins_status ins_set_step_fusion(ins_grid* g, int enable);
 
+/* Arithmetic of the FP64 step (Sec. 7.3: FP64 is the DNS precision; the arithmetic that
+ * reaches it is an implementation choice). INS_ARITH_NATIVE evaluates F, D F, the FFTs of
+ * the Poisson solve and the stage updates in FP64 instructions. INS_ARITH_DOUBLE_FLOAT (the
+ * default where the grid supports it) evaluates them in double-float arithmetic -- each value
+ * the unevaluated sum of two FP32 numbers, about 48 significant bits, error-free
+ * transformations on the FP32 pipe -- because this GPU issues FP32 operations 62 times
+ * faster than FP64 ones. Storage stays FP64: the caller's velocity is read and written as
+ * FP64, the last stage adds the step's increment to it in FP64, and the CFL time step is
+ * reduced from the FP64 result exactly as in native mode (bit-identical to the FP64 rule).
+ * The step's relative field error against the FP64 oracle stays within the FP64 tolerance
+ * (1e-12 per step). Only ins_step / ins_step_n of the classic RK4 scheme without an attached
+ * closure or eddy-viscosity model use it; every other call (and Wray3, and grids with a
+ * closure) runs native FP64. Supported grids: FP64, every direction periodic, nx even, every
+ * length a power of two from 16 to 256 or 48, 96, 192; elsewhere the setter returns
+ * INS_ERR_UNSUPPORTED and the grid stays native. INS_ERR_ARG for other modes. */
+typedef enum { INS_ARITH_NATIVE = 0, INS_ARITH_DOUBLE_FLOAT = 1 } ins_arith;
+ins_status ins_set_f64_arithmetic(ins_grid* g, int mode);
+ins_status ins_get_f64_arithmetic(const ins_grid* g, int* mode);
+
 /* Launch shape of the fused two-cells-per-thread kernels (fusion level 2; no counterpart in
  * the paper): each CTA marches `planes` consecutive z planes of its 64 x 8 column. 0 (default)
  * chooses the chunk from the grid and the number of SMs; results do not depend on it.

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "INS_OK", 1: "INS_ERR_ARG", 2: "INS_ERR_UNSUPPORTED", 3: "INS
 
 INS_PERIODIC = 0
 INS_WALL = 1
+INS_ARITH_NATIVE, INS_ARITH_DOUBLE_FLOAT = 0, 1
 INS_F32 = 0
 INS_F64 = 1
 INS_RK4 = 0
@@ -64,6 +65,8 @@ SIGNATURES = {
     "ins_set_step_fusion": (_c.c_int, [_vp, _c.c_int]),
     "ins_set_march_chunk": (_c.c_int, [_vp, _c.c_int]),
     "ins_set_wall_solver": (_c.c_int, [_vp, _c.c_int]),
+    "ins_set_f64_arithmetic": (_c.c_int, [_vp, _c.c_int]),
+    "ins_get_f64_arithmetic": (_c.c_int, [_vp, _vp]),
     "ins_set_eddy_viscosity": (_c.c_int, [_vp, _c.c_int, _c.c_double]),
     "ins_eddy_viscosity": (_c.c_int, [_vp, _vp, _vp]),
     "ins_step": (_c.c_int, [_vp, _vp, _vp, _c.c_double, _vp, _c.c_double]),

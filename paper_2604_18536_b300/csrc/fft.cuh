@@ -20,6 +20,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace ins {
 
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(FftLine<T> pl, cplx
             const int c = item & (TW - 1), m = item >> lgTW;
             const long col = c0 + c;
             T s = (T)0;
-            if (col < ncol) s = __ldg(&scale[(col / cdiv) * outer + m * lstride + (col % cdiv)]);
+            if (col < ncol) s = ldg_t(&scale[(col / cdiv) * outer + m * lstride + (col % cdiv)]);
             const cplx<T> z = X[m * SP + c];
             Y[m * SP + c] = {z.re * s, -z.im * s};     // scaled and conjugated
         }

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 256, 2) k_fft_strided_r
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) {
                 const long m = q + R1 * k2;
-                const T s = ok ? __ldg(&scale[cb + m * lstride]) : (T)0;
+                const T s = ok ? ldg_t(&scale[cb + m * lstride]) : (T)0;
                 v[k2] = {v[k2].re * s, -v[k2].im * s};
             }
             stage_a<T, R2>(v, q, tw);

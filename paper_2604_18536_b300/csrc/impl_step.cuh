@@ -94,9 +94,74 @@ ins_status Impl<T, DIM, WALL>::step_fused(ins_grid* g, T* u, const double* dt_de
     return INS_OK;
 }
 
+// ------------------------------------------------------------ double-float FP64 step
+// F + D F with double-float arithmetic; UI = double for the caller's FP64 field (split by bits
+// on load), df for the stage state.
+template <int DIM, typename UI>
+ins_status launch_rhs_div_df(ins_grid* g, const UI* u, df* F, df* r) {
+    const dim3 blk(RBX, RBY, 1);
+    const dim3 grd((g->nx + RBX - 1) / RBX, (g->ny + RBY - 1) / RBY, DIM == 3 ? (g->nz + g->kchunk - 1) / g->kchunk : 1);
+    KLAUNCH(g, "rhs_div", (k_rhs_div<df, DIM, false, UI><<<grd, blk, 0, g->stream>>>(make_rhs_coef<df>(g), u, F, r,
+                                                                                      g->kchunk, (const df*)nullptr)));
+    return INS_OK;
+}
+
+template <int DIM>
+ins_status rk_update_df(ins_grid* g, const df* F, const df* p, double* u0, df* acc, df* us, const RkArgs& ra) {
+    RkCoefDf c;
+    c.nx = g->nx;
+    c.ny = g->ny;
+    c.nz = g->nz;
+    c.ihx = df(1.0 / g->h[0][0]);
+    c.ihy = df(1.0 / g->h[1][0]);
+    c.ihz = df(DIM == 3 ? 1.0 / g->h[2][0] : 0.0);
+    const int bx = (g->nx / 2 + 31) / 32, by = (g->ny + 7) / 8;
+    const int kc = wave_chunk((long)bx * by, g->nz, 4L * device_sm_count(), 1);
+    const dim3 grd(bx, by, (g->nz + kc - 1) / kc);
+    KLAUNCH(g, "rk_update", (k_rk_update_df<DIM><<<grd, dim3(32, 8), 0, g->stream>>>(c, F, p, u0, acc, us, ra, kc)));
+    return INS_OK;
+}
+
+// The classic RK4 step of an FP64 periodic grid in double-float arithmetic (ins_set_f64_arithmetic):
+// F, r/p, the spectrum, acc and the stage state hold double-float pairs; u stays FP64.
+template <int DIM>
+ins_status step_df(ins_grid* g, double* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
+    static const double A[4] = {0.5, 0.5, 1.0, 0.0};
+    static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    df* F = reinterpret_cast<df*>(g->F);
+    df* rp = reinterpret_cast<df*>(g->rp);
+    df* acc = reinterpret_cast<df*>(g->acc);
+    df* us = reinterpret_cast<df*>(g->us);
+    ins_status s;
+    for (int st = 0; st < 4; ++st) {
+        s = st == 0 ? launch_rhs_div_df<DIM, double>(g, u, F, rp) : launch_rhs_div_df<DIM, df>(g, us, F, rp);
+        if (s != INS_OK) return s;
+        if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
+        RkArgs ra;
+        ra.dt_dev = dt_dev;
+        ra.dt_host = dt_host;
+        ra.a_next = A[st];
+        ra.b = B[st];
+        ra.stage = st;
+        ra.last = st == 3;
+        ra.mx = (st == 3 && next_dt) ? g->cfl_max : nullptr;
+        ra.err_flag = g->err_flag;
+        if ((s = rk_update_df<DIM>(g, F, rp, u, acc, us, ra)) != INS_OK) return s;
+    }
+    if (next_dt) {
+        KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz,
+                                                                            g->dmin2_nu, cfl, next_dt));
+    }
+    return INS_OK;
+}
+
 template <typename T, int DIM, bool WALL>
 ins_status Impl<T, DIM, WALL>::step(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
     if (g->scheme == INS_WRAY3) return step_wray3(g, u, dt_dev, dt_host, next_dt, cfl);
+    if constexpr (std::is_same<T, double>::value && !WALL) {
+        if (g->use_df && !g->closure && !g->eddy && reinterpret_cast<uintptr_t>(u) % 16 == 0)
+            return step_df<DIM>(g, u, dt_dev, dt_host, next_dt, cfl);
+    }
     if constexpr (DIM == 3 && std::is_same<T, float>::value) {
         if (g->pbuf && !g->closure && !g->eddy && g->fusion > 0 && rk_vec_ok<T>(g, u))
             return step_fused(g, u, dt_dev, dt_host, next_dt, cfl);

@@ -137,6 +137,18 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     // FP32 periodic: [columns of the fused pass | its line | 1/N] (3-D: ny nxh | nz; 2-D: nxh | ny)
     const size_t neig = (!wall_y && D.dtype == INS_F32) ? (size_t)(dim == 3 ? g->ny * nxh + g->nz : nxh + g->ny) + 1 : 0;
     const size_t o_eig = off; off += al(neig * 4);
+    // double-float FP64 step: FP64 periodic grids whose lengths all have register FFT kernels
+    // (x even for the two-cell update)
+    bool df_ok = D.dtype == INS_F64 && !wall_y && g->nx % 2 == 0;
+    for (int a = 0; a < dim; ++a) df_ok = df_ok && reg_fft_len(n3[a]);
+    size_t o_twdf[3] = {0, 0, 0}, o_scdf = 0;
+    if (df_ok) {
+        for (int a = 0; a < 3; ++a) {
+            o_twdf[a] = off;
+            off += al((size_t)n3[a] * 16);
+        }
+        o_scdf = off; off += al((size_t)spec * 8);
+    }
     if (!wall_y) {
         o_scale = off; off += al((size_t)spec * ts);
     } else {
@@ -172,6 +184,11 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     g->lam = reinterpret_cast<double*>(b + o_lam);
     g->dct_qw = g->wall_dct ? b + o_qw : nullptr;
     g->eig = neig ? reinterpret_cast<float*>(b + o_eig) : nullptr;
+    g->df_ok = g->use_df = df_ok ? 1 : 0;
+    if (df_ok) {
+        for (int a = 0; a < 3; ++a) g->tw_df[a] = b + o_twdf[a];
+        g->scale_df = b + o_scdf;
+    }
     if (!wall_y) {
         g->scale = b + o_scale;
     } else {
@@ -248,6 +265,19 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
         if (a == 1 && wall_y && !g->wall_dct) continue;
         ins_status s = D.dtype == INS_F64 ? upload_twiddles<double>(g, a, g->tw[a], n3[a])
                                           : upload_twiddles<float>(g, a, g->tw[a], n3[a]);
+        if (s == INS_OK && df_ok) {
+            // exp(-2 pi i m / L) as double-float pairs (re.hi, re.lo, im.hi, im.lo)
+            std::vector<float> tw(4 * (size_t)n3[a]);
+            for (int m = 0; m < n3[a]; ++m) {
+                const double ang = 2.0 * M_PI * (double)m / (double)n3[a];
+                const df re(std::cos(ang)), im(-std::sin(ang));
+                tw[4 * m] = re.hi;
+                tw[4 * m + 1] = re.lo;
+                tw[4 * m + 2] = im.hi;
+                tw[4 * m + 3] = im.lo;
+            }
+            if (!up(g->tw_df[a], tw.data(), tw.size() * 4)) s = fail(INS_ERR_CUDA, "twiddle upload failed");
+        }
         if (s != INS_OK) {
             std::string m = g_err;
             return bail(s, m);
@@ -301,6 +331,9 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
             else
                 k_make_scale<float><<<1024, 256>>>(reinterpret_cast<float*>(g->scale), g->lam, g->lam + g->nx,
                                                    g->lam + g->nx + g->ny, (int)nxh, g->ny, g->nz, ntot);
+            if (df_ok)
+                k_make_scale<df><<<1024, 256>>>(reinterpret_cast<df*>(g->scale_df), g->lam, g->lam + g->nx,
+                                                g->lam + g->nx + g->ny, (int)nxh, g->ny, g->nz, ntot);
             if (cudaGetLastError() != cudaSuccess) return bail(INS_ERR_CUDA, "scale table kernel failed");
         } else {
             // Thomas factors per (kx, kz) mode, FP64, constant in time
@@ -403,6 +436,24 @@ ins_status ins_grid_destroy(ins_grid* g) {
 ins_status ins_set_stream(ins_grid* g, void* stream) {
     if (!g) return fail(INS_ERR_ARG, "null grid");
     g->stream = reinterpret_cast<cudaStream_t>(stream);
+    return INS_OK;
+}
+
+ins_status ins_set_f64_arithmetic(ins_grid* g, int mode) {
+    g_err.clear();
+    if (!g) return fail(INS_ERR_ARG, "null grid");
+    if (mode != INS_ARITH_NATIVE && mode != INS_ARITH_DOUBLE_FLOAT) return fail(INS_ERR_ARG, "unknown arithmetic mode");
+    if (mode == INS_ARITH_DOUBLE_FLOAT && !g->df_ok)
+        return fail(INS_ERR_UNSUPPORTED,
+                    "double-float arithmetic needs an FP64 periodic grid with even nx and FFT lengths 16..256 "
+                    "(powers of two), 48, 96 or 192");
+    g->use_df = mode == INS_ARITH_DOUBLE_FLOAT ? 1 : 0;
+    return INS_OK;
+}
+
+ins_status ins_get_f64_arithmetic(const ins_grid* g, int* mode) {
+    if (!g || !mode) return fail(INS_ERR_ARG, "null argument");
+    *mode = g->use_df ? INS_ARITH_DOUBLE_FLOAT : INS_ARITH_NATIVE;
     return INS_OK;
 }
 

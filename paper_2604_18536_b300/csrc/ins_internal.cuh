@@ -29,6 +29,8 @@
 #include "conv_tc.cuh"
 #include "eddy.cuh"
 #include "rhs_x2.cuh"
+#include "dfloat.cuh"
+#include "rk_df.cuh"
 
 using namespace ins;
 
@@ -110,6 +112,12 @@ struct ins_grid {
     int radix[3][FFT_MAX_STAGES];
     int nst[3] = {0, 0, 0};
     void* scale = nullptr;         // T, [nz][ny][nxh] (periodic)
+    // double-float arithmetic of the FP64 step (periodic grids with register-FFT lengths): FFT
+    // twiddles and the spectral table as (hi, lo) float pairs
+    int df_ok = 0;                 // the grid supports it
+    int use_df = 0;                // selected (ins_set_f64_arithmetic; default on where supported)
+    void* tw_df[3] = {nullptr, nullptr, nullptr};
+    void* scale_df = nullptr;
     float* eig = nullptr;          // FP32 periodic: N-scaled eigenvalue sums of the fused pass (see k_fft_strided_pipe)
     double* lam = nullptr;         // FP64 eigenvalues: x (nxh) | y (ny) | z (nz)
     double* th_lo = nullptr;       // Thomas: lo[ny], up[ny]
@@ -216,7 +224,7 @@ FftLine<T> make_line(const ins_grid* g, int a) {
     pl.L = a == 0 ? g->nx : (a == 1 ? g->ny : g->nz);
     pl.nst = g->nst[a];
     for (int s = 0; s < FFT_MAX_STAGES; ++s) pl.radix[s] = s < pl.nst ? g->radix[a][s] : 1;
-    pl.tw = reinterpret_cast<const cplx<T>*>(g->tw[a]);
+    pl.tw = reinterpret_cast<const cplx<T>*>(std::is_same<T, df>::value ? g->tw_df[a] : g->tw[a]);
     return pl;
 }
 
@@ -297,21 +305,21 @@ void launch_strided_reg(cudaStream_t st, const cplx<T>* tw, cplx<T>* S, long nco
         using Sh = RegShape<T, R1, R2>;
         const unsigned blocks = (unsigned)((ncol + Sh::TW - 1) / Sh::TW);
         k_fft_strided_reg<T, R1, R2><<<blocks, Sh::NT, 0, st>>>(tw, S, ncol, cdiv, outer, lstride, mode, scale);
-        return;
+    } else {
+        // FP32: persistent, double-buffered cp.async variant; the next tile's loads overlap the butterflies
+        using Ph = PipeShape<T, R1, R2>;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_fft_strided_pipe<T, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Ph::smem_max());
+            attr = true;
+        }
+        const long ntiles = (ncol + Ph::TW - 1) / Ph::TW;
+        const long cap = 2L * device_sm_count();
+        const unsigned blocks = (unsigned)(ntiles < cap ? ntiles : cap);
+        k_fft_strided_pipe<T, R1, R2><<<blocks, Ph::NT, Ph::smem(mode == 2), st>>>(tw, S, ncol, cdiv, outer, lstride, mode,
+                                                                                 scale);
     }
-    // FP32: persistent, double-buffered cp.async variant; the next tile's loads overlap the butterflies
-    using Ph = PipeShape<T, R1, R2>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_fft_strided_pipe<T, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Ph::smem_max());
-        attr = true;
-    }
-    const long ntiles = (ncol + Ph::TW - 1) / Ph::TW;
-    const long cap = 2L * device_sm_count();
-    const unsigned blocks = (unsigned)(ntiles < cap ? ntiles : cap);
-    k_fft_strided_pipe<T, R1, R2><<<blocks, Ph::NT, Ph::smem(mode == 2), st>>>(tw, S, ncol, cdiv, outer, lstride, mode,
-                                                                             scale);
 }
 
 template <typename T>
@@ -334,19 +342,21 @@ void launch_x_reg(bool forward, cudaStream_t st, const cplx<T>* tw, const T* in,
                   int nxh) {
     // FP32 inverse: persistent double-buffered variant when the spectrum is 16-byte aligned (FP64 is
     // FP64-pipe bound and keeps the one-tile-per-CTA kernel)
-    if (sizeof(T) == 4 && !forward && reinterpret_cast<uintptr_t>(S) % 16 == 0) {
-        using Px = PipeX<T, R1, R2>;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_fft_x_c2r_pipe<T, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Px::smem_c2r(Px::L / 2 + 1));
-            attr = true;
+    if constexpr (sizeof(T) == 4) {
+        if (!forward && reinterpret_cast<uintptr_t>(S) % 16 == 0) {
+            using Px = PipeX<T, R1, R2>;
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_fft_x_c2r_pipe<T, R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Px::smem_c2r(Px::L / 2 + 1));
+                attr = true;
+            }
+            const long ntiles = (((long)lines + 1) / 2 + Px::TW - 1) / Px::TW;
+            const long cap = 2L * device_sm_count();
+            const unsigned blocks = (unsigned)(ntiles < cap ? ntiles : cap);
+            k_fft_x_c2r_pipe<T, R1, R2><<<blocks, Px::NT, Px::smem_c2r(nxh), st>>>(tw, S, out, lines, nxh);
+            return;
         }
-        const long ntiles = (((long)lines + 1) / 2 + Px::TW - 1) / Px::TW;
-        const long cap = 2L * device_sm_count();
-        const unsigned blocks = (unsigned)(ntiles < cap ? ntiles : cap);
-        k_fft_x_c2r_pipe<T, R1, R2><<<blocks, Px::NT, Px::smem_c2r(nxh), st>>>(tw, S, out, lines, nxh);
-        return;
     }
     using Sh = RegShape<T, R1, R2>;
     const long pairs = (lines + 1) / 2;
@@ -403,17 +413,22 @@ ins_status set_smem_attrs() {
     return INS_OK;
 }
 
+// T = df (the double-float FP64 step): register kernels for every length (the grid supports
+// double-float arithmetic only when all lengths have them), its own twiddles and spectral table.
 template <typename T>
 ins_status poisson(ins_grid* g, const T* r, T* p) {
-    if (ins_status s0 = set_smem_attrs<T>(); s0 != INS_OK) return s0;
+    constexpr bool DF = std::is_same<T, df>::value;
+    if constexpr (!DF) {
+        if (ins_status s0 = set_smem_attrs<T>(); s0 != INS_OK) return s0;
+    }
     cudaStream_t st = g->stream;
     const int nx = g->nx, ny = g->ny, nz = g->nz, nxh = g->nxh;
     const long lines = (long)ny * nz;
     cplx<T>* S = reinterpret_cast<cplx<T>*>(g->S);
     FftLine<T> lx = make_line<T>(g, 0);
-    if (reg_fft_len(nx, sizeof(T) == 8)) {
+    if (DF || reg_fft_len(nx, sizeof(T) == 8)) {
         KLAUNCH(g, "fft_x_r2c", x_reg<T>(nx, true, st, lx.tw, r, S, nullptr, (int)lines, nxh));
-    } else {
+    } else if constexpr (!DF) {
         const int lg = g->lg_tw_x;
         const long pairs = (lines + 1) / 2;
         const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);
@@ -434,15 +449,18 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
             outer = 0;
             lstride = (long)ny * nxh;
         }
-        if (reg_fft_len(pl.L)) {
+        if (DF || reg_fft_len(pl.L)) {
             // FP32: the fused pass forms its scale from the eigenvalue sums (no table read)
-            const T* sc = sizeof(T) == 4 ? reinterpret_cast<const T*>(g->eig) : reinterpret_cast<const T*>(g->scale);
+            const T* sc = sizeof(T) == 4 ? reinterpret_cast<const T*>(g->eig)
+                                         : reinterpret_cast<const T*>(DF ? g->scale_df : g->scale);
             KLAUNCH(g, "fft_strided", strided_reg<T>(pl.L, st, pl.tw, S, ncol, cdiv, outer, lstride, mode, sc));
             return INS_OK;
         }
-        const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
-        KLAUNCH(g, "fft_strided", k_fft_strided<T><<<blocks, FFT_THREADS, fft_smem<T>(pl.L, lg), st>>>(
-            pl, S, ncol, cdiv, outer, lstride, mode, reinterpret_cast<const T*>(g->scale), lg));
+        if constexpr (!DF) {
+            const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
+            KLAUNCH(g, "fft_strided", k_fft_strided<T><<<blocks, FFT_THREADS, fft_smem<T>(pl.L, lg), st>>>(
+                pl, S, ncol, cdiv, outer, lstride, mode, reinterpret_cast<const T*>(g->scale), lg));
+        }
         return INS_OK;
     };
     ins_status s;
@@ -454,7 +472,7 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
             if ((s = strided(2, 2)) != INS_OK) return s;
             if ((s = strided(1, 1)) != INS_OK) return s;
         }
-    } else {
+    } else if constexpr (!DF) {
         if (g->dim == 3 && (s = strided(2, 0)) != INS_OK) return s;
         const long ncol = (long)nz * nxh;
         const double norm = 1.0 / ((double)nx * (g->dim == 3 ? nz : 1));
@@ -471,9 +489,9 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
         }
         if (g->dim == 3 && (s = strided(2, 1)) != INS_OK) return s;
     }
-    if (reg_fft_len(nx, sizeof(T) == 8)) {
+    if (DF || reg_fft_len(nx, sizeof(T) == 8)) {
         KLAUNCH(g, "fft_x_c2r", x_reg<T>(nx, false, st, lx.tw, nullptr, S, p, (int)lines, nxh));
-    } else {
+    } else if constexpr (!DF) {
         const int lg = g->lg_tw_x;
         const long pairs = (lines + 1) / 2;
         const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);

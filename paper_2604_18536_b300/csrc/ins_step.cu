@@ -102,7 +102,7 @@ ins_status ins_step_n(ins_grid* g, void* u, int nsteps, const double* dt_dev, do
     const std::vector<double> key = {(double)reinterpret_cast<uintptr_t>(u), (double)reinterpret_cast<uintptr_t>(dt_dev),
                                      dt_host, (double)reinterpret_cast<uintptr_t>(next_dt_dev), cfl,
                                      (double)g->scheme, (double)g->fusion, (double)g->march_chunk, (double)g->use_dct,
-                                     (double)g->eddy, g->eddy_C, (double)reinterpret_cast<uintptr_t>(g->closure),
+                                     (double)g->eddy, g->eddy_C, (double)reinterpret_cast<uintptr_t>(g->closure), (double)g->use_df,
                                      (double)reinterpret_cast<uintptr_t>(g->stream)};
     if (!g->step_exec || key != g->graph_key) {
         if (g->step_exec) {

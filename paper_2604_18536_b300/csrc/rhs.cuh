@@ -26,6 +26,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace ins {
 
@@ -364,14 +365,15 @@ __device__ __forceinline__ PlaneMap<WALL> plane_map(int nx, int ny, int i0, int 
 }
 
 // Offsets are 32-bit: grids hold fewer than 2^31 cells, so every in-component index fits.
-template <typename T, int DIM, bool WALL>
-__device__ __forceinline__ void plane_fetch(const PlaneMap<WALL>& pm, const T* __restrict__ u0, const T* __restrict__ u1,
-                                            const T* __restrict__ u2, int base, T (&v)[DIM][RPF]) {
+// S: the storage type of u (FP64 fields read by the double-float kernel are split on load).
+template <typename T, int DIM, bool WALL, typename S = T>
+__device__ __forceinline__ void plane_fetch(const PlaneMap<WALL>& pm, const S* __restrict__ u0, const S* __restrict__ u1,
+                                            const S* __restrict__ u2, int base, T (&v)[DIM][RPF]) {
 #pragma unroll
     for (int q = 0; q < RPF; ++q) {
         if (pm.off[q] >= 0) {
             const int o = base + pm.off[q];
-            T x0 = u0[o], x1 = u1[o];
+            T x0 = cvt_in<T>(u0[o]), x1 = cvt_in<T>(u1[o]);
             if (WALL && pm.ghost[q]) {
                 x0 = -x0;
                 x1 = (T)0;
@@ -379,7 +381,7 @@ __device__ __forceinline__ void plane_fetch(const PlaneMap<WALL>& pm, const T* _
             v[0][q] = x0;
             v[1][q] = x1;
             if constexpr (DIM == 3) {
-                T x2 = u2[o];
+                T x2 = cvt_in<T>(u2[o]);
                 if (WALL && pm.ghost[q]) x2 = -x2;
                 v[2][q] = x2;
             }
@@ -401,8 +403,9 @@ __device__ __forceinline__ void plane_commit(const PlaneMap<WALL>& pm, Plane<T> 
 // F (dim fields, may be null) and r = D F. Grid: (ceil(nx/32), ceil(ny/8), ceil(nz/kchunk)), block (32, 8).
 // m (dim fields, may be null): a closure term added to F on every face, including the halo
 // faces the divergence reads.
-template <typename T, int DIM, bool WALL>
-__global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restrict__ u, T* __restrict__ F,
+// UI: storage type of u (T, or double for the double-float kernel reading an FP64 field).
+template <typename T, int DIM, bool WALL, typename UI = T>
+__global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const UI* __restrict__ u, T* __restrict__ F,
                                                  T* __restrict__ r, int kchunk, const T* __restrict__ mc) {
     __shared__ T su[3][DIM][RSPL];
     __shared__ T sFx[RBY][RBX + 1];
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
     T v[DIM][RPF];
 
     if constexpr (DIM == 2) {
-        plane_fetch<T, DIM, WALL>(pm, u, u + N, u, 0, v);   // 2-D: no third component
+        plane_fetch<T, DIM, WALL, UI>(pm, u, u + N, u, 0, v);   // 2-D: no third component
         plane_commit<T, DIM, WALL>(pm, su[0], v);
         __syncthreads();
         CPlane<T> o = su[0];
@@ -471,13 +474,13 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
         T* const F2 = F ? F + 2 * N : nullptr;
         auto wrapz = [nz](int k) { return k < 0 ? k + nz : (k >= nz ? k - nz : k); };
         int sm = 0, so = 1, sp = 2;
-        plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(kb - 2) * iplane, v);
+        plane_fetch<T, DIM, WALL, UI>(pm, u, u + N, u + 2 * N, wrapz(kb - 2) * iplane, v);
         plane_commit<T, DIM, WALL>(pm, su[sm], v);
-        plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(kb - 1) * iplane, v);
+        plane_fetch<T, DIM, WALL, UI>(pm, u, u + N, u + 2 * N, wrapz(kb - 1) * iplane, v);
         plane_commit<T, DIM, WALL>(pm, su[so], v);
-        plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(kb) * iplane, v);
+        plane_fetch<T, DIM, WALL, UI>(pm, u, u + N, u + 2 * N, wrapz(kb) * iplane, v);
         plane_commit<T, DIM, WALL>(pm, su[sp], v);
-        plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(kb + 1) * iplane, v);
+        plane_fetch<T, DIM, WALL, UI>(pm, u, u + N, u + 2 * N, wrapz(kb + 1) * iplane, v);
         __syncthreads();
         const int ic = i < nx ? i : nx - 1;
         const int jc = j < ny ? j : ny - 1;
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(RNT) k_rhs_div(RhsCoef<T> c, const T* __restri
         nb_carry_init<T, WALL>(nb, yr);
         for (int k = kb; k < ke; ++k) {
             const bool more = k + 1 < ke;
-            if (more) plane_fetch<T, DIM, WALL>(pm, u, u + N, u + 2 * N, wrapz(k + 2) * iplane, v);
+            if (more) plane_fetch<T, DIM, WALL, UI>(pm, u, u + N, u + 2 * N, wrapz(k + 2) * iplane, v);
             CPlane<T> m = su[sm];
             CPlane<T> o = su[so];
             CPlane<T> p = su[sp];

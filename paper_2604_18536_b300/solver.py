@@ -155,6 +155,17 @@ class Grid:
         code = {"thomas": 0, "dct": 1}[solver]
         check(lib().ins_set_wall_solver(self._h, code), "ins_set_wall_solver")
 
+    def set_f64_arithmetic(self, mode):
+        """FP64 step arithmetic (ins_set_f64_arithmetic): "native" FP64 instructions or "double-float"
+        (pairs of FP32 values, the default on the grids that support it)."""
+        code = {"native": 0, "double-float": 1}[mode]
+        check(lib().ins_set_f64_arithmetic(self._h, code), "ins_set_f64_arithmetic")
+
+    def f64_arithmetic(self):
+        m = ctypes.c_int()
+        check(lib().ins_get_f64_arithmetic(self._h, ctypes.byref(m)), "ins_get_f64_arithmetic")
+        return "double-float" if m.value == 1 else "native"
+
     def set_march_chunk(self, planes):
         """z planes per CTA of the fused pair kernels (ins_set_march_chunk; 0 = automatic)."""
         check(lib().ins_set_march_chunk(self._h, int(planes)), "ins_set_march_chunk")

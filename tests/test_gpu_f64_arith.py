@@ -1,0 +1,150 @@
+"""The FP64 step in double-float arithmetic (ins_set_f64_arithmetic) against the FP64 oracle.
+
+Double-float keeps F, the Poisson FFTs and the stage updates on the FP32 pipe with about 48
+significant bits; storage, the final update of the caller's field and the CFL rule stay FP64.
+It must meet the FP64 tolerances of the native path: relative field error <= 1e-12 per step and
+<= 1e-10 after 100 steps against the oracle, the next CFL time step bit for bit, and graph
+replay (ins_step_n) bit-identical to plain steps. Grids whose FFT lengths have no register
+kernel keep native FP64 and refuse the setting.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import poisson, timestep, diagnostics
+from oracle.grid import Grid as OGrid
+from paper_2604_18536_b300 import inputs
+from paper_2604_18536_b300.solver import Grid
+from paper_2604_18536_b300._lib import InsError, INS_ERR_UNSUPPORTED
+
+pytestmark = pytest.mark.gpu
+U = inputs.uniform_faces
+PI = np.pi
+
+CASES = {
+    "p3reg": ([U(32, 0, 2 * PI), U(16, 0, 1.0), U(64, 0, 3.0)], 0.02),
+    "p3r12": ([U(48, 0, 2 * PI), U(96, 0, 1.5 * PI), U(16, 0, 2 * PI)], 0.02),   # radix-3 lengths
+    "p3ragged": ([U(192, 0, 2 * PI), U(16, 0, 1.0), U(128, 0, 2 * PI)], 0.01),
+    "p2r12": ([U(192, 0, 2 * PI), U(96, 0, 1.5 * PI)], 0.02),
+    "p2pow": ([U(256, 0, 2 * PI), U(64, 0, 2 * PI)], 0.01),
+}
+
+
+def make(name, seed=3, spectrum=False):
+    faces, nu = CASES[name]
+    bc = ["periodic"] * len(faces)
+    og = OGrid(faces, bc, nu)
+    g = Grid(faces, bc, nu, dtype=torch.float64)
+    if spectrum and len(faces) == 3 and len({len(f) for f in faces}) == 1:
+        raw = inputs.spectrum_velocity_raw(len(faces[0]) - 1, 3, seed=seed, k0=4.0)
+    else:
+        raw = inputs.random_field((og.dim,) + og.shape, seed)
+    u0, _ = poisson.project(og, raw)
+    u0 /= np.sqrt(2 * diagnostics.kinetic_energy(og, u0))
+    return og, g, u0
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_default_is_double_float_where_supported(name):
+    og, g, u0 = make(name)
+    assert g.f64_arithmetic() == "double-float"
+    g.close()
+
+
+@pytest.mark.parametrize("mode", ["double-float", "native"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_step_matches_oracle(name, mode):
+    og, g, u0 = make(name)
+    g.set_f64_arithmetic(mode)
+    u = dev(u0)
+    dt = g.cfl_dt(u, 0.3)
+    assert dt.item() == timestep.cfl_dt(og, u0, 0.3)
+    g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=0.3)
+    u1 = u.cpu().numpy()
+    ref = timestep.rk4_step(og, u0, timestep.cfl_dt(og, u0, 0.3))
+    err = rel(u1, ref)
+    assert err <= 1e-12, (mode, err)
+    assert dt.item() == timestep.cfl_dt(og, u1, 0.3)       # next dt from the FP64 result, bit for bit
+    g.close()
+
+
+def test_double_float_differs_from_native_only_at_rounding_level():
+    og, g, u0 = make("p3reg", seed=8)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    ua, ub = dev(u0), dev(u0)
+    g.step(ua, dt=dt)
+    g.set_f64_arithmetic("native")
+    g.step(ub, dt=dt)
+    d = rel(ua.cpu().numpy(), ub.cpu().numpy())
+    assert 0.0 < d <= 1e-13, d        # different arithmetic, same FP64-level result
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["p3reg", "p2pow"])
+def test_100_steps(name):
+    """<= 1e-10 after 100 steps against the oracle (fixed dt)."""
+    og, g, u0 = make(name, seed=4)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    u = dev(u0)
+    g.step_n(u, 100, dt=dt)
+    ref = timestep.integrate(og, u0, dt, 100)
+    err = rel(u.cpu().numpy(), ref)
+    assert err <= 1e-10, err
+    g.close()
+
+
+def test_graph_replay_is_bit_identical():
+    og, g, u0 = make("p3r12", seed=5)
+    ua, ub = dev(u0), dev(u0)
+    da, db = g.cfl_dt(ua, 0.3), g.cfl_dt(ub, 0.3)
+    g.step_n(ua, 4, dt_dev=da, next_dt_dev=da, cfl=0.3)
+    for _ in range(4):
+        g.step(ub, dt_dev=db, next_dt_dev=db, cfl=0.3)
+    assert torch.equal(ua, ub) and torch.equal(da, db)
+    g.close()
+
+
+def test_unsupported_grids_stay_native():
+    faces = [U(40, 0, 2 * PI), U(24, 0, 1.5 * PI), U(36, 0, 3.0)]    # no register FFT for 40, 24, 36
+    g = Grid(faces, ["periodic"] * 3, 0.02, dtype=torch.float64)
+    assert g.f64_arithmetic() == "native"
+    with pytest.raises(InsError) as e:
+        g.set_f64_arithmetic("double-float")
+    assert e.value.status == INS_ERR_UNSUPPORTED
+    g.close()
+    ch = Grid(inputs.channel_faces(32, 16, 16), ["periodic", "wall", "periodic"], 1 / 180, [1.0, 0, 0],
+              dtype=torch.float64)
+    assert ch.f64_arithmetic() == "native"
+    ch.close()
+    g32 = Grid(inputs.periodic_box(32, 3), ["periodic"] * 3, 0.01, dtype=torch.float32)
+    assert g32.f64_arithmetic() == "native"
+    g32.close()
+
+
+def test_non_finite_flag_and_wray3_fallback():
+    """A NaN in the field sets the non-finite flag as in native mode; a Wray3 grid runs native."""
+    og, g, u0 = make("p3reg", seed=6)
+    u0[0, 3, 4, 5] = np.nan
+    u = dev(u0)
+    g.step(u, dt=1e-3)
+    with pytest.raises(InsError):
+        g.check_finite()
+    g.close()
+    faces, nu = CASES["p3reg"]
+    gw = Grid(faces, ["periodic"] * 3, nu, dtype=torch.float64, scheme="wray3")
+    ow = OGrid(faces, ["periodic"] * 3, nu)
+    _, _, v0 = make("p3reg", seed=7)
+    dt = 0.5 * timestep.cfl_dt(ow, v0, 0.3)
+    v = dev(v0)
+    gw.step(v, dt=dt)
+    assert rel(v.cpu().numpy(), timestep.wray3_step(ow, v0, dt)) <= 1e-12
+    gw.close()
