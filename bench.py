@@ -53,7 +53,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dtypes", default="f64,f32")
+    ap.add_argument("--dtypes", default="f64,f64n,f32",
+                    help="f64: FP64 step (double-float arithmetic where the grid supports it), f64n: FP64 with "
+                         "native FP64 arithmetic, f32: FP32")
     ap.add_argument("--no-closure", action="store_true")
     ap.add_argument("--no-channel", action="store_true")
     ap.add_argument("--no-channel-large", action="store_true", help="skip the 512x1024x256 channel point")
@@ -120,13 +122,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ byte/op model
-def kernel_model(name, n, s, fused=False):
-    """Algorithmic bytes and FP64-pipe operations per launch of each kernel family.
+# Double-float operations per cell of rhs_div (uniform periodic grid), counted from the kernel's
+# source: F^x and F^y 10 additions, 3 products, 11 fused multiply-adds each; F^z 11, 3, 11; D F 3, 1,
+# 2; the halo evaluations (one extra F^y per 8 cells, one extra F^x per 32 cells) 1.56, 0.47, 1.72.
+# FP32-pipe instructions per double-float operation: addition 11 (TwoSum 6 + 2 + FastTwoSum 3),
+# product 7 (TwoProd with fma 2 + 2 fma + FastTwoSum 3), fused multiply-add 15.
+DF_RHS_OPS = (35.56, 10.47, 36.72)
+DF_INST = (11, 7, 15)
+DF_RHS_INST = sum(a * b for a, b in zip(DF_RHS_OPS, DF_INST))   # ~1016 per cell
+
+
+def kernel_model(name, n, s, fused=False, arith="native"):
+    """Algorithmic bytes and arithmetic per launch of each kernel family.
 
     N cells, spec = (n/2+1) n^2 complex values of 2 s bytes; s = value size.
     rhs_div: reads u (3N), writes F (3N) and r (N); 79 FP64-pipe ops/cell for F and D F on a
              uniform grid (the count of the kernel as built, with the z-face products of a plane
-             carried to the next plane of the march instead of recomputed).
+             carried to the next plane of the march instead of recomputed); in double-float
+             arithmetic DF_RHS_INST FP32-pipe instructions per cell.
     update_rhs_div (FP32 fused stage boundary): reads F_s, u_0, acc (9N) and p_s (N), writes acc,
              F_{s+1} (6N) and r (N): 17 values per cell (14 for the first boundary, no acc read).
     fft_*:   each pass reads and writes its data once.
@@ -136,7 +149,7 @@ def kernel_model(name, n, s, fused=False):
     N = n ** 3
     spec = (n // 2 + 1) * n * n
     if name == "rhs_div":
-        return 7 * N * s, 79 * N
+        return 7 * N * s, (DF_RHS_INST if arith == "double-float" else 79) * N
     if name == "update_rhs_div":
         return 16 * N * s, None     # stage 1 -> 2 has no accumulator read: (14 + 17 + 17) / 3
     if name == "fft_x_r2c" or name == "fft_x_c2r":
@@ -150,7 +163,7 @@ def kernel_model(name, n, s, fused=False):
 
 # DRAM bytes per launch of the dominant kernels, from ncu captures of the current kernels at n = 256
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch).
-TRAFFIC = {("f64", "rhs_div"): 907.1e6, ("f32", "update_rhs_div"): 1071.0e6}
+TRAFFIC = {("f64n", "rhs_div"): 907.1e6, ("f32", "update_rhs_div"): 1071.0e6, ("f64df", "rhs_div"): 919.1e6}
 
 
 def step_model_bytes(n, s):
@@ -218,11 +231,16 @@ def run_ours(args):
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     fp64_flops = measure_fma_rate(torch.float64)
     fp64_ops_peak = fp64_flops / 2.0          # one FP64 add/mul/fma per pipe slot
+    fp32_flops = measure_fma_rate(torch.float32)
+    fp32_inst_peak = fp32_flops / 2.0         # FP32 FMA-pipe instructions per second
     results = {}
     for tag in args.dtypes.split(","):
-        dtype = torch.float64 if tag == "f64" else torch.float32
-        s = 8 if tag == "f64" else 4
+        dtype = torch.float32 if tag == "f32" else torch.float64
+        s = 4 if tag == "f32" else 8
         g = Grid(faces, ["periodic"] * 3, NU, dtype=dtype)
+        if tag == "f64n":
+            g.set_f64_arithmetic("native")
+        arith = g.f64_arithmetic() if dtype == torch.float64 else "fp32"
         stream = torch.cuda.current_stream()
         u = torch.tensor(raw, dtype=dtype, device="cuda")
         g.project(u, out=u)
@@ -273,10 +291,16 @@ def run_ours(args):
         tot = sum(v[1] for v in prof.values())
         dom = max(prof.items(), key=lambda kv: kv[1][1])
         dname, (dl, dms) = dom
-        b, ops = kernel_model(dname, n, s, fused=(tag == "f32" and "update_rhs_div" in prof))
+        b, ops = kernel_model(dname, n, s, fused=(tag == "f32" and "update_rhs_div" in prof), arith=arith)
         avg_s = dms / dl / 1e3
         traffic = TRAFFIC.get((tag, dname)) if n == 256 else None
-        if tag == "f64" and ops is not None:
+        if arith == "double-float" and ops is not None:
+            roof = {"bound": "alu", "kernel": dname, "achieved": ops / avg_s / 1e9, "peak": fp32_inst_peak / 1e9,
+                    "unit": "G FP32-pipe instructions/s (double-float arithmetic)", "frac": ops / avg_s / fp32_inst_peak,
+                    "traffic": TRAFFIC.get(("f64df", dname)) if n == 256 else None,
+                    "peak_source": "measured live: dependent FP32 FMA kernel, %.1f TFLOP/s / 2" % (fp32_flops / 1e12),
+                    "hbm_frac_of_kernel": (b / avg_s / 1e9) / hbm_peak}
+        elif arith == "native" and ops is not None:
             roof = {"bound": "alu", "kernel": dname, "achieved": ops / avg_s / 1e9, "peak": fp64_ops_peak / 1e9,
                     "unit": "Gop/s (FP64 pipe ops)", "frac": ops / avg_s / fp64_ops_peak, "traffic": traffic,
                     "peak_source": "measured live: dependent-FMA kernel, %.3f TFLOP/s / 2" % (fp64_flops / 1e12),
@@ -293,7 +317,15 @@ def run_ours(args):
                "ms_per_step_plain_launches": ms_plain / args.steps, "ms_per_step_profiled": ms_prof / args.steps,
                "gpu_launches": launches, "clocks": clocks,
                "step_hbm_frac": step_model_bytes(n, s) / step_s / 1e9 / hbm_peak,
-               "final_ke": diag["ke"], "final_max_div": diag["max_div"], "workspace_bytes": g.workspace_bytes()}
+               "final_ke": diag["ke"], "final_max_div": diag["max_div"], "workspace_bytes": g.workspace_bytes(),
+               "arithmetic": arith}
+        if tag == "f64n":
+            # native FP64 arithmetic: the step only (the step VJP and the copies are those of "f64")
+            results[tag] = res
+            g.close()
+            del u
+            torch.cuda.empty_cache()
+            continue
         # adjoint/forward ratio: ins_step_vjp (stage recompute + reverse sweep) vs ins_step
         kv = max(3, args.steps // 4)
         ybar = u.detach().clone()
@@ -363,7 +395,13 @@ def run_ours(args):
             "roofline": prim["roofline"], "e2e": prim.get("e2e"), "gpu_launches": prim["gpu_launches"],
             "clocks": prim["clocks"], "step_hbm_frac": prim["step_hbm_frac"], "kernels": prim["kernels"],
             "adjoint_forward_ratio": prim["adjoint"]["ratio"], "adjoint": prim["adjoint"],
+            "fp64_arithmetic": prim.get("arithmetic"),
         }
+        if "f64n" in results:
+            f = results["f64n"]
+            line["f64_native"] = {"value": f["value"], "ms_per_step": f["ms_per_step"], "roofline": f["roofline"],
+                                  "step_hbm_frac": f["step_hbm_frac"], "kernels": f["kernels"],
+                                  "speedup_of_double_float": prim["value"] / f["value"]}
         if "f32" in results and "f64" in results:
             f = results["f32"]
             line["fp32_detail"] = {k: f[k] for k in ("ms_per_step_plain_launches", "ms_per_step_profiled",
@@ -389,12 +427,14 @@ def run_ours(args):
             line["fp32"] = {"value": f["value"], "ms_per_step": f["ms_per_step"],
                             "step_hbm_frac": round(f["step_hbm_frac"], 4),
                             "speedup_vs_fp64": f["value"] / prim["value"],
-                            "rel_error_vs_fp64_step": fp32_step_error(n, seed=args.seed),
+                            "step_rel_diff": precision_errors(n, seed=args.seed),
                             "roofline": {"bound": r["bound"], "kernel": r["kernel"], "achieved": round(r["achieved"], 1),
                                          "peak": r["peak"], "unit": r["unit"], "frac": round(r["frac"], 4),
                                          "traffic": r["traffic"]},
                             "e2e": f["e2e"]["value"] if f.get("e2e") else None,
                             "adjoint_forward_ratio": round(f["adjoint"]["ratio"], 3)}
+            if "f64n" in results:
+                line["fp64_native_ms_per_step"] = results["f64n"]["ms_per_step"]
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -434,7 +474,8 @@ def run_sweep(sizes=(128, 256, 512, 840), steps=5, warmup=2, extra=(("wray3", 84
         torch.cuda.synchronize()
         free1, _ = torch.cuda.mem_get_info()
         ms = e0.elapsed_time(e1) / steps
-        out.append({"n": n, "scheme": scheme, "ms_per_step": ms, "cell_updates_per_s": n ** 3 / (ms / 1e3),
+        out.append({"n": n, "scheme": scheme, "arithmetic": g.f64_arithmetic(), "ms_per_step": ms,
+                    "cell_updates_per_s": n ** 3 / (ms / 1e3),
                     "workspace_gb": g.workspace_bytes() / 1e9, "velocity_gb": u.numel() * 8 / 1e9,
                     "device_used_gb": (free0 - free1) / 1e9})
         g.check_finite()
@@ -660,30 +701,41 @@ def bench_differentiation(n=128, nsteps=16, reps=3, seed=0):
     return out
 
 
-def fp32_step_error(n, seed=0):
-    """Relative L2 difference of one FP32 RK4 step from the FP64 step of the same (FP32-representable)
-    field with the same dt: the FP32 path's error at the benchmark size (the FP64 path itself is within
-    1e-12 of the FP64 oracle there)."""
+def precision_errors(n, seed=0):
+    """Relative L2 differences of one step from the native-FP64 step of the same (FP32-representable)
+    field with the same dt: the FP32 step and the double-float FP64 step, at the benchmark size (the
+    native FP64 path itself is within 1e-12 of the FP64 oracle there)."""
     import torch
     from paper_2604_18536_b300 import inputs
     from paper_2604_18536_b300.solver import Grid
     faces = inputs.periodic_box(n, 3)
     g64 = Grid(faces, ["periodic"] * 3, NU, dtype=torch.float64)
-    u64 = torch.tensor(inputs.spectrum_velocity_raw(n, 3, seed=seed, k0=4.0), dtype=torch.float64, device="cuda")
-    g64.project(u64, out=u64)
-    u64.mul_(1.0 / math.sqrt(g64.diag(u64)["ke"]))
-    u64 = u64.float().double()
-    u32 = u64.float()
-    dt = float(g64.cfl_dt(u64, CFL).item())
-    g64.step(u64, dt=dt)
+    u0 = torch.tensor(inputs.spectrum_velocity_raw(n, 3, seed=seed, k0=4.0), dtype=torch.float64, device="cuda")
+    g64.project(u0, out=u0)
+    u0.mul_(1.0 / math.sqrt(g64.diag(u0)["ke"]))
+    u0 = u0.float().double()
+    dt = float(g64.cfl_dt(u0, CFL).item())
+    out = {}
+    ref = u0.clone()
+    supports_df = g64.f64_arithmetic() == "double-float"
+    g64.set_f64_arithmetic("native")
+    g64.step(ref, dt=dt)
+    nrm = torch.linalg.vector_norm(ref)
+    if supports_df:
+        g64.set_f64_arithmetic("double-float")
+        udf = u0.clone()
+        g64.step(udf, dt=dt)
+        out["double_float_vs_native_fp64"] = float(torch.linalg.vector_norm(udf - ref) / nrm)
+        del udf
     g64.close()
     g32 = Grid(faces, ["periodic"] * 3, NU, dtype=torch.float32)
+    u32 = u0.float()
     g32.step(u32, dt=dt)
     g32.close()
-    err = float(torch.linalg.vector_norm(u32.double() - u64) / torch.linalg.vector_norm(u64))
-    del u64, u32
+    out["fp32_vs_native_fp64"] = float(torch.linalg.vector_norm(u32.double() - ref) / nrm)
+    del u0, u32, ref
     torch.cuda.empty_cache()
-    return err
+    return out
 
 
 def bench_closure(n=64, batch=8, reps=5):

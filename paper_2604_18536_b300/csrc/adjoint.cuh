@@ -23,6 +23,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace ins {
 
@@ -115,12 +116,12 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjCoef<T> c, const T* __restri
 }
 
 // out = (dt * beta) * x (the last stage's cotangent dt b_4 ybar); dt from the device or dt_host.
-template <typename T>
-__global__ void k_scale_dt(const T* __restrict__ x, T* __restrict__ out, const double* dt_dev, double dt_host,
+template <typename T, typename S = T>
+__global__ void k_scale_dt(const S* __restrict__ x, T* __restrict__ out, const double* dt_dev, double dt_host,
                            double beta, long n) {
     const T alpha = (T)((dt_dev ? *dt_dev : dt_host) * beta);
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
-        out[t] = alpha * x[t];
+        out[t] = alpha * cvt_in<T>(x[t]);
 }
 
 // *acc += sum of the partials, in a fixed order (one block of 256 threads).
@@ -152,12 +153,23 @@ constexpr int AJSX = AJX + 2, AJSY = AJY + 2, AJSP = AJSX * AJSY;
 constexpr int AJNT = AJX * AJY;
 constexpr int AJPF = (AJSP + AJNT - 1) / AJNT;
 
-template <typename T>
-__global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __restrict__ u, const T* __restrict__ w,
-                                                   const T* __restrict__ ybar, T* __restrict__ ubar0,
+// ubar0 <- old + ubs for a cotangent stored in the arithmetic type, or in FP64 for the double-float
+// kernel (the FP64 accumulator keeps its precision: the double-float increment is added in FP64)
+__device__ __forceinline__ float adj_accum(float old, float x) { return old + x; }
+__device__ __forceinline__ double adj_accum(double old, double x) { return old + x; }
+__device__ __forceinline__ double adj_accum(double old, df x) { return old + df_to_double(x); }
+__device__ __forceinline__ double to_f64(float x) { return (double)x; }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(df x) { return df_to_double(x); }
+
+// UI: storage type of the stage state u; Y: storage type of the cotangents ybar, uin and ubar0
+// (T, or double for the double-float kernel of an FP64 grid).
+template <typename T, typename UI = T, typename Y = T>
+__global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const UI* __restrict__ u, const T* __restrict__ w,
+                                                   const Y* __restrict__ ybar, Y* __restrict__ ubar0,
                                                    T* __restrict__ kb, double* __restrict__ nu_part,
                                                    const T* __restrict__ extra, int kchunk,
-                                                   const T* __restrict__ uin) {
+                                                   const Y* __restrict__ uin) {
     extern __shared__ __align__(16) unsigned char ajsm[];
     T(*s)[6][AJSP] = reinterpret_cast<T(*)[6][AJSP]>(ajsm);   // s[slot][comp: u 0-2, w 3-5][cell]
     const int nx = c.nx, ny = c.ny, nz = c.nz;
@@ -192,7 +204,7 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
             if (off[q] >= 0) {
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
-                    v[cc][q] = u[cc * N + base + off[q]];
+                    v[cc][q] = cvt_in<T>(u[cc * N + base + off[q]]);
                     v[3 + cc][q] = w[cc * N + base + off[q]];
                 }
             }
@@ -217,6 +229,7 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
     const int c0 = (ty + 1) * AJSX + (tx + 1);
     // offsets within a plane: +x = 1, +y = AJSX
     double nup = 0.0;
+    T nupt = (T)0;   // this thread's part of <u, diffusion(w)> in the arithmetic type
     for (int k = kb0; k < ke; ++k) {
         const bool more = k + 1 < ke;
         if (more) fetch(wz(k + 2));
@@ -225,11 +238,12 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
             T lpart = (T)0;   // sum over the three faces of u . diffusion(w) / nu
             // the finish's own-cell values first, so their loads overlap the stencil arithmetic
             const long Jc = (long)k * plane + (long)j * nx + i;
-            T oldv[3], yv[3], xv[3];
+            Y oldv[3];
+            T yv[3], xv[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 oldv[a] = uin[a * N + Jc];   // the accumulator's previous value (ubar0, or ybar first)
-                yv[a] = ybar ? ybar[a * N + Jc] : oldv[a];
+                yv[a] = cvt_in<T>(ybar ? ybar[a * N + Jc] : oldv[a]);
                 xv[a] = extra ? extra[a * N + Jc] : (T)0;
             }
             // value of field f (0-2 u, 3-5 w) at J + (dx, dy, dz)
@@ -263,15 +277,17 @@ __global__ void __launch_bounds__(AJNT) k_adj_rhs_z(AdjCoef<T> c, const T* __res
                 if (extra) ubs += xv[a];
                 lpart = fma(ua0, lap, lpart);
                 const long e = a * N + J;
-                ubar0[e] = oldv[a] + ubs;
+                ubar0[e] = adj_accum(oldv[a], ubs);
                 if (kb) kb[e] = fma(dtb, yv[a], dta * ubs);
             }
-            nup += (double)lpart;
+            if constexpr (std::is_same<T, df>::value) nupt += lpart;
+            else nup += (double)lpart;
         }
         // plane k + 2 into the slot of plane k - 2, which no thread reads after the previous barrier
         if (more) commit(slot(k + 2));
         __syncthreads();
     }
+    if constexpr (std::is_same<T, df>::value) nup = to_f64(nupt);
     for (int o = 16; o > 0; o >>= 1) nup += __shfl_xor_sync(0xffffffffu, nup, o);
     __shared__ double red[AJY];
     if (tx == 0) red[ty] = nup;

@@ -95,33 +95,6 @@ ins_status Impl<T, DIM, WALL>::step_fused(ins_grid* g, T* u, const double* dt_de
 }
 
 // ------------------------------------------------------------ double-float FP64 step
-// F + D F with double-float arithmetic; UI = double for the caller's FP64 field (split by bits
-// on load), df for the stage state.
-template <int DIM, typename UI>
-ins_status launch_rhs_div_df(ins_grid* g, const UI* u, df* F, df* r) {
-    const dim3 blk(RBX, RBY, 1);
-    const dim3 grd((g->nx + RBX - 1) / RBX, (g->ny + RBY - 1) / RBY, DIM == 3 ? (g->nz + g->kchunk - 1) / g->kchunk : 1);
-    KLAUNCH(g, "rhs_div", (k_rhs_div<df, DIM, false, UI><<<grd, blk, 0, g->stream>>>(make_rhs_coef<df>(g), u, F, r,
-                                                                                      g->kchunk, (const df*)nullptr)));
-    return INS_OK;
-}
-
-template <int DIM>
-ins_status rk_update_df(ins_grid* g, const df* F, const df* p, double* u0, df* acc, df* us, const RkArgs& ra) {
-    RkCoefDf c;
-    c.nx = g->nx;
-    c.ny = g->ny;
-    c.nz = g->nz;
-    c.ihx = df(1.0 / g->h[0][0]);
-    c.ihy = df(1.0 / g->h[1][0]);
-    c.ihz = df(DIM == 3 ? 1.0 / g->h[2][0] : 0.0);
-    const int bx = (g->nx / 2 + 31) / 32, by = (g->ny + 7) / 8;
-    const int kc = wave_chunk((long)bx * by, g->nz, 4L * device_sm_count(), 1);
-    const dim3 grd(bx, by, (g->nz + kc - 1) / kc);
-    KLAUNCH(g, "rk_update", (k_rk_update_df<DIM><<<grd, dim3(32, 8), 0, g->stream>>>(c, F, p, u0, acc, us, ra, kc)));
-    return INS_OK;
-}
-
 // The classic RK4 step of an FP64 periodic grid in double-float arithmetic (ins_set_f64_arithmetic):
 // F, r/p, the spectrum, acc and the stage state hold double-float pairs; u stays FP64.
 template <int DIM>

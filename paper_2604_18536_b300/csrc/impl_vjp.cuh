@@ -145,9 +145,117 @@ ins_status Impl<T, DIM, WALL>::step_vjp_wall(ins_grid* g, const T* un, const dou
     return INS_OK;
 }
 
+// Pullback of one classic RK4 step of an FP64 periodic 3-D grid in double-float arithmetic (the
+// counterpart of the double-float step, ins_set_f64_arithmetic): the stage states are recomputed
+// by the double-float step kernels and kept as double-float pairs, P^T = P runs the double-float
+// Poisson passes, and the adjoint stencil evaluates J_F^T in double-float while the state
+// cotangent ubar accumulates in FP64 (each stage's increment added in FP64) and the nu partials
+// are reduced in FP64.
+inline ins_status step_vjp_df(ins_grid* g, const double* un, const double* dt_dev, double dt_host,
+                              const double* ybar, double* ubar, double* nubar) {
+    static const double A[3] = {0.5, 0.5, 1.0};
+    static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const long N = g->N;
+    const size_t fld = (size_t)3 * N * sizeof(double);
+    const int abx = (g->nx + AJX - 1) / AJX, aby = (g->ny + AJY - 1) / AJY;
+    const size_t adj_smem = 4 * 6 * AJSP * sizeof(df);
+    static int per_sm = 0;
+    INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_z<df, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)adj_smem));
+    INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_z<df, df, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)adj_smem));
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_rhs_z<df, df, double>, AJX * AJY, adj_smem);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int akc = wave_chunk((long)abx * aby, g->nz, (long)per_sm * device_sm_count(), 2);
+    const dim3 ag(abx, aby, (g->nz + akc - 1) / akc);
+    const long nblk = (long)ag.x * ag.y * ag.z;
+    const size_t fa = (fld + 255) & ~size_t(255);
+    const size_t need = 5 * fa + (size_t)nblk * 8;
+    if (g->vjp_bytes < need) {
+        if (g->vjp) cudaFree(g->vjp);
+        g->vjp = nullptr;
+        g->vjp_bytes = 0;
+        cudaError_t e = cudaMalloc(&g->vjp, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(INS_ERR_OOM, std::string("step-VJP workspace: ") + cudaGetErrorString(e));
+        }
+        g->vjp_bytes = need;
+    }
+    char* vb = reinterpret_cast<char*>(g->vjp);
+    df* U[4] = {nullptr, reinterpret_cast<df*>(vb), reinterpret_cast<df*>(vb + fa), reinterpret_cast<df*>(vb + 2 * fa)};
+    df* W = reinterpret_cast<df*>(vb + 3 * fa);
+    double* part = reinterpret_cast<double*>(vb + 5 * fa);
+    df* F = reinterpret_cast<df*>(g->F);
+    df* rp = reinterpret_cast<df*>(g->rp);
+    ins_status s;
+    auto args = [&](double a_next, int stage) {
+        RkArgs ra;
+        ra.dt_dev = dt_dev;
+        ra.dt_host = dt_host;
+        ra.a_next = a_next;
+        ra.b = 0.0;
+        ra.stage = stage;
+        ra.last = 0;
+        ra.mx = nullptr;
+        ra.err_flag = g->err_flag;
+        return ra;
+    };
+    // forward: the stage states u_{s+1} = u_n + dt a_{s+1,s} k_s (stage 0 of the update without an
+    // accumulator writes only the stage state)
+    for (int st = 0; st < 3; ++st) {
+        s = st == 0 ? launch_rhs_div_df<3, double>(g, un, F, rp) : launch_rhs_div_df<3, df>(g, U[st], F, rp);
+        if (s != INS_OK) return s;
+        if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
+        if ((s = rk_update_df<3>(g, F, rp, const_cast<double*>(un), nullptr, U[st + 1], args(A[st], 0))) != INS_OK)
+            return s;
+    }
+    // reverse: ubar starts as ybar; kbar_4 = dt b_4 ybar
+    INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
+    KLAUNCH(g, "scale", (k_scale_dt<df, double><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host, B[3], 3 * N)));
+    AdjCoef<df> ac;
+    ac.nx = g->nx;
+    ac.ny = g->ny;
+    ac.nz = g->nz;
+    for (int a = 0; a < 3; ++a) {
+        const double D = g->d[a][0];
+        ac.c1[a] = df(0.5 / D);
+        ac.c2[a] = df(0.25 / D);
+        ac.l2[a] = df(1.0 / (D * D));
+    }
+    ac.nu = df(g->nu);
+    ac.dt_dev = dt_dev;
+    ac.dt_host = dt_host;
+    const df idx(1.0 / g->d[0][0]), idy(1.0 / g->d[1][0]), idz(1.0 / g->d[2][0]);
+    for (int st = 3; st >= 0; --st) {
+        // w = P kbar_s (P is symmetric on a uniform periodic grid)
+        KLAUNCH(g, "divergence", (k_div_df<3><<<4 * device_sm_count(), 256, 0, g->stream>>>(g->nx, g->ny, g->nz, idx, idy,
+                                                                                          idz, F, rp)));
+        if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
+        if ((s = rk_update_df<3>(g, F, rp, nullptr, nullptr, W, args(0.0, -1))) != INS_OK) return s;
+        ac.bn = st > 0 ? B[st - 1] : 0.0;
+        ac.an = st > 0 ? A[st - 1] : 0.0;
+        df* kb = st > 0 ? F : nullptr;
+        if (st == 0)
+            KLAUNCH(g, "adj_rhs", (k_adj_rhs_z<df, double, double><<<ag, dim3(AJX, AJY), adj_smem, g->stream>>>(
+                                      ac, un, W, ybar, ubar, kb, part, nullptr, akc, ubar)));
+        else
+            KLAUNCH(g, "adj_rhs", (k_adj_rhs_z<df, df, double><<<ag, dim3(AJX, AJY), adj_smem, g->stream>>>(
+                                      ac, U[st], W, ybar, ubar, kb, part, nullptr, akc, ubar)));
+        if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, nblk, nubar));
+    }
+    return INS_OK;
+}
+
 template <typename T, int DIM, bool WALL>
 ins_status Impl<T, DIM, WALL>::step_vjp(ins_grid* g, const T* un, const double* dt_dev, double dt_host, const T* ybar, T* ubar, double* nubar) {
     if constexpr (WALL) return step_vjp_wall(g, un, dt_dev, dt_host, ybar, ubar, nubar);
+    if constexpr (std::is_same<T, double>::value && DIM == 3 && !WALL) {
+        if (g->use_df && g->scheme == INS_RK4 && !g->closure && !g->eddy && reinterpret_cast<uintptr_t>(un) % 16 == 0)
+            return step_vjp_df(g, un, dt_dev, dt_host, ybar, ubar, nubar);
+    }
     static const double A[3] = {0.5, 0.5, 1.0};
     static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
     const long N = g->N;

@@ -5,6 +5,7 @@
 //   stage 0: acc = b0 k;  stages 1, 2: acc += b k;  us = u0 + dt a k;
 //   stage 3: u0 = u0 + dt (acc + b3 k) in place, the CFL per-index maxima of |u_{n+1}| and
 //            the non-finite flag,
+//   stage -1 (projection only, the step pullback's P^T): us = F - G p (u0 and acc untouched),
 // with F, p, acc and the stage state us stored as double-float pairs and u0 the caller's FP64
 // field. The arithmetic is double-float (FP32 pipe); u0 is split by bits when it is read, and
 // the last stage adds the double-float increment dt (acc + b3 k) to the FP64 u0 in FP64, so the
@@ -105,6 +106,10 @@ __global__ void __launch_bounds__(256) k_rk_update_df(RkCoefDf c, const df* __re
 #pragma unroll
             for (int cc = 0; cc < DIM; ++cc) {
                 const long ea = cc * N + a;
+                if (ra.stage < 0) {
+                    st2(us + ea, kk[cc]);
+                    continue;
+                }
                 double uv[VEC];
                 df av[VEC], sv[VEC];
                 ld2(u0 + ea, uv);
@@ -173,6 +178,30 @@ __global__ void __launch_bounds__(256) k_rk_update_df(RkCoefDf c, const df* __re
             }
         }
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(ra.err_flag, 1u);
+    }
+}
+
+// r = D F (App. B divergence kernel) in double-float on a uniform periodic grid:
+// r_I = sum_a (F^a_I - F^a_{I-e_a}) / d_a. One cell per thread (grid-stride); the neighbours below
+// come through the caches.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_div_df(int nx, int ny, int nz, df idx, df idy, df idz,
+                                                const df* __restrict__ F, df* __restrict__ r) {
+    const long N = (long)nx * ny * nz;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < N; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % nx);
+        const long rest = t / nx;
+        const int j = (int)(rest % ny);
+        const int k = (int)(rest / ny);
+        const long tx = i > 0 ? t - 1 : t + nx - 1;
+        const long ty = j > 0 ? t - nx : t + (long)(ny - 1) * nx;
+        df acc = (ldg_t(F + t) - ldg_t(F + tx)) * idx;
+        acc = fma(ldg_t(F + N + t) - ldg_t(F + N + ty), idy, acc);
+        if (DIM == 3) {
+            const long tz = k > 0 ? t - (long)nx * ny : t + (long)(nz - 1) * nx * ny;
+            acc = fma(ldg_t(F + 2 * N + t) - ldg_t(F + 2 * N + tz), idz, acc);
+        }
+        r[t] = acc;
     }
 }
 
