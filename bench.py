@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-channel-large", action="store_true", help="skip the 512x1024x256 channel point")
     ap.add_argument("--no-wray3", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
+    ap.add_argument("--no-les", action="store_true", help="skip the learned-closure training and evaluation")
     ap.add_argument("--sweep", action="store_true", help="FP64 size sweep 128^3..840^3 only (one JSON line)")
     return ap.parse_args()
 
@@ -417,8 +418,14 @@ def run_ours(args):
             line["wray3"] = bench_wray3(n, seed=args.seed)
         if not args.no_diff:
             line["differentiation"] = bench_differentiation(seed=args.seed)
+        les_res = None
+        if not args.no_les and world == 1:
+            les_res = bench_les()
+            line["closure_les_detail"] = les_res
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
+        if les_res is not None:
+            line["closure_les"] = les_summary(les_res)
         if "f32" in results and "f64" in results:
             # compact FP32 summary as the line's last key (kept short so that a truncated record of the
             # line's tail still carries it)
@@ -735,6 +742,44 @@ def precision_errors(n, seed=0):
     out["fp32_vs_native_fp64"] = float(torch.linalg.vector_norm(u32.double() - ref) / nrm)
     del u0, u32, ref
     torch.cuda.empty_cache()
+    return out
+
+
+def bench_les(seeds=64, test=16, nsnap=40, nsteps=10, stride=5, iters=150, batch=8, lr=1e-3):
+    """The learned closure end to end at the configured size: filtered DNS from 64 seeded 256^3 FP32
+    runs (nu = 1/2000, k0 = 4, 100 spin-up steps, face-averaged to 64^3, nsnap LES steps each), a
+    posteriori training of the tensor-core CNN through 10 unrolled LES steps on windows of the 48
+    training trajectories (batch 8, Adam lr 1e-3), and per-trajectory spectrum errors of the 16
+    held-out trajectories at 10, nsnap/2 and nsnap LES steps, paired against the no-closure LES."""
+    from paper_2604_18536_b300 import les
+    nu = 1.0 / 2000
+    t0 = time.time()
+    data = les.dns_dataset(range(seeds), 256, 64, nu, nsnap=nsnap, spinup=100)
+    t1 = time.time()
+    train_set, test_set = data[:seeds - test], data[seeds - test:]
+    windows = les.training_windows(train_set, nsteps, stride)
+    W, b, hist = les.train(windows, 64, nu, iters=iters, batch=batch, lr=lr, nsteps=nsteps)
+    t2 = time.time()
+    horizons = sorted({nsteps, nsnap // 2, nsnap})
+    ev = les.evaluate_paired(test_set, 64, nu, W, b, horizons)
+    res = {"workload": "learned LES closure: %d filtered 256^3 -> 64^3 DNS trajectories (%d train / %d held out), "
+                       "%d LES steps each; training through %d unrolled steps on %d windows, %d Adam iterations"
+                       % (seeds, seeds - test, test, nsnap, nsteps, len(windows), iters),
+           "final_horizon": nsnap, "loss_first": hist[0], "loss_last": hist[-1], "dns_s": t1 - t0,
+           "train_s": t2 - t1, "evaluation": {}}
+    for h, r in ev.items():
+        res["evaluation"]["H%d" % h] = r
+    return res
+
+
+def les_summary(res):
+    """Compact per-horizon summary: means and the paired difference (no closure - closure) +- its SE."""
+    out = {}
+    for k, r in res["evaluation"].items():
+        p = r["closure_vs_no_closure"]
+        out[k] = {"no_closure": round(r["no_closure_mean"], 5), "closure": round(r["closure_mean"], 5),
+                  "smagorinsky": round(r["smagorinsky_mean"], 5), "paired_diff": round(p["mean_diff"], 5),
+                  "se": round(p["se"], 5), "wins": "%d/%d" % (p["wins"], p["n"])}
     return out
 
 

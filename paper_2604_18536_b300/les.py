@@ -16,6 +16,14 @@ trajectory loss and applies Adam to the parameter tensors):
 3. Evaluation: spectrum error at the last snapshot, relative L2 distance of log E(k) over
    k = 1 .. n_les/2 - 1, against the filtered DNS, with and without the closure. If the
    closure produces a non-finite field the no-closure LES is used (fallback).
+4. Paired evaluation (evaluate_paired): the same errors per held-out trajectory at several
+   horizons, for the closure, the no-closure LES and the eddy-viscosity models, with the
+   mean paired difference (no closure minus closure) and its standard error, so that a gain
+   can be told apart from the spread between trajectories.
+
+The trajectories can be longer than the training unroll: training then draws windows of
+`nsteps` LES steps that start at every `stride`-th snapshot (training_windows), and the
+final evaluation time is the end of the filtered DNS trajectory.
 """
 
 import math
@@ -182,6 +190,63 @@ def evaluate(data, n_les, nu, W=None, b=None, nsteps=10, eddy=None):
     return sum(errs) / len(errs), fallbacks
 
 
+def training_windows(data, nsteps, stride):
+    """Windows of nsteps + 1 snapshots starting at every stride-th snapshot of each trajectory."""
+    out = []
+    for snaps, dt in data:
+        for k in range(0, snaps.shape[0] - nsteps, stride):
+            out.append((snaps[k:k + nsteps + 1], dt))
+    return out
+
+
+def _errors(data, n_les, nu, horizon, W=None, b=None, eddy=None):
+    """Spectrum error of each trajectory after `horizon` LES steps (closure W, b, an eddy model, or none)."""
+    g = _box(n_les, nu)
+    c = None
+    if W is not None:
+        c = Closure(g)
+        c.set_params(W, b)
+        g.set_closure(c)
+    elif eddy is not None:
+        g.set_eddy_viscosity(eddy)
+    errs = []
+    for snaps, dt in data:
+        u = snaps[0].clone()
+        for _ in range(horizon):
+            g.step(u, dt=dt)
+        g.check_finite()
+        errs.append(spectrum_error(g, u, snaps[horizon]))
+    g.set_closure(None)
+    if c is not None:
+        c.close()
+    g.close()
+    return errs
+
+
+def paired(base, other):
+    """Mean of base - other over trajectories, its standard error, and the count with base > other."""
+    d = [x - y for x, y in zip(base, other)]
+    n = len(d)
+    m = sum(d) / n
+    sd = math.sqrt(sum((x - m) ** 2 for x in d) / (n - 1)) if n > 1 else float("nan")
+    return {"mean_diff": m, "se": sd / math.sqrt(n), "wins": sum(1 for x in d if x > 0), "n": n}
+
+
+def evaluate_paired(data, n_les, nu, W, b, horizons, eddy=("smagorinsky", "wale")):
+    """Per-trajectory spectrum errors at each horizon and paired comparisons against no closure."""
+    out = {}
+    for h in horizons:
+        base = _errors(data, n_les, nu, h)
+        cl = _errors(data, n_les, nu, h, W, b)
+        rec = {"no_closure": base, "closure": cl, "no_closure_mean": sum(base) / len(base),
+               "closure_mean": sum(cl) / len(cl), "closure_vs_no_closure": paired(base, cl)}
+        for m in eddy:
+            e = _errors(data, n_les, nu, h, eddy=m)
+            rec[m + "_mean"] = sum(e) / len(e)
+        out[h] = rec
+    return out
+
+
 def main():
     import argparse
     import json
@@ -196,27 +261,27 @@ def main():
     ap.add_argument("--nsteps", type=int, default=10)
     ap.add_argument("--spinup", type=int, default=100)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--nsnap", type=int, default=40, help="LES steps of each filtered DNS trajectory")
+    ap.add_argument("--stride", type=int, default=5, help="start spacing of the training windows")
     a = ap.parse_args()
     nu = 1.0 / 2000
     t0 = time.time()
-    data = dns_dataset(range(a.seeds), a.n_dns, a.n_les, nu, nsnap=a.nsteps, spinup=a.spinup)
+    data = dns_dataset(range(a.seeds), a.n_dns, a.n_les, nu, nsnap=a.nsnap, spinup=a.spinup)
     t1 = time.time()
     train_set, test_set = data[: a.seeds - a.test], data[a.seeds - a.test:]
-    base, _ = evaluate(test_set, a.n_les, nu, nsteps=a.nsteps)
     import sys
 
     def log(it, loss):
         if it % 10 == 0 or it == a.iters - 1:
             print(f"iter {it} loss {loss:.6e} t {time.time() - t1:.1f}s", file=sys.stderr, flush=True)
 
-    W, b, hist = train(train_set, a.n_les, nu, a.iters, a.batch, a.lr, a.nsteps, log=log)
+    windows = training_windows(train_set, a.nsteps, a.stride)
+    W, b, hist = train(windows, a.n_les, nu, a.iters, a.batch, a.lr, a.nsteps, log=log)
     t2 = time.time()
-    err, fb = evaluate(test_set, a.n_les, nu, W, b, nsteps=a.nsteps)
-    eddy = {m: evaluate(test_set, a.n_les, nu, nsteps=a.nsteps, eddy=m)[0]
-            for m in ("smagorinsky", "wale", "qr", "vreman")}
-    print(json.dumps({"no_closure_spectrum_error": base, "closure_spectrum_error": err, "fallbacks": fb,
-                      "eddy_viscosity_spectrum_error": eddy,
-                      "loss_first": hist[0], "loss_last": hist[-1], "dns_s": t1 - t0, "train_s": t2 - t1}))
+    horizons = sorted({a.nsteps, a.nsnap // 2, a.nsnap})
+    ev = evaluate_paired(test_set, a.n_les, nu, W, b, horizons)
+    print(json.dumps({"final_horizon": a.nsnap, "evaluation": ev, "loss_first": hist[0], "loss_last": hist[-1],
+                      "windows": len(windows), "dns_s": t1 - t0, "train_s": t2 - t1}))
 
 
 if __name__ == "__main__":
