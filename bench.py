@@ -395,7 +395,8 @@ def run_ours(args):
             "ms_per_step_profiled": prim["ms_per_step_profiled"],
             "roofline": prim["roofline"], "e2e": prim.get("e2e"), "gpu_launches": prim["gpu_launches"],
             "clocks": prim["clocks"], "step_hbm_frac": prim["step_hbm_frac"], "kernels": prim["kernels"],
-            "adjoint_forward_ratio": prim["adjoint"]["ratio"], "adjoint": prim["adjoint"],
+            "adjoint_forward_ratio": prim["adjoint"]["ratio"] if "adjoint" in prim else None,
+            "adjoint": prim.get("adjoint"),
             "fp64_arithmetic": prim.get("arithmetic"),
         }
         if "f64n" in results:
