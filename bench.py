@@ -126,11 +126,11 @@ class ClockSampler:
 # Double-float operations per cell of rhs_div (uniform periodic grid), counted from the kernel's
 # source: F^x and F^y 10 additions, 3 products, 11 fused multiply-adds each; F^z 11, 3, 11; D F 3, 1,
 # 2; the halo evaluations (one extra F^y per 8 cells, one extra F^x per 32 cells) 1.56, 0.47, 1.72.
-# FP32-pipe instructions per double-float operation: addition 11 (TwoSum 6 + 2 + FastTwoSum 3),
-# product 7 (TwoProd with fma 2 + 2 fma + FastTwoSum 3), fused multiply-add 15.
+# FP32-pipe instructions per double-float operation (results left unnormalised): addition 8 (TwoSum 6 + 2),
+# product 4 (TwoProd with fma 2 + 2 fma), fused multiply-add 12.
 DF_RHS_OPS = (35.56, 10.47, 36.72)
-DF_INST = (11, 7, 15)
-DF_RHS_INST = sum(a * b for a, b in zip(DF_RHS_OPS, DF_INST))   # ~1016 per cell
+DF_INST = (8, 4, 12)
+DF_RHS_INST = sum(a * b for a, b in zip(DF_RHS_OPS, DF_INST))   # ~767 per cell
 
 
 def kernel_model(name, n, s, fused=False, arith="native"):

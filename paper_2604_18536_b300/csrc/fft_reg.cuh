@@ -180,6 +180,48 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 256, std::is_same<T, df
     const bool ok = col < ncol;
     const long cb = ok ? (col / cdiv) * outer + (col % cdiv) : 0;
     cplx<T> v[Sh::RM];
+    if constexpr (R1 == R2 && std::is_same<T, df>::value) {
+        // Square factorisation, double-float: the inverse half of mode 2 has the same thread roles,
+        // layouts and twiddles as the forward half, so both run through one copy of the code (a
+        // loop that is not unrolled): the fused pass then fits the instruction cache.
+        constexpr int R = R1;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cplx<T> z = {(T)0, (T)0};
+            if (ok) z = S[cb + (long)(q + R * r) * lstride];
+            if (mode == 1) z = cconj(z);
+            v[r] = z;
+        }
+        const int npass = mode == 2 ? 2 : 1;
+#pragma unroll 1
+        for (int pass = 0; pass < npass; ++pass) {
+            if (pass == 1) {
+                // scale and conjugate: v[k2] = X[q + R k2] becomes the inverse's stage-A input
+#pragma unroll
+                for (int k2 = 0; k2 < R; ++k2) {
+                    const T sc = ok ? ldg_t(&scale[cb + (long)(q + R * k2) * lstride]) : (T)0;
+                    v[k2] = {v[k2].re * sc, -v[k2].im * sc};
+                }
+                __syncthreads();   // everyone finished reading ex
+            }
+            stage_a<T, R>(v, q, tw);
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) ex[(q * R + k1) * SP + c] = v[k1];
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < R; ++j) v[j] = ex[(j * R + q) * SP + c];
+            DftR<T, R>::run(v);   // v[k2] = X[q + R k2] (pass 1: the conjugated inverse)
+        }
+        if (ok) {
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) {
+                cplx<T> z = v[k2];
+                if (mode != 0) z = cconj(z);
+                S[cb + (long)(q + R * k2) * lstride] = z;
+            }
+        }
+        return;
+    }
     // ---- forward stage A (R1 x R2): thread (c, j = q < R2)
     if (q < R2) {
 #pragma unroll

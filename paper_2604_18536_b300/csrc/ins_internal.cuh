@@ -340,9 +340,9 @@ void strided_reg(int L, cudaStream_t st, const cplx<T>* tw, cplx<T>* S, long nco
 template <typename T, int R1, int R2>
 void launch_x_reg(bool forward, cudaStream_t st, const cplx<T>* tw, const T* in, cplx<T>* S, T* out, int lines,
                   int nxh) {
-    // FP32 inverse: persistent double-buffered variant when the spectrum is 16-byte aligned (FP64 is
-    // FP64-pipe bound and keeps the one-tile-per-CTA kernel)
-    if constexpr (sizeof(T) == 4) {
+    // FP32 and double-float inverse: persistent double-buffered variant when the spectrum is 16-byte
+    // aligned (native FP64 is FP64-pipe bound and keeps the one-tile-per-CTA kernel)
+    if constexpr (sizeof(T) == 4 || std::is_same<T, df>::value) {
         if (!forward && reinterpret_cast<uintptr_t>(S) % 16 == 0) {
             using Px = PipeX<T, R1, R2>;
             static bool attr = false;
