@@ -145,16 +145,17 @@ ins_status Impl<T, DIM, WALL>::step_vjp_wall(ins_grid* g, const T* un, const dou
     return INS_OK;
 }
 
-// Pullback of one classic RK4 step of an FP64 periodic 3-D grid in double-float arithmetic (the
-// counterpart of the double-float step, ins_set_f64_arithmetic): the stage states are recomputed
-// by the double-float step kernels and kept as double-float pairs, P^T = P runs the double-float
-// Poisson passes, and the adjoint stencil evaluates J_F^T in double-float while the state
-// cotangent ubar accumulates in FP64 (each stage's increment added in FP64) and the nu partials
-// are reduced in FP64.
+// Pullback of one step (classic RK4 or Wray's low-storage RK3) of an FP64 periodic 3-D grid in
+// double-float arithmetic (the counterpart of the double-float step, ins_set_f64_arithmetic): the
+// stage states are recomputed by the double-float step kernels, P^T = P runs the double-float Poisson
+// passes, and the adjoint stencil evaluates J_F^T in double-float while the state cotangent ubar
+// accumulates in FP64 (each stage's increment added in FP64) and the nu partials are reduced in FP64.
 inline ins_status step_vjp_df(ins_grid* g, const double* un, const double* dt_dev, double dt_host,
                               const double* ybar, double* ubar, double* nubar) {
     static const double A[3] = {0.5, 0.5, 1.0};
     static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const bool lowst = g->scheme == INS_WRAY3;
+    const int nst = lowst ? 3 : 4;
     const long N = g->N;
     const size_t fld = (size_t)3 * N * sizeof(double);
     const int abx = (g->nx + AJX - 1) / AJX, aby = (g->ny + AJY - 1) / AJY;
@@ -184,37 +185,53 @@ inline ins_status step_vjp_df(ins_grid* g, const double* un, const double* dt_de
         }
         g->vjp_bytes = need;
     }
+    // stage states: RK4 keeps u_2 .. u_4 as double-float pairs (u_s = u_n + dt a k_{s-1}); Wray's
+    // low-storage states chain (u_{s+1} = u_s + dt (gamma k_s + zeta k_{s-1})) and stay FP64
     char* vb = reinterpret_cast<char*>(g->vjp);
     df* U[4] = {nullptr, reinterpret_cast<df*>(vb), reinterpret_cast<df*>(vb + fa), reinterpret_cast<df*>(vb + 2 * fa)};
+    double* U64[3] = {const_cast<double*>(un), reinterpret_cast<double*>(vb), reinterpret_cast<double*>(vb + fa)};
     df* W = reinterpret_cast<df*>(vb + 3 * fa);
     double* part = reinterpret_cast<double*>(vb + 5 * fa);
     df* F = reinterpret_cast<df*>(g->F);
     df* rp = reinterpret_cast<df*>(g->rp);
+    df* kprev = reinterpret_cast<df*>(g->acc);
     ins_status s;
-    auto args = [&](double a_next, int stage) {
+    auto args = [&](double a_next, double b, int stage) {
         RkArgs ra;
         ra.dt_dev = dt_dev;
         ra.dt_host = dt_host;
         ra.a_next = a_next;
-        ra.b = 0.0;
+        ra.b = b;
         ra.stage = stage;
         ra.last = 0;
         ra.mx = nullptr;
         ra.err_flag = g->err_flag;
         return ra;
     };
-    // forward: the stage states u_{s+1} = u_n + dt a_{s+1,s} k_s (stage 0 of the update without an
-    // accumulator writes only the stage state)
-    for (int st = 0; st < 3; ++st) {
-        s = st == 0 ? launch_rhs_div_df<3, double>(g, un, F, rp) : launch_rhs_div_df<3, df>(g, U[st], F, rp);
-        if (s != INS_OK) return s;
-        if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
-        if ((s = rk_update_df<3>(g, F, rp, const_cast<double*>(un), nullptr, U[st + 1], args(A[st], 0))) != INS_OK)
-            return s;
+    if (lowst) {
+        for (int st = 0; st < 2; ++st) {
+            if ((s = launch_rhs_div_df<3, double>(g, U64[st], F, rp)) != INS_OK) return s;
+            if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
+            if ((s = rk_update_df<3, true>(g, F, rp, U64[st], kprev, nullptr, args(WRAY3_GAMMA[st], WRAY3_ZETA[st], st),
+                                           U64[st + 1])) != INS_OK)
+                return s;
+        }
+    } else {
+        // the stage states u_{s+1} = u_n + dt a_{s+1,s} k_s (stage 0 of the update without an
+        // accumulator writes only the stage state)
+        for (int st = 0; st < 3; ++st) {
+            s = st == 0 ? launch_rhs_div_df<3, double>(g, un, F, rp) : launch_rhs_div_df<3, df>(g, U[st], F, rp);
+            if (s != INS_OK) return s;
+            if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
+            if ((s = rk_update_df<3>(g, F, rp, const_cast<double*>(un), nullptr, U[st + 1], args(A[st], 0.0, 0))) !=
+                INS_OK)
+                return s;
+        }
     }
-    // reverse: ubar starts as ybar; kbar_4 = dt b_4 ybar
+    // reverse: ubar starts as ybar; the last stage's cotangent dt b_last ybar
+    const double blast = lowst ? WRAY3_GAMMA[2] : B[3];
     INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
-    KLAUNCH(g, "scale", (k_scale_dt<df, double><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host, B[3], 3 * N)));
+    KLAUNCH(g, "scale", (k_scale_dt<df, double><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host, blast, 3 * N)));
     AdjCoef<df> ac;
     ac.nx = g->nx;
     ac.ny = g->ny;
@@ -229,21 +246,28 @@ inline ins_status step_vjp_df(ins_grid* g, const double* un, const double* dt_de
     ac.dt_dev = dt_dev;
     ac.dt_host = dt_host;
     const df idx(1.0 / g->d[0][0]), idy(1.0 / g->d[1][0]), idz(1.0 / g->d[2][0]);
-    for (int st = 3; st >= 0; --st) {
+    for (int st = nst - 1; st >= 0; --st) {
         // w = P kbar_s (P is symmetric on a uniform periodic grid)
         KLAUNCH(g, "divergence", (k_div_df<3><<<4 * device_sm_count(), 256, 0, g->stream>>>(g->nx, g->ny, g->nz, idx, idy,
                                                                                           idz, F, rp)));
         if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
-        if ((s = rk_update_df<3>(g, F, rp, nullptr, nullptr, W, args(0.0, -1))) != INS_OK) return s;
-        ac.bn = st > 0 ? B[st - 1] : 0.0;
-        ac.an = st > 0 ? A[st - 1] : 0.0;
+        if ((s = rk_update_df<3>(g, F, rp, nullptr, nullptr, W, args(0.0, 0.0, -1))) != INS_OK) return s;
+        if (lowst) {
+            // kbar_{s-1} = dt gamma_{s-1} (Ubar_{s+1} + ubar_s) + dt zeta_s Ubar_{s+1}
+            ac.bn = st > 0 ? WRAY3_GAMMA[st - 1] + WRAY3_ZETA[st] : 0.0;
+            ac.an = st > 0 ? WRAY3_GAMMA[st - 1] : 0.0;
+        } else {
+            ac.bn = st > 0 ? B[st - 1] : 0.0;
+            ac.an = st > 0 ? A[st - 1] : 0.0;
+        }
+        const double* ysrc = lowst ? nullptr : ybar;   // null: the kernel chains ubar itself
         df* kb = st > 0 ? F : nullptr;
-        if (st == 0)
+        if (lowst || st == 0)
             KLAUNCH(g, "adj_rhs", (k_adj_rhs_z<df, double, double><<<ag, dim3(AJX, AJY), adj_smem, g->stream>>>(
-                                      ac, un, W, ybar, ubar, kb, part, nullptr, akc, ubar)));
+                                      ac, lowst ? U64[st] : un, W, ysrc, ubar, kb, part, nullptr, akc, ubar)));
         else
             KLAUNCH(g, "adj_rhs", (k_adj_rhs_z<df, df, double><<<ag, dim3(AJX, AJY), adj_smem, g->stream>>>(
-                                      ac, U[st], W, ybar, ubar, kb, part, nullptr, akc, ubar)));
+                                      ac, U[st], W, ysrc, ubar, kb, part, nullptr, akc, ubar)));
         if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, nblk, nubar));
     }
     return INS_OK;
@@ -253,7 +277,7 @@ template <typename T, int DIM, bool WALL>
 ins_status Impl<T, DIM, WALL>::step_vjp(ins_grid* g, const T* un, const double* dt_dev, double dt_host, const T* ybar, T* ubar, double* nubar) {
     if constexpr (WALL) return step_vjp_wall(g, un, dt_dev, dt_host, ybar, ubar, nubar);
     if constexpr (std::is_same<T, double>::value && DIM == 3 && !WALL) {
-        if (g->use_df && g->scheme == INS_RK4 && !g->closure && !g->eddy && reinterpret_cast<uintptr_t>(un) % 16 == 0)
+        if (g->use_df && !g->closure && !g->eddy && reinterpret_cast<uintptr_t>(un) % 16 == 0)
             return step_vjp_df(g, un, dt_dev, dt_host, ybar, ubar, nubar);
     }
     static const double A[3] = {0.5, 0.5, 1.0};

@@ -620,8 +620,9 @@ ins_status launch_rhs_div_df(ins_grid* g, const UI* u, df* F, df* r) {
     return INS_OK;
 }
 
-template <int DIM>
-ins_status rk_update_df(ins_grid* g, const df* F, const df* p, double* u0, df* acc, df* us, const RkArgs& ra) {
+template <int DIM, bool LS = false>
+ins_status rk_update_df(ins_grid* g, const df* F, const df* p, double* u0, df* acc, df* us, const RkArgs& ra,
+                        double* uto = nullptr) {
     RkCoefDf c;
     c.nx = g->nx;
     c.ny = g->ny;
@@ -632,7 +633,7 @@ ins_status rk_update_df(ins_grid* g, const df* F, const df* p, double* u0, df* a
     const int bx = (g->nx / 2 + 31) / 32, by = (g->ny + 7) / 8;
     const int kc = wave_chunk((long)bx * by, g->nz, 4L * device_sm_count(), 1);
     const dim3 grd(bx, by, (g->nz + kc - 1) / kc);
-    KLAUNCH(g, "rk_update", (k_rk_update_df<DIM><<<grd, dim3(32, 8), 0, g->stream>>>(c, F, p, u0, acc, us, ra, kc)));
+    KLAUNCH(g, "rk_update", (k_rk_update_df<DIM, LS><<<grd, dim3(32, 8), 0, g->stream>>>(c, F, p, u0, acc, us, ra, kc, uto)));
     return INS_OK;
 }
 

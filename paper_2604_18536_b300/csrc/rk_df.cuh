@@ -6,6 +6,10 @@
 //   stage 3: u0 = u0 + dt (acc + b3 k) in place, the CFL per-index maxima of |u_{n+1}| and
 //            the non-finite flag,
 //   stage -1 (projection only, the step pullback's P^T): us = F - G p (u0 and acc untouched),
+// and for Wray's low-storage scheme (LS; two registers u and k_{s-1})
+//   u0 = u0 + dt (gamma_s k + zeta_s acc) in place (the increment added in FP64; into uto instead when
+//   uto is given, the stage recompute of the pullback), acc = k (not on the last stage), the maxima and
+//   the flag on the last stage,
 // with F, p, acc and the stage state us stored as double-float pairs and u0 the caller's FP64
 // field. The arithmetic is double-float (FP32 pipe); u0 is split by bits when it is read, and
 // the last stage adds the double-float increment dt (acc + b3 k) to the FP64 u0 in FP64, so the
@@ -50,10 +54,11 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 
 // Block (32, 8); grid (ceil(nx/2/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx even and 16-byte
 // aligned fields.
-template <int DIM>
+template <int DIM, bool LS = false>
 __global__ void __launch_bounds__(256) k_rk_update_df(RkCoefDf c, const df* __restrict__ F, const df* __restrict__ p,
                                                       double* __restrict__ u0, df* __restrict__ acc,
-                                                      df* __restrict__ us, RkArgs ra, int kchunk) {
+                                                      df* __restrict__ us, RkArgs ra, int kchunk,
+                                                      double* __restrict__ uto = nullptr) {
     constexpr int VEC = 2;
     const int nx = c.nx, ny = c.ny, nz = c.nz;
     const long N = (long)nx * ny * nz;
@@ -67,8 +72,8 @@ __global__ void __launch_bounds__(256) k_rk_update_df(RkCoefDf c, const df* __re
     const int kb = blockIdx.z * kchunk;
     const int ke = min(kb + kchunk, nz);
     const double dt = ra.dt_dev ? *ra.dt_dev : ra.dt_host;
-    const df dta = df(dt * ra.a_next), bb = df(ra.b), dtt = df(dt);
-    const bool fin = ra.stage == 3;
+    const df dta = df(dt * ra.a_next), bb = df(ra.b), dtt = df(dt), dtz = df(dt * ra.b);
+    const bool fin = LS ? ra.last != 0 : ra.stage == 3;
     const bool last_vec = iv == nvx - 1;
     const bool need_global_next = last_vec || lane == 31;
     const long jrow = (long)(j < ny ? j : 0) * nx;
@@ -113,7 +118,23 @@ __global__ void __launch_bounds__(256) k_rk_update_df(RkCoefDf c, const df* __re
                 double uv[VEC];
                 df av[VEC], sv[VEC];
                 ld2(u0 + ea, uv);
-                if (ra.stage == 0) {
+                if (LS) {
+                    if (ra.stage > 0) ld2(acc + ea, av);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        const df inc = ra.stage > 0 ? fma(dtz, av[e], dta * kk[cc][e]) : dta * kk[cc][e];
+                        uv[e] += df_to_double(inc);
+                        if (ra.last) {
+                            const unsigned long long q = abs_bits(uv[e]);
+                            bad |= (q >> 52) == 0x7ffull;
+                            if (cc == 0) mxx[e] = q > mxx[e] ? q : mxx[e];
+                            else if (cc == 1) mxy = q > mxy ? q : mxy;
+                            else qz = q > qz ? q : qz;
+                        }
+                    }
+                    if (!ra.last) st2(acc + ea, kk[cc]);
+                    st2((uto ? uto : u0) + ea, uv);
+                } else if (ra.stage == 0) {
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) {
                         av[e] = bb * kk[cc][e];

@@ -130,8 +130,9 @@ def test_unsupported_grids_stay_native():
     g32.close()
 
 
-def test_non_finite_flag_and_wray3_fallback():
-    """A NaN in the field sets the non-finite flag as in native mode; a Wray3 grid runs native."""
+def test_non_finite_flag_and_wray3():
+    """A NaN in the field sets the non-finite flag as in native mode; Wray's low-storage step in
+    double-float arithmetic is within 1e-12 of the oracle and its CFL maxima are bit-exact."""
     og, g, u0 = make("p3reg", seed=6)
     u0[0, 3, 4, 5] = np.nan
     u = dev(u0)
@@ -144,9 +145,16 @@ def test_non_finite_flag_and_wray3_fallback():
     ow = OGrid(faces, ["periodic"] * 3, nu)
     _, _, v0 = make("p3reg", seed=7)
     dt = 0.5 * timestep.cfl_dt(ow, v0, 0.3)
+    assert gw.f64_arithmetic() == "double-float"
     v = dev(v0)
-    gw.step(v, dt=dt)
-    assert rel(v.cpu().numpy(), timestep.wray3_step(ow, v0, dt)) <= 1e-12
+    dtd = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    gw.step(v, dt_dev=dtd, next_dt_dev=dtd, cfl=0.3)
+    v1 = v.cpu().numpy()
+    assert rel(v1, timestep.wray3_step(ow, v0, dt)) <= 1e-12
+    assert dtd.item() == timestep.cfl_dt(ow, v1, 0.3)
+    w = dev(v0)
+    gw.step_n(w, 50, dt=dt)
+    assert rel(w.cpu().numpy(), timestep.integrate(ow, v0, dt, 50, scheme="wray3")) <= 1e-10
     gw.close()
 
 
@@ -186,4 +194,20 @@ def test_step_vjp_central_differences_double_float():
         v, _ = poisson.project(og, inputs.random_field(u0.shape, 210 + seed))
         fd = (L(u0 + eps * v) - L(u0 - eps * v)) / (2 * eps)
         assert abs(fd - np.sum(ub * v)) <= 1e-7 * max(1.0, abs(fd))
+    g.close()
+
+
+def test_wray3_step_vjp_matches_oracle():
+    """The Wray3 step pullback in double-float arithmetic against the oracle's (<= 1e-12)."""
+    from oracle import adjoint
+    faces, nu = CASES["p3r12"]
+    g = Grid(faces, ["periodic"] * 3, nu, dtype=torch.float64, scheme="wray3")
+    og = OGrid(faces, ["periodic"] * 3, nu)
+    _, _, u0 = make("p3r12", seed=12)
+    ybar = inputs.random_field((3,) + og.shape, 112)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    ub, nb = g.step_vjp(dev(u0), dev(ybar), dt=dt)
+    ub_o, nb_o = adjoint.wray3_step_vjp(og, u0, dt, ybar)
+    assert rel(ub.cpu().numpy(), ub_o) <= 1e-12
+    assert abs(nb.item() - nb_o) <= 5e-11 * abs(nb_o)
     g.close()
