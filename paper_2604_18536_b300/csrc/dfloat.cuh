@@ -134,6 +134,22 @@ __device__ __forceinline__ double f2d_bits(float f) {
     const unsigned l32 = e == 0 ? 0u : (b << 29);
     return __hiloint2double((int)h32, (int)l32);
 }
+// FP64 -> FP32 rounded to nearest (ties to even) by bits: the same value as the convert instruction
+// for results in the normal FP32 range; |x| < 2^-126 gives a signed 0 (no FP32 denormals), |x| >=
+// the FP32 overflow threshold gives inf, NaN stays NaN.
+__device__ __forceinline__ float d2f_bits_rn(double x) {
+    const unsigned h32 = (unsigned)__double2hiint(x);
+    const unsigned l32 = (unsigned)__double2loint(x);
+    const unsigned sgn = h32 & 0x80000000u;
+    const int e = (int)((h32 >> 20) & 0x7ffu) - 896;   // FP32 biased exponent
+    const unsigned m23 = ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+    const unsigned rest = l32 & 0x1fffffffu;
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+    unsigned b = (((unsigned)e << 23) | m23) + up;       // a carry out of the mantissa bumps the exponent
+    if (e <= 0) b = 0u;
+    else if (e >= 255 || b >= 0x7f800000u) b = ((e == 1151 && (m23 | rest)) ? 0x7fc00000u : 0x7f800000u);
+    return __uint_as_float(b | sgn);
+}
 // hi + lo in FP64: exact (the two parts span fewer than 53 bits), one FP64 add.
 __device__ __forceinline__ double df_to_double(df a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
@@ -160,5 +176,15 @@ struct Cvt<df, double> {
 };
 template <typename T, typename S>
 __device__ __forceinline__ T cvt_in(S x) { return Cvt<T, S>::in(x); }
+
+// field value <-> FP64 for FP64 arithmetic on FP32 or FP64 fields, off the FP64 pipe for FP32
+__device__ __forceinline__ double as_f64(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double as_f64(double x) { return x; }
+template <typename T>
+__device__ __forceinline__ T from_f64(double x);
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) { return d2f_bits_rn(x); }
+template <>
+__device__ __forceinline__ double from_f64<double>(double x) { return x; }
 
 }  // namespace ins

@@ -326,7 +326,8 @@ __global__ void k_make_scale(T* __restrict__ s, const double* __restrict__ lx, c
 // then x_j = d_j - g_j x_{j+1} upwards from m and x_j = e_j - g_j x_{j-1} downwards from m
 // (f = th_invm, g = th_cp, per row and column). The normalisation s = 1/(nx nz) of the two
 // inverse FFTs is folded into the factors (f' = s f, lo' = lo / s, up' = up / s give s x with
-// the same operations). Two threads per column, one per end, so twice
+// the same operations). FP32 spectra are converted to and from FP64 by bit operations (the
+// convert instructions would run on the FP64 pipe). Two threads per column, one per end, so twice
 // the columns' parallelism of a one-sided sweep; the middle values pass through shared memory.
 // col = kz * nxh + kx; element (col, j) at (col / nxh) * ny * nxh + j * nxh + col % nxh.
 // The mean mode (col 0) has its first row replaced by p_0 = 0 (r_0 taken as 0).
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
             for (int q = 0; q < CH; ++q) {
                 if (s0 + q < nrows) {
                     const int j = j0 + dir * (s0 + q);
-                    double rre = (double)r[q].re, rim = (double)r[q].im;
+                    double rre = as_f64(r[q].re), rim = as_f64(r[q].im);
                     if (j == 0 && col == 0) {
                         rre = 0.0;
                         rim = 0.0;
@@ -399,9 +400,9 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
     // x_m, computed by both ends of the column
     const double2 dm = mid[0][lc], em = mid[1][lc];
     const double lom = __ldg(&lo[m]), upm = __ldg(&up[m]);
-    double xre = ((double)rm.re - lom * dm.x - upm * em.x) * fm;
-    double xim = ((double)rm.im - lom * dm.y - upm * em.y) * fm;
-    if (top) S[base + (long)m * nxh] = {(T)xre, (T)xim};
+    double xre = (as_f64(rm.re) - lom * dm.x - upm * em.x) * fm;
+    double xim = (as_f64(rm.im) - lom * dm.y - upm * em.y) * fm;
+    if (top) S[base + (long)m * nxh] = {from_f64<T>(xre), from_f64<T>(xim)};
     // back-substitution from the middle outwards: top m-1 .. 0, bottom m+1 .. ny-1
     const int jb = top ? m - 1 : m + 1;
     for (int s0 = 0; s0 < nrows; s0 += CH) {
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
                 const int j = jb - dir * (s0 + q);
                 xre = d[q].re - g[q] * xre;
                 xim = d[q].im - g[q] * xim;
-                S[base + (long)j * nxh] = {(T)xre, (T)xim};
+                S[base + (long)j * nxh] = {from_f64<T>(xre), from_f64<T>(xim)};
             }
         }
     }
