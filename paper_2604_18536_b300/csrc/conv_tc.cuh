@@ -1,24 +1,35 @@
 // 3x3x3 circular convolutions of the CNN closure on the 5th-generation tensor
 // cores (tcgen05, kind::f16: BF16 operands, FP32 accumulation in TMEM).
 //
-// Implicit GEMM without an im2col buffer. One MMA tile = 128 output voxels
-// (8 in x by 16 in y of one z plane) by N output channels. Input planes (with
-// a one-voxel periodic halo) are staged in shared memory as 16-byte entries of
-// 8 channels, laid out [channel group][plane slot][y (18)][x (10)]. For tap
-// (dx, dy, dz) the A operand of the MMA is a shared-memory descriptor pointing
-// at entry (slot(z+dz), 1+dy, 1+dx): its 8-row core matrices are 8 consecutive
-// x voxels (16 B apart) and consecutive core matrices are consecutive y rows
-// (SBO = one padded row, 160 B); the two core matrices of a K=16 step are two
-// channel groups (LBO = one channel-group block). The B operand is the tap's
-// weight block [N rows x K channels], K-major. D (128 lanes x N FP32 columns)
-// lives in TMEM; the epilogue reads it with tcgen05.ld (one voxel per thread).
+// Implicit GEMM without an im2col buffer. One MMA tile = 128 output voxels (8 in x by 16 in y of
+// one z plane) by N output channels. Input planes (with a one-voxel periodic halo) are staged in
+// shared memory as 16-byte entries of 8 channels, a ring slot per plane laid out
+// [channel group][y (18)][x (10)]. For tap (dx, dy) of a staged plane the A operand of the MMA is
+// a shared-memory descriptor pointing at entry (1+dy, 1+dx) of the slot: its 8-row core matrices
+// are 8 consecutive x voxels (16 B apart) and consecutive core matrices are consecutive y rows
+// (SBO = one padded row, 160 B); the two core matrices of a K=16 step are two channel groups
+// (LBO = one channel-group block). The B operand is a weight block [rows x K channels], K-major.
+// D lives in TMEM; the epilogue reads it with tcgen05.ld (one voxel per thread).
 //
-// A CTA of 256 threads owns one 8 x 16 column of one z chunk. Two TMEM accumulators
-// alternate between tiles: while the epilogue reads tile z, the MMAs of tile z+1 run.
-// Planes go through a 5-slot ring: tile z+1 reads slots z..z+2 while plane z+3 is in
-// flight (cp.async). Thread 0 issues the MMAs and commits them to the accumulator's
-// mbarrier; every wait is bounded and reports through an error flag instead of hanging.
-// The epilogue splits a tile's channels over two warps per TMEM lane quarter.
+// A CTA owns one 8 x 16 column of one z chunk and computes it in groups of four output planes
+// z0 .. z0+3, which read input planes z0-1 .. z0+4. The weights of one (dx, dy) are stored as the
+// N rows of dz = +1, 0, -1 stacked (3N rows), and output plane z0+o reads input plane z0+r with
+// dz = r - o: one MMA of (number of outputs) x N columns applies a staged plane to every output
+// plane of the group that reads it, writing adjacent N-column blocks of the group's accumulator
+// (4N TMEM columns): 27 MMAs per output plane for 32 input channels instead of 54 with one plane
+// per tile. Measured on this part: an MMA of 128 x N x 16 from one issuing thread takes about 58
+// cycles for N <= 64 and 61 for N = 96, bound by its shared-memory operand reads (A is 4 KB per
+// MMA whatever N), so wider MMAs do more work per operand byte. Three roles synchronise through
+// mbarriers only:
+//  * two loader warps stage the planes of the chunk into a 12-slot ring with cp.async (offsets
+//    formed once per CTA) and publish each plane on its slot's barrier; a slot is refilled once the
+//    MMAs of the last group that reads it have completed (a commit of that group arrives on the
+//    slot's release barrier). The weights arrive by one bulk copy at the start;
+//  * an MMA warp waits for the group's planes and for a free accumulator (two alternate), and one
+//    lane issues the group's MMAs and commits them to the accumulator's barrier;
+//  * eight epilogue warps wait for the accumulator, read its four planes with tcgen05.ld (two warps
+//    per TMEM lane quarter split the channels), release it, and form and store the outputs.
+// Every wait is bounded and reports through an error flag instead of hanging.
 //
 // The same kernel runs the backward data gradient (a convolution with the taps
 // reversed and the channel roles swapped) with a different epilogue.
@@ -34,10 +45,13 @@ namespace ins {
 constexpr int CV_TX = 8, CV_TY = 16;           // output tile: 8 x 16 voxels = 128 rows
 constexpr int CV_PX = CV_TX + 2, CV_PY = CV_TY + 2;
 constexpr int CV_ROW = CV_PX * 16;              // bytes per padded row of 16-byte entries
-constexpr int CV_PLANE = CV_PY * CV_ROW;        // bytes per staged plane of one channel group
-constexpr int CV_SLOTS = 5;
-constexpr int CV_CGS = CV_SLOTS * CV_PLANE;     // bytes per channel group (all slots)
-constexpr int CV_THREADS = 256;
+constexpr int CV_CGB = CV_PY * CV_ROW;          // bytes of one channel group of a staged plane
+constexpr int CV_G = 4;                         // output planes per MMA group
+constexpr int CV_LAG = 2;                       // plane copies in flight beyond the one published
+constexpr int CV_SLOTS = 12;                    // plane ring (>= 10 + CV_LAG: see the loader warps)
+constexpr int CV_EPI_WARPS = 8;                 // epilogue warps
+constexpr int CV_LD_WARPS = 2;                  // plane-loader warps
+constexpr int CV_THREADS = 32 * (CV_EPI_WARPS + CV_LD_WARPS + 1);   // + one MMA warp
 constexpr long CV_SPIN = 1L << 24;              // bound on every mbarrier wait
 
 enum ConvEpi {
@@ -77,234 +91,392 @@ __device__ __forceinline__ void cv_cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
-__device__ __forceinline__ float cv_gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752440f)); }
+// erf(x) and exp(-x^2) by the rational approximation of Hastings as given by Abramowitz and Stegun,
+// Handbook of Mathematical Functions, formula 7.1.26: for x >= 0,
+//   erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),  t = 1 / (1 + p x),
+// with |error| <= 1.5e-7, extended to x < 0 by oddness. The exponential is shared with the GELU
+// derivative. The error is far below the BF16 resolution (2^-8) of the activations written.
+__device__ __forceinline__ float cv_erf(float x, float& ex2) {
+    const float ax = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    float q = fmaf(1.061405429f, t, -1.453152027f);
+    q = fmaf(q, t, 1.421413741f);
+    q = fmaf(q, t, -0.284496736f);
+    q = fmaf(q, t, 0.254829592f);
+    ex2 = __expf(-ax * ax);
+    return copysignf(fmaf(-q * t, ex2, 1.0f), x);
+}
+// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 and its derivative Phi(z) + z phi(z)
+__device__ __forceinline__ float cv_gelu(float z) {
+    float e;
+    const float er = cv_erf(z * 0.70710678118654752440f, e);
+    return 0.5f * z * (1.0f + er);
+}
 __device__ __forceinline__ float cv_gelu_grad(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752440f)) + z * 0.39894228040143267794f * expf(-0.5f * z * z);
+    float e;   // exp(-z^2 / 2)
+    const float er = cv_erf(z * 0.70710678118654752440f, e);
+    return fmaf(z * 0.39894228040143267794f, e, 0.5f * (1.0f + er));
 }
 
-// Stage plane gz (periodic) of the column into ring slot `slot` with cp.async.
-template <int CG>
-__device__ __forceinline__ void cv_load_plane(const ConvArgs& a, unsigned char* sA, int slot, int gz, int x0, int y0) {
-    const int nx = a.nx, ny = a.ny;
-    const unsigned char* xb = reinterpret_cast<const unsigned char*>(a.x);
-    constexpr int VB = CG * 16;   // bytes per voxel
-    for (int e = threadIdx.x; e < CG * CV_PY * CV_PX; e += CV_THREADS) {
-        const int cg = e / (CV_PY * CV_PX);
-        const int r = e - cg * (CV_PY * CV_PX);
-        const int yy = r / CV_PX, xx = r - yy * CV_PX;
-        int gx = x0 - 1 + xx, gy = y0 - 1 + yy;
-        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
-        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-        const long vox = ((long)gz * ny + gy) * nx + gx;
-        cv_cp_async16(cv_smem(sA + cg * CV_CGS + slot * CV_PLANE + yy * CV_ROW + xx * 16), xb + vox * VB + cg * 16);
+// Ring-slot layout of a staged plane: CG blocks of CV_CGB bytes, block cg holding [y (18)][x (10)]
+// 16-byte entries of channels 8 cg .. 8 cg + 7 (the A operand's core matrices), with the periodic
+// wrap in x and y applied. CvPlaneCopy holds the entries e = first + COUNT k (k < K) one thread
+// copies of every plane, ordered [y][x][channel group] so that a warp's reads are contiguous, with
+// their byte offsets within a z plane of the input (g) and within a slot (s): they are the same
+// for every plane, so a plane costs one cp.async per entry.
+template <int CG, int COUNT>
+struct CvPlaneCopy {
+    static constexpr int EPP = CG * CV_PY * CV_PX;    // entries per plane
+    static constexpr int K = (EPP + COUNT - 1) / COUNT;
+    uint32_t g[K], s[K];
+    bool last;                                        // entry K-1 exists for this thread
+    __device__ __forceinline__ CvPlaneCopy(int first, int x0, int y0, int nx, int ny) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int e = min(first + COUNT * k, EPP - 1);
+            const int cg = e % CG;
+            const int r = e / CG;
+            const int yy = r / CV_PX, xx = r - yy * CV_PX;
+            int gx = x0 - 1 + xx, gy = y0 - 1 + yy;
+            gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+            gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+            g[k] = (uint32_t)((gy * nx + gx) * (CG * 16) + cg * 16);
+            s[k] = (uint32_t)(cg * CV_CGB + yy * CV_ROW + xx * 16);
+        }
+        last = first + COUNT * (K - 1) < EPP;
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
+    // plane gz of x (bytes) into the slot at shared address dst, as one cp.async group
+    __device__ __forceinline__ void load(const unsigned char* x, int gz, int nx, int ny, uint32_t dst) const {
+        const unsigned char* src = x + (size_t)gz * nx * ny * (CG * 16);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (k < K - 1 || last) cv_cp_async16(dst + s[k], src + g[k]);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+};
 
 // CG: channel groups of 8 in the input (1 or 4); N: MMA N (16 or 32); KG: K channel groups in
 // the weight blob (2 when CG == 1, the second group being zero; else CG).
 template <int CG, int N, int EPI>
-__global__ void __launch_bounds__(CV_THREADS) k_conv3d_tc(ConvArgs a) {
+__global__ void __launch_bounds__(CV_THREADS, 1) k_conv3d_tc(ConvArgs a) {
     constexpr int KG = CG == 1 ? 2 : CG;
     constexpr int KSTEPS = KG / 2;                   // MMAs (K = 16) per tap
-    constexpr int TAPB = N * KG * 16;                // weight bytes per tap
-    constexpr int SBO_B = KG * 128;
-    constexpr int NH = N / 2;                        // channels per epilogue warp
-    constexpr uint32_t TCOLS = 2 * N < 32 ? 32 : 2 * N;
+    constexpr int XYB = 3 * N * KG * 16;             // weight bytes per (dx, dy): rows dz = +1, 0, -1
+    constexpr int SBO_B = KG * 128;                  // byte stride of 8-row groups in a weight block
+    constexpr int NH = N / (CV_EPI_WARPS / 4);       // channels per epilogue warp
+    constexpr int ACC = CV_G * N;                    // TMEM columns per accumulator (one group)
+    constexpr uint32_t TCOLS = 2 * ACC < 32 ? 32 : 2 * ACC;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;                        // CG * CV_CGS bytes
-    unsigned char* sB = smem + CG * CV_CGS;          // 27 * TAPB bytes
-    __shared__ __align__(8) uint64_t mbar[2];
+    constexpr int SLOTB = CG * CV_CGB;               // bytes per ring slot
+    unsigned char* sA = smem;                        // CV_SLOTS * SLOTB bytes
+    unsigned char* sB = smem + CV_SLOTS * SLOTB;     // 9 * XYB bytes
+    __shared__ __align__(8) uint64_t full[2];        // accumulator b holds a finished group (MMA commit)
+    __shared__ __align__(8) uint64_t empty[2];       // the epilogue warps have read accumulator b
+    __shared__ __align__(8) uint64_t pfull[CV_SLOTS];    // ring slot s holds its plane (loader warps)
+    __shared__ __align__(8) uint64_t pempty[CV_SLOTS];   // the MMAs that read slot s's plane have completed
+    __shared__ __align__(8) uint64_t wbar;               // the weights have landed (bulk copy)
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x0 = blockIdx.x * CV_TX, y0 = blockIdx.y * CV_TY;
     const int zb = blockIdx.z * a.zchunk, ze = min(zb + a.zchunk, nz);
+    const int ngroups = (ze - zb + CV_G - 1) / CV_G;
     const long nvox = (long)nx * ny * nz;
 
-    // weights: 27 taps of the B layout, copied as-is
-    {
-        const unsigned char* wb = reinterpret_cast<const unsigned char*>(a.wblob);
-        for (int e = tid; e < 27 * TAPB / 16; e += CV_THREADS) cv_cp_async16(cv_smem(sB + e * 16), wb + e * 16);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cv_smem(&tbase)),
                      "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&mbar[1])));
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&full[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cv_smem(&empty[b])), "r"(CV_EPI_WARPS));
+        }
+        for (int q = 0; q < CV_SLOTS; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cv_smem(&pfull[q])), "r"(CV_LD_WARPS));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&pempty[q])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cv_smem(&wbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // weights: 9 (dx, dy) blocks of 3N rows (dz = +1, 0, -1), one bulk copy (the blob is
+        // 256-byte aligned and a multiple of 16 bytes long) completing on wbar
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cv_smem(&wbar)), "r"(9 * XYB)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                cv_smem(sB)),
+            "l"(a.wblob), "r"(9 * XYB), "r"(cv_smem(&wbar))
+            : "memory");
     }
-    auto slot_of = [](int z) { return ((z % CV_SLOTS) + CV_SLOTS) % CV_SLOTS; };
-    auto wrapz = [nz](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
-    // prologue planes zb-1 .. zb+2
-    for (int z = zb - 1; z <= zb + 2; ++z) cv_load_plane<CG>(a, sA, slot_of(z), wrapz(z), x0, y0);
+    // plane p (p >= zb - 1) has ring index i = p - zb + 1 and sits in slot i % CV_SLOTS
+    auto slot_of = [zb](int p) { return (p - zb + 1) % CV_SLOTS; };
+    auto wrapz = [nz](int z) { return ((z % nz) + nz) % nz; };
+    // prologue: the first group's planes (ring indices 0 .. 5), by every thread
+    const unsigned char* xin = reinterpret_cast<const unsigned char*>(a.x);
+    {
+        const CvPlaneCopy<CG, CV_THREADS> pc(tid, x0, y0, nx, ny);
+        for (int i = 0; i < CV_G + 2; ++i) pc.load(xin, wrapz(zb - 1 + i), nx, ny, cv_smem(sA + i * SLOTB));
+    }
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tbase;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
-    // MMAs of tile z into accumulator acc (thread 0), committed to mbar[acc]. Descriptors are
-    // formed by adding the operand's byte offset / 16 to the address field of a base descriptor
-    // (all shared addresses stay below 256 KB, so the 14-bit field never carries); with the taps
-    // unrolled, every offset but the three plane slots is a constant.
-    const uint64_t adesc0 = cv_desc(cv_smem(sA), CG == 1 ? 0 : CV_CGS, CV_ROW);
+    // instruction descriptors for MMAs of N, 2N and 3N columns (BF16 x BF16 -> FP32, M = 128)
+    auto idesc_n = [](int n) {
+        return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+    };
+    const uint64_t adesc0 = cv_desc(cv_smem(sA), CG == 1 ? 0 : CV_CGB, CV_ROW);
     const uint64_t bdesc0 = cv_desc(cv_smem(sB), 128, SBO_B);
-    auto issue_tile = [&](int z, int acc) {
-        const uint32_t dcol = tmem + (uint32_t)(acc * N);
-        const uint64_t as[3] = {adesc0 + (uint64_t)((slot_of(z - 1) * CV_PLANE) >> 4),
-                                adesc0 + (uint64_t)((slot_of(z) * CV_PLANE) >> 4),
-                                adesc0 + (uint64_t)((slot_of(z + 1) * CV_PLANE) >> 4)};
+    // a descriptor = base descriptor + operand byte offset / 16 in the start-address field (bits
+    // 0..13): shared addresses stay below 256 KB, so the sum never carries out of the field and
+    // only the low word changes (one 32-bit add per operand)
+    auto desc_at = [](uint64_t base, uint32_t off16) {
+        uint64_t d;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"((uint32_t)base + off16), "r"((uint32_t)(base >> 32)));
+        return d;
+    };
+    // MMAs of the group of output planes z0 .. z0+3 into accumulator acc (one thread). Input plane
+    // z0 + r (r = -1 .. 4) contributes to outputs o = max(0, r-1) .. min(3, r+1) with dz = r - o; their
+    // weight rows (dz = +1, 0, -1 stacked) are contiguous, so one MMA of N (o_last - o_first + 1)
+    // columns covers them, into columns N o_first of the accumulator. r = 1 (outputs 0..2) and r = 4
+    // (output 3) go first: their first MMAs overwrite every column, all later ones accumulate.
+    auto issue_group = [&](int z0, int acc) {
+        const uint32_t dbase = tmem + (uint32_t)(acc * ACC);
+        const int rorder[6] = {1, 4, -1, 0, 2, 3};
 #pragma unroll
-        for (int t = 0; t < 27; ++t) {
-            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        for (int ri = 0; ri < 6; ++ri) {
+            const int r = rorder[ri];
+            const int of = r - 1 > 0 ? r - 1 : 0, ol = r + 1 < CV_G - 1 ? r + 1 : CV_G - 1;
+            const uint32_t idesc = idesc_n(N * (ol - of + 1));
+            const uint32_t ap = (uint32_t)((slot_of(z0 + r) * SLOTB) >> 4);
+            const uint32_t dcol = dbase + (uint32_t)(N * of);
+            const int rowb = N * (1 - r + of);   // first weight row of the block
 #pragma unroll
-            for (int s = 0; s < KSTEPS; ++s) {
-                const uint64_t ad = as[dz + 1] + (uint64_t)(((1 + dy) * CV_ROW + (1 + dx) * 16 + 2 * s * CV_CGS) >> 4);
-                const uint64_t bd = bdesc0 + (uint64_t)((t * TAPB + 2 * s * 128) >> 4);
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"((t | s) ? 1 : 0));
+            for (int xy = 0; xy < 9; ++xy) {
+                const int dy = xy / 3 - 1, dx = xy % 3 - 1;
+#pragma unroll
+                for (int s = 0; s < KSTEPS; ++s) {
+                    const uint64_t ad =
+                        desc_at(adesc0, ap + (uint32_t)(((1 + dy) * CV_ROW + (1 + dx) * 16 + 2 * s * CV_CGB) >> 4));
+                    const uint64_t bd = desc_at(bdesc0, (uint32_t)((xy * XYB + (rowb / 8) * SBO_B + 2 * s * 128) >> 4));
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"((ri >= 2 || xy > 0 || s > 0) ? 1u : 0u));
+                }
             }
         }
+    };
+    // planes z0-1 .. z0+2 are not read by later groups: their slots are free once the group's MMAs
+    // complete. The accumulator's commit goes last, so its completion implies the others'.
+    auto commit_group = [&](int z0, int acc) {
+#pragma unroll
+        for (int p = -1; p <= 2; ++p)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             cv_smem(&pempty[slot_of(z0 + p)]))
+                         : "memory");
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         cv_smem(&mbar[acc]))
+                         cv_smem(&full[acc]))
                      : "memory");
     };
-    if (tid == 0 && zb < ze) issue_tile(zb, 0);
-    uint32_t phase = 0u;   // bit b: parity of accumulator b's barrier
-    bool alive = true;
-    // epilogue ownership: warp w reads TMEM lanes 32 (w % 4) .. +31 (voxel rows) and channels
-    // (w / 4) NH .. +NH of the tile
-    const int q4 = warp & 3, half = warp >> 2;
-    const int m = q4 * 32 + lane;
-    const int vx = x0 + (m & 7), vy = y0 + (m >> 3);
-    const bool inside = vx < nx && vy < ny;
-    const int c0 = half * NH;
-    float bv[NH];
-#pragma unroll
-    for (int c = 0; c < NH; ++c) bv[c] = (a.bias && (EPI == EPI_GELU || EPI == EPI_OUT)) ? a.bias[c0 + c] : 0.f;
-
-    for (int z = zb; z < ze; ++z) {   // every thread reaches the barrier below (uniform exit)
-        const int b = (z - zb) & 1;
-        const bool more = z + 1 < ze;
-        // plane z+3 (tile z+2) into the slot of plane z-2, whose last reader (tile z-1) has finished
-        if (more) cv_load_plane<CG>(a, sA, slot_of(z + 3), wrapz(z + 3), x0, y0);
-        else asm volatile("cp.async.commit_group;" ::: "memory");
-        // plane z+2 has landed; the epilogue of tile z-1 is done with accumulator b^1
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        // one barrier per tile; it also spreads a failed wait of the previous tile to every thread
-        if (__syncthreads_or(!alive)) {
-            alive = false;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0 && more) issue_tile(z + 1, b ^ 1);
-        // the data gradient's pre-activations of tile z, loaded before the wait so that their
-        // latency overlaps the MMAs
-        __align__(16) float zi[EPI == EPI_DGELU ? NH : 1];
-        if constexpr (EPI == EPI_DGELU) {
-            if (inside) {
-                const float4* zs = reinterpret_cast<const float4*>(a.zin + (((long)z * ny + vy) * nx + vx) * N + c0);
-#pragma unroll
-                for (int q = 0; q < NH / 4; ++q) reinterpret_cast<float4*>(zi)[q] = zs[q];
-            }
-        }
-        // wait for the MMAs of tile z (bounded)
+    // bounded wait for the completion of the phase of parity `par` (false: gave up)
+    auto wait_par = [](uint64_t* bar, uint32_t par) {
         uint32_t done = 0;
         for (long it = 0; it < CV_SPIN && !done; ++it) {
             asm volatile(
                 "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                 : "=r"(done)
-                : "r"(cv_smem(&mbar[b])), "r"((phase >> b) & 1u)
+                : "r"(cv_smem(bar)), "r"(par)
                 : "memory");
         }
-        phase ^= 1u << b;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // the warp reads the accumulator only when all its lanes saw the MMAs complete (the
-        // TMEM load is warp-collective); a failed wait ends the loop at the next barrier
-        if (!__all_sync(0xffffffffu, done)) {
-            if (lane == 0) atomicOr(a.err, 2u);
-            alive = false;
-            continue;
-        }
-        // epilogue: D row m -> voxel (vx, vy, z), channels c0 .. c0 + NH
-        uint32_t r[NH];
-        {
-            const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * N + c0);
-            if constexpr (NH == 16) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(taddr));
+        return done != 0;
+    };
+    const int plast = zb + CV_G * ngroups;   // the last plane any group reads
+    const int nplanes = plast - zb + 2;        // ring indices 0 .. plast - zb + 1
+    if (warp >= CV_EPI_WARPS && warp < CV_EPI_WARPS + CV_LD_WARPS) {
+        // ---- loader warps: planes 6, 7, ... (ring index i) in order, each warp a fixed share of
+        // every plane's entries, CV_LAG + 1 planes in flight. Plane i goes into the slot of plane
+        // i - CV_SLOTS, free once the group whose MMAs read that plane last has completed (pempty).
+        // A warp's share of a plane counts on the plane's barrier (pfull, one arrival per loader
+        // warp) once its copies have landed and been fenced for the tensor cores' (async-proxy)
+        // reads. A warp waits for the slot of plane i before it publishes planes i - CV_LAG .. i - 1;
+        // with 10 + CV_LAG or more slots none of those is read before the group after the one that
+        // frees the slot, so the MMA warp always has a complete group queued while the loaders wait.
+        const int lw = warp - CV_EPI_WARPS;
+        const CvPlaneCopy<CG, 32 * CV_LD_WARPS> pc(lw * 32 + lane, x0, y0, nx, ny);
+        bool alive = true;
+        for (int i = CV_G + 2; i < nplanes + CV_LAG && alive; ++i) {
+            if (i < nplanes) {
+                const int slot = i % CV_SLOTS;
+                if (i >= CV_SLOTS) {
+                    alive = __all_sync(0xffffffffu,
+                                       wait_par(&pempty[slot], (uint32_t)(((i - CV_SLOTS) / CV_SLOTS) & 1)));
+                    if (!alive) break;
+                }
+                pc.load(xin, wrapz(zb - 1 + i), nx, ny, cv_smem(sA + slot * SLOTB));
             } else {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                               "=r"(r[7])
-                             : "r"(taddr));
+                asm volatile("cp.async.commit_group;" ::: "memory");   // empty group: keeps the count
+            }
+            asm volatile("cp.async.wait_group %0;" ::"n"(CV_LAG) : "memory");   // plane i - CV_LAG has landed
+            const int q = i - CV_LAG;
+            if (q >= CV_G + 2) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(cv_smem(&pfull[q % CV_SLOTS]))
+                                 : "memory");
+            }
+        }
+        if (!alive && lane == 0) atomicOr(a.err, 2u);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == CV_EPI_WARPS + CV_LD_WARPS) {
+        // ---- MMA warp: group g needs accumulator g & 1 free (group g-2 read out) and its new planes
+        // z0+1 .. z0+4 published (ring indices 4g+2 .. 4g+5; those of group 0 come from the
+        // prologue; planes z0-1, z0 were waited for by group g-1). The loaders publish ring indices
+        // 6, 7, ..., so plane i is the ((i - 6) / CV_SLOTS)-th published in its slot. Lane 0 issues
+        // the group's MMAs.
+        bool alive = __all_sync(0xffffffffu, wait_par(&wbar, 0u));
+        for (int g = 0; g < ngroups && alive; ++g) {
+            const int z0 = zb + CV_G * g, b = g & 1, u = g >> 1;
+            bool ok = true;
+            if (g >= 2) ok = wait_par(&empty[b], (uint32_t)((u - 1) & 1));
+            for (int i = CV_G * g + 2; g > 0 && ok && i <= CV_G * g + CV_G + 1; ++i)
+                ok = wait_par(&pfull[i % CV_SLOTS], (uint32_t)(((i - CV_G - 2) / CV_SLOTS) & 1));
+            alive = __all_sync(0xffffffffu, ok);
+            if (!alive) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (lane == 0) {
+                issue_group(z0, b);
+                commit_group(z0, b);
+            }
+            __syncwarp();
+        }
+        // no MMA may still write TMEM when it is freed: wait for the last group issued
+        if (alive && ngroups > 0) alive = wait_par(&full[(ngroups - 1) & 1], (uint32_t)(((ngroups - 1) >> 1) & 1));
+        if (!alive && lane == 0) atomicOr(a.err, 2u);
+    } else {
+        // ---- epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (voxel rows) and channels
+        // (w / 4) NH .. +NH of each output plane of a group, releases the accumulator, then forms and
+        // stores the outputs
+        const int q4 = warp & 3, part = warp >> 2;
+        const int m = q4 * 32 + lane;
+        const int vx = x0 + (m & 7), vy = y0 + (m >> 3);
+        const bool inside = vx < nx && vy < ny;
+        const int c0 = part * NH;
+        float bv[NH];
+#pragma unroll
+        for (int c = 0; c < NH; ++c) bv[c] = (a.bias && (EPI == EPI_GELU || EPI == EPI_OUT)) ? a.bias[c0 + c] : 0.f;
+        for (int g = 0; g < ngroups; ++g) {
+            const int z0 = zb + CV_G * g, b = g & 1, u = g >> 1;
+            if (!__all_sync(0xffffffffu, wait_par(&full[b], (uint32_t)(u & 1)))) {
+                if (lane == 0) atomicOr(a.err, 2u);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t rr[CV_G][NH];
+#pragma unroll
+            for (int o = 0; o < CV_G; ++o) {
+                const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * ACC + o * N + c0);
+                uint32_t* r = rr[o];
+                if constexpr (NH == 16) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                          "=r"(r[15])
+                        : "r"(taddr));
+                } else if constexpr (NH == 4) {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                                 : "r"(taddr));
+                } else {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                                   "=r"(r[7])
+                                 : "r"(taddr));
+                }
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        }
-        if (inside) {
-            const long v = ((long)z * ny + vy) * nx + vx;
-            if (EPI == EPI_GELU) {
-                __align__(16) __nv_bfloat16 o[NH];
-                __align__(16) float zz[NH];
+            // release the accumulator to the MMA warp (its next MMAs into it follow these reads)
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(cv_smem(&empty[b])) : "memory");
+            // one copy of the per-plane code (instruction cache): plane o is always rr[0], and the
+            // planes move down one register block after each
+#pragma unroll 1
+            for (int o = 0; o < CV_G; ++o) {
+                const int z = z0 + o;
+                if (z >= ze) break;
+                if (o > 0) {
 #pragma unroll
-                for (int c = 0; c < NH; ++c) {
-                    zz[c] = __uint_as_float(r[c]) + bv[c];
-                    o[c] = __float2bfloat16_rn(cv_gelu(zz[c]));
+                    for (int q = 0; q + 1 < CV_G; ++q)
+#pragma unroll
+                        for (int c = 0; c < NH; ++c) rr[q][c] = rr[q + 1][c];
                 }
-                if (a.zout) {
-                    float4* zd = reinterpret_cast<float4*>(a.zout + v * N + c0);
+                const uint32_t* r = rr[0];
+                // epilogue: D row m -> voxel (vx, vy, z), channels c0 .. c0 + NH
+                if (inside) {
+                    const long v = ((long)z * ny + vy) * nx + vx;
+                    if (EPI == EPI_GELU) {
+                        __align__(16) __nv_bfloat16 ob[NH];
+                        __align__(16) float zz[NH];
 #pragma unroll
-                    for (int q = 0; q < NH / 4; ++q) zd[q] = reinterpret_cast<const float4*>(zz)[q];
-                }
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N + c0);
+                        for (int c = 0; c < NH; ++c) {
+                            zz[c] = __uint_as_float(r[c]) + bv[c];
+                            ob[c] = __float2bfloat16_rn(cv_gelu(zz[c]));
+                        }
+                        if (a.zout) {
+                            float4* zd = reinterpret_cast<float4*>(a.zout + v * N + c0);
 #pragma unroll
-                for (int q = 0; q < NH / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
-            } else if (EPI == EPI_DGELU) {
-                __align__(16) __nv_bfloat16 o[NH];
+                            for (int q = 0; q < NH / 4; ++q) zd[q] = reinterpret_cast<const float4*>(zz)[q];
+                        }
+                        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N + c0);
 #pragma unroll
-                for (int c = 0; c < NH; ++c) o[c] = __float2bfloat16_rn(__uint_as_float(r[c]) * cv_gelu_grad(zi[c]));
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N + c0);
+                        for (int q = 0; q < NH / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(ob)[q];
+                    } else if (EPI == EPI_DGELU) {
+                        __align__(16) float zi[NH];
+                        const float4* zs = reinterpret_cast<const float4*>(a.zin + v * N + c0);
 #pragma unroll
-                for (int q = 0; q < NH / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
-            } else {
+                        for (int q = 0; q < NH / 4; ++q) reinterpret_cast<float4*>(zi)[q] = zs[q];
+                        __align__(16) __nv_bfloat16 ob[NH];
 #pragma unroll
-                for (int cc = 0; cc < NH; ++cc) {
-                    const int c = c0 + cc;
-                    if (c >= a.nreal) continue;
-                    float val = __uint_as_float(r[cc]);
-                    if (EPI == EPI_OUT) val += bv[cc];
-                    if (a.out_f64) {
-                        double* o = reinterpret_cast<double*>(a.out) + c * nvox + v;
-                        *o = EPI == EPI_ACCUM ? *o + (double)val : (double)val;
+                        for (int c = 0; c < NH; ++c) ob[c] = __float2bfloat16_rn(__uint_as_float(r[c]) * cv_gelu_grad(zi[c]));
+                        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + v * N + c0);
+#pragma unroll
+                        for (int q = 0; q < NH / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(ob)[q];
                     } else {
-                        float* o = reinterpret_cast<float*>(a.out) + c * nvox + v;
-                        *o = EPI == EPI_ACCUM ? *o + val : val;
+#pragma unroll
+                        for (int cc = 0; cc < NH; ++cc) {
+                            const int c = c0 + cc;
+                            if (c >= a.nreal) continue;
+                            float val = __uint_as_float(r[cc]);
+                            if (EPI == EPI_OUT) val += bv[cc];
+                            if (a.out_f64) {
+                                double* od = reinterpret_cast<double*>(a.out) + c * nvox + v;
+                                *od = EPI == EPI_ACCUM ? *od + (double)val : (double)val;
+                            } else {
+                                float* of = reinterpret_cast<float*>(a.out) + c * nvox + v;
+                                *of = EPI == EPI_ACCUM ? *of + val : val;
+                            }
+                        }
                     }
                 }
             }
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    // the weight copy has landed before the CTA leaves, even on a path that gave up
+    if (tid == 0) wait_par(&wbar, 0u);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
-// Pack weights W[27][cin][cout] (FP32 master copy) into the B layout of k_conv3d_tc as BF16.
+// Pack weights W[27][cin][cout] (FP32 master copy) into the B layout of k_conv3d_tc as BF16:
+// 9 (dx, dy) blocks of 3N rows, the N rows of dz = +1, 0, -1 stacked.
 // forward: row n = co, channel k = ci, tap t; data gradient: row n = ci, channel k = co, tap 26 - t.
 static __global__ void k_pack_weights(const float* __restrict__ W, int cin, int cout, int N, int KG, int transpose,
                                __nv_bfloat16* __restrict__ blob) {
@@ -320,7 +492,9 @@ static __global__ void k_pack_weights(const float* __restrict__ W, int cin, int 
         } else {
             if (n < cin && k < cout) v = W[((long)(26 - t) * cin + n) * cout + k];
         }
-        const long off = (long)t * N * K + (n / 8) * (KG * 64) + (k / 8) * 64 + (n % 8) * 8 + (k % 8);
+        // the taps of one (dx, dy) are stacked as rows dz = +1, 0, -1 (3N rows, t = 9 (dz + 1) + xy)
+        const int xy = t % 9, ns = (2 - t / 9) * N + n;
+        const long off = (long)xy * 3 * N * K + (ns / 8) * (KG * 64) + (k / 8) * 64 + (ns % 8) * 8 + (k % 8);
         blob[off] = __float2bfloat16_rn(v);
     }
 }

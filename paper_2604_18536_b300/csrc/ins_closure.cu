@@ -13,7 +13,7 @@ constexpr int CL_TN[4] = {16, 32, 32, 32}, CL_TKG[4] = {4, 4, 4, 2};
 template <int CG, int N, int EPI>
 size_t conv_smem() {
     constexpr int KG = CG == 1 ? 2 : CG;
-    return (size_t)CG * CV_CGS + 27 * (size_t)N * KG * 16;
+    return (size_t)CV_SLOTS * CG * CV_CGB + 27 * (size_t)N * KG * 16;
 }
 
 template <int CG, int N, int EPI>
@@ -28,15 +28,28 @@ ins_status conv_launch(ins_grid* g, ConvArgs a) {
     a.nx = g->nx;
     a.ny = g->ny;
     a.nz = g->nz;
-    // about one wave of two CTAs per SM: each CTA loads the weights once for ~nz*cols/296 tiles
-    // (measured faster than a strictly single wave of longer chunks, which leaves SMs with one CTA)
-    const int cols = (g->nx / CV_TX) * (g->ny / CV_TY);
-    const int slots = 2 * device_sm_count();
-    int zc = (int)(((long)cols * g->nz + slots - 1) / slots);
-    zc = zc < 2 ? 2 : (zc > g->nz ? g->nz : zc);
+    // z chunks of whole 4-plane groups, one CTA per SM: the chunk with the shortest estimated
+    // makespan (waves x groups per CTA), the longest among equals (fewer weight and halo loads)
+    const long cols = (long)(g->nx / CV_TX) * (g->ny / CV_TY);
+    const long sms = device_sm_count();
+    int zc = CV_G;
+    long best = -1;
+    for (int c = CV_G; c < g->nz + CV_G; c += CV_G) {
+        const long ctas = cols * ((g->nz + c - 1) / c);
+        const long cost = (ctas + sms - 1) / sms * (c / CV_G);
+        if (best < 0 || cost <= best) {
+            best = cost;
+            zc = c;
+        }
+    }
     a.zchunk = zc;
     const dim3 grd(g->nx / CV_TX, g->ny / CV_TY, (g->nz + zc - 1) / zc);
-    KLAUNCH(g, "conv3d_tc", k_conv3d_tc<CG, N, EPI><<<grd, CV_THREADS, conv_smem<CG, N, EPI>(), g->stream>>>(a));
+    // profile names by shape: 8 -> 32 channels (first layer, last data gradient), 32 -> 32 forward
+    // and data gradient, 32 -> 16 (3 used; last layer, first data gradient)
+    constexpr const char* name = CG == 1 ? "conv3d_tc_8to32"
+                                 : N == 16 ? "conv3d_tc_32to16"
+                                 : EPI == EPI_GELU ? "conv3d_tc_32to32" : "conv3d_tc_32to32_dgrad";
+    KLAUNCH(g, name, k_conv3d_tc<CG, N, EPI><<<grd, CV_THREADS, conv_smem<CG, N, EPI>(), g->stream>>>(a));
     return INS_OK;
 }
 
