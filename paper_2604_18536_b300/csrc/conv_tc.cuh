@@ -212,6 +212,13 @@ __global__ void __launch_bounds__(CV_THREADS, 1) k_conv3d_tc(ConvArgs a) {
     // plane p (p >= zb - 1) has ring index i = p - zb + 1 and sits in slot i % CV_SLOTS
     auto slot_of = [zb](int p) { return (p - zb + 1) % CV_SLOTS; };
     auto wrapz = [nz](int z) { return ((z % nz) + nz) % nz; };
+    // Launched as a programmatic dependent of the previous kernel in the stream: the set-up above
+    // (barriers, TMEM, the weights, which no kernel of the closure writes) overlaps that kernel's
+    // tail; everything below reads or writes activations, so it waits for the previous grid to
+    // have completed and flushed. Dependents of this grid may be scheduled at once: they wait the
+    // same way before touching its outputs.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // prologue: the first group's planes (ring indices 0 .. 5), by every thread
     const unsigned char* xin = reinterpret_cast<const unsigned char*>(a.x);
     {

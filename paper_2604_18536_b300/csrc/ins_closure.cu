@@ -49,7 +49,18 @@ ins_status conv_launch(ins_grid* g, ConvArgs a) {
     constexpr const char* name = CG == 1 ? "conv3d_tc_8to32"
                                  : N == 16 ? "conv3d_tc_32to16"
                                  : EPI == EPI_GELU ? "conv3d_tc_32to32" : "conv3d_tc_32to32_dgrad";
-    KLAUNCH(g, name, k_conv3d_tc<CG, N, EPI><<<grd, CV_THREADS, conv_smem<CG, N, EPI>(), g->stream>>>(a));
+    // programmatic dependent launch: the kernel's set-up may overlap the previous kernel's tail
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grd;
+    cfg.blockDim = dim3(CV_THREADS);
+    cfg.dynamicSmemBytes = conv_smem<CG, N, EPI>();
+    cfg.stream = g->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    KLAUNCH(g, name, INS_CUDA(cudaLaunchKernelEx(&cfg, k_conv3d_tc<CG, N, EPI>, a)));
     return INS_OK;
 }
 
