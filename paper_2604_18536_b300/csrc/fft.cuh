@@ -333,18 +333,40 @@ __global__ void k_make_scale(T* __restrict__ s, const double* __restrict__ lx, c
 // The mean mode (col 0) has its first row replaced by p_0 = 0 (r_0 taken as 0).
 // Block 2 * TH_COLS threads: threads [0, TH_COLS) the top ends, the rest the bottom ends of
 // TH_COLS consecutive columns.
+// FP32 spectra are solved in double-float arithmetic (pairs of FP32 numbers, about 48 significant
+// bits: dfloat.cuh) on the FP32 pipe instead of FP64 arithmetic on the FP64 pipe; the FP64 factors
+// are split by bits (2^-47 relative) and the scratch holds double-float pairs. FP64 spectra keep
+// FP64 arithmetic.
 constexpr int TH_COLS = 64;
+
+template <typename T>
+struct ThArith {
+    using A = double;
+    static __device__ __forceinline__ A in(T x) { return as_f64(x); }
+    static __device__ __forceinline__ A fac(double x) { return x; }
+    static __device__ __forceinline__ T out(A x) { return from_f64<T>(x); }
+};
+template <>
+struct ThArith<float> {
+    using A = df;
+    static __device__ __forceinline__ A in(float x) { return df(x); }
+    static __device__ __forceinline__ A fac(double x) { return df_split(x); }
+    static __device__ __forceinline__ float out(A x) { return __fadd_rn(x.hi, x.lo); }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S, const double* __restrict__ lo,
                                                          const double* __restrict__ up,
                                                          const double* __restrict__ invm,
                                                          const double* __restrict__ cp,
-                                                         cplx<double>* __restrict__ dscr, int nxh, int ny, long ncol) {
+                                                         cplx<typename ThArith<T>::A>* __restrict__ dscr, int nxh,
+                                                         int ny, long ncol) {
+    using Ar = ThArith<T>;
+    using A = typename Ar::A;
     // The loads do not depend on the recurrence: rows are fetched in batches of CH before
     // each CH-step stretch of the (sequential) sweep, so CH loads per array are in flight.
     constexpr int CH = 16;
-    __shared__ double2 mid[2][TH_COLS];   // d_{m-1} (top ends), e_{m+1} (bottom ends)
+    __shared__ cplx<A> mid[2][TH_COLS];   // d_{m-1} (top ends), e_{m+1} (bottom ends)
     const int lc = threadIdx.x % TH_COLS;
     const bool top = threadIdx.x < TH_COLS;
     const long col = blockIdx.x * (long)TH_COLS + lc;
@@ -356,7 +378,8 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
     const int dir = top ? 1 : -1;
     const int j0 = top ? 0 : ny - 1;
     const double* cpl = top ? lo : up;   // the coupling to the previous row of the sweep
-    double dre = 0.0, dim_ = 0.0;
+    const A zero = Ar::fac(0.0);
+    cplx<A> dv = {zero, zero};
     if (ok) {
         for (int s0 = 0; s0 < nrows; s0 += CH) {
             cplx<T> r[CH];
@@ -374,19 +397,17 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
             for (int q = 0; q < CH; ++q) {
                 if (s0 + q < nrows) {
                     const int j = j0 + dir * (s0 + q);
-                    double rre = as_f64(r[q].re), rim = as_f64(r[q].im);
-                    if (j == 0 && col == 0) {
-                        rre = 0.0;
-                        rim = 0.0;
-                    }
-                    dre = (rre - a[q] * dre) * f[q];
-                    dim_ = (rim - a[q] * dim_) * f[q];
-                    dscr[(long)j * ncol + col] = {dre, dim_};
+                    A rre = Ar::in(r[q].re), rim = Ar::in(r[q].im);
+                    if (j == 0 && col == 0) rre = rim = zero;
+                    const A aq = Ar::fac(a[q]), fq = Ar::fac(f[q]);
+                    dv.re = (rre - aq * dv.re) * fq;
+                    dv.im = (rim - aq * dv.im) * fq;
+                    dscr[(long)j * ncol + col] = dv;
                 }
             }
         }
     }
-    mid[top ? 0 : 1][lc] = make_double2(dre, dim_);   // 0 when this end has no rows
+    mid[top ? 0 : 1][lc] = dv;   // 0 when this end has no rows
     // row m's right-hand side is read by both ends before the barrier (the top end rewrites it)
     cplx<T> rm = {(T)0, (T)0};
     double fm = 0.0;
@@ -398,15 +419,16 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
     __syncthreads();
     if (!ok) return;
     // x_m, computed by both ends of the column
-    const double2 dm = mid[0][lc], em = mid[1][lc];
-    const double lom = __ldg(&lo[m]), upm = __ldg(&up[m]);
-    double xre = (as_f64(rm.re) - lom * dm.x - upm * em.x) * fm;
-    double xim = (as_f64(rm.im) - lom * dm.y - upm * em.y) * fm;
-    if (top) S[base + (long)m * nxh] = {from_f64<T>(xre), from_f64<T>(xim)};
+    const cplx<A> dm = mid[0][lc], em = mid[1][lc];
+    const A lom = Ar::fac(__ldg(&lo[m])), upm = Ar::fac(__ldg(&up[m])), fmA = Ar::fac(fm);
+    cplx<A> x;
+    x.re = (Ar::in(rm.re) - lom * dm.re - upm * em.re) * fmA;
+    x.im = (Ar::in(rm.im) - lom * dm.im - upm * em.im) * fmA;
+    if (top) S[base + (long)m * nxh] = {Ar::out(x.re), Ar::out(x.im)};
     // back-substitution from the middle outwards: top m-1 .. 0, bottom m+1 .. ny-1
     const int jb = top ? m - 1 : m + 1;
     for (int s0 = 0; s0 < nrows; s0 += CH) {
-        cplx<double> d[CH];
+        cplx<A> d[CH];
         double g[CH];
 #pragma unroll
         for (int q = 0; q < CH; ++q) {
@@ -420,9 +442,10 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
         for (int q = 0; q < CH; ++q) {
             if (s0 + q < nrows) {
                 const int j = jb - dir * (s0 + q);
-                xre = d[q].re - g[q] * xre;
-                xim = d[q].im - g[q] * xim;
-                S[base + (long)j * nxh] = {from_f64<T>(xre), from_f64<T>(xim)};
+                const A gq = Ar::fac(g[q]);
+                x.re = d[q].re - gq * x.re;
+                x.im = d[q].im - gq * x.im;
+                S[base + (long)j * nxh] = {Ar::out(x.re), Ar::out(x.im)};
             }
         }
     }

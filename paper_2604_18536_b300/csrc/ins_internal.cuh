@@ -485,7 +485,8 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
                 g->lam + nx, g->lam + nx + ny, norm / ny, lg));
         } else {
             KLAUNCH(g, "thomas", k_thomas2<T><<<(unsigned)((ncol + TH_COLS - 1) / TH_COLS), 2 * TH_COLS, 0, st>>>(
-                S, g->th_lo, g->th_up, g->th_invm, g->th_cp, reinterpret_cast<cplx<double>*>(g->th_d), nxh, ny, ncol));
+                S, g->th_lo, g->th_up, g->th_invm, g->th_cp,
+                reinterpret_cast<cplx<typename ThArith<T>::A>*>(g->th_d), nxh, ny, ncol));
         }
         if (g->dim == 3 && (s = strided(2, 1)) != INS_OK) return s;
     }
