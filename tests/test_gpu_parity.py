@@ -374,3 +374,24 @@ def test_march_chunk_is_launch_shape_only(name):
     assert all(torch.equal(out[0], o) for o in out[1:])
     with pytest.raises(InsError):
         gg.set_march_chunk(-1)
+
+
+# ------------------------------------------------------------------ square x-y planes, thin z
+# FP32 periodic 3-D grids with square x-y planes of the register FFT lengths 64, 128 and 256 and a
+# few odd z planes (the z pass on a ragged length with the Stockham kernel).
+@pytest.mark.parametrize("nxy,nz", [(64, 9), (128, 5), (256, 3)])
+def test_fp32_square_plane_projection_and_step(nxy, nz):
+    U = inputs.uniform_faces
+    faces = [U(nxy, 0, 2 * PI), U(nxy, 0, 1.5 * PI), U(nz, 0, 0.5)]
+    og = OGrid(faces, ["periodic"] * 3, 0.02)
+    gg = Grid(faces, ["periodic"] * 3, 0.02, dtype=torch.float32)
+    u = rounded(rand_u(og, 21), torch.float32)
+    out = host(gg.project(dev(u, torch.float32)))
+    ref, _ = poisson.project(og, u)
+    assert rel(out, ref) <= 2e-5, rel(out, ref)
+    u0 = rounded(rand_u(og, 22, project=True), torch.float32)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    ut = dev(u0, torch.float32)
+    gg.step(ut, dt=dt)
+    assert rel(host(ut), timestep.rk4_step(og, u0, dt)) <= 2e-5
+    gg.close()
