@@ -1006,16 +1006,29 @@ __global__ void __launch_bounds__(256, 1) k_wgrad_plane(const __nv_bfloat16* __r
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::TCOLS));
 }
 
-// dW[t][ci][co] += sum over the CTAs' partial blocks part[c][t][ci][0..N) (co < cout); one
-// thread per weight, fixed summation order.
-static __global__ void k_wgrad_reduce(const float* __restrict__ part, int ncta, int N, int cout, float* __restrict__ dW) {
+// dW[t][ci][co] += sum over the CTAs' partial blocks part[c][t][ci][0..N) (co < cout). A block of
+// 256 threads takes 32 consecutive weights (one per lane); warp w sums the blocks c = w, w + 8, ...
+// in order and the eight warp sums are added in warp order: a fixed summation order, with eight
+// times the loads in flight of one thread per weight.
+static __global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ part, int ncta, int N, int cout,
+                                                             float* __restrict__ dW) {
+    __shared__ float ws[8][32];
     const int total = 27 * 32 * cout;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    float sum = 0.f;
+    if (e < total) {
         const int tci = e / cout, co = e - tci * cout;
         const float* p = part + (long)tci * N + co;
-        float sum = 0.f;
-        for (int c = 0; c < ncta; ++c) sum += p[(long)c * 27 * 32 * N];
-        dW[e] += sum;
+        for (int c = warp; c < ncta; c += 8) sum += p[(long)c * 27 * 32 * N];
+    }
+    ws[warp][lane] = sum;
+    __syncthreads();
+    if (warp == 0 && e < total) {
+        float t = ws[0][lane];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) t += ws[w][lane];
+        dW[e] += t;
     }
 }
 

@@ -94,7 +94,7 @@ ins_status wgrad_launch(ins_grid* g, const __nv_bfloat16* X, const __nv_bfloat16
             KLAUNCH(g, "wgrad", (k_wgrad_plane<CY><<<grd, 256, WpShape<N>::SMEM, g->stream>>>(
                                     X, dY, g->nx, g->ny, g->nz, cout, zc, part, db, err)));
             const int ncta = (int)(grd.x * grd.y * grd.z);
-            KLAUNCH(g, "wgrad_reduce", k_wgrad_reduce<<<(27 * 32 * cout + 255) / 256, 256, 0, g->stream>>>(
+            KLAUNCH(g, "wgrad_reduce", k_wgrad_reduce<<<(27 * 32 * cout + 31) / 32, 256, 0, g->stream>>>(
                                            part, ncta, N, cout, dW));
             return INS_OK;
         }
