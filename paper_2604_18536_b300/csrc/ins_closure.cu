@@ -64,12 +64,24 @@ ins_status conv_launch(ins_grid* g, ConvArgs a) {
     return INS_OK;
 }
 
-// Grid of k_wgrad_plane: 16 x 8 columns, z chunks for about one CTA per SM.
+// Grid of k_wgrad_plane: 16 x 8 columns, z chunks.
+// One CTA per SM at a time: the z chunk with the shortest estimated time in units of one plane's
+// MMAs (measured: about 2.4 us per plane, 7 us of set-up and accumulator read-out per CTA, and the
+// reduction of one 110 KB partial block per CTA): waves x (planes + 3) + CTAs / 40. A second
+// partial wave of CTAs doubles the time.
 dim3 wgrad_plane_grid(const ins_grid* g, int* zchunk) {
     const long cols = (long)(g->nx / WP_TX) * (g->ny / WP_TY);
     const long sms = device_sm_count();
-    int zc = (int)((cols * g->nz + sms - 1) / sms);
-    zc = zc < 1 ? 1 : (zc > g->nz ? g->nz : zc);
+    int zc = g->nz;
+    long best = -1;
+    for (int c = 1; c <= g->nz; ++c) {
+        const long ctas = cols * ((g->nz + c - 1) / c);
+        const long cost = 40 * ((ctas + sms - 1) / sms) * (c + 3) + ctas;
+        if (best < 0 || cost <= best) {
+            best = cost;
+            zc = c;
+        }
+    }
     *zchunk = zc;
     return dim3(g->nx / WP_TX, g->ny / WP_TY, (g->nz + zc - 1) / zc);
 }
@@ -91,7 +103,7 @@ ins_status wgrad_launch(ins_grid* g, const __nv_bfloat16* X, const __nv_bfloat16
             }
             int zc;
             const dim3 grd = wgrad_plane_grid(g, &zc);
-            KLAUNCH(g, "wgrad", (k_wgrad_plane<CY><<<grd, 256, WpShape<N>::SMEM, g->stream>>>(
+            KLAUNCH(g, "wgrad_plane", (k_wgrad_plane<CY><<<grd, 256, WpShape<N>::SMEM, g->stream>>>(
                                     X, dY, g->nx, g->ny, g->nz, cout, zc, part, db, err)));
             const int ncta = (int)(grd.x * grd.y * grd.z);
             KLAUNCH(g, "wgrad_reduce", k_wgrad_reduce<<<(27 * 32 * cout + 31) / 32, 256, 0, g->stream>>>(
@@ -113,7 +125,7 @@ ins_status wgrad_launch(ins_grid* g, const __nv_bfloat16* X, const __nv_bfloat16
     nchunk = nchunk > stages ? stages : (nchunk < 1 ? 1 : nchunk);
     const long vchunk = ((stages + nchunk - 1) / nchunk) * WG_S;
     nchunk = (nvox + vchunk - 1) / vchunk;
-    KLAUNCH(g, "wgrad", k_wgrad_tc<CX, CY><<<dim3(ngroups, (unsigned)nchunk), WG_THREADS, WgShape<N>::SMEM, g->stream>>>(
+    KLAUNCH(g, "wgrad_gather", k_wgrad_tc<CX, CY><<<dim3(ngroups, (unsigned)nchunk), WG_THREADS, WgShape<N>::SMEM, g->stream>>>(
                             X, dY, g->nx, g->ny, g->nz, cin, cout, vchunk, dW, db, err));
     return INS_OK;
 }
