@@ -28,6 +28,9 @@ CASES = {
     "p3ragged": ([U(192, 0, 2 * PI), U(16, 0, 1.0), U(128, 0, 2 * PI)], 0.01),
     "p2r12": ([U(192, 0, 2 * PI), U(96, 0, 1.5 * PI)], 0.02),
     "p2pow": ([U(256, 0, 2 * PI), U(64, 0, 2 * PI)], 0.01),
+    # y and z lines of 256 in the strided passes (64 in p3reg and p2pow)
+    "p3r4y": ([U(16, 0, 2 * PI), U(256, 0, 2 * PI), U(16, 0, 1.0)], 0.02),
+    "p3r4z": ([U(32, 0, 2 * PI), U(16, 0, 1.0), U(256, 0, 3.0)], 0.02),
 }
 
 
@@ -89,7 +92,7 @@ def test_double_float_differs_from_native_only_at_rounding_level():
     g.close()
 
 
-@pytest.mark.parametrize("name", ["p3reg", "p2pow"])
+@pytest.mark.parametrize("name", ["p3reg", "p2pow", "p3r4z"])
 def test_100_steps(name):
     """<= 1e-10 after 100 steps against the oracle (fixed dt)."""
     og, g, u0 = make(name, seed=4)
@@ -159,7 +162,7 @@ def test_non_finite_flag_and_wray3():
 
 
 @pytest.mark.parametrize("mode", ["double-float", "native"])
-@pytest.mark.parametrize("name", ["p3reg", "p3r12", "p3ragged"])
+@pytest.mark.parametrize("name", ["p3reg", "p3r12", "p3ragged", "p3r4y", "p3r4z"])
 def test_step_vjp_matches_oracle(name, mode):
     """The step pullback in double-float arithmetic (3-D grids): ubar within 1e-12 of the oracle's,
     nubar within 5e-11 relative."""
