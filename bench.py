@@ -164,7 +164,8 @@ def kernel_model(name, n, s, fused=False, arith="native"):
 
 # DRAM bytes per launch of the dominant kernels, from ncu captures of the current kernels at n = 256
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch).
-TRAFFIC = {("f64n", "rhs_div"): 907.1e6, ("f32", "update_rhs_div"): 1071.0e6, ("f64df", "rhs_div"): 919.1e6}
+TRAFFIC = {("f64n", "rhs_div"): 907.1e6, ("f32", "update_rhs_div"): 1071.0e6,
+           ("f64df", "rhs_div"): 913.9e6}   # double-float: mean of stage 1 (916.1 MB) and stages 2-4 (913.2 MB)
 
 
 def step_model_bytes(n, s):
@@ -523,7 +524,21 @@ def bench_channel(n=(192, 128, 192), steps=10, warmup=3):
         prof = g.profile_read()
         g.profile(False)
         ms = e0.elapsed_time(e1) / steps
-        # step VJP on the wall-bounded grid (scatter-form transposes, P^T = M Omega P Omega^-1 M)
+        arith = g.f64_arithmetic() if dtype == torch.float64 else "fp32"
+        ms_native = None
+        if arith == "double-float":
+            # the same steps in native FP64 arithmetic (the step VJP of a wall-bounded grid runs native)
+            g.set_f64_arithmetic("native")
+            g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(steps):
+                g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=CFL)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms_native = e0.elapsed_time(e1) / steps
+            g.set_f64_arithmetic("double-float")
+        # step VJP on the wall-bounded grid (gather-form transposes, P^T = M Omega P Omega^-1 M)
         ybar = u.detach().clone()
         ubar = g.new_velocity()
         g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar)
@@ -534,10 +549,13 @@ def bench_channel(n=(192, 128, 192), steps=10, warmup=3):
         e1.record(st)
         torch.cuda.synchronize()
         vms = e0.elapsed_time(e1) / 3
-        out[tag] = {"ms_per_step": ms, "value": cells / (ms / 1e3), "unit": UNIT,
+        out[tag] = {"ms_per_step": ms, "value": cells / (ms / 1e3), "unit": UNIT, "arithmetic": arith,
                     "ms_per_vjp": vms, "adjoint_forward_ratio": vms / ms,
                     "kernels": {k: {"launches": v[0], "avg_us": round(v[1] / v[0] * 1e3, 2)}
                                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+        if ms_native is not None:
+            out[tag]["native_ms_per_step"] = ms_native
+            out[tag]["adjoint_forward_ratio_vs_native_step"] = vms / ms_native
         g.check_finite()
         g.close()
         del ybar, ubar

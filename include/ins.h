@@ -178,13 +178,15 @@ ins_status ins_set_step_fusion(ins_grid* g, int enable);
  * FP64, the last stage adds the step's increment to it in FP64, and the CFL time step is
  * reduced from the FP64 result exactly as in native mode (bit-identical to the FP64 rule).
  * The step's relative field error against the FP64 oracle stays within the FP64 tolerance
- * (1e-12 per step). It is used by ins_step / ins_step_n (classic RK4 and Wray3) and, on 3-D
+ * (1e-12 per step). It is used by ins_step / ins_step_n (periodic grids: classic RK4 and
+ * Wray3; 3-D channels: classic RK4 with the Thomas wall-normal solve) and, on 3-D periodic
  * grids, ins_step_vjp (the state cotangent accumulates in FP64), without an attached closure
- * or eddy-viscosity model; every other call (ins_rhs, ins_project, 2-D pullbacks, grids with
- * a closure) runs native FP64. Supported grids:
- * FP64, every direction periodic, nx even, every
- * length a power of two from 16 to 256 or 48, 96, 192; elsewhere the setter returns
- * INS_ERR_UNSUPPORTED and the grid stays native. INS_ERR_ARG for other modes. */
+ * or eddy-viscosity model; every other call (ins_rhs, ins_project, 2-D pullbacks, wall-bounded
+ * pullbacks, Wray3 or the DCT solve on a channel, grids with a closure) runs native FP64.
+ * Supported grids: FP64, nx even, every periodic length a power of two from 16 to 256 or 48,
+ * 96, 192, and either every direction periodic or a 3-D channel (walls in y, any ny);
+ * elsewhere the setter returns INS_ERR_UNSUPPORTED and the grid stays native. INS_ERR_ARG for
+ * other modes. */
 typedef enum { INS_ARITH_NATIVE = 0, INS_ARITH_DOUBLE_FLOAT = 1 } ins_arith;
 ins_status ins_set_f64_arithmetic(ins_grid* g, int mode);
 ins_status ins_get_f64_arithmetic(const ins_grid* g, int* mode);

@@ -335,34 +335,54 @@ __global__ void k_make_scale(T* __restrict__ s, const double* __restrict__ lx, c
 // TH_COLS consecutive columns.
 // FP32 spectra are solved in double-float arithmetic (pairs of FP32 numbers, about 48 significant
 // bits: dfloat.cuh) on the FP32 pipe instead of FP64 arithmetic on the FP64 pipe; the FP64 factors
-// are split by bits (2^-47 relative) and the scratch holds double-float pairs. FP64 spectra keep
+// are stored as double-float pairs (rounded from FP64 on the host, 2^-48 relative; no conversion
+// in the sweeps) and the scratch holds double-float pairs. Double-float spectra (the double-float
+// FP64 step on a channel) use the same arithmetic with the FP64 tables split by bits. FP64 spectra keep
 // FP64 arithmetic.
 constexpr int TH_COLS = 64;
 
+// A: the arithmetic type; F: the stored factor type (the grid holds its factor tables as FP64 for
+// FP64 spectra and as double-float pairs, rounded from the same FP64 values, for FP32 spectra).
 template <typename T>
 struct ThArith {
     using A = double;
+    using F = double;
     static __device__ __forceinline__ A in(T x) { return as_f64(x); }
-    static __device__ __forceinline__ A fac(double x) { return x; }
+    static __device__ __forceinline__ A fac(F x) { return x; }
+    static __device__ __forceinline__ F ld(const F* p) { return __ldg(p); }
     static __device__ __forceinline__ T out(A x) { return from_f64<T>(x); }
+};
+// double-float spectra (the double-float FP64 step on a wall-bounded grid): FP64 tables split by bits
+template <>
+struct ThArith<df> {
+    using A = df;
+    using F = double;
+    static __device__ __forceinline__ A in(df x) { return x; }
+    static __device__ __forceinline__ A fac(F x) { return df_split(x); }
+    static __device__ __forceinline__ F ld(const F* p) { return __ldg(p); }
+    static __device__ __forceinline__ df out(A x) { return x; }
 };
 template <>
 struct ThArith<float> {
     using A = df;
+    using F = df;
     static __device__ __forceinline__ A in(float x) { return df(x); }
-    static __device__ __forceinline__ A fac(double x) { return df_split(x); }
+    static __device__ __forceinline__ A fac(F x) { return x; }
+    static __device__ __forceinline__ F ld(const F* p) { return ldg_t(p); }
     static __device__ __forceinline__ float out(A x) { return __fadd_rn(x.hi, x.lo); }
 };
 
 template <typename T>
-__global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S, const double* __restrict__ lo,
-                                                         const double* __restrict__ up,
-                                                         const double* __restrict__ invm,
-                                                         const double* __restrict__ cp,
+__global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S,
+                                                         const typename ThArith<T>::F* __restrict__ lo,
+                                                         const typename ThArith<T>::F* __restrict__ up,
+                                                         const typename ThArith<T>::F* __restrict__ invm,
+                                                         const typename ThArith<T>::F* __restrict__ cp,
                                                          cplx<typename ThArith<T>::A>* __restrict__ dscr, int nxh,
                                                          int ny, long ncol) {
     using Ar = ThArith<T>;
     using A = typename Ar::A;
+    using Fc = typename Ar::F;
     // The loads do not depend on the recurrence: rows are fetched in batches of CH before
     // each CH-step stretch of the (sequential) sweep, so CH loads per array are in flight.
     constexpr int CH = 16;
@@ -377,20 +397,20 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
     const int nrows = top ? m : ny - 1 - m;
     const int dir = top ? 1 : -1;
     const int j0 = top ? 0 : ny - 1;
-    const double* cpl = top ? lo : up;   // the coupling to the previous row of the sweep
-    const A zero = Ar::fac(0.0);
+    const Fc* cpl = top ? lo : up;   // the coupling to the previous row of the sweep
+    const A zero = A(0.0);
     cplx<A> dv = {zero, zero};
     if (ok) {
         for (int s0 = 0; s0 < nrows; s0 += CH) {
             cplx<T> r[CH];
-            double a[CH], f[CH];
+            Fc a[CH], f[CH];
 #pragma unroll
             for (int q = 0; q < CH; ++q) {
                 if (s0 + q < nrows) {
                     const int j = j0 + dir * (s0 + q);
                     r[q] = S[base + (long)j * nxh];
-                    a[q] = __ldg(&cpl[j]);
-                    f[q] = __ldg(&invm[(long)j * ncol + col]);
+                    a[q] = Ar::ld(&cpl[j]);
+                    f[q] = Ar::ld(&invm[(long)j * ncol + col]);
                 }
             }
 #pragma unroll
@@ -400,8 +420,18 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
                     A rre = Ar::in(r[q].re), rim = Ar::in(r[q].im);
                     if (j == 0 && col == 0) rre = rim = zero;
                     const A aq = Ar::fac(a[q]), fq = Ar::fac(f[q]);
-                    dv.re = (rre - aq * dv.re) * fq;
-                    dv.im = (rim - aq * dv.im) * fq;
+                    if constexpr (std::is_same<A, df>::value) {
+                        // (r - a d) f as r f - (a f) d: only one product and one difference on the
+                        // sequential dependence from row to row (double-float; in FP64 the extra
+                        // product costs the FP64 pipe more than the shorter chain saves)
+                        const A bq = aq * fq;
+                        const A are = rre * fq, aim = rim * fq;
+                        dv.re = are - bq * dv.re;
+                        dv.im = aim - bq * dv.im;
+                    } else {
+                        dv.re = (rre - aq * dv.re) * fq;
+                        dv.im = (rim - aq * dv.im) * fq;
+                    }
                     dscr[(long)j * ncol + col] = dv;
                 }
             }
@@ -410,17 +440,17 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
     mid[top ? 0 : 1][lc] = dv;   // 0 when this end has no rows
     // row m's right-hand side is read by both ends before the barrier (the top end rewrites it)
     cplx<T> rm = {(T)0, (T)0};
-    double fm = 0.0;
+    Fc fm = Fc(0.0);
     if (ok) {
         rm = S[base + (long)m * nxh];
         if (m == 0 && col == 0) rm = {(T)0, (T)0};   // ny == 1: the mean mode's p_0 = 0 row is the middle
-        fm = __ldg(&invm[(long)m * ncol + col]);
+        fm = Ar::ld(&invm[(long)m * ncol + col]);
     }
     __syncthreads();
     if (!ok) return;
     // x_m, computed by both ends of the column
     const cplx<A> dm = mid[0][lc], em = mid[1][lc];
-    const A lom = Ar::fac(__ldg(&lo[m])), upm = Ar::fac(__ldg(&up[m])), fmA = Ar::fac(fm);
+    const A lom = Ar::fac(Ar::ld(&lo[m])), upm = Ar::fac(Ar::ld(&up[m])), fmA = Ar::fac(fm);
     cplx<A> x;
     x.re = (Ar::in(rm.re) - lom * dm.re - upm * em.re) * fmA;
     x.im = (Ar::in(rm.im) - lom * dm.im - upm * em.im) * fmA;
@@ -429,13 +459,13 @@ __global__ void __launch_bounds__(2 * TH_COLS) k_thomas2(cplx<T>* __restrict__ S
     const int jb = top ? m - 1 : m + 1;
     for (int s0 = 0; s0 < nrows; s0 += CH) {
         cplx<A> d[CH];
-        double g[CH];
+        Fc g[CH];
 #pragma unroll
         for (int q = 0; q < CH; ++q) {
             if (s0 + q < nrows) {
                 const int j = jb - dir * (s0 + q);
                 d[q] = dscr[(long)j * ncol + col];
-                g[q] = __ldg(&cp[(long)j * ncol + col]);
+                g[q] = Ar::ld(&cp[(long)j * ncol + col]);
             }
         }
 #pragma unroll

@@ -124,9 +124,10 @@ ins_status step_wray3_df(ins_grid* g, double* u, const double* dt_dev, double dt
     return INS_OK;
 }
 
-// The classic RK4 step of an FP64 periodic grid in double-float arithmetic (ins_set_f64_arithmetic):
-// F, r/p, the spectrum, acc and the stage state hold double-float pairs; u stays FP64.
-template <int DIM>
+// The classic RK4 step of an FP64 grid in double-float arithmetic (ins_set_f64_arithmetic): F, r/p,
+// the spectrum, acc and the stage state hold double-float pairs; u stays FP64. WALL: 3-D channel
+// grids (walls in y, stretched rows; the wall-normal solve is the double-float Thomas sweep).
+template <int DIM, bool WALL = false>
 ins_status step_df(ins_grid* g, double* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
     static const double A[4] = {0.5, 0.5, 1.0, 0.0};
     static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
@@ -136,7 +137,7 @@ ins_status step_df(ins_grid* g, double* u, const double* dt_dev, double dt_host,
     df* us = reinterpret_cast<df*>(g->us);
     ins_status s;
     for (int st = 0; st < 4; ++st) {
-        s = st == 0 ? launch_rhs_div_df<DIM, double>(g, u, F, rp) : launch_rhs_div_df<DIM, df>(g, us, F, rp);
+        s = st == 0 ? launch_rhs_div_df<DIM, double, WALL>(g, u, F, rp) : launch_rhs_div_df<DIM, df, WALL>(g, us, F, rp);
         if (s != INS_OK) return s;
         if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
         RkArgs ra;
@@ -148,7 +149,7 @@ ins_status step_df(ins_grid* g, double* u, const double* dt_dev, double dt_host,
         ra.last = st == 3;
         ra.mx = (st == 3 && next_dt) ? g->cfl_max : nullptr;
         ra.err_flag = g->err_flag;
-        if ((s = rk_update_df<DIM>(g, F, rp, u, acc, us, ra)) != INS_OK) return s;
+        if ((s = rk_update_df<DIM, false, WALL>(g, F, rp, u, acc, us, ra)) != INS_OK) return s;
     }
     if (next_dt) {
         KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz,
@@ -164,9 +165,9 @@ ins_status Impl<T, DIM, WALL>::step(ins_grid* g, T* u, const double* dt_dev, dou
             return step_wray3_df<DIM>(g, u, dt_dev, dt_host, next_dt, cfl);
     }
     if (g->scheme == INS_WRAY3) return step_wray3(g, u, dt_dev, dt_host, next_dt, cfl);
-    if constexpr (std::is_same<T, double>::value && !WALL) {
-        if (g->use_df && !g->closure && !g->eddy && reinterpret_cast<uintptr_t>(u) % 16 == 0)
-            return step_df<DIM>(g, u, dt_dev, dt_host, next_dt, cfl);
+    if constexpr (std::is_same<T, double>::value && (!WALL || DIM == 3)) {
+        if (g->use_df && !g->closure && !g->eddy && !(WALL && g->use_dct) && reinterpret_cast<uintptr_t>(u) % 16 == 0)
+            return step_df<DIM, WALL>(g, u, dt_dev, dt_host, next_dt, cfl);
     }
     if constexpr (DIM == 3 && std::is_same<T, float>::value) {
         if (g->pbuf && !g->closure && !g->eddy && g->fusion > 0 && rk_vec_ok<T>(g, u))

@@ -137,17 +137,21 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     // FP32 periodic: [columns of the fused pass | its line | 1/N] (3-D: ny nxh | nz; 2-D: nxh | ny)
     const size_t neig = (!wall_y && D.dtype == INS_F32) ? (size_t)(dim == 3 ? g->ny * nxh + g->nz : nxh + g->ny) + 1 : 0;
     const size_t o_eig = off; off += al(neig * 4);
-    // double-float FP64 step: FP64 periodic grids whose lengths all have register FFT kernels
-    // (x even for the two-cell update)
-    bool df_ok = D.dtype == INS_F64 && !wall_y && g->nx % 2 == 0;
-    for (int a = 0; a < dim; ++a) df_ok = df_ok && reg_fft_len(n3[a]);
+    // double-float FP64 step: FP64 grids whose periodic lengths all have register FFT kernels (x
+    // even for the two-cell update): periodic grids, and 3-D channels (walls in y, any ny: the
+    // wall-normal direction is solved by the Thomas sweep)
+    bool df_ok = D.dtype == INS_F64 && (!wall_y || dim == 3) && g->nx % 2 == 0;
+    for (int a = 0; a < dim; ++a) df_ok = df_ok && (reg_fft_len(n3[a]) || (a == 1 && wall_y));
     size_t o_twdf[3] = {0, 0, 0}, o_scdf = 0;
     if (df_ok) {
         for (int a = 0; a < 3; ++a) {
             o_twdf[a] = off;
             off += al((size_t)n3[a] * 16);
         }
-        o_scdf = off; off += al((size_t)spec * 8);
+        if (!wall_y) {
+            o_scdf = off;
+            off += al((size_t)spec * 8);
+        }
     }
     if (!wall_y) {
         o_scale = off; off += al((size_t)spec * ts);
@@ -187,7 +191,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     g->df_ok = g->use_df = df_ok ? 1 : 0;
     if (df_ok) {
         for (int a = 0; a < 3; ++a) g->tw_df[a] = b + o_twdf[a];
-        g->scale_df = b + o_scdf;
+        g->scale_df = wall_y ? nullptr : b + o_scdf;
     }
     if (!wall_y) {
         g->scale = b + o_scale;
@@ -389,6 +393,21 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
                 los[j] = lo[j] / sn;
                 ups[j] = upc[j] / sn;
             }
+            if (D.dtype == INS_F32) {
+                // FP32 spectra are solved in double-float arithmetic: the tables go to the device as
+                // (hi, lo) float pairs in the same 8 bytes, so the sweeps need no FP64 -> double-float split
+                auto to_df = [](std::vector<double>& v) {
+                    for (double& x : v) {
+                        const float hi = (float)x, lo = (float)(x - (double)hi);
+                        float pr[2] = {hi, lo};
+                        std::memcpy(&x, pr, 8);
+                    }
+                };
+                to_df(los);
+                to_df(ups);
+                to_df(invm);
+                to_df(cp);
+            }
             ok &= up(g->th_lo, los.data(), (size_t)ny * 8);
             ok &= up(g->th_up, ups.data(), (size_t)ny * 8);
             ok &= up(g->th_invm, invm.data(), invm.size() * 8);
@@ -445,8 +464,8 @@ ins_status ins_set_f64_arithmetic(ins_grid* g, int mode) {
     if (mode != INS_ARITH_NATIVE && mode != INS_ARITH_DOUBLE_FLOAT) return fail(INS_ERR_ARG, "unknown arithmetic mode");
     if (mode == INS_ARITH_DOUBLE_FLOAT && !g->df_ok)
         return fail(INS_ERR_UNSUPPORTED,
-                    "double-float arithmetic needs an FP64 periodic grid with even nx and FFT lengths 16..256 "
-                    "(powers of two), 48, 96 or 192");
+                    "double-float arithmetic needs an FP64 grid, periodic or a 3-D channel with walls in y, with "
+                    "even nx and periodic lengths 16..256 (powers of two), 48, 96 or 192");
     g->use_df = mode == INS_ARITH_DOUBLE_FLOAT ? 1 : 0;
     return INS_OK;
 }

@@ -122,9 +122,9 @@ struct ins_grid {
     double* lam = nullptr;         // FP64 eigenvalues: x (nxh) | y (ny) | z (nz)
     double* th_lo = nullptr;       // Thomas: lo[ny], up[ny]
     double* th_up = nullptr;
-    double* th_invm = nullptr;     // [ny][ncol]
+    double* th_invm = nullptr;     // [ny][ncol] (FP32 grids: double-float pairs in the same bytes)
     double* th_cp = nullptr;       // [ny][ncol]
-    void* th_d = nullptr;          // cplx<double> [ny][ncol]
+    void* th_d = nullptr;          // [ny][ncol] complex FP64 or double-float (16 bytes)
     // DCT-II solve along a uniform wall-normal y (available when y is uniform and ny factorises)
     int wall_dct = 0;              // available
     int use_dct = 0;               // selected (ins_set_wall_solver; default Thomas)
@@ -472,20 +472,28 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
             if ((s = strided(2, 2)) != INS_OK) return s;
             if ((s = strided(1, 1)) != INS_OK) return s;
         }
-    } else if constexpr (!DF) {
+    } else {
         if (g->dim == 3 && (s = strided(2, 0)) != INS_OK) return s;
         const long ncol = (long)nz * nxh;
         const double norm = 1.0 / ((double)nx * (g->dim == 3 ? nz : 1));
-        if (g->use_dct) {
+        bool dct = false;
+        if constexpr (DF) {
+            if (g->use_dct) return fail(INS_ERR_UNSUPPORTED, "the DCT wall solve has no double-float pass");
+        } else if (g->use_dct) {
             FftLine<T> py = make_line<T>(g, 1);
             const int lg = g->lg_tw_y;
             const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
             KLAUNCH(g, "dct_solve", k_dct_solve_y<T><<<blocks, FFT_THREADS, fft_smem<T>(ny, lg), st>>>(
                 py, S, ncol, nxh, (long)ny * nxh, nxh, reinterpret_cast<const cplx<T>*>(g->dct_qw), g->lam,
                 g->lam + nx, g->lam + nx + ny, norm / ny, lg));
-        } else {
+            dct = true;
+        }
+        if (!dct) {
             KLAUNCH(g, "thomas", k_thomas2<T><<<(unsigned)((ncol + TH_COLS - 1) / TH_COLS), 2 * TH_COLS, 0, st>>>(
-                S, g->th_lo, g->th_up, g->th_invm, g->th_cp,
+                S, reinterpret_cast<const typename ThArith<T>::F*>(g->th_lo),
+                reinterpret_cast<const typename ThArith<T>::F*>(g->th_up),
+                reinterpret_cast<const typename ThArith<T>::F*>(g->th_invm),
+                reinterpret_cast<const typename ThArith<T>::F*>(g->th_cp),
                 reinterpret_cast<cplx<typename ThArith<T>::A>*>(g->th_d), nxh, ny, ncol));
         }
         if (g->dim == 3 && (s = strided(2, 1)) != INS_OK) return s;
@@ -527,6 +535,7 @@ RhsCoef<T> make_rhs_coef(const ins_grid* g) {
     c.fy = (T)g->force[1];
     c.fz = (T)g->force[2];
     c.yc = reinterpret_cast<const T*>(g->ycoef);
+    c.yc64 = g->dtype == INS_F64 ? reinterpret_cast<const double*>(g->ycoef) : nullptr;
     return c;
 }
 
@@ -612,16 +621,16 @@ ins_status launch_rhs_div(ins_grid* g, const T* u, T* F, T* r, const T* m = null
 
 // F + D F with double-float arithmetic; UI = double for the caller's FP64 field (split by bits
 // on load), df for the stage state.
-template <int DIM, typename UI>
+template <int DIM, typename UI, bool WALL = false>
 ins_status launch_rhs_div_df(ins_grid* g, const UI* u, df* F, df* r) {
     const dim3 blk(RBX, RBY, 1);
     const dim3 grd((g->nx + RBX - 1) / RBX, (g->ny + RBY - 1) / RBY, DIM == 3 ? (g->nz + g->kchunk - 1) / g->kchunk : 1);
-    KLAUNCH(g, "rhs_div", (k_rhs_div<df, DIM, false, UI><<<grd, blk, 0, g->stream>>>(make_rhs_coef<df>(g), u, F, r,
-                                                                                      g->kchunk, (const df*)nullptr)));
+    KLAUNCH(g, "rhs_div", (k_rhs_div<df, DIM, WALL, UI><<<grd, blk, 0, g->stream>>>(make_rhs_coef<df>(g), u, F, r,
+                                                                                     g->kchunk, (const df*)nullptr)));
     return INS_OK;
 }
 
-template <int DIM, bool LS = false>
+template <int DIM, bool LS = false, bool WALL = false>
 ins_status rk_update_df(ins_grid* g, const df* F, const df* p, double* u0, df* acc, df* us, const RkArgs& ra,
                         double* uto = nullptr) {
     RkCoefDf c;
@@ -631,10 +640,11 @@ ins_status rk_update_df(ins_grid* g, const df* F, const df* p, double* u0, df* a
     c.ihx = df(1.0 / g->h[0][0]);
     c.ihy = df(1.0 / g->h[1][0]);
     c.ihz = df(DIM == 3 ? 1.0 / g->h[2][0] : 0.0);
+    c.ihy_row = WALL ? make_geo<double>(g).c[1] + (size_t)C_INV_H * g->ny : nullptr;
     const int bx = (g->nx / 2 + 31) / 32, by = (g->ny + 7) / 8;
     const int kc = wave_chunk((long)bx * by, g->nz, 4L * device_sm_count(), 1);
     const dim3 grd(bx, by, (g->nz + kc - 1) / kc);
-    KLAUNCH(g, "rk_update", (k_rk_update_df<DIM, LS><<<grd, dim3(32, 8), 0, g->stream>>>(c, F, p, u0, acc, us, ra, kc, uto)));
+    KLAUNCH(g, "rk_update", (k_rk_update_df<DIM, LS, WALL><<<grd, dim3(32, 8), 0, g->stream>>>(c, F, p, u0, acc, us, ra, kc, uto)));
     return INS_OK;
 }
 

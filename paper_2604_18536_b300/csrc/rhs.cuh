@@ -55,6 +55,7 @@ struct RhsCoef {
     T ix, iy, iz;   // 1/D
     T fx, fy, fz;   // body force
     const T* yc;    // wall: CY_COUNT arrays of ny values
+    const double* yc64;   // double-float arithmetic: the FP64 arrays, split by bits when a row is read
 };
 
 template <typename T>
@@ -65,7 +66,20 @@ struct YRow {
 template <typename T, bool WALL>
 __device__ __forceinline__ YRow<T> yrow(const RhsCoef<T>& c, int j) {
     YRow<T> r;
-    if constexpr (WALL) {
+    if constexpr (WALL && std::is_same<T, df>::value) {
+        // the FP64 row coefficients, split once per row (a thread's row stays fixed along its march)
+        const double* y = c.yc64;
+        const int n = c.ny;
+        r.f = df_split(__ldg(y + CY_F * n + j));
+        r.s = df_split(__ldg(y + CY_S * n + j));
+        r.wl = df_split(__ldg(y + CY_WL * n + j));
+        r.wr = df_split(__ldg(y + CY_WR * n + j));
+        r.ap = df_split(__ldg(y + CY_AP * n + j));
+        r.am = df_split(__ldg(y + CY_AM * n + j));
+        r.bp = df_split(__ldg(y + CY_BP * n + j));
+        r.bm = df_split(__ldg(y + CY_BM * n + j));
+        r.i = df_split(__ldg(y + CY_I * n + j));
+    } else if constexpr (WALL) {
         const T* y = c.yc;
         const int n = c.ny;
         r.f = __ldg(y + CY_F * n + j);

@@ -29,6 +29,7 @@ namespace ins {
 struct RkCoefDf {
     int nx, ny, nz;
     df ihx, ihy, ihz;   // 1/h of the uniform periodic directions
+    const double* ihy_row;   // WALL: 1/h_y per row (FP64, split by bits once per thread)
 };
 
 __device__ __forceinline__ void ld2(const df* p, df (&x)[2]) {
@@ -53,8 +54,9 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 }
 
 // Block (32, 8); grid (ceil(nx/2/32), ceil(ny/8), ceil(nz/kchunk)). Needs nx even and 16-byte
-// aligned fields.
-template <int DIM, bool LS = false>
+// aligned fields. WALL: y is a no-slip wall direction with a stretched spacing (1/h_y per row); the
+// stored top wall face of u^y (row ny - 1) is no unknown: its k is 0, so it keeps its value.
+template <int DIM, bool LS = false, bool WALL = false>
 __global__ void __launch_bounds__(256) k_rk_update_df(RkCoefDf c, const df* __restrict__ F, const df* __restrict__ p,
                                                       double* __restrict__ u0, df* __restrict__ acc,
                                                       df* __restrict__ us, RkArgs ra, int kchunk,
@@ -77,6 +79,8 @@ __global__ void __launch_bounds__(256) k_rk_update_df(RkCoefDf c, const df* __re
     const bool last_vec = iv == nvx - 1;
     const bool need_global_next = last_vec || lane == 31;
     const long jrow = (long)(j < ny ? j : 0) * nx;
+    const df ihy = WALL ? (j < ny ? df_split(__ldg(&c.ihy_row[j])) : df(0.0f, 0.0f)) : c.ihy;
+    const bool ytop = WALL && j == ny - 1;   // the top wall face of u^y
     const long jnext = (long)(j + 1 < ny ? j + 1 : 0) * nx;   // periodic wrap in y
     unsigned long long mxx[VEC] = {0ull, 0ull}, mxy = 0ull;
     bool bad = false;
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(256) k_rk_update_df(RkCoefDf c, const df* __re
             for (int e = 0; e < VEC; ++e) {
                 const df pe = e + 1 < VEC ? P0[e + 1] : pnext;
                 kk[0][e] = fma(P0[e] - pe, c.ihx, f[0][e]);
-                kk[1][e] = fma(P0[e] - Pn[e], c.ihy, f[1][e]);
+                kk[1][e] = ytop ? df(0.0f, 0.0f) : fma(P0[e] - Pn[e], ihy, f[1][e]);
                 if (DIM == 3) kk[2][e] = fma(P0[e] - Pt[e], c.ihz, f[2][e]);
             }
 #pragma unroll

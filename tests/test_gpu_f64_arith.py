@@ -124,10 +124,14 @@ def test_unsupported_grids_stay_native():
         g.set_f64_arithmetic("double-float")
     assert e.value.status == INS_ERR_UNSUPPORTED
     g.close()
-    ch = Grid(inputs.channel_faces(32, 16, 16), ["periodic", "wall", "periodic"], 1 / 180, [1.0, 0, 0],
-              dtype=torch.float64)
+    ch = Grid(inputs.channel_faces(40, 16, 16), ["periodic", "wall", "periodic"], 1 / 180, [1.0, 0, 0],
+              dtype=torch.float64)                                         # no register FFT for x = 40
     assert ch.f64_arithmetic() == "native"
     ch.close()
+    c2 = Grid([U(32, 0, 4 * PI), inputs.tanh_faces(12, 0, 2, 1.5)], ["periodic", "wall"], 0.05, [1.0, 0],
+              dtype=torch.float64)                                         # 2-D channels stay native
+    assert c2.f64_arithmetic() == "native"
+    c2.close()
     g32 = Grid(inputs.periodic_box(32, 3), ["periodic"] * 3, 0.01, dtype=torch.float32)
     assert g32.f64_arithmetic() == "native"
     g32.close()
@@ -213,4 +217,69 @@ def test_wray3_step_vjp_matches_oracle():
     ub_o, nb_o = adjoint.wray3_step_vjp(og, u0, dt, ybar)
     assert rel(ub.cpu().numpy(), ub_o) <= 1e-12
     assert abs(nb.item() - nb_o) <= 5e-11 * abs(nb_o)
+    g.close()
+
+
+# ---------------------------------------------------------------- channels (walls in y)
+# The double-float step also runs on 3-D channels whose periodic x and z lengths have register FFT
+# kernels: stretched wall-normal rows, wall ghosts and the top wall face of u^y in double-float, the
+# wall-normal Poisson solve by the double-float Thomas sweep.
+CHB = ["periodic", "wall", "periodic"]
+CH_CASES = {
+    "c3df": [U(64, 0, 4 * PI), inputs.tanh_faces(20, 0, 2, 1.5), U(32, 0, 4 * PI / 3)],
+    "c3dfodd": [U(96, 0, 4 * PI), inputs.tanh_faces(15, 0, 2, 1.5), U(16, 0, 4 * PI / 3)],
+}
+
+
+def make_channel(name, seed):
+    faces = CH_CASES[name]
+    og = OGrid(faces, CHB, 1 / 180, [1.0, 0.0, 0.0])
+    g = Grid(faces, CHB, 1 / 180, [1.0, 0.0, 0.0], dtype=torch.float64)
+    u0, _ = poisson.project(og, inputs.channel_velocity_raw(faces, seed=seed))
+    return og, g, u0
+
+
+@pytest.mark.parametrize("mode", ["double-float", "native"])
+@pytest.mark.parametrize("name", list(CH_CASES))
+def test_channel_step_matches_oracle(name, mode):
+    og, g, u0 = make_channel(name, 21)
+    assert g.f64_arithmetic() == "double-float"
+    g.set_f64_arithmetic(mode)
+    u = dev(u0)
+    dt = g.cfl_dt(u, 0.3)
+    assert dt.item() == timestep.cfl_dt(og, u0, 0.3)
+    g.step(u, dt_dev=dt, next_dt_dev=dt, cfl=0.3)
+    u1 = u.cpu().numpy()
+    err = rel(u1, timestep.rk4_step(og, u0, timestep.cfl_dt(og, u0, 0.3)))
+    assert err <= 1e-12, (mode, err)
+    assert dt.item() == timestep.cfl_dt(og, u1, 0.3)
+    assert np.all(u1[1][:, -1, :] == 0.0)    # the top wall face of u^y stays 0
+    g.close()
+
+
+def test_channel_100_steps_and_graph_replay():
+    """<= 1e-10 after 100 steps against the oracle (fixed dt); ins_step_n bit-identical to plain steps."""
+    og, g, u0 = make_channel("c3df", 22)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    u = dev(u0)
+    g.step_n(u, 100, dt=dt)
+    assert rel(u.cpu().numpy(), timestep.integrate(og, u0, dt, 100)) <= 1e-10
+    ua, ub = dev(u0), dev(u0)
+    da, db = g.cfl_dt(ua, 0.3), g.cfl_dt(ub, 0.3)
+    g.step_n(ua, 4, dt_dev=da, next_dt_dev=da, cfl=0.3)
+    for _ in range(4):
+        g.step(ub, dt_dev=db, next_dt_dev=db, cfl=0.3)
+    assert torch.equal(ua, ub) and torch.equal(da, db)
+    g.close()
+
+
+def test_channel_double_float_differs_from_native_only_at_rounding_level():
+    og, g, u0 = make_channel("c3dfodd", 23)
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    ua, ub = dev(u0), dev(u0)
+    g.step(ua, dt=dt)
+    g.set_f64_arithmetic("native")
+    g.step(ub, dt=dt)
+    d = rel(ua.cpu().numpy(), ub.cpu().numpy())
+    assert 0.0 < d <= 1e-13, d
     g.close()
