@@ -549,10 +549,17 @@ def bench_channel(n=(192, 128, 192), steps=10, warmup=3):
         e1.record(st)
         torch.cuda.synchronize()
         vms = e0.elapsed_time(e1) / 3
+        g.profile(True)      # per-kernel durations of one more step VJP (a separate pass)
+        g.step_vjp(u, ybar, dt_dev=dt, ubar_n=ubar)
+        torch.cuda.synchronize()
+        vprof = g.profile_read()
+        g.profile(False)
         out[tag] = {"ms_per_step": ms, "value": cells / (ms / 1e3), "unit": UNIT, "arithmetic": arith,
                     "ms_per_vjp": vms, "adjoint_forward_ratio": vms / ms,
                     "kernels": {k: {"launches": v[0], "avg_us": round(v[1] / v[0] * 1e3, 2)}
                                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+        out[tag]["vjp_kernels"] = {k: {"launches": v[0], "avg_us": round(v[1] / v[0] * 1e3, 2)}
+                                   for k, v in sorted(vprof.items(), key=lambda kv: -kv[1][1])}
         if ms_native is not None:
             out[tag]["native_ms_per_step"] = ms_native
             out[tag]["adjoint_forward_ratio_vs_native_step"] = vms / ms_native

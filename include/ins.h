@@ -179,10 +179,10 @@ ins_status ins_set_step_fusion(ins_grid* g, int enable);
  * reduced from the FP64 result exactly as in native mode (bit-identical to the FP64 rule).
  * The step's relative field error against the FP64 oracle stays within the FP64 tolerance
  * (1e-12 per step). It is used by ins_step / ins_step_n (periodic grids: classic RK4 and
- * Wray3; 3-D channels: classic RK4 with the Thomas wall-normal solve) and, on 3-D periodic
- * grids, ins_step_vjp (the state cotangent accumulates in FP64), without an attached closure
- * or eddy-viscosity model; every other call (ins_rhs, ins_project, 2-D pullbacks, wall-bounded
- * pullbacks, Wray3 or the DCT solve on a channel, grids with a closure) runs native FP64.
+ * Wray3; 3-D channels: classic RK4 with the Thomas wall-normal solve) and ins_step_vjp (3-D
+ * periodic grids; 3-D channels with classic RK4; the state cotangent accumulates in FP64),
+ * without an attached closure or eddy-viscosity model; every other call (ins_rhs, ins_project,
+ * 2-D pullbacks, Wray3 or the DCT solve on a channel, grids with a closure) runs native FP64.
  * Supported grids: FP64, nx even, every periodic length a power of two from 16 to 256 or 48,
  * 96, 192, and either every direction periodic or a 3-D channel (walls in y, any ny);
  * elsewhere the setter returns INS_ERR_UNSUPPORTED and the grid stays native. INS_ERR_ARG for

@@ -16,6 +16,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace ins {
 
@@ -195,13 +196,17 @@ __device__ __forceinline__ void wall_adj_cell(const WallRowCoef<T>& R, int ny, T
         q[2] = a + nu * d;
         lpart = fma(w0, lap, lpart);
     }
-    nup += (double)lpart;
+    if constexpr (std::is_same<T, df>::value)
+        nup += df_to_double(lpart);
+    else
+        nup += (double)lpart;
 }
 
-// Accessor of wall_adj_cell on global memory (x, z wrap; the wall rules by row).
-template <typename T>
+// Accessor of wall_adj_cell on global memory (x, z wrap; the wall rules by row). US: the storage
+// type of u (the double-float pullback reads the FP64 step input and double-float stage states).
+template <typename T, typename US = T>
 struct GlobalWallAcc {
-    const T* uu;
+    const US* uu;
     const T* ww;
     int nx, ny, N, i, j, ip, im, k, kp, km;
     __device__ __forceinline__ int at(int di, int jj, int dk) const {
@@ -211,10 +216,10 @@ struct GlobalWallAcc {
     }
     __device__ __forceinline__ T u(int c, int di, int dj, int dk) const {
         const int jj = j + dj;
-        if (c == 1) return (jj < 0 || jj >= ny - 1) ? (T)0 : uu[N + at(di, jj, dk)];
-        if (jj < 0) return -uu[c * N + at(di, 0, dk)];
-        if (jj >= ny) return -uu[c * N + at(di, ny - 1, dk)];
-        return uu[c * N + at(di, jj, dk)];
+        if (c == 1) return (jj < 0 || jj >= ny - 1) ? (T)0 : cvt_in<T>(uu[N + at(di, jj, dk)]);
+        if (jj < 0) return -cvt_in<T>(uu[c * N + at(di, 0, dk)]);
+        if (jj >= ny) return -cvt_in<T>(uu[c * N + at(di, ny - 1, dk)]);
+        return cvt_in<T>(uu[c * N + at(di, jj, dk)]);
     }
     __device__ __forceinline__ T w(int c, int di, int dj, int dk) const {
         const int jj = j + dj;
@@ -232,17 +237,23 @@ struct WallAdjG {
     double bn, an;
 };
 
-// finish of one cell: ubar0 += q, kbar = dt (bn y + an q)
-template <typename T, int DIM>
+// finish of one cell: ubar0 += q, kbar = dt (bn y + an q). UB: the storage type of the state
+// cotangents (FP64 in the double-float pullback: q is added to ubar0 in FP64).
+template <typename T, int DIM, typename UB = T>
 __device__ __forceinline__ void wall_adj_finish(const WallAdjG<T>& c, int N, int P, const T (&q)[3],
-                                                const T* __restrict__ ybar, T* __restrict__ ubar0,
+                                                const UB* __restrict__ ybar, UB* __restrict__ ubar0,
                                                 T* __restrict__ kbar, T dtb, T dta) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         const int t = a * N + P;
-        const T old = ubar0[t];
-        ubar0[t] = old + q[a];
-        if (kbar) kbar[t] = fma(dtb, ybar ? ybar[t] : old, dta * q[a]);
+        const UB old = ubar0[t];
+        if constexpr (std::is_same<T, UB>::value) {
+            ubar0[t] = old + q[a];
+            if (kbar) kbar[t] = fma(dtb, ybar ? ybar[t] : old, dta * q[a]);
+        } else {
+            ubar0[t] = old + df_to_double(q[a]);
+            if (kbar) kbar[t] = fma(dtb, cvt_in<T>(ybar ? ybar[t] : old), dta * q[a]);
+        }
     }
 }
 
@@ -260,10 +271,12 @@ __device__ __forceinline__ void block_partial(double nup, double* __restrict__ n
 
 // One thread per cell, neighbours from global memory (2-D grids and FP64). Block (32, 8),
 // grid (ceil(nx/32), ceil(ny/8), nz).
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_adj_rhs_wall_g(WallAdjG<T> c, const T* __restrict__ u,
-                                                        const T* __restrict__ w, const T* __restrict__ ybar,
-                                                        T* __restrict__ ubar0, T* __restrict__ kbar,
+// US, UB: storage types of u and of the state cotangents (the double-float pullback of an FP64
+// channel: T = df, u FP64 in the first stage and double-float after it, ybar and ubar0 FP64).
+template <typename T, int DIM, typename US = T, typename UB = T>
+__global__ void __launch_bounds__(256) k_adj_rhs_wall_g(WallAdjG<T> c, const US* __restrict__ u,
+                                                        const T* __restrict__ w, const UB* __restrict__ ybar,
+                                                        UB* __restrict__ ubar0, T* __restrict__ kbar,
                                                         double* __restrict__ nu_part) {
     const Geo<T>& G = c.g;
     const int nx = G.nx, ny = G.ny, nz = G.nz;
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(256) k_adj_rhs_wall_g(WallAdjG<T> c, const T* 
     const int k = blockIdx.z;
     double nup = 0.0;
     if (i < nx && j < ny) {
-        GlobalWallAcc<T> A;
+        GlobalWallAcc<T, US> A;
         A.uu = u;
         A.ww = w;
         A.nx = nx;
@@ -289,7 +302,8 @@ __global__ void __launch_bounds__(256) k_adj_rhs_wall_g(WallAdjG<T> c, const T* 
         T q[3];
         wall_adj_cell<T, DIM>(wall_row_coef<T, DIM>(G, i, j), ny, c.nu, j, A, q, nup);
         const double dt = c.dt_dev ? *c.dt_dev : c.dt_host;
-        wall_adj_finish<T, DIM>(c, N, (k * ny + j) * nx + i, q, ybar, ubar0, kbar, (T)(dt * c.bn), (T)(dt * c.an));
+        wall_adj_finish<T, DIM, UB>(c, N, (k * ny + j) * nx + i, q, ybar, ubar0, kbar, cvt_in<T>(dt * c.bn),
+                                    cvt_in<T>(dt * c.an));
     }
     block_partial(nup, nu_part);
 }
@@ -319,13 +333,15 @@ struct SharedWallAcc {
 };
 
 // UIN: the accumulator's previous value comes from uin (the first stage of the pullback reads
-// ybar there); otherwise from ubar0 itself (uin unused).
-template <typename T, bool UIN = false>
-__global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const T* __restrict__ u,
-                                                        const T* __restrict__ w, const T* __restrict__ ybar,
-                                                        T* __restrict__ ubar0, T* __restrict__ kbar,
+// ybar there); otherwise from ubar0 itself (uin unused). US, UB: storage types of u and of the
+// state cotangents (the double-float pullback of an FP64 channel: T = df, u FP64 in the first stage
+// and double-float after it, ybar and ubar0 FP64 with q added in FP64).
+template <typename T, bool UIN = false, typename US = T, typename UB = T>
+__global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const US* __restrict__ u,
+                                                        const T* __restrict__ w, const UB* __restrict__ ybar,
+                                                        UB* __restrict__ ubar0, T* __restrict__ kbar,
                                                         double* __restrict__ nu_part, int kchunk,
-                                                        const T* __restrict__ uin) {
+                                                        const UB* __restrict__ uin) {
     extern __shared__ __align__(16) unsigned char wz_smem[];
     T* const ring = reinterpret_cast<T*>(wz_smem);
     const Geo<T>& G = c.g;
@@ -372,9 +388,9 @@ __global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const 
             const int a = base + off[e], gj = gjr[e];
             const bool in = gj >= 0 && gj < ny, top = gj >= ny - 1;
             const T sg = in ? (T)1 : (T)-1;   // odd ghost of u^x, u^z beyond a wall
-            v[e][0] = sg * u[a];
-            v[e][1] = (in && !top) ? u[N + a] : (T)0;
-            v[e][2] = sg * u[2 * N + a];
+            v[e][0] = sg * cvt_in<T>(u[a]);
+            v[e][1] = (in && !top) ? cvt_in<T>(u[N + a]) : (T)0;
+            v[e][2] = sg * cvt_in<T>(u[2 * N + a]);
             v[e][3] = in ? w[a] : (T)0;
             v[e][4] = (in && !top) ? w[N + a] : (T)0;
             v[e][5] = in ? w[2 * N + a] : (T)0;
@@ -395,7 +411,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const 
     }
     __syncthreads();
     const double dt = c.dt_dev ? *c.dt_dev : c.dt_host;
-    const T dtb = (T)(dt * c.bn), dta = (T)(dt * c.an);
+    const T dtb = cvt_in<T>(dt * c.bn), dta = cvt_in<T>(dt * c.an);
     double nup = 0.0;
     SharedWallAcc<T> A;
     A.s = ring;
@@ -407,7 +423,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const 
         if (own) {
             // the finish's own-cell values first, so their loads overlap the stencil arithmetic
             const int P = (k * ny + j) * nx + i;
-            T old[3], yv[3];
+            UB old[3], yv[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 old[a] = UIN ? uin[a * N + P] : ubar0[a * N + P];   // the accumulator's previous value
@@ -420,8 +436,13 @@ __global__ void __launch_bounds__(256, 2) k_adj_rhs_wall_z(WallAdjG<T> c, const 
             wall_adj_cell<T, 3>(rc, ny, c.nu, j, A, q, nup);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                ubar0[a * N + P] = old[a] + q[a];
-                if (kbar) kbar[a * N + P] = fma(dtb, yv[a], dta * q[a]);
+                if constexpr (std::is_same<T, UB>::value) {
+                    ubar0[a * N + P] = old[a] + q[a];
+                    if (kbar) kbar[a * N + P] = fma(dtb, yv[a], dta * q[a]);
+                } else {
+                    ubar0[a * N + P] = old[a] + df_to_double(q[a]);
+                    if (kbar) kbar[a * N + P] = fma(dtb, cvt_in<T>(yv[a]), dta * q[a]);
+                }
             }
         }
         if (more) store(k + 2);
@@ -468,7 +489,7 @@ __global__ void k_wall_sub_scaled(Geo<T> g, const T* __restrict__ kb, const T* _
     const int k = blockIdx.z;
     if (i >= nx || j >= ny) return;
     const long a = ((long)k * ny + j) * nx + i;
-    const T idy = g.coef(1, C_INV_D, j), sd = (T)dy[j];
+    const T idy = g.coef(1, C_INV_D, j), sd = cvt_in<T>(dy[j]);
     const T p0 = p[a];
     const T pe = p[a - i + (i + 1 == nx ? 0 : i + 1)];
     w[a] = (kb[a] * idy - (pe - p0) * g.coef(0, C_INV_H, i)) * sd;
@@ -476,7 +497,7 @@ __global__ void k_wall_sub_scaled(Geo<T> g, const T* __restrict__ kb, const T* _
         w[N + a] = (T)0;
     } else {
         const T pn = p[a + nx];
-        w[N + a] = (kb[N + a] * g.coef(1, C_INV_H, j) - (pn - p0) * g.coef(1, C_INV_H, j)) * (T)hy[j];
+        w[N + a] = (kb[N + a] * g.coef(1, C_INV_H, j) - (pn - p0) * g.coef(1, C_INV_H, j)) * cvt_in<T>(hy[j]);
     }
     if (DIM == 3) {
         const long plane = (long)nx * ny;

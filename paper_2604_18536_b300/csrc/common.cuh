@@ -54,6 +54,10 @@ enum Coef {
     C_COUNT
 };
 
+// read-only loads of coefficient tables (a double-float overload sits with that type)
+__device__ __forceinline__ float geo_ldg(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double geo_ldg(const double* p) { return __ldg(p); }
+
 template <typename T>
 struct Geo {
     int nx, ny, nz;          // nz = 1 in 2-D
@@ -62,7 +66,7 @@ struct Geo {
     T fx, fy, fz;            // body force
     __device__ __forceinline__ T coef(int a, int m, int i) const {
         int n = a == 0 ? nx : (a == 1 ? ny : nz);
-        return __ldg(c[a] + (size_t)m * n + i);
+        return geo_ldg(c[a] + (size_t)m * n + i);
     }
 };
 

@@ -160,6 +160,7 @@ __device__ __forceinline__ df ldg_t(const df* p) {
 }
 __device__ __forceinline__ double ldg_t(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ldg_t(const float* p) { return __ldg(p); }
+__device__ __forceinline__ df geo_ldg(const df* p) { return ldg_t(p); }
 __device__ __forceinline__ cplx<df> ldg_c(const cplx<df>* p) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
     return {df(v.x, v.y), df(v.z, v.w)};

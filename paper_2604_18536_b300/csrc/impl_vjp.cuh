@@ -145,6 +145,110 @@ ins_status Impl<T, DIM, WALL>::step_vjp_wall(ins_grid* g, const T* un, const dou
     return INS_OK;
 }
 
+// Pullback of one classic RK4 step of an FP64 3-D channel in double-float arithmetic (the
+// counterpart of the double-float channel step): the stage states are recomputed by the
+// double-float step kernels, P^T = M Omega P Omega^-1 M runs the row-scaled passes and the Poisson
+// solve in double-float, and J_F^T (k_adj_rhs_wall_g<df, ...>) in double-float, while the state
+// cotangent ubar accumulates in FP64 and the nu partials are reduced in FP64. The stored top wall
+// faces of u^y are not unknowns (cotangents there are ignored and returned as 0).
+inline ins_status step_vjp_wall_df(ins_grid* g, const double* un, const double* dt_dev, double dt_host,
+                                   const double* ybar, double* ubar, double* nubar) {
+    if (3 * g->N >= (1L << 31)) return fail(INS_ERR_UNSUPPORTED, "ins_step_vjp: wall grids need 3 x cells < 2^31");
+    static const double A[3] = {0.5, 0.5, 1.0};
+    static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const long N = g->N;
+    const size_t fld = (size_t)3 * N * sizeof(double);
+    const size_t fa = (fld + 255) & ~size_t(255);
+    const dim3 cg = cell_grid(g);
+    const long nblk = (long)cg.x * cg.y * cg.z;
+    const size_t need = 4 * fa + (size_t)nblk * 8;
+    if (g->vjp_bytes < need) {
+        if (g->vjp) cudaFree(g->vjp);
+        g->vjp = nullptr;
+        g->vjp_bytes = 0;
+        cudaError_t e = cudaMalloc(&g->vjp, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(INS_ERR_OOM, std::string("step-VJP workspace: ") + cudaGetErrorString(e));
+        }
+        g->vjp_bytes = need;
+    }
+    char* vb = reinterpret_cast<char*>(g->vjp);
+    df* U[4] = {nullptr, reinterpret_cast<df*>(vb), reinterpret_cast<df*>(vb + fa), reinterpret_cast<df*>(vb + 2 * fa)};
+    df* W = reinterpret_cast<df*>(vb + 3 * fa);
+    double* part = reinterpret_cast<double*>(vb + 4 * fa);
+    df* F = reinterpret_cast<df*>(g->F);
+    df* rp = reinterpret_cast<df*>(g->rp);
+    ins_status s;
+    // stage states u_1 .. u_3 (u_{s+1} = u_n + dt a_s k_s, no accumulator)
+    for (int st = 0; st < 3; ++st) {
+        s = st == 0 ? launch_rhs_div_df<3, double, true>(g, un, F, rp) : launch_rhs_div_df<3, df, true>(g, U[st], F, rp);
+        if (s != INS_OK) return s;
+        if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
+        RkArgs ra;
+        ra.dt_dev = dt_dev;
+        ra.dt_host = dt_host;
+        ra.mx = nullptr;
+        ra.err_flag = g->err_flag;
+        ra.last = 0;
+        ra.a_next = A[st];
+        ra.b = 0.0;
+        ra.stage = 0;
+        if ((s = rk_update_df<3, false, true>(g, F, rp, const_cast<double*>(un), nullptr, U[st + 1], ra)) != INS_OK)
+            return s;
+    }
+    const long n = 3 * N;
+    const double* hy = g->geo64 + g->nx;
+    const double* dy = g->geo64 + (g->nx + g->ny + g->nz) + g->nx;
+    INS_CUDA(cudaMemcpyAsync(ubar, ybar, fld, cudaMemcpyDeviceToDevice, g->stream));
+    KLAUNCH(g, "scale", (k_scale_dt<df, double><<<1184, 256, 0, g->stream>>>(ybar, F, dt_dev, dt_host, B[3], n)));
+    const Geo<df> geo = make_geo<df>(g);
+    // the adjoint stencil as a z march (shared-memory ring of u and w), about two waves of two CTAs
+    // per SM; the chunk from the wave count
+    const long cols = (long)cg.x * cg.y;
+    const long nch = std::max(1L, std::min((long)g->nz, (4L * device_sm_count() + cols / 2) / cols));
+    const int zkc = (int)((g->nz + nch - 1) / nch);
+    const dim3 zg(cg.x, cg.y, (g->nz + zkc - 1) / zkc);
+    const long znblk = (long)zg.x * zg.y * zg.z;
+    {
+        static bool attr[64] = {};
+        int dev = 0;
+        INS_CUDA(cudaGetDevice(&dev));
+        if (dev >= 0 && dev < 64 && !attr[dev]) {
+            INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_wall_z<df, false, double, double>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, wall_adj_smem<df>()));
+            INS_CUDA(cudaFuncSetAttribute(k_adj_rhs_wall_z<df, false, df, double>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, wall_adj_smem<df>()));
+            attr[dev] = true;
+        }
+    }
+    WallAdjG<df> wa;
+    wa.g = geo;
+    wa.nu = df(g->nu);
+    wa.dt_dev = dt_dev;
+    wa.dt_host = dt_host;
+    for (int st = 3; st >= 0; --st) {
+        // w = P^T kbar = M Omega P (Omega^-1 M kbar)
+        KLAUNCH(g, "divergence", (k_wall_div_scaled<df, 3><<<cg, dim3(32, 8), 0, g->stream>>>(geo, F, rp)));
+        if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
+        KLAUNCH(g, "sub_grad", (k_wall_sub_scaled<df, 3><<<cg, dim3(32, 8), 0, g->stream>>>(geo, F, rp, W, hy, dy)));
+        wa.bn = st > 0 ? B[st - 1] : 0.0;
+        wa.an = st > 0 ? A[st - 1] : 0.0;
+        // ubar += J_F^T w (FP64 accumulation); the next stage cotangent into F
+        if (st == 0)
+            KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_z<df, false, double, double><<<zg, dim3(32, 8), wall_adj_smem<df>(),
+                                                                              g->stream>>>(
+                                      wa, un, W, ybar, ubar, nullptr, part, zkc, nullptr)));
+        else
+            KLAUNCH(g, "adj_rhs", (k_adj_rhs_wall_z<df, false, df, double><<<zg, dim3(32, 8), wall_adj_smem<df>(),
+                                                                          g->stream>>>(
+                                      wa, U[st], W, ybar, ubar, F, part, zkc, nullptr)));
+        if (nubar) KLAUNCH(g, "sum_partials", k_sum_partials<<<1, 256, 0, g->stream>>>(part, znblk, nubar));
+    }
+    KLAUNCH(g, "mask_top", k_mask_top<double><<<592, 256, 0, g->stream>>>(ubar, g->nx, g->ny, g->nz, N));
+    return INS_OK;
+}
+
 // Pullback of one step (classic RK4 or Wray's low-storage RK3) of an FP64 periodic 3-D grid in
 // double-float arithmetic (the counterpart of the double-float step, ins_set_f64_arithmetic): the
 // stage states are recomputed by the double-float step kernels, P^T = P runs the double-float Poisson
@@ -275,6 +379,11 @@ inline ins_status step_vjp_df(ins_grid* g, const double* un, const double* dt_de
 
 template <typename T, int DIM, bool WALL>
 ins_status Impl<T, DIM, WALL>::step_vjp(ins_grid* g, const T* un, const double* dt_dev, double dt_host, const T* ybar, T* ubar, double* nubar) {
+    if constexpr (WALL && DIM == 3 && std::is_same<T, double>::value) {
+        if (g->use_df && !g->closure && !g->eddy && !g->use_dct && g->scheme == INS_RK4 &&
+            reinterpret_cast<uintptr_t>(un) % 16 == 0)
+            return step_vjp_wall_df(g, un, dt_dev, dt_host, ybar, ubar, nubar);
+    }
     if constexpr (WALL) return step_vjp_wall(g, un, dt_dev, dt_host, ybar, ubar, nubar);
     if constexpr (std::is_same<T, double>::value && DIM == 3 && !WALL) {
         if (g->use_df && !g->closure && !g->eddy && reinterpret_cast<uintptr_t>(un) % 16 == 0)

@@ -126,6 +126,9 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     const size_t nsum = (size_t)g->nx + g->ny + g->nz;
     o_coef = off; off += al((size_t)C_COUNT * nsum * ts);
     const size_t o_ycoef = off; off += al((size_t)CY_COUNT * g->ny * ts);
+    // double-float copy of the coefficients: the double-float pullback of an FP64 channel
+    const bool coef_df = D.dtype == INS_F64 && wall_y && dim == 3;
+    const size_t o_coefdf = off; off += coef_df ? al((size_t)C_COUNT * nsum * 8) : 0;
     o_geo = off; off += al(2 * nsum * 8);
     o_one = off; off += al(8);
     for (int a = 0; a < 3; ++a) {
@@ -182,6 +185,7 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     char* b = reinterpret_cast<char*>(g->base);
     g->coef = b + o_coef;
     g->ycoef = b + o_ycoef;
+    g->coef_df = coef_df ? b + o_coefdf : nullptr;
     g->geo64 = reinterpret_cast<double*>(b + o_geo);
     g->one = reinterpret_cast<double*>(b + o_one);
     for (int a = 0; a < 3; ++a) g->tw[a] = b + o_tw[a];
@@ -222,6 +226,14 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
         std::vector<double> c;
         fill_coefs<double>(g, c);
         ok &= up(g->coef, c.data(), c.size() * 8);
+        if (g->coef_df) {
+            std::vector<float> cd(2 * c.size());
+            for (size_t q = 0; q < c.size(); ++q) {
+                cd[2 * q] = (float)c[q];
+                cd[2 * q + 1] = (float)(c[q] - (double)cd[2 * q]);
+            }
+            ok &= up(g->coef_df, cd.data(), cd.size() * 4);
+        }
     } else {
         std::vector<float> c;
         fill_coefs<float>(g, c);

@@ -105,6 +105,7 @@ struct ins_grid {
     void* base = nullptr;
     size_t bytes = 0;
     void* coef = nullptr;          // T[3][C_COUNT][n_a] (per direction contiguous)
+    void* coef_df = nullptr;       // the same as double-float pairs (FP64 channels with double-float arithmetic)
     void* ycoef = nullptr;         // T[CY_COUNT][ny]: per-row coefficients of a stretched wall direction
     double* geo64 = nullptr;       // h_x h_y h_z | d_x d_y d_z  (nx+ny+nz each)
     double* one = nullptr;         // a device 1.0 (divisor of an already divided maximum)
@@ -208,7 +209,7 @@ Geo<T> make_geo(const ins_grid* g) {
     G.ny = g->ny;
     G.nz = g->nz;
     G.wall_y = g->wall_y;
-    const T* c = reinterpret_cast<const T*>(g->coef);
+    const T* c = reinterpret_cast<const T*>(std::is_same<T, df>::value ? g->coef_df : g->coef);
     G.c[0] = c;
     G.c[1] = c + (size_t)C_COUNT * g->nx;
     G.c[2] = c + (size_t)C_COUNT * (g->nx + g->ny);

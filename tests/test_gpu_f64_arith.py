@@ -283,3 +283,47 @@ def test_channel_double_float_differs_from_native_only_at_rounding_level():
     d = rel(ua.cpu().numpy(), ub.cpu().numpy())
     assert 0.0 < d <= 1e-13, d
     g.close()
+
+
+@pytest.mark.parametrize("mode", ["double-float", "native"])
+@pytest.mark.parametrize("name", list(CH_CASES))
+def test_channel_step_vjp_matches_oracle(name, mode):
+    """The channel step pullback in double-float arithmetic: ubar within 1e-12 of the oracle's (the
+    stored top wall faces of u^y returned as 0), nubar within 5e-11 relative."""
+    from oracle import adjoint
+    og, g, u0 = make_channel(name, 24)
+    g.set_f64_arithmetic(mode)
+    ybar = inputs.random_field((3,) + og.shape, 124)
+    ybar[1][:, -1, :] = 0.0                  # the top wall faces of u^y are no unknowns
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    ub, nb = g.step_vjp(dev(u0), dev(ybar), dt=dt)
+    ub_o, nb_o = adjoint.rk4_step_vjp(og, u0, dt, ybar)
+    ub = ub.cpu().numpy()
+    assert rel(ub, ub_o) <= 1e-12, (mode, rel(ub, ub_o))
+    assert abs(nb.item() - nb_o) <= 5e-11 * abs(nb_o)
+    assert np.all(ub[1][:, -1, :] == 0.0)
+    g.close()
+
+
+def test_channel_step_vjp_central_differences_double_float():
+    """<ubar, v> against central differences of the double-float channel step (eps = 1e-6). The
+    directions v keep the stored top wall faces of u^y at 0: they are no unknowns, and the pullback
+    returns 0 there."""
+    og, g, u0 = make_channel("c3df", 25)
+    c = inputs.random_field((3,) + og.shape, 125)
+    c[1][:, -1, :] = 0.0
+    dt = 0.5 * timestep.cfl_dt(og, u0, 0.3)
+    ub = g.step_vjp(dev(u0), dev(c), dt=dt)[0].cpu().numpy()
+    eps = 1e-6
+
+    def L(u):
+        t = dev(u)
+        g.step(t, dt=dt)
+        return float(np.sum(c * t.cpu().numpy()))
+
+    for seed in range(3):
+        v, _ = poisson.project(og, inputs.random_field(u0.shape, 225 + seed))
+        v[1][:, -1, :] = 0.0
+        fd = (L(u0 + eps * v) - L(u0 - eps * v)) / (2 * eps)
+        assert abs(fd - np.sum(ub * v)) <= 1e-7 * max(1.0, abs(fd))
+    g.close()
