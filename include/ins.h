@@ -183,10 +183,9 @@ ins_status ins_set_step_fusion(ins_grid* g, int enable);
  * periodic grids; 3-D channels with classic RK4; the state cotangent accumulates in FP64),
  * without an attached closure or eddy-viscosity model; every other call (ins_rhs, ins_project,
  * 2-D pullbacks, Wray3 or the DCT solve on a channel, grids with a closure) runs native FP64.
- * Supported grids: FP64, nx even, every periodic length a power of two from 16 to 256 or 48,
- * 96, 192, and either every direction periodic or a 3-D channel (walls in y, any ny);
- * elsewhere the setter returns INS_ERR_UNSUPPORTED and the grid stays native. INS_ERR_ARG for
- * other modes. */
+ * Supported grids: FP64, nx even, and either every direction periodic or a 3-D channel
+ * (walls in y); elsewhere the setter returns INS_ERR_UNSUPPORTED and the grid stays native.
+ * INS_ERR_ARG for other modes. */
 typedef enum { INS_ARITH_NATIVE = 0, INS_ARITH_DOUBLE_FLOAT = 1 } ins_arith;
 ins_status ins_set_f64_arithmetic(ins_grid* g, int mode);
 ins_status ins_get_f64_arithmetic(const ins_grid* g, int* mode);

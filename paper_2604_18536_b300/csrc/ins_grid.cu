@@ -140,11 +140,10 @@ ins_status ins_grid_create(const ins_grid_desc* desc, void* stream, ins_grid** o
     // FP32 periodic: [columns of the fused pass | its line | 1/N] (3-D: ny nxh | nz; 2-D: nxh | ny)
     const size_t neig = (!wall_y && D.dtype == INS_F32) ? (size_t)(dim == 3 ? g->ny * nxh + g->nz : nxh + g->ny) + 1 : 0;
     const size_t o_eig = off; off += al(neig * 4);
-    // double-float FP64 step: FP64 grids whose periodic lengths all have register FFT kernels (x
-    // even for the two-cell update): periodic grids, and 3-D channels (walls in y, any ny: the
-    // wall-normal direction is solved by the Thomas sweep)
-    bool df_ok = D.dtype == INS_F64 && (!wall_y || dim == 3) && g->nx % 2 == 0;
-    for (int a = 0; a < dim; ++a) df_ok = df_ok && (reg_fft_len(n3[a]) || (a == 1 && wall_y));
+    // double-float FP64 step: FP64 periodic grids and 3-D channels (walls in y: the wall-normal
+    // direction is solved by the Thomas sweep), x even for the two-cell update; the periodic FFT
+    // lengths run the register kernels where they have them, else the Stockham kernels
+    const bool df_ok = D.dtype == INS_F64 && (!wall_y || dim == 3) && g->nx % 2 == 0;
     size_t o_twdf[3] = {0, 0, 0}, o_scdf = 0;
     if (df_ok) {
         for (int a = 0; a < 3; ++a) {
@@ -477,7 +476,7 @@ ins_status ins_set_f64_arithmetic(ins_grid* g, int mode) {
     if (mode == INS_ARITH_DOUBLE_FLOAT && !g->df_ok)
         return fail(INS_ERR_UNSUPPORTED,
                     "double-float arithmetic needs an FP64 grid, periodic or a 3-D channel with walls in y, with "
-                    "even nx and periodic lengths 16..256 (powers of two), 48, 96 or 192");
+                    "even nx");
     g->use_df = mode == INS_ARITH_DOUBLE_FLOAT ? 1 : 0;
     return INS_OK;
 }

@@ -409,27 +409,27 @@ ins_status set_smem_attrs() {
     INS_CUDA(cudaFuncSetAttribute(k_fft_x_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     INS_CUDA(cudaFuncSetAttribute(k_fft_x_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     INS_CUDA(cudaFuncSetAttribute(k_fft_strided<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    INS_CUDA(cudaFuncSetAttribute(k_dct_solve_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    if constexpr (!std::is_same<T, df>::value)
+        INS_CUDA(cudaFuncSetAttribute(k_dct_solve_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     if (dev >= 0 && dev < 64) done[dev] = true;
     return INS_OK;
 }
 
-// T = df (the double-float FP64 step): register kernels for every length (the grid supports
-// double-float arithmetic only when all lengths have them), its own twiddles and spectral table.
+// T = df (the double-float FP64 step): the register kernels for their lengths (16 .. 256 powers of
+// two, 48, 96, 192), the shared-memory Stockham kernels for the other lengths, with the grid's
+// double-float twiddles and spectral table.
 template <typename T>
 ins_status poisson(ins_grid* g, const T* r, T* p) {
     constexpr bool DF = std::is_same<T, df>::value;
-    if constexpr (!DF) {
-        if (ins_status s0 = set_smem_attrs<T>(); s0 != INS_OK) return s0;
-    }
+    if (ins_status s0 = set_smem_attrs<T>(); s0 != INS_OK) return s0;
     cudaStream_t st = g->stream;
     const int nx = g->nx, ny = g->ny, nz = g->nz, nxh = g->nxh;
     const long lines = (long)ny * nz;
     cplx<T>* S = reinterpret_cast<cplx<T>*>(g->S);
     FftLine<T> lx = make_line<T>(g, 0);
-    if (DF || reg_fft_len(nx, sizeof(T) == 8)) {
+    if (reg_fft_len(nx, sizeof(T) == 8 && !DF)) {
         KLAUNCH(g, "fft_x_r2c", x_reg<T>(nx, true, st, lx.tw, r, S, nullptr, (int)lines, nxh));
-    } else if constexpr (!DF) {
+    } else {
         const int lg = g->lg_tw_x;
         const long pairs = (lines + 1) / 2;
         const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);
@@ -450,18 +450,16 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
             outer = 0;
             lstride = (long)ny * nxh;
         }
-        if (DF || reg_fft_len(pl.L)) {
+        if (reg_fft_len(pl.L)) {
             // FP32: the fused pass forms its scale from the eigenvalue sums (no table read)
             const T* sc = sizeof(T) == 4 ? reinterpret_cast<const T*>(g->eig)
                                          : reinterpret_cast<const T*>(DF ? g->scale_df : g->scale);
             KLAUNCH(g, "fft_strided", strided_reg<T>(pl.L, st, pl.tw, S, ncol, cdiv, outer, lstride, mode, sc));
             return INS_OK;
         }
-        if constexpr (!DF) {
-            const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
-            KLAUNCH(g, "fft_strided", k_fft_strided<T><<<blocks, FFT_THREADS, fft_smem<T>(pl.L, lg), st>>>(
-                pl, S, ncol, cdiv, outer, lstride, mode, reinterpret_cast<const T*>(g->scale), lg));
-        }
+        const unsigned blocks = (unsigned)((ncol + (1 << lg) - 1) >> lg);
+        KLAUNCH(g, "fft_strided", k_fft_strided<T><<<blocks, FFT_THREADS, fft_smem<T>(pl.L, lg), st>>>(
+            pl, S, ncol, cdiv, outer, lstride, mode, reinterpret_cast<const T*>(DF ? g->scale_df : g->scale), lg));
         return INS_OK;
     };
     ins_status s;
@@ -499,9 +497,9 @@ ins_status poisson(ins_grid* g, const T* r, T* p) {
         }
         if (g->dim == 3 && (s = strided(2, 1)) != INS_OK) return s;
     }
-    if (DF || reg_fft_len(nx, sizeof(T) == 8)) {
+    if (reg_fft_len(nx, sizeof(T) == 8 && !DF)) {
         KLAUNCH(g, "fft_x_c2r", x_reg<T>(nx, false, st, lx.tw, nullptr, S, p, (int)lines, nxh));
-    } else if constexpr (!DF) {
+    } else {
         const int lg = g->lg_tw_x;
         const long pairs = (lines + 1) / 2;
         const unsigned blocks = (unsigned)((pairs + (1 << lg) - 1) >> lg);

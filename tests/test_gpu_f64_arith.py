@@ -4,8 +4,9 @@ Double-float keeps F, the Poisson FFTs and the stage updates on the FP32 pipe wi
 significant bits; storage, the final update of the caller's field and the CFL rule stay FP64.
 It must meet the FP64 tolerances of the native path: relative field error <= 1e-12 per step and
 <= 1e-10 after 100 steps against the oracle, the next CFL time step bit for bit, and graph
-replay (ins_step_n) bit-identical to plain steps. Grids whose FFT lengths have no register
-kernel keep native FP64 and refuse the setting.
+replay (ins_step_n) bit-identical to plain steps. FFT lengths without register kernels run the
+shared-memory Stockham passes in double-float; grids with odd nx keep native FP64 and refuse
+the setting.
 """
 
 import numpy as np
@@ -31,6 +32,9 @@ CASES = {
     # y and z lines of 256 in the strided passes (64 in p3reg and p2pow)
     "p3r4y": ([U(16, 0, 2 * PI), U(256, 0, 2 * PI), U(16, 0, 1.0)], 0.02),
     "p3r4z": ([U(32, 0, 2 * PI), U(16, 0, 1.0), U(256, 0, 3.0)], 0.02),
+    # lengths without register kernels: the shared-memory Stockham passes in double-float
+    "p3stock": ([U(40, 0, 2 * PI), U(24, 0, 1.5 * PI), U(36, 0, 3.0)], 0.02),
+    "p3stock7": ([U(14, 0, 2 * PI), U(20, 0, 1.5 * PI), U(42, 0, 3.0)], 0.02),
 }
 
 
@@ -92,7 +96,7 @@ def test_double_float_differs_from_native_only_at_rounding_level():
     g.close()
 
 
-@pytest.mark.parametrize("name", ["p3reg", "p2pow", "p3r4z"])
+@pytest.mark.parametrize("name", ["p3reg", "p2pow", "p3r4z", "p3stock"])
 def test_100_steps(name):
     """<= 1e-10 after 100 steps against the oracle (fixed dt)."""
     og, g, u0 = make(name, seed=4)
@@ -117,17 +121,13 @@ def test_graph_replay_is_bit_identical():
 
 
 def test_unsupported_grids_stay_native():
-    faces = [U(40, 0, 2 * PI), U(24, 0, 1.5 * PI), U(36, 0, 3.0)]    # no register FFT for 40, 24, 36
+    faces = [U(45, 0, 2 * PI), U(24, 0, 1.5 * PI), U(36, 0, 3.0)]    # odd nx (the two-cell update)
     g = Grid(faces, ["periodic"] * 3, 0.02, dtype=torch.float64)
     assert g.f64_arithmetic() == "native"
     with pytest.raises(InsError) as e:
         g.set_f64_arithmetic("double-float")
     assert e.value.status == INS_ERR_UNSUPPORTED
     g.close()
-    ch = Grid(inputs.channel_faces(40, 16, 16), ["periodic", "wall", "periodic"], 1 / 180, [1.0, 0, 0],
-              dtype=torch.float64)                                         # no register FFT for x = 40
-    assert ch.f64_arithmetic() == "native"
-    ch.close()
     c2 = Grid([U(32, 0, 4 * PI), inputs.tanh_faces(12, 0, 2, 1.5)], ["periodic", "wall"], 0.05, [1.0, 0],
               dtype=torch.float64)                                         # 2-D channels stay native
     assert c2.f64_arithmetic() == "native"
@@ -166,7 +166,7 @@ def test_non_finite_flag_and_wray3():
 
 
 @pytest.mark.parametrize("mode", ["double-float", "native"])
-@pytest.mark.parametrize("name", ["p3reg", "p3r12", "p3ragged", "p3r4y", "p3r4z"])
+@pytest.mark.parametrize("name", ["p3reg", "p3r12", "p3ragged", "p3r4y", "p3r4z", "p3stock"])
 def test_step_vjp_matches_oracle(name, mode):
     """The step pullback in double-float arithmetic (3-D grids): ubar within 1e-12 of the oracle's,
     nubar within 5e-11 relative."""
@@ -228,6 +228,7 @@ CHB = ["periodic", "wall", "periodic"]
 CH_CASES = {
     "c3df": [U(64, 0, 4 * PI), inputs.tanh_faces(20, 0, 2, 1.5), U(32, 0, 4 * PI / 3)],
     "c3dfodd": [U(96, 0, 4 * PI), inputs.tanh_faces(15, 0, 2, 1.5), U(16, 0, 4 * PI / 3)],
+    "c3dfstock": [U(40, 0, 4 * PI), inputs.tanh_faces(12, 0, 2, 1.5), U(20, 0, 4 * PI / 3)],   # Stockham x, z
 }
 
 
