@@ -178,11 +178,11 @@ ins_status ins_set_step_fusion(ins_grid* g, int enable);
  * FP64, the last stage adds the step's increment to it in FP64, and the CFL time step is
  * reduced from the FP64 result exactly as in native mode (bit-identical to the FP64 rule).
  * The step's relative field error against the FP64 oracle stays within the FP64 tolerance
- * (1e-12 per step). It is used by ins_step / ins_step_n (periodic grids: classic RK4 and
- * Wray3; 3-D channels: classic RK4 with the Thomas wall-normal solve) and ins_step_vjp (3-D
- * periodic grids; 3-D channels with classic RK4; the state cotangent accumulates in FP64),
- * without an attached closure or eddy-viscosity model; every other call (ins_rhs, ins_project,
- * 2-D pullbacks, Wray3 or the DCT solve on a channel, grids with a closure) runs native FP64.
+ * (1e-12 per step). It is used by ins_step / ins_step_n (classic RK4 and Wray3; on 3-D
+ * channels with the Thomas wall-normal solve) and ins_step_vjp (3-D periodic grids; 3-D
+ * channels with classic RK4; the state cotangent accumulates in FP64), without an attached
+ * closure or eddy-viscosity model; every other call (ins_rhs, ins_project, 2-D pullbacks, the
+ * Wray3 pullback or the DCT solve on a channel, grids with a closure) runs native FP64.
  * Supported grids: FP64, nx even, and either every direction periodic or a 3-D channel
  * (walls in y); elsewhere the setter returns INS_ERR_UNSUPPORTED and the grid stays native.
  * INS_ERR_ARG for other modes. */

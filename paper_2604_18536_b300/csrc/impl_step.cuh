@@ -95,16 +95,16 @@ ins_status Impl<T, DIM, WALL>::step_fused(ins_grid* g, T* u, const double* dt_de
 }
 
 // ------------------------------------------------------------ double-float FP64 step
-// Wray's low-storage RK3 on an FP64 periodic grid in double-float arithmetic: u (FP64) is updated in
-// place each stage (the stage's increment added in FP64), k_{s-1} kept as double-float pairs.
-template <int DIM>
+// Wray's low-storage RK3 on an FP64 grid in double-float arithmetic: u (FP64) is updated in place each
+// stage (the stage's increment added in FP64), k_{s-1} kept as double-float pairs. WALL: 3-D channels.
+template <int DIM, bool WALL = false>
 ins_status step_wray3_df(ins_grid* g, double* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
     df* F = reinterpret_cast<df*>(g->F);
     df* rp = reinterpret_cast<df*>(g->rp);
     df* kprev = reinterpret_cast<df*>(g->acc);
     ins_status s;
     for (int st = 0; st < 3; ++st) {
-        if ((s = launch_rhs_div_df<DIM, double>(g, u, F, rp)) != INS_OK) return s;
+        if ((s = launch_rhs_div_df<DIM, double, WALL>(g, u, F, rp)) != INS_OK) return s;
         if ((s = poisson<df>(g, rp, rp)) != INS_OK) return s;
         RkArgs ra;
         ra.dt_dev = dt_dev;
@@ -115,7 +115,7 @@ ins_status step_wray3_df(ins_grid* g, double* u, const double* dt_dev, double dt
         ra.last = st == 2;
         ra.mx = (st == 2 && next_dt) ? g->cfl_max : nullptr;
         ra.err_flag = g->err_flag;
-        if ((s = rk_update_df<DIM, true>(g, F, rp, u, kprev, nullptr, ra)) != INS_OK) return s;
+        if ((s = rk_update_df<DIM, true, WALL>(g, F, rp, u, kprev, nullptr, ra)) != INS_OK) return s;
     }
     if (next_dt) {
         KLAUNCH(g, "cfl_finalize", k_cfl_finalize<<<1, 256, 0, g->stream>>>(g->cfl_max, g->geo64, g->nx + g->ny + g->nz,
@@ -160,9 +160,10 @@ ins_status step_df(ins_grid* g, double* u, const double* dt_dev, double dt_host,
 
 template <typename T, int DIM, bool WALL>
 ins_status Impl<T, DIM, WALL>::step(ins_grid* g, T* u, const double* dt_dev, double dt_host, double* next_dt, double cfl) {
-    if constexpr (std::is_same<T, double>::value && !WALL) {
-        if (g->scheme == INS_WRAY3 && g->use_df && !g->closure && !g->eddy && reinterpret_cast<uintptr_t>(u) % 16 == 0)
-            return step_wray3_df<DIM>(g, u, dt_dev, dt_host, next_dt, cfl);
+    if constexpr (std::is_same<T, double>::value && (!WALL || DIM == 3)) {
+        if (g->scheme == INS_WRAY3 && g->use_df && !g->closure && !g->eddy && !(WALL && g->use_dct) &&
+            reinterpret_cast<uintptr_t>(u) % 16 == 0)
+            return step_wray3_df<DIM, WALL>(g, u, dt_dev, dt_host, next_dt, cfl);
     }
     if (g->scheme == INS_WRAY3) return step_wray3(g, u, dt_dev, dt_host, next_dt, cfl);
     if constexpr (std::is_same<T, double>::value && (!WALL || DIM == 3)) {
