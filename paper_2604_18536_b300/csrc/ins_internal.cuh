@@ -303,6 +303,8 @@ void launch_strided_reg(cudaStream_t st, const cplx<T>* tw, cplx<T>* S, long nco
     if constexpr (sizeof(T) == 8) {
         // FP64 is bound by the FP64 pipe, not by latency: the one-tile-per-CTA kernel (the
         // pipelined one measured 2 % slower here)
+        // one CTA per tile (the double-float square kernels can walk tiles, but as many CTAs as stay
+        // resident measured slower: 118.6 against 113.1 us per pass at 256^3)
         using Sh = RegShape<T, R1, R2>;
         const unsigned blocks = (unsigned)((ncol + Sh::TW - 1) / Sh::TW);
         k_fft_strided_reg<T, R1, R2><<<blocks, Sh::NT, 0, st>>>(tw, S, ncol, cdiv, outer, lstride, mode, scale);
@@ -363,9 +365,10 @@ void launch_x_reg(bool forward, cudaStream_t st, const cplx<T>* tw, const T* in,
     const long pairs = (lines + 1) / 2;
     const long ntiles = (pairs + Sh::TW - 1) / Sh::TW;
     if (forward) {
-        // FP32: as many CTAs as stay resident, each walking tiles (twiddles loaded once per CTA)
+        // FP32 and double-float: as many CTAs as stay resident, each walking tiles (FP32: twiddles
+        // loaded once per CTA; double-float 256^3: 101.5 against 102.8 us with one CTA per tile)
         long cap = ntiles;
-        if (sizeof(T) == 4) {
+        if (sizeof(T) == 4 || std::is_same<T, df>::value) {
             static int per_sm = 0;
             if (!per_sm) {
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_x_r2c_reg<T, R1, R2>, Sh::NT, 0);
