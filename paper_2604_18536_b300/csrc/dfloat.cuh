@@ -107,11 +107,13 @@ __device__ __forceinline__ df& operator-=(df& a, df b) { return a = a - b; }
 __device__ __forceinline__ df& operator*=(df& a, df b) { return a = a * b; }
 
 // ------------------------------------------------------------------ packed complex arithmetic
-// The real and imaginary parts of a complex double-float operation run the same sequence of FP32
-// operations, so complex sums, differences and products (the FFT butterflies and twiddles) use the
-// paired instructions add/sub/mul/fma.rn.f32x2 on (re, im) lanes. Each lane rounds like the scalar
-// instruction and the sequences are those of the scalar operations above, so the results are the
-// same bit for bit; a pair instruction issues once for two lanes. DF_PACKED (default 1) selects them.
+// The real and imaginary parts of a complex double-float sum or difference run the same sequence of
+// FP32 operations, so complex sums and differences (the FFT butterflies) use the paired instructions
+// add/sub.rn.f32x2 on (re, im) lanes. Each lane rounds like the scalar instruction and the sequences
+// are those of the scalar operations above, so the results are the same bit for bit; a pair
+// instruction issues once for two lanes. DF_PACKED (default 1) selects them. (Complex products on
+// lane pairs measured slower: the broadcast and swapped operand pairs cost more moves than the
+// pairing saved.)
 #ifndef DF_PACKED
 #define DF_PACKED 1
 #endif
@@ -134,21 +136,6 @@ __device__ __forceinline__ float2 pk_sub(float2 a, float2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(R.u) : "l"(A.u), "l"(B.u));
     return R.f;
 }
-__device__ __forceinline__ float2 pk_mul(float2 a, float2 b) {
-    DfPk A, B, R;
-    A.f = a;
-    B.f = b;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(R.u) : "l"(A.u), "l"(B.u));
-    return R.f;
-}
-__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) {
-    DfPk A, B, C, R;
-    A.f = a;
-    B.f = b;
-    C.f = c;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(R.u) : "l"(A.u), "l"(B.u), "l"(C.u));
-    return R.f;
-}
 // (a.hi + b.hi, its error) + (a.lo + b.lo) per lane: the scalar operator+ on both lanes
 __device__ __forceinline__ void pk_df_add(float2 ah, float2 al, float2 bh, float2 bl, float2& sh, float2& sl) {
     const float2 s = pk_add(ah, bh);
@@ -168,34 +155,6 @@ __device__ __forceinline__ cplx<df> csub(cplx<df> a, cplx<df> b) {
     pk_df_add(make_float2(a.re.hi, a.im.hi), make_float2(a.re.lo, a.im.lo), make_float2(-b.re.hi, -b.im.hi),
               make_float2(-b.re.lo, -b.im.lo), sh, sl);
     return {df(sh.x, sl.x), df(sh.y, sl.y)};
-}
-// {fma(a.re, b.re, -a.im b.im), fma(a.re, b.im, a.im b.re)} as in the generic cmul: the product
-// pair a.im (b.im, b.re), the first lane negated (exact), then the fused multiply-add pair
-// a.re (b.re, b.im) + that
-__device__ __forceinline__ cplx<df> cmul(cplx<df> a, cplx<df> b) {
-    const float2 bh = make_float2(b.re.hi, b.im.hi), bl = make_float2(b.re.lo, b.im.lo);
-    const float2 bsh = make_float2(b.im.hi, b.re.hi), bsl = make_float2(b.im.lo, b.re.lo);
-    const float2 ih = make_float2(a.im.hi, a.im.hi), il = make_float2(a.im.lo, a.im.lo);
-    const float2 rh = make_float2(a.re.hi, a.re.hi), rl = make_float2(a.re.lo, a.re.lo);
-    // q = a.im * (b.im, b.re)
-    const float2 qp = pk_mul(ih, bsh);
-    float2 qe = pk_fma(ih, bsh, make_float2(-qp.x, -qp.y));
-    qe = pk_fma(ih, bsl, qe);
-    qe = pk_fma(il, bsh, qe);
-    const float2 ch = make_float2(-qp.x, qp.y), cl = make_float2(-qe.x, qe.y);
-    // a.re * (b.re, b.im) + c
-    const float2 p = pk_mul(rh, bh);
-    float2 e = pk_fma(rh, bh, make_float2(-p.x, -p.y));
-    e = pk_fma(rh, bl, e);
-    e = pk_fma(rl, bh, e);
-    float2 s, t;
-    {
-        s = pk_add(p, ch);
-        const float2 bb = pk_sub(s, p);
-        t = pk_add(pk_sub(p, pk_sub(s, bb)), pk_sub(ch, bb));
-    }
-    t = pk_add(t, pk_add(e, cl));
-    return {df(s.x, t.x), df(s.y, t.y)};
 }
 #endif
 
